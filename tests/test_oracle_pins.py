@@ -1,0 +1,374 @@
+"""Pins of the FP64 oracle against closed forms, library routines, invariants and brute force.
+
+Each test fixes a result by something other than the oracle's own formulas:
+* Sec. 3 (first equation, projection): closed forms of the 2D covariance for isotropic and
+  axis-aligned Gaussians, and Sigma' against a finite-difference Jacobian of the pinhole map
+  with the rotation from scipy (scalar-last quaternion convention).
+* Sec. 3 (second equation, compositing): two-layer "over" and k identical layers.
+* Sec. 3 (Blinn-Phong): n parallel / perpendicular to l, beta -> 0, a 45-degree half vector.
+* Sec. 4.5 (composition and edits): spatially disjoint models, hidden models, zero opacity
+  scale, affinity in the palette colour.
+* Brute force over all Gaussians per pixel on tiny scenes (no tiles, lists or key sort).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+import oracle
+import scenegen as sg
+from oracle import brute
+from tests._util import axis_camera, cat_models, logit, single_model
+
+
+def _proj1(model, cam, lowpass=oracle.LOWPASS, edits=None):
+    edits = sg.identity_edits([model]) if edits is None else edits
+    comp = oracle.compose([model])
+    return oracle.project(comp, oracle.edit_table(edits), cam, lowpass)
+
+
+@pytest.mark.parametrize("lowpass", [0.0, 0.3])
+@pytest.mark.parametrize("sigma", [0.004, 0.011, 0.05])
+def test_isotropic_on_axis(lowpass, sigma):
+    cam = axis_camera(W=64, H=64, z=3.0)
+    m = single_model([0, 0, 0], log_scale=[math.log(sigma)] * 3, quat=[0.3, -0.2, 0.5, 0.7])
+    p = _proj1(m, cam, lowpass)
+    sigma = math.exp(float(m.log_scale[0, 0]))  # the stored (float32) log-scale
+    s2 = (cam.fx * sigma / 3.0) ** 2 + lowpass
+    assert p.cov[0] == pytest.approx([s2, 0.0, s2], rel=1e-12, abs=1e-12)
+    assert p.conic[0] == pytest.approx([1 / s2, 0.0, 1 / s2], rel=1e-12, abs=1e-12)
+    assert p.radius[0] == math.ceil(3.0 * math.sqrt(s2))
+    assert p.uv[0] == pytest.approx([32.0, 32.0], abs=1e-12)
+    assert p.depth[0] == pytest.approx(3.0)
+
+
+def test_axis_aligned_and_quarter_turn():
+    cam = axis_camera(W=64, H=64, z=4.0)
+    ls = np.log(np.array([0.02, 0.005, 0.03])).astype(np.float32)
+    sx, sy, sz = np.exp(ls.astype(np.float64))
+    p = _proj1(single_model([0, 0, 0], log_scale=ls), cam, 0.3)
+    fz = cam.fx / 4.0
+    assert p.cov[0] == pytest.approx([(fz * sx) ** 2 + 0.3, 0.0, (fz * sy) ** 2 + 0.3], rel=1e-12, abs=1e-14)
+    c45 = math.cos(math.pi / 4)
+    p2 = _proj1(single_model([0, 0, 0], log_scale=ls, quat=[c45, 0, 0, c45]), cam, 0.3)
+    assert p2.cov[0] == pytest.approx([(fz * sy) ** 2 + 0.3, 0.0, (fz * sx) ** 2 + 0.3], rel=1e-6, abs=1e-9)
+
+
+def test_covariance_matches_fd_jacobian_and_scipy_rotation():
+    rng = np.random.default_rng(11)
+    cams = [sg.look_at(3.0 * sg.random_direction(rng), 256, 192) for _ in range(4)]
+    for cam in cams:
+        for _ in range(8):
+            mu = rng.uniform(-0.5, 0.5, 3)
+            q = rng.standard_normal(4)
+            ls = rng.normal(-4.0, 0.5, 3)
+            m = single_model(mu, log_scale=ls, quat=q)
+            p = _proj1(m, cam, 0.0)
+            qf = np.asarray(m.quat[0], np.float64)
+            Rq = Rotation.from_quat([qf[1], qf[2], qf[3], qf[0]]).as_matrix()
+            Sig = Rq @ np.diag(np.exp(2.0 * np.asarray(m.log_scale[0], np.float64))) @ Rq.T
+            Rw = np.asarray(cam.R, np.float64).reshape(3, 3)
+            mc = Rw @ np.asarray(m.mean[0], np.float64) + np.asarray(cam.t, np.float64)
+
+            def pin(xc):
+                return np.array([cam.fx * xc[0] / xc[2] + cam.cx, cam.fy * xc[1] / xc[2] + cam.cy])
+
+            h = 1e-6
+            J = np.stack([(pin(mc + h * e) - pin(mc - h * e)) / (2 * h) for e in np.eye(3)], 1)
+            cov = J @ Rw @ Sig @ Rw.T @ J.T
+            assert p.cov[0] == pytest.approx([cov[0, 0], cov[0, 1], cov[1, 1]], rel=2e-6, abs=1e-9)
+            assert p.uv[0] == pytest.approx(pin(mc), rel=1e-12)
+
+
+def test_culling_near_plane_and_hidden_model():
+    cam = axis_camera(z=0.1)  # the point is 0.1 in front of the camera: behind the 0.2 near plane
+    assert _proj1(single_model([0, 0, 0]), cam).radius[0] == 0
+    cam = axis_camera(z=3.0)
+    m = single_model([0, 0, 0])
+    ed = sg.identity_edits([m])
+    ed.visible[0] = 0
+    assert _proj1(m, cam, edits=ed).radius[0] == 0
+
+
+# ------------------------------------------------------------------ shading (Blinn-Phong)
+def _rgb(m, cam, edits=None):
+    return _proj1(m, cam, edits=edits).rgb[0]
+
+
+def test_shading_headlight_normal_parallel():
+    cam = axis_camera(z=3.0)
+    alb = np.array([0.2, 0.5, 0.9])
+    m = single_model([0, 0, 0], albedo=alb, normal=[0, 0, -1])  # normal points at the camera
+    ka, kd, ks, _ = sg.KADS_DEFAULT
+    assert _rgb(m, cam) == pytest.approx((ka + kd) * alb + ks, rel=1e-6)
+    m2 = single_model([0, 0, 0], albedo=alb, normal=[0, 0, 5])  # unnormalised, facing away: |n.l|
+    assert _rgb(m2, cam) == pytest.approx((ka + kd) * alb + ks, rel=1e-6)
+
+
+def test_shading_normal_perpendicular_is_ambient_only():
+    cam = axis_camera(z=3.0)
+    alb = np.array([0.3, 0.6, 0.1])
+    m = single_model([0, 0, 0], albedo=alb, normal=[1, 0, 0])
+    cv = m.palette.astype(np.float64) + m.dcolor[0].astype(np.float64)  # stored c_p + dc
+    assert _rgb(m, cam) == pytest.approx(float(np.float32(0.2)) * cv, rel=1e-12, abs=1e-15)
+
+
+def test_shading_orbital_half_vector_and_beta():
+    cam = axis_camera(z=3.0, headlight=False, light_dir=[1, 0, 0])
+    alb = np.array([0.4, 0.4, 0.4])
+    # v = (0,0,-1) towards the camera, l = (1,0,0), n = l: n.l = 1, n.h = 1/sqrt(2)
+    m = single_model([0, 0, 0], albedo=alb, normal=[1, 0, 0], kads=[0.2, 0.7, 0.3, 1.0])
+    cv = m.palette.astype(np.float64) + m.dcolor[0].astype(np.float64)
+    ka, kd, ks = (float(np.float32(x)) for x in (0.2, 0.7, 0.3))
+    assert _rgb(m, cam) == pytest.approx((ka + kd) * cv + ks / math.sqrt(2.0), rel=1e-12)
+    m0 = single_model([0, 0, 0], albedo=alb, normal=[1, 0, 0], kads=[0.2, 0.7, 0.3, 0.0])
+    assert _rgb(m0, cam) == pytest.approx((ka + kd) * cv + ks, rel=1e-12)
+
+
+def test_light_magnitude_edit():
+    cam = axis_camera(z=3.0)
+    alb = np.array([0.2, 0.5, 0.9])
+    m = single_model([0, 0, 0], albedo=alb, normal=[0, 0, -1])
+    ed = sg.identity_edits([m])
+    ed.lam = np.array([2.0, 0.5, 3.0, 1.0], np.float32)
+    ed.bias = np.array([0.1, 0.0, -0.2, 0.0], np.float32)
+    ka, kd, ks = 2 * 0.2 + 0.1, 0.5 * 0.7, 3 * 0.3 - 0.2
+    assert _rgb(m, cam, ed) == pytest.approx((ka + kd) * alb + ks, rel=1e-6)
+
+
+def test_palette_edit_replaces_cp():
+    cam = axis_camera(z=3.0)
+    alb = np.array([0.2, 0.5, 0.9])
+    m = single_model([0, 0, 0], albedo=alb, palette=[0.4, 0.4, 0.4], normal=[1, 0, 0])
+    ed = sg.identity_edits([m])
+    ed.palette[0] = [0.9, 0.1, 0.0]
+    cp = np.asarray(ed.palette[0], np.float64)
+    cv = cp + m.dcolor[0].astype(np.float64)
+    assert _rgb(m, cam, ed) == pytest.approx(float(np.float32(0.2)) * cv, rel=1e-12, abs=1e-15)
+
+
+# ------------------------------------------------------------------ compositing closed forms
+def _records(uv, conic, opacity, rgb):
+    return oracle.Projected(uv=np.asarray(uv, float).reshape(-1, 2), cov=np.zeros((len(opacity), 3)),
+                            conic=np.asarray(conic, float).reshape(-1, 3), opacity=np.asarray(opacity, float),
+                            rgb=np.asarray(rgb, float).reshape(-1, 3), depth=np.arange(1, len(opacity) + 1.0),
+                            radius=np.full(len(opacity), 3, np.int32), radius_margin=np.ones(len(opacity)))
+
+
+def _blend(p, px, bg=(0, 0, 0)):
+    cam = sg.Camera(W=32, H=32, fx=1, fy=1, cx=16, cy=16, R=np.eye(3).reshape(9), t=np.zeros(3),
+                    campos=np.zeros(3))
+    return oracle.render_pixels(p, cam, np.array([px]), bg=bg)
+
+
+def test_peak_alpha_and_clamp():
+    for o, expect in [(0.5, 0.5), (0.98, 0.98), (0.995, 0.99), (3.0, 0.99)]:
+        p = _records([[10.5, 7.5]], [[0.2, 0.0, 0.2]], [o], [[1.0, 0.5, 0.25]])
+        rgba, T, last, _ = _blend(p, (10, 7))
+        assert rgba[0, 3] == pytest.approx(expect, abs=1e-15)
+        assert rgba[0, :3] == pytest.approx(np.array([1.0, 0.5, 0.25]) * expect, abs=1e-15)
+        assert last[0] == 1
+
+
+@pytest.mark.parametrize("side", [+1, -1])
+def test_alpha_cutoff_1_over_255(side):
+    a = 0.25
+    o = 0.8
+    target = (1.0 / 255.0) * (1.0 + side * 1e-6)
+    d = math.sqrt(2.0 * math.log(o / target) / a)  # alpha = o exp(-a d^2 / 2) == target
+    p = _records([[10.5 + d, 7.5]], [[a, 0.0, a]], [o], [[1.0, 1.0, 1.0]])
+    rgba, T, last, _ = _blend(p, (10, 7))
+    if side > 0:
+        assert last[0] == 1 and rgba[0, 3] == pytest.approx(target, rel=1e-9)
+    else:
+        assert last[0] == 0 and rgba[0, 3] == 0.0
+
+
+def test_two_layer_over():
+    c1, c2, bg = np.array([1.0, 0.2, 0.1]), np.array([0.1, 0.9, 0.3]), np.array([0.05, 0.1, 0.7])
+    p = _records([[10.5, 7.5], [10.5, 7.5]], [[0.2, 0, 0.2]] * 2, [0.6, 0.3], [c1, c2])
+    rgba, T, last, _ = _blend(p, (10, 7), bg=bg)
+    a1, a2 = 0.6, 0.3
+    assert rgba[0, :3] == pytest.approx(a1 * c1 + (1 - a1) * a2 * c2 + (1 - a1) * (1 - a2) * bg, abs=1e-15)
+    assert T[0] == pytest.approx((1 - a1) * (1 - a2), abs=1e-15)
+    assert rgba[0, 3] == pytest.approx(1 - T[0], abs=1e-15)
+
+
+@pytest.mark.parametrize("alpha", [0.1, 0.37, 0.5, 0.9, 0.99])
+def test_k_identical_layers_termination(alpha):
+    k = 200
+    p = _records([[10.5, 7.5]] * k, [[0.2, 0, 0.2]] * k, [alpha] * k, [[1.0, 1.0, 1.0]] * k)
+    rgba, T, last, _ = _blend(p, (10, 7))
+    kk = max(j for j in range(k + 1) if (1 - alpha) ** j >= 1e-4)  # largest count keeping T >= 1e-4
+    assert last[0] == kk
+    assert T[0] == pytest.approx((1 - alpha) ** kk, rel=1e-12)
+    assert rgba[0, 0] == pytest.approx(1 - (1 - alpha) ** kk, rel=1e-12)
+
+
+def test_transmittance_monotone_over_prefixes():
+    rng = np.random.default_rng(5)
+    n = 40
+    p = _records(np.c_[10.5 + rng.normal(0, 2, n), 7.5 + rng.normal(0, 2, n)],
+                 np.c_[rng.uniform(0.05, 0.3, n), rng.uniform(-0.02, 0.02, n), rng.uniform(0.05, 0.3, n)],
+                 rng.uniform(0.05, 0.9, n), rng.random((n, 3)))
+    cam = sg.Camera(W=32, H=32, fx=1, fy=1, cx=16, cy=16, R=np.eye(3).reshape(9), t=np.zeros(3), campos=np.zeros(3))
+    Ts = []
+    for k in range(1, n + 1):
+        sub = oracle.Projected(p.uv[:k], p.cov[:k], p.conic[:k], p.opacity[:k], p.rgb[:k], p.depth[:k],
+                               p.radius[:k], p.radius_margin[:k])
+        Ts.append(oracle.render_pixels(sub, cam, np.array([(10, 7)]))[1][0])
+    assert all(b <= a for a, b in zip(Ts, Ts[1:]))
+    assert Ts[-1] >= 1e-4
+
+
+# ------------------------------------------------------------------ tiled oracle vs brute force
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("headlight", [True, False])
+def test_tiled_matches_brute_force(seed, headlight):
+    w = sg.tiny_scene(48, 40, 24, seed, log_scale_mu=-2.6, headlight=headlight, n_models=2)
+    bg = np.array([0.1, 0.2, 0.3])
+    r = oracle.render(w.models, w.edits, w.cameras, bg=bg)
+    p = r.projs[0]
+    ref = brute.render_view(p.uv, p.conic, p.opacity, p.rgb, p.depth, p.radius, 40, 24, bg=bg)
+    assert (p.radius > 0).sum() > 20
+    assert r.images[0][..., 3].max() > 0.5
+    np.testing.assert_allclose(r.images[0], ref, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r.images[0][..., 3], 1.0 - r.final_T[0], rtol=0, atol=0)
+
+
+def test_sampled_pixels_match_full_render():
+    w = sg.tiny_scene(300, 96, 64, 3, log_scale_mu=-3.0, n_models=3)
+    r = oracle.render(w.models, w.edits, w.cameras)
+    rng = np.random.default_rng(0)
+    pix = np.c_[rng.integers(0, 96, 200), rng.integers(0, 64, 200)]
+    rgba, T, last, _ = oracle.render_pixels(r.projs[0], w.cameras[0], pix)
+    np.testing.assert_array_equal(rgba, r.images[0][pix[:, 1], pix[:, 0]])
+    np.testing.assert_array_equal(last, r.last[0][pix[:, 1], pix[:, 0]])
+
+
+# ------------------------------------------------------------------ invariants (Sec. 4.5)
+def test_spatially_disjoint_models_compose_to_union():
+    a = sg.tiny_scene(30, 64, 32, 7, log_scale_mu=-3.2).models[0]
+    b = sg.tiny_scene(30, 64, 32, 8, log_scale_mu=-3.2).models[0]
+    cam = axis_camera(W=64, H=32, z=3.0)
+    # push a to the left third and b to the right third of the image (tiles never shared)
+    a.mean[:, 0] = a.mean[:, 0] * 0.25 - 0.75
+    b.mean[:, 0] = b.mean[:, 0] * 0.25 + 0.75
+    a.mean[:, 1] *= 0.3
+    b.mean[:, 1] *= 0.3
+    ra = oracle.render([a], sg.identity_edits([a]), [cam])
+    rb = oracle.render([b], sg.identity_edits([b]), [cam])
+    rab = oracle.render([a, b], sg.identity_edits([a, b]), [cam])
+    ta = ra.images[0][..., 3] > 0
+    tb = rb.images[0][..., 3] > 0
+    assert ta.any() and tb.any() and not (ta & tb).any()
+    expect = np.where(ta[..., None], ra.images[0], rb.images[0])
+    np.testing.assert_array_equal(rab.images[0], expect)
+
+
+def test_composition_equals_concatenated_single_model():
+    w = sg.tiny_scene(60, 48, 48, 9, log_scale_mu=-3.0, n_models=3)
+    ms = w.models
+    flat = cat_models(ms)
+    cp = np.concatenate([np.repeat(m.palette[None].astype(np.float64), m.n, 0) for m in ms])
+    flat.dcolor = (cp + np.concatenate([m.dcolor for m in ms]).astype(np.float64))
+    flat.palette = np.zeros(3, np.float32)
+    comp = oracle.compose([flat])
+    comp.dcolor = np.ascontiguousarray(flat.dcolor, np.float64)
+    r1 = oracle.render(ms, w.edits, w.cameras)
+    r2 = oracle.render([flat], sg.identity_edits([flat]), w.cameras, comp=comp,
+                       table=oracle.edit_table(sg.Edits(np.zeros((1, 3), np.float32), np.ones(1, np.float32),
+                                                        np.ones(1, np.int32))))
+    np.testing.assert_array_equal(r1.images[0], r2.images[0])
+
+
+def test_hidden_model_edits_change_nothing_and_zero_opacity_scale_hides():
+    w = sg.tiny_scene(60, 48, 48, 10, log_scale_mu=-3.0, n_models=3)
+    ed = w.edits.copy()
+    ed.visible[1] = 0
+    r1 = oracle.render(w.models, ed, w.cameras)
+    ed2 = ed.copy()
+    ed2.palette[1] = [0.9, 0.0, 0.4]
+    ed2.opacity_scale[1] = 7.0
+    r2 = oracle.render(w.models, ed2, w.cameras)
+    np.testing.assert_array_equal(r1.images[0], r2.images[0])
+    ed3 = w.edits.copy()
+    ed3.opacity_scale[1] = 0.0
+    r3 = oracle.render(w.models, ed3, w.cameras)
+    np.testing.assert_array_equal(r1.images[0], r3.images[0])
+    assert len(r3.bins.keys) > len(r1.bins.keys)  # the lists differ, the image does not
+
+
+def test_image_affine_in_palette():
+    w = sg.tiny_scene(60, 48, 48, 12, log_scale_mu=-3.0, n_models=2)
+    e1, e2, e3 = w.edits.copy(), w.edits.copy(), w.edits.copy()
+    e1.palette[0] = [0.125, 0.25, 0.375]  # dyadic values: the midpoint is exact in float32
+    e2.palette[0] = [0.875, 0.5, 0.0]
+    e3.palette[0] = [0.5, 0.375, 0.1875]
+    i1, i2, i3 = (oracle.render(w.models, e, w.cameras).images[0] for e in (e1, e2, e3))
+    np.testing.assert_allclose(i3, 0.5 * (i1 + i2), rtol=0, atol=1e-13)
+
+
+def test_camera_roll_rotates_image():
+    w = sg.tiny_scene(80, 64, 64, 13, log_scale_mu=-3.0)
+    cam = w.cameras[0]
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    roll = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1]], np.float64)  # 90 deg about the optical axis
+    cam2 = sg.Camera(**{**cam.__dict__, "R": (roll @ R).astype(np.float32).reshape(9),
+                        "t": (roll @ np.asarray(cam.t, np.float64)).astype(np.float32)})
+    r1 = oracle.render(w.models, w.edits, [cam])
+    r2 = oracle.render(w.models, w.edits, [cam2])
+    # camera-space (x, y) -> (-y, x): pixel (i, j) of view 1 lands at (W-1-j, i) of view 2
+    rot = np.rot90(r1.images[0], k=-1, axes=(0, 1))
+    ok = np.abs(r2.images[0] - rot).max(-1) < 1e-9
+    assert ok.mean() > 0.995
+
+
+def test_permutation_invariance_with_distinct_depths():
+    w = sg.tiny_scene(70, 48, 48, 14, log_scale_mu=-3.0)
+    m = w.models[0]
+    perm = np.random.default_rng(3).permutation(m.n)
+    mp = sg.Model(**{k: getattr(m, k)[perm] for k in sg.ATTRS}, palette=m.palette)
+    r1 = oracle.render([m], w.edits, w.cameras)
+    r2 = oracle.render([mp], w.edits, w.cameras)
+    assert len(np.unique(r1.projs[0].depth.astype(np.float32))) == m.n
+    np.testing.assert_array_equal(r1.images[0], r2.images[0])
+
+
+# ------------------------------------------------------------------ binning / ordering
+def test_bin_matches_python_sort_with_ties():
+    sizes = [(64, 48), (40, 40), (100, 30)]
+    xy, rad, depth = sg.synthetic_projected(sizes, 300, seed=4)
+    b = oracle.bin_pairs(xy, rad, depth, sizes)
+    exp = []
+    toff = 0
+    for v, (W, H) in enumerate(sizes):
+        gx, gy = -(-W // 16), -(-H // 16)
+        for g in range(300):
+            r = int(rad[v, g])
+            if r <= 0:
+                continue
+            u, vv = float(xy[v, g, 0]), float(xy[v, g, 1])
+            # exact real-number rectangle (float32 inputs; r integer; u -+ r exact in float64)
+            x0 = min(max(math.floor((u - r) / 16), 0), gx)
+            x1 = min(max(math.floor((u + r) / 16) + 1, 0), gx)
+            y0 = min(max(math.floor((vv - r) / 16), 0), gy)
+            y1 = min(max(math.floor((vv + r) / 16) + 1, 0), gy)
+            bits = int(np.float32(depth[v, g]).view(np.uint32))
+            for ty in range(y0, y1):
+                for tx in range(x0, x1):
+                    exp.append((((toff + ty * gx + tx) << 32) | bits, len(exp), g))
+        toff += gx * gy
+    exp.sort(key=lambda e: (e[0], e[1]))
+    assert len(exp) == len(b.keys) > 1000
+    np.testing.assert_array_equal(b.keys, np.array([e[0] for e in exp], np.uint64))
+    np.testing.assert_array_equal(b.values, np.array([e[2] for e in exp], np.uint32))
+    tiles = b.keys >> np.uint64(32)
+    for t in range(len(b.ranges)):
+        s, e = b.ranges[t]
+        idx = np.nonzero(tiles == t)[0]
+        if len(idx):
+            assert (s, e) == (idx[0], idx[-1] + 1)
+        else:
+            assert s == e == 0
