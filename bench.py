@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the editable-Gaussian rasterizer path on GB300.
+
+One step = one pass of the whole path over one batch: edit table (compose/edit), projection +
+shading of every (view, Gaussian), tile binning + radix sort, compositing of every view, and
+the backward of all of it for a fixed dL/dRGBA. Default workload: 1,000,000 Gaussians over 4
+basic models, 8 views of uneven sizes (512^2, 800^2, 1024x768, 1280^2, twice), 6.65 Mpix.
+Metric: Mpix/s of forward+backward (also reported: forward only).
+
+`--impl reference` times the FP64 CPU oracle instead (a bounded sample of the same workload).
+Multi-GPU (torchrun): every rank renders its own replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd / fwd+bwd Mpix/s at 1M Gaussians, batched-mixed vs plain, max|Δ|≤2e-4"
+UNIT = "Mpix/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ivrgs", choices=["ivrgs", "reference"])
+    ap.add_argument("--workload", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true", help="run warmup + 2 steps, print nothing else")
+    return ap.parse_args()
+
+
+def workload(name):
+    import scenegen as sg
+    return {"cfg1": sg.config1, "cfg2": sg.config2, "cfg3": sg.config3, "cfg4": sg.config4}[name]()
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ roofline
+def peaks():
+    p = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p.update({"hbm_gbs": float(m["hbm_gbs"]), "sm_max_mhz": float(m.get("sm_max_mhz", 2070.0)),
+                  "source": "measured"})
+    return p
+
+
+N_SM = 152
+FP32_LANES = 128
+OPS_FWD = 20.0  # FP32 lane operations per evaluated (pixel, Gaussian) entry in the forward blend
+OPS_BWD = 40.0  # backward blend: recompute alpha + transmittance recovery + nine gradient terms
+
+
+def kernel_work(name, w, stats):
+    """Algorithmic work of one launch of `name`: (bound, amount, unit, per-unit note)."""
+    n, V, pairs, evals = stats["n"], stats["V"], stats["pairs"], stats["evals"]
+    if name == "k_render":
+        return "alu", OPS_FWD * evals, "op"
+    if name == "k_render_bwd":
+        return "alu", OPS_BWD * evals, "op"
+    if name == "k_onesweep":
+        return "hbm", 24.0 * pairs, "B"
+    if name == "k_project":
+        return "hbm", 88.0 * n + 44.0 * n * V, "B"
+    if name == "k_project_bwd":
+        return "hbm", 88.0 * n + 36.0 * n * V + 88.0 * n, "B"
+    if name == "k_emit":
+        return "hbm", 16.0 * n * V + 12.0 * pairs, "B"
+    if name == "k_count":
+        return "hbm", 12.0 * n * V, "B"
+    return None
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_2504_17954_gb300 import _native as N
+    from paper_2504_17954_gb300 import build as B
+    from paper_2504_17954_gb300 import Gaussians, Rasterizer, compose_edit
+
+    B.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    ed = w.edits
+    models = [Gaussians.from_arrays({k: getattr(m, k) for k in
+                                     ("mean", "log_scale", "quat", "opacity_logit", "dcolor", "normal", "kads")},
+                                    device=dev) for m in w.models]
+    comp, table = compose_edit(models, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias, device=dev)
+    del models
+    rast = Rasterizer(w.cameras, comp.n, len(w.models), device=dev, lowpass=w.lowpass, bg=w.bg)
+    rast.forward(comp, table, mode="exact")  # sizes the pair buffer
+    torch.cuda.synchronize()
+    n_pairs = rast.n_pairs
+    rast._ensure_capacity(int(n_pairs * 1.1) + 4096)
+    gen = torch.Generator(device=dev).manual_seed(4)
+    dL = torch.randn((rast.n_pix, 4), generator=gen, device=dev, dtype=torch.float32) * 1e-3
+    grad = Gaussians.empty(comp.n, len(w.models), dev)
+    grad.model_id = None
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(backward=True):
+        compose_edit(None, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias, device=dev,
+                     edit_table=table)
+        rast.forward(comp, table, mode="capacity")
+        if backward:
+            rast.backward(comp, table, dL, grad=grad)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if args.profile_only:  # a short run for profilers: warm-up plus one step, no report
+        step()
+        torch.cuda.synchronize()
+        return None
+    if int(rast.d_n_pairs.item()) > rast.capacity:
+        raise RuntimeError("pair buffer overflow")
+    evals = float(rast.last.double().sum().item())
+
+    def timed(k, backward, prof=False):
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        if prof:
+            N.prof_report()
+            N.prof_enable(True)
+        for _ in range(k):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step(backward)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        rep = {}
+        if prof:
+            N.prof_enable(False)
+            rep = N.prof_report()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item()), rep
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    ms_total, kernels = timed(args.steps, True, prof=True)
+    ms_fwd_total, _ = timed(args.steps, False)
+    clocks = sampler.stop()
+    K = args.steps
+    pix_all = rast.n_pix * world
+    value = pix_all * K / (ms_total / 1e3) / 1e6
+    fwd_value = pix_all * K / (ms_fwd_total / 1e3) / 1e6
+
+    # roofline of the dominant kernel (largest share of device time in the timed steps)
+    pk = peaks()
+    stats = {"n": comp.n, "V": len(w.cameras), "pairs": n_pairs, "evals": evals}
+    kern_table = {}
+    for name, (cnt, tot) in kernels.items():
+        kern_table[name] = {"launches": cnt, "ms_per_launch": tot / cnt, "share": tot / sum(x[1] for x in kernels.values())}
+    dom = max(kernels.items(), key=lambda kv: kv[1][1])[0]
+    cnt, tot = kernels[dom]
+    per_launch_s = tot / cnt / 1e3
+    wk = kernel_work(dom, w, stats)
+    launches_per_step = sum(c for c, _ in kernels.values()) / K
+    if dom == "k_onesweep":
+        per_launch_s = tot / cnt / 1e3  # one launch = one 8-bit pass over all pairs
+    if wk is None:
+        roof = {"bound": None, "kernel": dom}
+    elif wk[0] == "hbm":
+        ach = wk[1] / per_launch_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "peak_source": pk["source"], "traffic": None}
+    else:
+        peak = N_SM * FP32_LANES * pk["sm_max_mhz"] * 1e6 / 1e12
+        ach = wk[1] / per_launch_s / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "Top/s (FP32 lane ops)",
+                "frac": ach / peak, "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x {pk['sm_max_mhz']:.0f} MHz",
+                "traffic": None}
+    roof["work_per_launch"] = wk[1] if wk else None
+    roof["evaluated_entries_per_launch"] = evals
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+           "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic (seeded volume-band Gaussians; no paper datasets)",
+           "config": {"workload": w.name, "gaussians": comp.n, "models": len(w.models), "views": len(w.cameras),
+                      "pixels_per_replica": rast.n_pix, "pairs": n_pairs, "l2": "flushed between timed steps",
+                      "parallelism": f"replicas x{world}"},
+           "fwd_mpix_s": fwd_value, "fwd_ms_per_step": ms_fwd_total / K,
+           "roofline": roof, "kernels": kern_table, "clocks": clocks,
+           "gpu_launches": int(round(launches_per_step * K))}
+
+    if not args.no_e2e:
+        out["e2e"] = e2e(rast, comp, table, w, ed, dL, grad, K, dev, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w)
+    return out
+
+
+def e2e(rast, comp, table, w, ed, dL, grad, K, dev, world):
+    """Same metric through the public API with the inputs in pinned host memory: every step
+    copies the Gaussian attributes in, runs forward + backward, and reads the image and the
+    gradients back."""
+    import torch
+
+    from paper_2504_17954_gb300 import compose_edit
+    names = ("mean", "log_scale", "quat", "opacity_logit", "dcolor", "normal", "kads")
+    host = {k: getattr(comp, k).cpu().pin_memory() for k in names}
+    out_img = torch.empty(rast.rgba.shape, dtype=torch.float32).pin_memory()
+    out_grad = {k: torch.empty(getattr(comp, k).shape, dtype=torch.float32).pin_memory() for k in names}
+    h2d = sum(t.numel() * 4 for t in host.values())
+    d2h = out_img.numel() * 4 + sum(t.numel() * 4 for t in out_grad.values())
+    stream = torch.cuda.current_stream()
+
+    def one():
+        for k in names:
+            getattr(comp, k).copy_(host[k], non_blocking=True)
+        compose_edit(None, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias, device=dev, edit_table=table)
+        rast.forward(comp, table, mode="capacity")
+        rast.backward(comp, table, dL, grad=grad)
+        out_img.copy_(rast.rgba, non_blocking=True)
+        for k in names:
+            out_grad[k].copy_(getattr(grad, k), non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(K):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    ms = float(t.item())
+    return {"value": rast.n_pix * world * K / (ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms / K}
+
+
+# ------------------------------------------------------------------------------------ oracle
+def oracle_sample_step(w, comp, table):
+    """One bounded sample of the workload on the FP64 oracle: view 0, forward + backward."""
+    import numpy as np
+
+    import oracle
+    cam = w.cameras[0]
+    r = oracle.render(w.models, w.edits, [cam], bg=w.bg, comp=comp, table=table)
+    dl = np.full((cam.H, cam.W, 4), 1e-3)
+    oracle.render_backward(r, [cam], [dl], bg=w.bg)
+    return cam.W * cam.H
+
+
+def cpu_baseline(w, steps=1):
+    import oracle
+    oracle.build()
+    comp = oracle.compose(w.models)
+    table = oracle.edit_table(w.edits)
+    t0 = time.perf_counter()
+    px = 0
+    for _ in range(steps):
+        px += oracle_sample_step(w, comp, table)
+    dt = time.perf_counter() - t0
+    c = w.cameras[0]
+    return {"value": px / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"view 0 ({c.W}x{c.H}) of the workload, forward + backward, all {comp.n} Gaussians, "
+                      f"{steps} step(s), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    w = workload(args.workload)
+    comp = oracle.compose(w.models)
+    table = oracle.edit_table(w.edits)
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample_step(w, comp, table)
+    t0 = time.perf_counter()
+    px = 0
+    for _ in range(args.steps):
+        px += oracle_sample_step(w, comp, table)
+    dt = time.perf_counter() - t0
+    v = px / dt / 1e6
+    c = w.cameras[0]
+    sample = (f"view 0 ({c.W}x{c.H}) of {w.name}, forward + backward over all {comp.n} Gaussians per step, "
+              f"single-threaded FP64 C oracle")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "gaussians": comp.n, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl != "reference":
+        import torch
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world)
+    if rank == 0 and out is not None and not args.profile_only:
+        print(json.dumps(out))
+    if world > 1 and args.impl != "reference":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * ivrgs.h -- C ABI of libivrgs.so, the GB300 (sm_103a) rasterizer for composed, editable
+ * 3D Gaussians (iVR-GS, arXiv 2504.17954).
+ *
+ * The path: compose basic models and apply edits (Sec. 4.5, 4.6) -> project each Gaussian
+ * to the image and shade it with Blinn-Phong (Sec. 3, Sec. 4.3) -> bin the projected
+ * footprints into screen tiles and radix-sort them by (tile, depth) -> composite every
+ * pixel front to back (Sec. 3, second equation) -> and the reverse mode of all of it.
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer named d_* and every pointer inside the structs below is DEVICE memory
+ *     owned by the caller. The library never allocates or frees device memory; where it
+ *     needs scratch space it takes a caller-provided workspace whose size a *_workspace
+ *     query returns.
+ *   - Host structs and host arrays (cameras, edits, bg) are read during the call only.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream). Every call is asynchronous on
+ *     that stream and does not synchronise, except ivrgs_bin in IVRGS_BIN_EXACT mode, which
+ *     reads the pair count back to the host.
+ *   - Return value: IVRGS_OK or an error code; no exception crosses the ABI.
+ *     ivrgs_last_error() returns a message for the calling thread's last failure.
+ *   - Argument errors are detected on the host before anything is launched.
+ *   - Layouts are structure-of-arrays, float32 unless stated, row-major, no padding
+ *     between elements. Alignment: 16 bytes for float4-typed arrays (conic_o, rgbd,
+ *     quat, kads), 8 bytes for xy and keys, 4 bytes otherwise.
+ *
+ * Camera model: world -> camera x_c = R x + t (camera looks along +z, x right, y down),
+ * pixel (i, j) is sampled at (i + 0.5, j + 0.5), u = fx x_c/z_c + cx, v = fy y_c/z_c + cy.
+ * Images of all views are packed in one buffer: view v occupies pixels
+ * [pix_offset, pix_offset + W*H), row-major.
+ *
+ * Parameters fixed by the 3DGS lineage the paper builds on (the paper itself is silent):
+ * opacity = sigmoid(logit), scale = exp(log s), Sigma' dilated by `lowpass` * I, x/z and
+ * y/z clamped to 1.3x the half field of view inside the Jacobian, Gaussians at z <= znear
+ * culled, radius = ceil(3 sqrt(lambda_max(Sigma'))), alpha = min(0.99, o' G), alpha < 1/255
+ * skipped, the walk ends before a Gaussian that would take the transmittance below 1e-4.
+ */
+#ifndef IVRGS_H
+#define IVRGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ivrgs_status;
+enum {
+    IVRGS_OK = 0,
+    IVRGS_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or enum */
+    IVRGS_ERR_CAPACITY = 2,    /* output/workspace too small; the required size is reported */
+    IVRGS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+    IVRGS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (see ivrgs_bin) */
+    IVRGS_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+};
+
+#define IVRGS_MAX_VIEWS 128    /* views per call (cameras travel as kernel parameters) */
+#define IVRGS_MAX_MODELS 1024  /* basic models per composed scene */
+#define IVRGS_EDIT_STRIDE 8    /* floats per model in the edit table */
+#define IVRGS_MAX_PAIRS ((int64_t)1 << 30) /* (tile, Gaussian) pairs per ivrgs_bin call */
+
+enum { IVRGS_FP32 = 0 };
+enum { IVRGS_BIN_EXACT = 0, IVRGS_BIN_CAPACITY = 1 };
+
+/* One pinhole view. light_dir is the direction towards an orbital (directional) light in
+   world space, used when headlight == 0; with headlight != 0 the light sits at the camera
+   and l equals the viewing direction v of each Gaussian (Sec. 3, Blinn-Phong paragraph). */
+typedef struct {
+    int32_t W, H;
+    float fx, fy, cx, cy;
+    float R[9];        /* world -> camera rotation, row-major */
+    float t[3];
+    float campos[3];   /* camera centre in world space (= -R^T t) */
+    float znear;
+    int32_t headlight;
+    float light_dir[3];
+    int64_t pix_offset;
+} ivrgs_camera;
+
+/* Per-basic-model edits (Sec. 4.5): palette colour c_p replaces the model's colour
+   anchor, the opacity of all its Gaussians is multiplied by opacity_scale, and a model with
+   visible == 0 is left out of the composition. */
+typedef struct {
+    float palette[3];
+    float opacity_scale;
+    int32_t visible;
+} ivrgs_model_edit;
+
+/* Global light-magnitude edit (Sec. 4.5, Sec. 4.6): k' = lambda * k + bias for
+   k = (k_a, k_d, k_s, beta). */
+typedef struct {
+    float lambda[4];
+    float bias[4];
+} ivrgs_light;
+
+/* Editable Gaussians (Sec. 4.3 attribute set), structure of arrays, n entries.
+   mean [n][3], log_scale [n][3], quat [n][4] as (w, x, y, z) (need not be normalised),
+   opacity_logit [n], dcolor [n][3] (offset colour dc, c_v = c_p + dc), normal [n][3] (need
+   not be normalised), kads [n][4] = (k_a, k_d, k_s, beta), model_id [n] (basic model of
+   each Gaussian, < n_models). */
+typedef struct {
+    int64_t n;
+    int32_t precision; /* IVRGS_FP32 */
+    int32_t n_models;
+    float* mean;
+    float* log_scale;
+    float* quat;
+    float* opacity_logit;
+    float* dcolor;
+    float* normal;
+    float* kads;
+    uint16_t* model_id;
+} ivrgs_gaussians;
+
+/* Projected Gaussians, one record per (view v, Gaussian g) at index v * n + g.
+   xy [.][2] = (u, v) pixel-space mean; conic_o [.][4] = (a, b, c, o') with (a, b; b, c) the
+   inverse of Sigma' and o' the edited opacity; rgbd [.][4] = (r, g, b, depth) shaded colour
+   and camera-space depth; radius [.] = ceil(3 sqrt(lambda_max)) in pixels, 0 if culled
+   (the other fields of a culled record are unspecified). */
+typedef struct {
+    int64_t n;
+    int32_t n_views;
+    float* xy;
+    float* conic_o;
+    float* rgbd;
+    int32_t* radius;
+} ivrgs_projected;
+
+/* Tile bins. Global tile ids run over all views: view v's tiles start at the sum of the
+   tile counts of views < v, row-major inside a view. keys [capacity] = (tile << 32) |
+   bits(float depth), sorted ascending, ties in (view, Gaussian) order; values [capacity] =
+   Gaussian index g of each key; ranges [n_tiles][2] = [start, end) of each tile's run in the
+   sorted arrays ((0, 0) for an empty tile). d_n_pairs: device uint64 scalar receiving the
+   number of pairs (in CAPACITY mode a value > capacity means the outputs are incomplete). */
+typedef struct {
+    int32_t tile_w, tile_h; /* 16 x 16 in this build */
+    int64_t n_tiles;
+    int64_t capacity;
+    uint64_t* keys;
+    uint32_t* values;
+    uint32_t* ranges;
+    uint64_t* d_n_pairs;
+    int64_t n_pairs; /* out: filled by IVRGS_BIN_EXACT mode */
+} ivrgs_bins;
+
+/* Message of the calling thread's last failed call ("" if none). Never NULL. */
+const char* ivrgs_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t ivrgs_version(void);
+
+/* Number of floats in an edit table for n_models models: IVRGS_EDIT_STRIDE * n_models + 8.
+   Layout: per model m, [c_p(3), opacity scale, visible (0/1), 0, 0, 0]; then lambda(4), b(4).
+   The edit-gradient buffer of ivrgs_render_backward has the same layout followed by
+   4 floats per view (d light_dir (3), 0). */
+int64_t ivrgs_edit_table_floats(int32_t n_models);
+
+/* Composition and edits (Sec. 4.5: the composed model is the concatenation of the basic
+   models' Gaussian attributes; colour, opacity and light edits; Sec. 4.6: lambda, b).
+   models: host array of n_models structs, each naming one basic model's device arrays
+   (their model_id and n_models fields are ignored). If `composed` is non-NULL its arrays
+   (composed->n must equal the sum of the models' n) receive the concatenation in model
+   order and model_id is set to the model index. If `composed` is NULL only the edit table is
+   written, so re-editing costs O(n_models). d_edit_table: device float array of
+   ivrgs_edit_table_floats(n_models) entries, written from `edits` and `light`. */
+ivrgs_status ivrgs_compose_edit(const ivrgs_gaussians* models, int32_t n_models, const ivrgs_model_edit* edits,
+                                const ivrgs_light* light, ivrgs_gaussians* composed, float* d_edit_table,
+                                void* stream);
+
+/* EWA projection + Blinn-Phong shading with edits applied (Sec. 3 first equation and
+   the Blinn-Phong system; Sec. 4.3 c_v = c_p + dc; Sec. 4.5/4.6 edits). For every view
+   v < n_views and Gaussian g: culls hidden models, z_c <= znear and det(Sigma') <= 0;
+   Sigma = R(q) diag(exp 2 s) R(q)^T, Sigma' = J R Sigma R^T J^T + lowpass I; writes
+   out (n = g->n, n_views). The depth is the float64 sum ((R20 mx + R21 my) + R22 mz) + t2
+   rounded to float, so sort keys are exactly reproducible. */
+ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_camera* cams,
+                           int32_t n_views, float lowpass, ivrgs_projected* out, void* stream);
+
+/* Workspace bytes ivrgs_bin needs for p->n * n_views records and `capacity` pairs. */
+ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera* cams, int32_t tile_w,
+                                 int32_t tile_h, int64_t capacity, size_t* bytes);
+
+/* Tile binning by radix sort (the tile-based rasterisation of 3DGS that Sec. 3 builds on:
+   projected Gaussians are composited in depth order per screen tile). Per record: tile rectangle (half-open)
+   x0 = clamp(floor((u - r)/tile_w), 0, Gx), x1 = clamp(floor((u + r)/tile_w) + 1, 0, Gx)
+   (same for y) evaluated in float32; one (key, value) pair per covered tile; a stable LSD
+   radix sort (8-bit digits, onesweep with decoupled look-back) over the bits the keys use;
+   per-tile [start, end) ranges.
+   mode IVRGS_BIN_EXACT: counts the pairs, copies the count to the host (synchronises the
+   stream), returns IVRGS_ERR_CAPACITY with out->n_pairs = required count if it exceeds
+   out->capacity, else finishes and sets out->n_pairs.
+   mode IVRGS_BIN_CAPACITY: never synchronises (usable inside CUDA graph capture); works
+   on min(count, capacity) pairs and leaves the true count in *out->d_n_pairs.
+   A device-side wait of the sort that exceeds its iteration bound sets a flag in the
+   workspace; EXACT mode reports it as IVRGS_ERR_TIMEOUT, CAPACITY mode via
+   ivrgs_bin_check(). */
+ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32_t n_views, int32_t mode,
+                       void* d_workspace, size_t ws_bytes, ivrgs_bins* out, void* stream);
+
+/* Reads (synchronously) the error flag a previous ivrgs_bin left in d_workspace:
+   IVRGS_OK or IVRGS_ERR_TIMEOUT. */
+ivrgs_status ivrgs_bin_check(const void* d_workspace, void* stream);
+
+/* Front-to-back alpha compositing per tile (Sec. 3 second equation, C = sum T_i alpha_i c_i,
+   T_i = prod_{j<i}(1 - alpha_j); alpha channel as in Sec. 4.2). One CTA per 16x16 tile.
+   Outputs per packed pixel: d_rgba [.][4] = (C + T bg, 1 - T), d_final_T [.] = T after the
+   last contributor, d_last [.] = 1 + position (within the tile's run) of the last
+   contributing Gaussian, 0 if none. bg: host float[3]. */
+ivrgs_status ivrgs_render(const ivrgs_projected* p, const ivrgs_bins* b, const ivrgs_camera* cams,
+                          int32_t n_views, const float* bg, float* d_rgba, float* d_final_T, uint32_t* d_last,
+                          void* stream);
+
+/* Workspace bytes ivrgs_render_backward needs for n Gaussians and n_views views. */
+ivrgs_status ivrgs_render_backward_workspace(int64_t n, int32_t n_views, size_t* bytes);
+
+/* Reverse mode of ivrgs_compose_edit (edit table) + ivrgs_project + ivrgs_render.
+   Inputs: the same g, d_edit_table, p, b, cams, lowpass and bg as the forward, its
+   d_final_T and d_last, and d_dL_drgba [.][4] = dL/d(r, g, b, alpha) per packed pixel.
+   The blend is walked back to front from each pixel's last contributor with the
+   transmittance recomputed as T_i = T_{i+1} / (1 - alpha_i) from the stored final T.
+   Outputs (overwritten): grad arrays with the layout of g (float32, model_id unused) =
+   dL/d{mean, log_scale, quat, opacity_logit, dcolor, normal, kads}; d_edit_grad
+   (ivrgs_edit_table_floats(n_models) + 4 * n_views floats) = dL/d{c_p, opacity scale} per
+   model, dL/d{lambda, b}, and dL/d light_dir per view (zero for headlight views).
+   The workspace also holds, on return, the per-(view, Gaussian) gradients of the 2D
+   quantities: float4 [V*n] (du, dv, da, db), float4 [V*n] (dc, do', dr, dg), float [V*n] (db). */
+ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
+                                   const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float lowpass,
+                                   const float* bg, const float* d_final_T, const uint32_t* d_last,
+                                   const float* d_dL_drgba, void* d_workspace, size_t ws_bytes,
+                                   ivrgs_gaussians* grad, float* d_edit_grad, void* stream);
+
+/* Opt-in per-kernel timing (measurement support; the paper has no counterpart). With
+   on != 0 every kernel launch of the library is bracketed by two CUDA events on its stream.
+   Must be off while a stream is being captured into a CUDA graph. */
+void ivrgs_prof_enable(int32_t on);
+
+/* Synchronises on the recorded events and writes one line "kernel launches total_ms" per
+   kernel launched since the previous report into buf (NUL-terminated, truncated to len);
+   returns the full length of the report. */
+int64_t ivrgs_prof_report(char* buf, int64_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IVRGS_H */

@@ -1,0 +1,308 @@
+// Host entry points of libivrgs: argument checks, camera packing, launches.
+#include <math.h>
+
+#include <cstdio>
+#include <string>
+
+#include "common.cuh"
+
+namespace ivrgs {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+ivrgs_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return IVRGS_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return IVRGS_ERR_CUDA;
+}
+
+static ivrgs_status invalid(const std::string& msg) {
+    set_error(msg);
+    return IVRGS_ERR_INVALID_ARG;
+}
+
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb) {
+    if (!cams) return invalid("cams is NULL");
+    if (n_views < 1 || n_views > IVRGS_MAX_VIEWS)
+        return invalid("n_views must be in [1, " + std::to_string(IVRGS_MAX_VIEWS) + "]");
+    cb->n = n_views;
+    cb->pad = 0;
+    long long tiles = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const ivrgs_camera& c = cams[v];
+        if (c.W <= 0 || c.H <= 0 || c.W > 32768 || c.H > 32768)
+            return invalid("camera " + std::to_string(v) + ": W and H must be in [1, 32768]");
+        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !isfinite(c.fx) || !isfinite(c.fy))
+            return invalid("camera " + std::to_string(v) + ": focal lengths must be positive and finite");
+        if (c.pix_offset < 0) return invalid("camera " + std::to_string(v) + ": negative pix_offset");
+        CamDev& d = cb->c[v];
+        d.W = c.W;
+        d.H = c.H;
+        d.gx = (c.W + kTile - 1) / kTile;
+        d.gy = (c.H + kTile - 1) / kTile;
+        d.tile0 = tiles;
+        tiles += (long long)d.gx * d.gy;
+        d.pix0 = c.pix_offset;
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        for (int k = 0; k < 9; ++k) d.R[k] = c.R[k];
+        for (int k = 0; k < 3; ++k) { d.t[k] = c.t[k]; d.campos[k] = c.campos[k]; }
+        d.znear = c.znear;
+        d.limx = kGuard * (0.5f * (float)c.W) / c.fx;
+        d.limy = kGuard * (0.5f * (float)c.H) / c.fy;
+        d.headlight = c.headlight ? 1 : 0;
+        const float ll = sqrtf(c.light_dir[0] * c.light_dir[0] + c.light_dir[1] * c.light_dir[1] +
+                               c.light_dir[2] * c.light_dir[2]);
+        if (!c.headlight && !(ll > 0.f)) return invalid("camera " + std::to_string(v) + ": zero light_dir");
+        d.light_len = ll > 0.f ? ll : 1.f;
+        for (int k = 0; k < 3; ++k) d.light[k] = ll > 0.f ? c.light_dir[k] / ll : 0.f;
+    }
+    // views must not overlap in the packed image
+    for (int v = 0; v < n_views; ++v)
+        for (int u = v + 1; u < n_views; ++u) {
+            const long long a0 = cams[v].pix_offset, a1 = a0 + (long long)cams[v].W * cams[v].H;
+            const long long b0 = cams[u].pix_offset, b1 = b0 + (long long)cams[u].W * cams[u].H;
+            if (a0 < b1 && b0 < a1)
+                return invalid("cameras " + std::to_string(v) + " and " + std::to_string(u) + " overlap in pix_offset");
+        }
+    cb->n_tiles = tiles;
+    return IVRGS_OK;
+}
+
+static ivrgs_status check_gaussians(const ivrgs_gaussians* g, const char* name, bool need_model_id) {
+    if (!g) return invalid(std::string(name) + " is NULL");
+    if (g->n < 0) return invalid(std::string(name) + ": negative n");
+    if (g->precision != IVRGS_FP32) {
+        set_error(std::string(name) + ": only IVRGS_FP32 storage is implemented");
+        return IVRGS_ERR_UNSUPPORTED;
+    }
+    if (g->n == 0) return IVRGS_OK;
+    if (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->dcolor || !g->normal || !g->kads ||
+        (need_model_id && !g->model_id))
+        return invalid(std::string(name) + ": NULL attribute array");
+    if (!aligned(g->quat, 16) || !aligned(g->kads, 16))
+        return invalid(std::string(name) + ": quat and kads must be 16-byte aligned");
+    if (!aligned(g->mean, 4) || !aligned(g->log_scale, 4) || !aligned(g->dcolor, 4) || !aligned(g->normal, 4) ||
+        !aligned(g->opacity_logit, 4) || (need_model_id && !aligned(g->model_id, 2)))
+        return invalid(std::string(name) + ": misaligned attribute array");
+    return IVRGS_OK;
+}
+
+static ivrgs_status check_projected(const ivrgs_projected* p, int64_t n, int32_t n_views) {
+    if (!p) return invalid("projected is NULL");
+    if (p->n != n || p->n_views != n_views) return invalid("projected: n / n_views do not match");
+    if (n == 0) return IVRGS_OK;
+    if (!p->xy || !p->conic_o || !p->rgbd || !p->radius) return invalid("projected: NULL array");
+    if (!aligned(p->xy, 8) || !aligned(p->conic_o, 16) || !aligned(p->rgbd, 16) || !aligned(p->radius, 4))
+        return invalid("projected: misaligned array (xy 8, conic_o/rgbd 16 bytes)");
+    return IVRGS_OK;
+}
+
+static ivrgs_status check_bins(const ivrgs_bins* b, const CamBatch& cb) {
+    if (!b) return invalid("bins is NULL");
+    if (b->tile_w != kTile || b->tile_h != kTile) {
+        set_error("bins: only 16x16 tiles are implemented");
+        return IVRGS_ERR_UNSUPPORTED;
+    }
+    if (b->n_tiles != cb.n_tiles)
+        return invalid("bins: n_tiles = " + std::to_string(b->n_tiles) + " but the cameras have " +
+                       std::to_string(cb.n_tiles) + " tiles");
+    if (b->capacity < 0 || b->capacity >= IVRGS_MAX_PAIRS) return invalid("bins: capacity must be in [0, 2^30)");
+    if (!b->ranges || !b->d_n_pairs || (b->capacity > 0 && (!b->keys || !b->values)))
+        return invalid("bins: NULL array");
+    if (!aligned(b->keys, 8) || !aligned(b->ranges, 8) || !aligned(b->d_n_pairs, 8))
+        return invalid("bins: keys, ranges and d_n_pairs must be 8-byte aligned");
+    return IVRGS_OK;
+}
+
+}  // namespace ivrgs
+
+using namespace ivrgs;
+
+extern "C" {
+
+const char* ivrgs_last_error(void) { return g_last_error.c_str(); }
+
+int32_t ivrgs_version(void) { return 100; }
+
+int64_t ivrgs_edit_table_floats(int32_t n_models) { return (int64_t)IVRGS_EDIT_STRIDE * n_models + 8; }
+
+ivrgs_status ivrgs_compose_edit(const ivrgs_gaussians* models, int32_t n_models, const ivrgs_model_edit* edits,
+                                const ivrgs_light* light, ivrgs_gaussians* composed, float* d_edit_table,
+                                void* stream) {
+    set_error("");
+    if (n_models < 1 || n_models > IVRGS_MAX_MODELS)
+        return invalid("n_models must be in [1, " + std::to_string(IVRGS_MAX_MODELS) + "]");
+    if (!edits || !light || !d_edit_table) return invalid("edits, light and d_edit_table must be non-NULL");
+    if (!aligned(d_edit_table, 4)) return invalid("d_edit_table misaligned");
+    for (int m = 0; m < n_models; ++m)
+        if (!isfinite(edits[m].opacity_scale)) return invalid("non-finite opacity_scale");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (composed) {
+        if (!models) return invalid("models is NULL while composed is given");
+        ivrgs_status st = check_gaussians(composed, "composed", true);
+        if (st) return st;
+        long long total = 0;
+        for (int m = 0; m < n_models; ++m) {
+            if ((st = check_gaussians(&models[m], "models[m]", false))) return st;
+            total += models[m].n;
+        }
+        if (total != composed->n)
+            return invalid("composed->n = " + std::to_string(composed->n) + " but the models hold " +
+                           std::to_string(total));
+        if (composed->n_models != n_models) return invalid("composed->n_models must equal n_models");
+        if ((st = cuda_status(launch_compose(models, n_models, composed, s), "ivrgs_compose_edit"))) return st;
+    }
+    return cuda_status(launch_edit_table(edits, n_models, light, d_edit_table, s), "ivrgs_compose_edit");
+}
+
+ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_camera* cams,
+                           int32_t n_views, float lowpass, ivrgs_projected* out, void* stream) {
+    set_error("");
+    ivrgs_status st = check_gaussians(g, "g", true);
+    if (st) return st;
+    if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
+    if (!d_edit_table) return invalid("d_edit_table is NULL");
+    if (!(lowpass >= 0.f) || !isfinite(lowpass)) return invalid("lowpass must be finite and >= 0");
+    static thread_local CamBatch cb;
+    if ((st = make_cam_batch(cams, n_views, &cb))) return st;
+    if ((st = check_projected(out, g->n, n_views))) return st;
+    return cuda_status(launch_project(g, d_edit_table, cb, lowpass, out, (cudaStream_t)stream), "ivrgs_project");
+}
+
+ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera* cams, int32_t tile_w,
+                                 int32_t tile_h, int64_t capacity, size_t* bytes) {
+    set_error("");
+    if (!bytes) return invalid("bytes is NULL");
+    if (tile_w != kTile || tile_h != kTile) {
+        set_error("only 16x16 tiles are implemented");
+        return IVRGS_ERR_UNSUPPORTED;
+    }
+    if (n < 0 || capacity < 0 || capacity >= IVRGS_MAX_PAIRS) return invalid("bad n or capacity");
+    static thread_local CamBatch cb;
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    if (st) return st;
+    *bytes = plan_bin(n * (long long)n_views, cb.n_tiles, capacity).total_bytes;
+    return IVRGS_OK;
+}
+
+ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32_t n_views, int32_t mode,
+                       void* d_workspace, size_t ws_bytes, ivrgs_bins* out, void* stream) {
+    set_error("");
+    static thread_local CamBatch cb;
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    if (st) return st;
+    if (!p) return invalid("projected is NULL");
+    if ((st = check_projected(p, p->n, n_views))) return st;
+    if ((st = check_bins(out, cb))) return st;
+    if (mode != IVRGS_BIN_EXACT && mode != IVRGS_BIN_CAPACITY) return invalid("mode must be EXACT or CAPACITY");
+    if (p->n * (long long)n_views >= (1ll << 40)) return invalid("too many records");
+    const BinPlan plan = plan_bin(p->n * (long long)n_views, cb.n_tiles, out->capacity);
+    if (!d_workspace || ws_bytes < plan.total_bytes) {
+        set_error("workspace too small: need " + std::to_string(plan.total_bytes) + " bytes");
+        return IVRGS_ERR_CAPACITY;
+    }
+    if (!aligned(d_workspace, 256)) return invalid("workspace must be 256-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = static_cast<char*>(d_workspace);
+    if ((st = cuda_status(launch_bin_count(p, cb, plan, ws, out->d_n_pairs, s), "ivrgs_bin count"))) return st;
+    long long exact = -1;
+    if (mode == IVRGS_BIN_EXACT) {
+        unsigned long long total = 0;
+        if ((st = cuda_status(cudaMemcpyAsync(&total, out->d_n_pairs, 8, cudaMemcpyDeviceToHost, s), "ivrgs_bin")))
+            return st;
+        if ((st = cuda_status(cudaStreamSynchronize(s), "ivrgs_bin"))) return st;
+        out->n_pairs = (int64_t)total;
+        if ((long long)total > out->capacity) {
+            set_error("capacity " + std::to_string(out->capacity) + " < " + std::to_string(total) + " pairs");
+            return IVRGS_ERR_CAPACITY;
+        }
+        exact = (long long)total;
+    }
+    if ((st = cuda_status(launch_bin_sort(p, cb, plan, ws, out, exact, s), "ivrgs_bin sort"))) return st;
+    if (mode == IVRGS_BIN_EXACT) {
+        unsigned flag = 0;
+        if ((st = cuda_status(cudaMemcpyAsync(&flag, ws + plan.off_flag, 4, cudaMemcpyDeviceToHost, s), "ivrgs_bin")))
+            return st;
+        if ((st = cuda_status(cudaStreamSynchronize(s), "ivrgs_bin"))) return st;
+        if (flag) {
+            set_error("radix sort look-back wait exceeded its bound");
+            return IVRGS_ERR_TIMEOUT;
+        }
+    }
+    return IVRGS_OK;
+}
+
+ivrgs_status ivrgs_bin_check(const void* d_workspace, void* stream) {
+    set_error("");
+    if (!d_workspace) return invalid("workspace is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned flag = 0;  // the flag is the first word of every bin workspace
+    ivrgs_status st;
+    if ((st = cuda_status(cudaMemcpyAsync(&flag, d_workspace, 4, cudaMemcpyDeviceToHost, s), "ivrgs_bin_check")))
+        return st;
+    if ((st = cuda_status(cudaStreamSynchronize(s), "ivrgs_bin_check"))) return st;
+    if (flag) {
+        set_error("radix sort look-back wait exceeded its bound");
+        return IVRGS_ERR_TIMEOUT;
+    }
+    return IVRGS_OK;
+}
+
+ivrgs_status ivrgs_render(const ivrgs_projected* p, const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views,
+                          const float* bg, float* d_rgba, float* d_final_T, uint32_t* d_last, void* stream) {
+    set_error("");
+    static thread_local CamBatch cb;
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    if (st) return st;
+    if (!p) return invalid("projected is NULL");
+    if ((st = check_projected(p, p->n, n_views))) return st;
+    if ((st = check_bins(b, cb))) return st;
+    if (!bg || !d_rgba || !d_final_T || !d_last) return invalid("bg and output arrays must be non-NULL");
+    if (!aligned(d_rgba, 16)) return invalid("d_rgba must be 16-byte aligned");
+    return cuda_status(launch_render(p, b, cb, bg, d_rgba, d_final_T, d_last, (cudaStream_t)stream), "ivrgs_render");
+}
+
+ivrgs_status ivrgs_render_backward_workspace(int64_t n, int32_t n_views, size_t* bytes) {
+    set_error("");
+    if (!bytes || n < 0 || n_views < 1 || n_views > IVRGS_MAX_VIEWS) return invalid("bad arguments");
+    *bytes = (size_t)n * (size_t)n_views * 36 + 256;
+    return IVRGS_OK;
+}
+
+ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
+                                   const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float lowpass,
+                                   const float* bg, const float* d_final_T, const uint32_t* d_last,
+                                   const float* d_dL_drgba, void* d_workspace, size_t ws_bytes,
+                                   ivrgs_gaussians* grad, float* d_edit_grad, void* stream) {
+    set_error("");
+    ivrgs_status st = check_gaussians(g, "g", true);
+    if (st) return st;
+    if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
+    if ((st = check_gaussians(grad, "grad", false))) return st;
+    if (grad->n != g->n) return invalid("grad->n must equal g->n");
+    static thread_local CamBatch cb;
+    if ((st = make_cam_batch(cams, n_views, &cb))) return st;
+    if ((st = check_projected(p, g->n, n_views))) return st;
+    if ((st = check_bins(b, cb))) return st;
+    if (!d_edit_table || !bg || !d_final_T || !d_last || !d_dL_drgba || !d_edit_grad)
+        return invalid("NULL input/output array");
+    if (!aligned(d_dL_drgba, 16)) return invalid("d_dL_drgba must be 16-byte aligned");
+    if (!(lowpass >= 0.f) || !isfinite(lowpass)) return invalid("lowpass must be finite and >= 0");
+    size_t need = 0;
+    ivrgs_render_backward_workspace(g->n, n_views, &need);
+    if (!d_workspace || ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return IVRGS_ERR_CAPACITY;
+    }
+    if (!aligned(d_workspace, 256)) return invalid("workspace must be 256-byte aligned");
+    return cuda_status(launch_render_backward(g, d_edit_table, p, b, cb, lowpass, bg, d_final_T, d_last, d_dL_drgba,
+                                              static_cast<char*>(d_workspace), grad, d_edit_grad,
+                                              (cudaStream_t)stream),
+                       "ivrgs_render_backward");
+}
+
+}  // extern "C"

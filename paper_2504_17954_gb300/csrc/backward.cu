@@ -1,0 +1,406 @@
+// Reverse mode of the path (rows a6, a7).
+//
+// a6, per tile: every pixel walks its run back to front from its last contributor. The
+// transmittance in front of contributor i is recovered from the stored final T as
+// T_i = T_{i+1} / (1 - alpha_i) (not stored in the forward). With
+// S_i = sum_{j>i} T_j alpha_j c_j + T_final bg, each contributor receives
+//   dL/dc_i = T_i alpha_i dL/dC,
+//   dL/dalpha_i = dL/dC . (T_i c_i - S_i / (1 - alpha_i)) + dL/dA T_final / (1 - alpha_i),
+// chained through alpha = min(0.99, o' exp(P)) to (u, v), the conic and o'. The nine
+// per-Gaussian sums are reduced across the warp (all lanes walk the same entry) and added
+// with one vector atomic per warp.
+//
+// a7, per Gaussian: the projection and shading are recomputed per view; dL/dSigma,
+// dL/dc_v, dL/dk', dL/dn and dL/do' are accumulated over views in registers and pushed
+// through the view-independent parts (quaternion, scale, edits) once.
+#include "blend_alpha.cuh"
+#include "gauss_math.cuh"
+
+namespace ivrgs {
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(kTilePix) k_render_bwd(
+    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
+    const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
+    float3 bg, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
+    const float4* __restrict__ dL, float4* __restrict__ g0, float4* __restrict__ g1, float* __restrict__ g2) {
+    __shared__ float4 s_a[kTilePix];
+    __shared__ float4 s_b[kTilePix];
+    __shared__ float s_blue[kTilePix];
+    __shared__ long long s_gi[kTilePix];
+    __shared__ unsigned s_max;
+    const long long tile = blockIdx.x;
+    const int v = view_of_tile(cb, tile);
+    const CamDev& cam = cb.c[v];
+    const int local = (int)(tile - cam.tile0);
+    const int tx = local % cam.gx, ty = local / cam.gx;
+    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int py = ty * kTile + (threadIdx.x / kTile);
+    const bool inside = px < cam.W && py < cam.H;
+    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const uint2 rg = ranges[tile];
+    const long long vbase = (long long)v * n;
+    const int lane = threadIdx.x & 31;
+
+    float Tf = 1.0f;
+    unsigned my_last = 0;
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (inside) {
+        const long long pix = cam.pix0 + (long long)py * cam.W + px;
+        Tf = final_T[pix];
+        my_last = last_in[pix];
+        d = dL[pix];
+    }
+    if (threadIdx.x == 0) s_max = 0u;
+    __syncthreads();
+    atomicMax(&s_max, my_last);
+    __syncthreads();
+    const int max_last = (int)s_max;
+    float T = Tf;
+    float S0 = Tf * bg.x, S1 = Tf * bg.y, S2 = Tf * bg.z;
+    const float dA_T = d.w * Tf;  // dL/dA * T_final
+
+    for (int b_end = max_last; b_end > 0; b_end -= kTilePix) {
+        const int b_start = max(0, b_end - kTilePix);
+        const int e = b_end - 1 - (int)threadIdx.x;
+        __syncthreads();
+        if (e >= b_start) {
+            const long long gi = vbase + values[rg.x + e];
+            float4 sa, sb;
+            const float4 cd = rgbd[gi];
+            stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
+            s_a[threadIdx.x] = sa;
+            s_b[threadIdx.x] = sb;
+            s_blue[threadIdx.x] = cd.z;
+            s_gi[threadIdx.x] = gi;
+        }
+        __syncthreads();
+        const int cnt = b_end - b_start;
+        for (int j = 0; j < cnt; ++j) {
+            const int ee = b_end - 1 - j;
+            float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
+            bool contrib = false;
+            if (ee < (int)my_last) {
+                const float4 a = s_a[j];
+                const float4 bb = s_b[j];
+                float dx, dy;
+                const float p2 = blend_p2(a, bb, fx, fy, dx, dy);
+                if (p2 <= 0.0f) {
+                    const float G = fast_ex2(p2);
+                    const float raw = bb.y * G;
+                    const float alpha = fminf(kAlphaMax, raw);
+                    if (alpha >= kAlphaMin) {
+                        contrib = true;
+                        const float om = 1.0f - alpha;
+                        const float Ti = T / om;
+                        const float blue = s_blue[j];
+                        const float w = Ti * alpha;
+                        gr = w * d.x;
+                        gg = w * d.y;
+                        gbl = w * d.z;
+                        const float dalpha = (d.x * (Ti * bb.z) + d.y * (Ti * bb.w) + d.z * (Ti * blue)) -
+                                             (d.x * S0 + d.y * S1 + d.z * S2 - dA_T) / om;
+                        S0 = fmaf(w, bb.z, S0);
+                        S1 = fmaf(w, bb.w, S1);
+                        S2 = fmaf(w, blue, S2);
+                        T = Ti;
+                        if (raw < kAlphaMax) {
+                            const float dP = dalpha * raw;  // dalpha/dP = o' G
+                            go = dalpha * G;
+                            // P = p2 / log2(e): dP/du = (2A' dx + B' dy)/log2e, dP/dv = (B' dx + 2C' dy)/log2e
+                            const float il = 1.0f / kLog2e;
+                            gu = dP * (2.0f * a.z * dx + a.w * dy) * il;
+                            gv = dP * (a.w * dx + 2.0f * bb.x * dy) * il;
+                            ga = dP * (-0.5f * dx * dx);
+                            gb = dP * (-dx * dy);
+                            gc = dP * (-0.5f * dy * dy);
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb); gc = warp_sum(gc);
+                go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl);
+                if (lane == 0) {
+                    const long long gi = s_gi[j];
+                    atomicAdd(&g0[gi], make_float4(gu, gv, ga, gb));
+                    atomicAdd(&g1[gi], make_float4(gc, go, gr, gg));
+                    atomicAdd(&g2[gi], gbl);
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------- a7
+__global__ void __launch_bounds__(256) k_project_bwd(const ivrgs_gaussians g, const float* __restrict__ table,
+                                                     const __grid_constant__ CamBatch cb, float lowpass,
+                                                     const float4* __restrict__ g0, const float4* __restrict__ g1,
+                                                     const float* __restrict__ g2, const ivrgs_gaussians grad,
+                                                     float* __restrict__ egrad) {
+    __shared__ float s_red[8][8];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = g.n;
+    const bool active = i < n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int M = g.n_models;
+    GaussLocal G;
+    if (active) load_gauss(g, table, M, i, G);
+    else G.visible = false;
+    float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float dcv[3] = {0.f, 0.f, 0.f}, dkp[4] = {0.f, 0.f, 0.f, 0.f}, dnn[3] = {0.f, 0.f, 0.f}, dop = 0.f;
+    for (int v = 0; v < cb.n; ++v) {
+        const CamDev& c = cb.c[v];
+        float dlv[3] = {0.f, 0.f, 0.f};
+        if (G.visible) {
+            const long long o = (long long)v * n + i;
+            const float4 a = g0[o], b = g1[o];
+            const float bl = g2[o];
+            const bool any = (a.x != 0.f) | (a.y != 0.f) | (a.z != 0.f) | (a.w != 0.f) | (b.x != 0.f) |
+                             (b.y != 0.f) | (b.z != 0.f) | (b.w != 0.f) | (bl != 0.f);
+            ViewLocal V;
+            if (any) project_view(G, c, lowpass, V);
+            if (any && V.visible) {
+                dop += b.y;
+                // ---- shading
+                const float Gr[3] = {b.z, b.w, bl};
+                const float Gc = Gr[0] * G.cv[0] + Gr[1] * G.cv[1] + Gr[2] * G.cv[2];
+                const float Gs = Gr[0] + Gr[1] + Gr[2];
+                const float kd = G.kp[0] + G.kp[1] * V.nl;
+                for (int k = 0; k < 3; ++k) dcv[k] += kd * Gr[k];
+                dkp[0] += Gc;
+                dkp[1] += V.nl * Gc;
+                float dnh = 0.f;
+                if (V.gate) {
+                    dkp[2] += Gs * V.spow;
+                    dkp[3] += Gs * G.kp[2] * V.spow * logf(V.nh);
+                    dnh = Gs * G.kp[2] * G.kp[3] * V.spow / V.nh;
+                }
+                const float dnl = G.kp[1] * Gc;
+                const float snl = V.ndl > 0.f ? 1.f : (V.ndl < 0.f ? -1.f : 0.f);
+                const float snh = V.ndh > 0.f ? 1.f : (V.ndh < 0.f ? -1.f : 0.f);
+                float dl[3], dh[3], dv[3] = {0.f, 0.f, 0.f};
+                for (int k = 0; k < 3; ++k) {
+                    dnn[k] += dnl * snl * V.l[k] + dnh * snh * V.h[k];
+                    dl[k] = dnl * snl * G.nn[k];
+                    dh[k] = dnh * snh * G.nn[k];
+                }
+                if (V.hlen > 0.f) {
+                    const float hd = V.h[0] * dh[0] + V.h[1] * dh[1] + V.h[2] * dh[2];
+                    const float ih = 1.0f / V.hlen;
+                    for (int k = 0; k < 3; ++k) {
+                        const float t = (dh[k] - V.h[k] * hd) * ih;
+                        dv[k] += t;
+                        dl[k] += t;
+                    }
+                }
+                if (c.headlight) {
+                    for (int k = 0; k < 3; ++k) dv[k] += dl[k];
+                } else {
+                    const float ld = c.light[0] * dl[0] + c.light[1] * dl[1] + c.light[2] * dl[2];
+                    for (int k = 0; k < 3; ++k) dlv[k] = (dl[k] - c.light[k] * ld) / c.light_len;
+                }
+                {
+                    const float vd = V.vd[0] * dv[0] + V.vd[1] * dv[1] + V.vd[2] * dv[2];
+                    const float iv = 1.0f / V.vlen;
+                    for (int k = 0; k < 3; ++k) dmu[k] -= (dv[k] - V.vd[k] * vd) * iv;
+                }
+                // ---- conic -> Sigma'
+                const float A = V.A, B = V.B, C = V.C;
+                const float id2 = 1.0f / (V.det * V.det);
+                const float dA = (a.z * (-C * C) + a.w * (B * C) + b.x * (-B * B)) * id2;
+                const float dB = (a.z * (2.f * B * C) + a.w * (-(A * C + B * B)) + b.x * (2.f * A * B)) * id2;
+                const float dC = (a.z * (-B * B) + a.w * (A * B) + b.x * (-A * A)) * id2;
+                const float G00 = dA, G01 = 0.5f * dB, G11 = dC;
+                const float* T = V.T;
+                // dSigma += T^T G2 T (symmetric; store xx, xy, xz, yy, yz, zz)
+                float GT[6];  // G2 T (2x3)
+                for (int j = 0; j < 3; ++j) {
+                    GT[j] = G00 * T[j] + G01 * T[3 + j];
+                    GT[3 + j] = G01 * T[j] + G11 * T[3 + j];
+                }
+                dSig[0] += T[0] * GT[0] + T[3] * GT[3];
+                dSig[1] += T[0] * GT[1] + T[3] * GT[4];
+                dSig[2] += T[0] * GT[2] + T[3] * GT[5];
+                dSig[3] += T[1] * GT[1] + T[4] * GT[4];
+                dSig[4] += T[1] * GT[2] + T[4] * GT[5];
+                dSig[5] += T[2] * GT[2] + T[5] * GT[5];
+                // dT = 2 G2 T Sigma
+                const float* S = G.Sig;
+                float dT[6];
+                for (int r = 0; r < 2; ++r) {
+                    const float* q = GT + 3 * r;
+                    dT[3 * r + 0] = 2.f * (q[0] * S[0] + q[1] * S[1] + q[2] * S[2]);
+                    dT[3 * r + 1] = 2.f * (q[0] * S[1] + q[1] * S[3] + q[2] * S[4]);
+                    dT[3 * r + 2] = 2.f * (q[0] * S[2] + q[1] * S[4] + q[2] * S[5]);
+                }
+                // dJ = dT W^T; only J00, J02, J11, J12 are non-zero
+                const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
+                const float dJ02 = dT[0] * c.R[6] + dT[1] * c.R[7] + dT[2] * c.R[8];
+                const float dJ11 = dT[3] * c.R[3] + dT[4] * c.R[4] + dT[5] * c.R[5];
+                const float dJ12 = dT[3] * c.R[6] + dT[4] * c.R[7] + dT[5] * c.R[8];
+                const float iz = V.iz, iz2 = iz * iz;
+                float dmc[3] = {0.f, 0.f, 0.f};
+                dmc[2] += dJ00 * (-c.fx * iz2) + dJ11 * (-c.fy * iz2);
+                if (V.clx) {
+                    dmc[2] += dJ02 * (c.fx * V.txc * iz2);
+                } else {
+                    dmc[0] += dJ02 * (-c.fx * iz2);
+                    dmc[2] += dJ02 * (2.f * c.fx * V.x * iz2 * iz);
+                }
+                if (V.cly) {
+                    dmc[2] += dJ12 * (c.fy * V.tyc * iz2);
+                } else {
+                    dmc[1] += dJ12 * (-c.fy * iz2);
+                    dmc[2] += dJ12 * (2.f * c.fy * V.y * iz2 * iz);
+                }
+                // mean2D: u = fx x/z + cx
+                dmc[0] += a.x * c.fx * iz;
+                dmc[1] += a.y * c.fy * iz;
+                dmc[2] += -(a.x * c.fx * V.x + a.y * c.fy * V.y) * iz2;
+                for (int k = 0; k < 3; ++k) dmu[k] += c.R[k] * dmc[0] + c.R[3 + k] * dmc[1] + c.R[6 + k] * dmc[2];
+            }
+        }
+        if (!c.headlight) {  // uniform across the grid: per-view light gradient, block-reduced
+            float r0 = warp_sum(dlv[0]), r1 = warp_sum(dlv[1]), r2 = warp_sum(dlv[2]);
+            __syncthreads();
+            if (lane == 0) { s_red[warp][0] = r0; s_red[warp][1] = r1; s_red[warp][2] = r2; }
+            __syncthreads();
+            if (threadIdx.x < 3) {
+                float t = 0.f;
+                for (int w = 0; w < 8; ++w) t += s_red[w][threadIdx.x];
+                if (t != 0.f) atomicAdd(&egrad[(long long)M * IVRGS_EDIT_STRIDE + 8 + 4 * v + threadIdx.x], t);
+            }
+        }
+    }
+    // ---- view-independent chains
+    float dlam[4] = {0.f, 0.f, 0.f, 0.f}, dbias[4] = {0.f, 0.f, 0.f, 0.f};
+    float dcp[3] = {0.f, 0.f, 0.f}, dsm = 0.f;
+    if (active) {
+        float gm[3] = {0.f, 0.f, 0.f}, gls[3] = {0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f}, gn[3] = {0.f, 0.f, 0.f};
+        float glogit = 0.f, gdc[3] = {0.f, 0.f, 0.f}, gk[4] = {0.f, 0.f, 0.f, 0.f};
+        if (G.visible) {
+            for (int k = 0; k < 3; ++k) gm[k] = dmu[k];
+            // Sigma = M M^T, M = Rq diag(sc): dM = 2 dSigma M
+            float M_[9], dS[9];
+            for (int r = 0; r < 3; ++r)
+                for (int k = 0; k < 3; ++k) M_[3 * r + k] = G.Rq[3 * r + k] * G.sc[k];
+            dS[0] = dSig[0]; dS[1] = dSig[1]; dS[2] = dSig[2];
+            dS[3] = dSig[1]; dS[4] = dSig[3]; dS[5] = dSig[4];
+            dS[6] = dSig[2]; dS[7] = dSig[4]; dS[8] = dSig[5];
+            float dR[9];
+            for (int k = 0; k < 3; ++k) {
+                float ds = 0.f;
+                for (int r = 0; r < 3; ++r) {
+                    const float dM = 2.f * (dS[3 * r] * M_[k] + dS[3 * r + 1] * M_[3 + k] + dS[3 * r + 2] * M_[6 + k]);
+                    ds += G.Rq[3 * r + k] * dM;
+                    dR[3 * r + k] = dM * G.sc[k];
+                }
+                gls[k] = ds * G.sc[k];
+            }
+            const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
+            float dq[4];
+            dq[0] = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+            dq[1] = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] + w * dR[7] -
+                           2.f * x * dR[8]);
+            dq[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] + z * dR[7] -
+                           2.f * y * dR[8]);
+            dq[3] = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] + y * dR[5] +
+                           x * dR[6] + y * dR[7]);
+            const float qd = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
+            for (int k = 0; k < 4; ++k) gq[k] = (dq[k] - G.qn[k] * qd) / G.qlen;
+            const float nd = G.nn[0] * dnn[0] + G.nn[1] * dnn[1] + G.nn[2] * dnn[2];
+            for (int k = 0; k < 3; ++k) gn[k] = (dnn[k] - G.nn[k] * nd) / G.nlen;
+            glogit = dop * G.sm * G.sig * (1.f - G.sig);
+            dsm = dop * G.sig;
+            const float* lam = table + (long long)M * IVRGS_EDIT_STRIDE;
+            for (int k = 0; k < 4; ++k) {
+                gk[k] = __ldg(lam + k) * dkp[k];
+                dlam[k] = G.k[k] * dkp[k];
+                dbias[k] = dkp[k];
+            }
+            for (int k = 0; k < 3; ++k) {
+                gdc[k] = dcv[k];
+                dcp[k] = dcv[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            grad.mean[3 * i + k] = gm[k];
+            grad.log_scale[3 * i + k] = gls[k];
+            grad.dcolor[3 * i + k] = gdc[k];
+            grad.normal[3 * i + k] = gn[k];
+        }
+        reinterpret_cast<float4*>(grad.quat)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        reinterpret_cast<float4*>(grad.kads)[i] = make_float4(gk[0], gk[1], gk[2], gk[3]);
+        grad.opacity_logit[i] = glogit;
+    }
+    // ---- edit gradients: global lambda, b block-reduced; per-model terms warp-reduced when the warp is
+    // uniform in its model (composed models are contiguous), else per lane
+    {
+        float r[8];
+        for (int k = 0; k < 4; ++k) { r[k] = warp_sum(dlam[k]); r[4 + k] = warp_sum(dbias[k]); }
+        __syncthreads();
+        if (lane == 0)
+            for (int k = 0; k < 8; ++k) s_red[warp][k] = r[k];
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            float t = 0.f;
+            for (int w = 0; w < 8; ++w) t += s_red[w][threadIdx.x];
+            if (t != 0.f) atomicAdd(&egrad[(long long)M * IVRGS_EDIT_STRIDE + threadIdx.x], t);
+        }
+    }
+    {
+        const int model = active ? G.model : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, model);
+        if (peers == 0xffffffffu) {
+            float r0 = warp_sum(dcp[0]), r1 = warp_sum(dcp[1]), r2 = warp_sum(dcp[2]), r3 = warp_sum(dsm);
+            if (lane == 0 && model >= 0) {
+                float* eg = egrad + (long long)model * IVRGS_EDIT_STRIDE;
+                if (r0 != 0.f) atomicAdd(eg + 0, r0);
+                if (r1 != 0.f) atomicAdd(eg + 1, r1);
+                if (r2 != 0.f) atomicAdd(eg + 2, r2);
+                if (r3 != 0.f) atomicAdd(eg + 3, r3);
+            }
+        } else if (model >= 0) {
+            float* eg = egrad + (long long)model * IVRGS_EDIT_STRIDE;
+            if (dcp[0] != 0.f) atomicAdd(eg + 0, dcp[0]);
+            if (dcp[1] != 0.f) atomicAdd(eg + 1, dcp[1]);
+            if (dcp[2] != 0.f) atomicAdd(eg + 2, dcp[2]);
+            if (dsm != 0.f) atomicAdd(eg + 3, dsm);
+        }
+    }
+}
+
+cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table, const ivrgs_projected* p,
+                                   const ivrgs_bins* b, const CamBatch& cb, float lowpass, const float* bg,
+                                   const float* final_T, const uint32_t* last, const float* dL, char* ws,
+                                   ivrgs_gaussians* grad, float* edit_grad, cudaStream_t s) {
+    const long long vn = p->n * (long long)cb.n;
+    float4* g0 = reinterpret_cast<float4*>(ws);
+    float4* g1 = g0 + vn;
+    float* g2 = reinterpret_cast<float*>(g1 + vn);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ws, 0, (size_t)vn * 36, s)) != cudaSuccess) return e;
+    const long long ne = (long long)g->n_models * IVRGS_EDIT_STRIDE + 8 + 4ll * cb.n;
+    if ((e = cudaMemsetAsync(edit_grad, 0, sizeof(float) * (size_t)ne, s)) != cudaSuccess) return e;
+    if (cb.n_tiles > 0) {
+        IVRGS_PROF("k_render_bwd", s);
+        k_render_bwd<<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(
+            reinterpret_cast<const float2*>(p->xy), reinterpret_cast<const float4*>(p->conic_o),
+            reinterpret_cast<const float4*>(p->rgbd), p->n, b->values, reinterpret_cast<const uint2*>(b->ranges), cb,
+            make_float3(bg[0], bg[1], bg[2]), final_T, last, reinterpret_cast<const float4*>(dL), g0, g1, g2);
+    }
+    if (g->n > 0) {
+        IVRGS_PROF("k_project_bwd", s);
+        k_project_bwd<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1, g2, *grad,
+                                                                     edit_grad);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ivrgs

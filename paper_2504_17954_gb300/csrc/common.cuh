@@ -1,0 +1,111 @@
+// Shared device-side definitions of libivrgs (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "ivrgs.h"
+#include "prof.cuh"
+
+namespace ivrgs {
+
+constexpr int kTile = 16;              // tile edge (pixels); one CTA of 256 threads per tile
+constexpr int kTilePix = kTile * kTile;
+constexpr float kGuard = 1.3f;         // guard band of x/z, y/z inside the Jacobian
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTMin = 1e-4f;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Camera as the kernels see it (travels in kernel parameter space).
+struct CamDev {
+    int W, H, gx, gy;
+    long long tile0, pix0;
+    float fx, fy, cx, cy;
+    float R[9], t[3], campos[3];
+    float znear, limx, limy;
+    int headlight;
+    float light[3];   // normalised light_dir (orbital light)
+    float light_len;  // |light_dir|
+};
+
+struct CamBatch {
+    int n;
+    int pad;
+    long long n_tiles;
+    CamDev c[IVRGS_MAX_VIEWS];
+};
+
+// view of a global tile id (binary search over the per-view first tile)
+__device__ __forceinline__ int view_of_tile(const CamBatch& cb, long long t) {
+    int lo = 0, hi = cb.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (cb.c[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// float32 tile rectangle, half-open: x0 = clamp(floor((u - r)/T), 0, G), x1 = clamp(floor((u + r)/T) + 1, 0, G)
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int gx, int gy, int& x0, int& x1, int& y0,
+                                          int& y1) {
+    const float fr = (float)r;
+    const float inv = 1.0f / (float)kTile;  // exact: power of two
+    float a = floorf(__fmul_rn(__fsub_rn(u, fr), inv));
+    float b = floorf(__fmul_rn(__fadd_rn(u, fr), inv)) + 1.0f;
+    float c = floorf(__fmul_rn(__fsub_rn(v, fr), inv));
+    float d = floorf(__fmul_rn(__fadd_rn(v, fr), inv)) + 1.0f;
+    x0 = (int)fminf(fmaxf(a, 0.0f), (float)gx);
+    x1 = (int)fminf(fmaxf(b, 0.0f), (float)gx);
+    y0 = (int)fminf(fmaxf(c, 0.0f), (float)gy);
+    y1 = (int)fminf(fmaxf(d, 0.0f), (float)gy);
+}
+
+__device__ __forceinline__ float fast_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------------------------------
+// host-side helpers
+// ---------------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+ivrgs_status cuda_status(cudaError_t e, const char* what);
+
+struct BinPlan {
+    int n_passes;          // 8-bit digit passes over the key bits in use
+    int key_bits;
+    long long n_records;   // n * n_views
+    long long n_scan_blocks;
+    long long capacity;
+    long long sort_tiles;  // ceil(capacity / kSortTile)
+    // workspace layout (byte offsets)
+    size_t off_block_sums, off_hist, off_base, off_counter, off_lookback, off_keys_alt, off_vals_alt, off_flag,
+        off_total, total_bytes;
+};
+
+ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb);
+BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity);
+
+// launchers (each returns cudaGetLastError() of its launches)
+cudaError_t launch_compose(const ivrgs_gaussians* models, int32_t n_models, ivrgs_gaussians* composed,
+                           cudaStream_t s);
+cudaError_t launch_edit_table(const ivrgs_model_edit* edits, int32_t n_models, const ivrgs_light* light,
+                              float* table, cudaStream_t s);
+cudaError_t launch_project(const ivrgs_gaussians* g, const float* table, const CamBatch& cb, float lowpass,
+                           ivrgs_projected* out, cudaStream_t s);
+cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
+                             uint64_t* d_n_pairs, cudaStream_t s);
+cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
+                            ivrgs_bins* out, long long exact_pairs, cudaStream_t s);
+cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const CamBatch& cb, const float* bg,
+                          float* rgba, float* final_T, uint32_t* last, cudaStream_t s);
+cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table, const ivrgs_projected* p,
+                                   const ivrgs_bins* b, const CamBatch& cb, float lowpass, const float* bg,
+                                   const float* final_T, const uint32_t* last, const float* dL, char* ws,
+                                   ivrgs_gaussians* grad, float* edit_grad, cudaStream_t s);
+
+}  // namespace ivrgs

@@ -1,0 +1,159 @@
+// Per-Gaussian projection and shading math (float32, one thread per Gaussian), shared by
+// the forward projection kernel and the backward kernel, which recomputes it.
+//   Sec. 3: Sigma = R(q) S S^T R(q)^T, Sigma' = J W Sigma W^T J^T (+ lowpass I), 2D mean
+//   through the pinhole; Blinn-Phong c = k_a c_v + k_d c_v |n.l| + [|n.l|>0] k_s |n.h|^beta.
+//   Sec. 4.3: c_v = c_p + dc.  Sec. 4.5/4.6: o' = s_m sigmoid(logit), k' = lambda k + b.
+#pragma once
+
+#include "common.cuh"
+
+namespace ivrgs {
+
+// view-independent quantities of one Gaussian
+struct GaussLocal {
+    float mu[3];
+    float qn[4], qlen;       // normalised quaternion, |q|
+    float Rq[9];            // rotation of qn
+    float sc[3];            // exp(log s)
+    float Sig[6];           // Sigma: xx, xy, xz, yy, yz, zz
+    float nn[3], nlen;      // normalised normal, |n|
+    float cv[3];            // c_p + dc
+    float k[4], kp[4];      // stored k and edited k' = lambda k + b
+    float sig, o;           // sigmoid(logit), o' = s_m sigmoid
+    float sm;               // opacity scale of the model
+    int model;
+    bool visible;
+};
+
+__device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float* __restrict__ table, int n_models,
+                                           long long i, GaussLocal& G) {
+    G.model = g.model_id[i];
+    const float* me = table + (long long)G.model * IVRGS_EDIT_STRIDE;
+    G.visible = __ldg(me + 4) != 0.0f;
+    G.mu[0] = g.mean[3 * i]; G.mu[1] = g.mean[3 * i + 1]; G.mu[2] = g.mean[3 * i + 2];
+    const float4 q = reinterpret_cast<const float4*>(g.quat)[i];
+    G.qlen = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float iq = 1.0f / G.qlen;
+    const float w = q.x * iq, x = q.y * iq, y = q.z * iq, z = q.w * iq;
+    G.qn[0] = w; G.qn[1] = x; G.qn[2] = y; G.qn[3] = z;
+    G.Rq[0] = 1.f - 2.f * (y * y + z * z); G.Rq[1] = 2.f * (x * y - w * z); G.Rq[2] = 2.f * (x * z + w * y);
+    G.Rq[3] = 2.f * (x * y + w * z); G.Rq[4] = 1.f - 2.f * (x * x + z * z); G.Rq[5] = 2.f * (y * z - w * x);
+    G.Rq[6] = 2.f * (x * z - w * y); G.Rq[7] = 2.f * (y * z + w * x); G.Rq[8] = 1.f - 2.f * (x * x + y * y);
+    for (int k = 0; k < 3; ++k) G.sc[k] = expf(g.log_scale[3 * i + k]);
+    float M[9];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) M[3 * r + k] = G.Rq[3 * r + k] * G.sc[k];
+    G.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+    G.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+    G.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+    G.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+    G.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+    G.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+    const float n0 = g.normal[3 * i], n1 = g.normal[3 * i + 1], n2 = g.normal[3 * i + 2];
+    G.nlen = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+    const float inl = 1.0f / G.nlen;
+    G.nn[0] = n0 * inl; G.nn[1] = n1 * inl; G.nn[2] = n2 * inl;
+    for (int c = 0; c < 3; ++c) G.cv[c] = __ldg(me + c) + g.dcolor[3 * i + c];
+    const float4 kk = reinterpret_cast<const float4*>(g.kads)[i];
+    G.k[0] = kk.x; G.k[1] = kk.y; G.k[2] = kk.z; G.k[3] = kk.w;
+    const float* lam = table + (long long)n_models * IVRGS_EDIT_STRIDE;
+    for (int c = 0; c < 4; ++c) G.kp[c] = __ldg(lam + c) * G.k[c] + __ldg(lam + 4 + c);
+    G.sig = 1.0f / (1.0f + expf(-g.opacity_logit[i]));
+    G.sm = __ldg(me + 3);
+    G.o = G.sm * G.sig;
+}
+
+// per-view quantities
+struct ViewLocal {
+    bool visible;
+    float x, y, z, iz;
+    float txc, tyc;
+    bool clx, cly;
+    float T[6];           // J W (2x3)
+    float A, B, C, det;   // Sigma' (dilated) and its determinant
+    float conic[3];
+    int radius;
+    float u, v;
+    float depth;
+    // shading
+    float vd[3], vlen, l[3], h[3], hlen;
+    float ndl, ndh, nl, nh, spow;
+    bool gate;
+    float rgb[3];
+};
+
+__device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& c, float lowpass, ViewLocal& V) {
+    V.visible = false;
+    // depth in float64: products of float32 values are exact, summation order fixed
+    const double zd = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)c.R[6], (double)G.mu[0]),
+                                                    __dmul_rn((double)c.R[7], (double)G.mu[1])),
+                                          __dmul_rn((double)c.R[8], (double)G.mu[2])),
+                                (double)c.t[2]);
+    if (!(zd > (double)c.znear)) return;
+    V.depth = (float)zd;
+    V.z = V.depth;
+    V.x = fmaf(c.R[0], G.mu[0], fmaf(c.R[1], G.mu[1], fmaf(c.R[2], G.mu[2], c.t[0])));
+    V.y = fmaf(c.R[3], G.mu[0], fmaf(c.R[4], G.mu[1], fmaf(c.R[5], G.mu[2], c.t[1])));
+    V.iz = 1.0f / V.z;
+    const float tx = V.x * V.iz, ty = V.y * V.iz;
+    V.txc = fminf(fmaxf(tx, -c.limx), c.limx);
+    V.tyc = fminf(fmaxf(ty, -c.limy), c.limy);
+    V.clx = (tx < -c.limx) || (tx > c.limx);
+    V.cly = (ty < -c.limy) || (ty > c.limy);
+    const float J00 = c.fx * V.iz, J02 = -c.fx * V.txc * V.iz;
+    const float J11 = c.fy * V.iz, J12 = -c.fy * V.tyc * V.iz;
+    for (int j = 0; j < 3; ++j) {
+        V.T[j] = J00 * c.R[j] + J02 * c.R[6 + j];
+        V.T[3 + j] = J11 * c.R[3 + j] + J12 * c.R[6 + j];
+    }
+    const float* S = G.Sig;
+    // U = T Sigma (2x3)
+    float U[6];
+    for (int a = 0; a < 2; ++a) {
+        const float* t = V.T + 3 * a;
+        U[3 * a + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
+        U[3 * a + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
+        U[3 * a + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+    }
+    V.A = U[0] * V.T[0] + U[1] * V.T[1] + U[2] * V.T[2] + lowpass;
+    V.B = U[0] * V.T[3] + U[1] * V.T[4] + U[2] * V.T[5];
+    V.C = U[3] * V.T[3] + U[4] * V.T[4] + U[5] * V.T[5] + lowpass;
+    V.det = V.A * V.C - V.B * V.B;
+    if (!(V.det > 0.0f)) return;
+    const float idet = 1.0f / V.det;
+    V.conic[0] = V.C * idet;
+    V.conic[1] = -V.B * idet;
+    V.conic[2] = V.A * idet;
+    const float mid = 0.5f * (V.A + V.C);
+    const float lmax = mid + sqrtf(fmaxf(mid * mid - V.det, 0.0f));
+    V.radius = (int)ceilf(3.0f * sqrtf(lmax));
+    if (V.radius <= 0) return;
+    V.u = c.fx * tx + c.cx;
+    V.v = c.fy * ty + c.cy;
+    // Blinn-Phong shading
+    float d[3] = {c.campos[0] - G.mu[0], c.campos[1] - G.mu[1], c.campos[2] - G.mu[2]};
+    V.vlen = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const float ivl = 1.0f / V.vlen;
+    for (int k = 0; k < 3; ++k) V.vd[k] = d[k] * ivl;
+    if (c.headlight) {
+        for (int k = 0; k < 3; ++k) V.l[k] = V.vd[k];
+    } else {
+        for (int k = 0; k < 3; ++k) V.l[k] = c.light[k];
+    }
+    float hv[3] = {V.vd[0] + V.l[0], V.vd[1] + V.l[1], V.vd[2] + V.l[2]};
+    V.hlen = sqrtf(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);
+    const float ihl = V.hlen > 0.0f ? 1.0f / V.hlen : 0.0f;
+    for (int k = 0; k < 3; ++k) V.h[k] = hv[k] * ihl;
+    V.ndl = G.nn[0] * V.l[0] + G.nn[1] * V.l[1] + G.nn[2] * V.l[2];
+    V.ndh = G.nn[0] * V.h[0] + G.nn[1] * V.h[1] + G.nn[2] * V.h[2];
+    V.nl = fabsf(V.ndl);
+    V.nh = fabsf(V.ndh);
+    V.gate = (V.nl > 0.0f) && (V.nh > 0.0f);
+    V.spow = V.gate ? powf(V.nh, G.kp[3]) : 0.0f;
+    const float spec = V.gate ? G.kp[2] * V.spow : 0.0f;
+    const float diff = G.kp[0] + G.kp[1] * V.nl;
+    for (int k = 0; k < 3; ++k) V.rgb[k] = diff * G.cv[k] + spec;
+    V.visible = true;
+}
+
+}  // namespace ivrgs

@@ -1,0 +1,297 @@
+"""PyTorch-facing wrapper of libivrgs: device buffers, streams and a torch.autograd.Function.
+
+PyTorch provides device memory and the current stream; every computation runs in the
+library's kernels (``_native``). Nothing here computes any part of the rendering.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _native as N
+
+ATTRS = ("mean", "log_scale", "quat", "opacity_logit", "dcolor", "normal", "kads")
+WIDTH = {"mean": 3, "log_scale": 3, "quat": 4, "opacity_logit": 1, "dcolor": 3, "normal": 3, "kads": 4}
+
+
+def _vp(t: Optional[torch.Tensor]):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check_cuda(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+# ----------------------------------------------------------------------------------------
+@dataclass
+class Gaussians:
+    """Editable Gaussians on the device, structure of arrays (Sec. 4.3 attribute set)."""
+    mean: torch.Tensor
+    log_scale: torch.Tensor
+    quat: torch.Tensor
+    opacity_logit: torch.Tensor
+    dcolor: torch.Tensor
+    normal: torch.Tensor
+    kads: torch.Tensor
+    model_id: Optional[torch.Tensor]
+    n_models: int
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[0])
+
+    def struct(self, tensors: Optional[Sequence[torch.Tensor]] = None) -> N.ivrgs_gaussians:
+        ts = [getattr(self, k) for k in ATTRS] if tensors is None else list(tensors)
+        s = N.ivrgs_gaussians()
+        s.n = self.n
+        s.precision = N.IVRGS_FP32
+        s.n_models = self.n_models
+        for k, t in zip(ATTRS, ts):
+            setattr(s, k, t.data_ptr())
+        s.model_id = self.model_id.data_ptr() if self.model_id is not None else None
+        return s
+
+    @staticmethod
+    def empty(n: int, n_models: int, device="cuda") -> "Gaussians":
+        z = lambda w: torch.empty((n, w) if w > 1 else (n,), dtype=torch.float32, device=device)
+        return Gaussians(*(z(WIDTH[k]) for k in ATTRS), model_id=torch.empty(n, dtype=torch.int16, device=device),
+                         n_models=n_models)
+
+    @staticmethod
+    def from_arrays(arrs: dict, n_models: int = 1, device="cuda") -> "Gaussians":
+        t = lambda a: torch.as_tensor(a, dtype=torch.float32).to(device).contiguous()
+        return Gaussians(*(t(arrs[k]) for k in ATTRS), model_id=None, n_models=n_models)
+
+
+def edit_structs(palette, opacity_scale, visible, lam, bias):
+    M = len(opacity_scale)
+    ed = (N.ivrgs_model_edit * M)()
+    for m in range(M):
+        for k in range(3):
+            ed[m].palette[k] = float(palette[m][k])
+        ed[m].opacity_scale = float(opacity_scale[m])
+        ed[m].visible = int(bool(visible[m]))
+    li = N.ivrgs_light()
+    for k in range(4):
+        li.lambda_[k] = float(lam[k])
+        li.bias[k] = float(bias[k])
+    return ed, li
+
+
+def compose_edit(models: Sequence[Gaussians], palette, opacity_scale, visible, lam, bias, device="cuda",
+                 composed: Optional[Gaussians] = None, edit_table: Optional[torch.Tensor] = None, stream=None):
+    """Concatenate basic models on the device and write the edit table (ivrgs_compose_edit).
+
+    With ``models`` empty (or None) and ``composed`` None only the edit table is rewritten."""
+    M = len(opacity_scale)
+    ed, li = edit_structs(palette, opacity_scale, visible, lam, bias)
+    if edit_table is None:
+        edit_table = torch.empty(N.lib().ivrgs_edit_table_floats(M), dtype=torch.float32, device=device)
+    comp_s = None
+    arr = None
+    if models:
+        n = sum(m.n for m in models)
+        if composed is None:
+            composed = Gaussians.empty(n, M, device)
+        arr = (N.ivrgs_gaussians * M)(*[m.struct() for m in models])
+        comp_s = composed.struct()
+    N.ivrgs_compose_edit(arr, M, ed, C.byref(li), C.byref(comp_s) if comp_s is not None else None,
+                         _vp(edit_table), _stream(stream))
+    return composed, edit_table
+
+
+# ----------------------------------------------------------------------------------------
+def camera_structs(cams) -> (C.Array, int):
+    """Pack cameras (objects with W, H, fx, fy, cx, cy, R, t, campos, znear, headlight, light_dir)."""
+    V = len(cams)
+    arr = (N.ivrgs_camera * V)()
+    off = 0
+    for v, c in enumerate(cams):
+        a = arr[v]
+        a.W, a.H = int(c.W), int(c.H)
+        a.fx, a.fy, a.cx, a.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        for k in range(9):
+            a.R[k] = float(c.R[k])
+        for k in range(3):
+            a.t[k] = float(c.t[k])
+            a.campos[k] = float(c.campos[k])
+            a.light_dir[k] = float(c.light_dir[k])
+        a.znear = float(c.znear)
+        a.headlight = int(c.headlight)
+        a.pix_offset = off
+        off += int(c.W) * int(c.H)
+    return arr, off
+
+
+def n_tiles(cams, tile: int = 16) -> int:
+    return sum(((c.W + tile - 1) // tile) * ((c.H + tile - 1) // tile) for c in cams)
+
+
+class Rasterizer:
+    """Device buffers for one camera set and one scene size; forward and backward calls.
+
+    ``capacity`` fixes the pair buffer (required for CUDA-graph capture, mode="capacity");
+    with mode="exact" the buffer grows to the exact pair count when needed.
+    """
+
+    def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", capacity: Optional[int] = None,
+                 lowpass: float = 0.3, bg=(0.0, 0.0, 0.0)):
+        self.cams = list(cams)
+        self.V = len(self.cams)
+        self.n = int(n_gaussians)
+        self.n_models = int(n_models)
+        self.device = torch.device(device)
+        self.lowpass = float(lowpass)
+        self.cam_arr, self.n_pix = camera_structs(self.cams)
+        self.bg = (C.c_float * 3)(*[float(x) for x in bg])
+        self.n_tiles = n_tiles(self.cams)
+        VN = self.V * self.n
+        dev = self.device
+        self.xy = torch.empty((VN, 2), dtype=torch.float32, device=dev)
+        self.conic_o = torch.empty((VN, 4), dtype=torch.float32, device=dev)
+        self.rgbd = torch.empty((VN, 4), dtype=torch.float32, device=dev)
+        self.radius = torch.empty(VN, dtype=torch.int32, device=dev)
+        self.rgba = torch.empty((self.n_pix, 4), dtype=torch.float32, device=dev)
+        self.final_T = torch.empty(self.n_pix, dtype=torch.float32, device=dev)
+        self.last = torch.empty(self.n_pix, dtype=torch.int32, device=dev)
+        self.ranges = torch.empty((self.n_tiles, 2), dtype=torch.int32, device=dev)
+        self.d_n_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.n_pairs = 0
+        self.keys = self.values = self.ws_bin = None
+        self.capacity = 0
+        self._ensure_capacity(int(capacity) if capacity else max(1024, 8 * VN))
+        self.ws_bwd_bytes = N.ivrgs_render_backward_workspace(self.n, self.V)
+        self.ws_bwd = None
+        self.edit_grad = torch.empty(N.lib().ivrgs_edit_table_floats(self.n_models) + 4 * self.V,
+                                     dtype=torch.float32, device=dev)
+
+    # -- buffers
+    def _ensure_capacity(self, cap: int):
+        cap = min(int(cap), N.IVRGS_MAX_PAIRS - 1)
+        if cap <= self.capacity:
+            return
+        self.capacity = cap
+        self.keys = torch.empty(cap, dtype=torch.int64, device=self.device)
+        self.values = torch.empty(cap, dtype=torch.int32, device=self.device)
+        self.ws_bin_bytes = N.ivrgs_bin_workspace(self.n, self.V, self.cam_arr, 16, 16, cap)
+        self.ws_bin = torch.empty(self.ws_bin_bytes, dtype=torch.uint8, device=self.device)
+
+    def projected_struct(self) -> N.ivrgs_projected:
+        p = N.ivrgs_projected()
+        p.n, p.n_views = self.n, self.V
+        p.xy, p.conic_o, p.rgbd, p.radius = (t.data_ptr() for t in (self.xy, self.conic_o, self.rgbd, self.radius))
+        return p
+
+    def bins_struct(self) -> N.ivrgs_bins:
+        b = N.ivrgs_bins()
+        b.tile_w = b.tile_h = 16
+        b.n_tiles = self.n_tiles
+        b.capacity = self.capacity
+        b.keys, b.values = self.keys.data_ptr(), self.values.data_ptr()
+        b.ranges = self.ranges.data_ptr()
+        b.d_n_pairs = self.d_n_pairs.data_ptr()
+        b.n_pairs = self.n_pairs
+        return b
+
+    # -- steps
+    def project(self, g: Gaussians, edit_table: torch.Tensor, stream=None, tensors=None):
+        gs = g.struct(tensors)
+        p = self.projected_struct()
+        N.ivrgs_project(C.byref(gs), _vp(edit_table), self.cam_arr, self.V, self.lowpass, C.byref(p), _stream(stream))
+
+    def bin(self, mode: str = "exact", stream=None) -> int:
+        p = self.projected_struct()
+        if mode == "exact":
+            while True:
+                b = self.bins_struct()
+                st = N.ivrgs_bin(C.byref(p), self.cam_arr, self.V, N.IVRGS_BIN_EXACT, _vp(self.ws_bin), self.ws_bin_bytes,
+                                 C.byref(b), _stream(stream), allow=(N.IVRGS_OK, N.IVRGS_ERR_CAPACITY))
+                if st == N.IVRGS_OK:
+                    self.n_pairs = int(b.n_pairs)
+                    return self.n_pairs
+                need = int(b.n_pairs)
+                if need >= N.IVRGS_MAX_PAIRS:
+                    raise N.IvrgsError("ivrgs_bin", st, f"{need} pairs exceed the per-call limit")
+                self._ensure_capacity(int(need * 1.25) + 1024)
+        b = self.bins_struct()
+        N.ivrgs_bin(C.byref(p), self.cam_arr, self.V, N.IVRGS_BIN_CAPACITY, _vp(self.ws_bin), self.ws_bin_bytes,
+                    C.byref(b), _stream(stream))
+        return -1
+
+    def render(self, stream=None):
+        p, b = self.projected_struct(), self.bins_struct()
+        N.ivrgs_render(C.byref(p), C.byref(b), self.cam_arr, self.V, self.bg, _vp(self.rgba), _vp(self.final_T),
+                       _vp(self.last), _stream(stream))
+        return self.rgba
+
+    def forward(self, g: Gaussians, edit_table: torch.Tensor, mode: str = "exact", stream=None, tensors=None):
+        self.project(g, edit_table, stream, tensors)
+        self.bin(mode, stream)
+        return self.render(stream)
+
+    def backward(self, g: Gaussians, edit_table: torch.Tensor, dL_drgba: torch.Tensor, grad: Optional[Gaussians] = None,
+                 stream=None, tensors=None):
+        _check_cuda(dL_drgba, "dL_drgba")
+        if self.ws_bwd is None:
+            self.ws_bwd = torch.empty(self.ws_bwd_bytes, dtype=torch.uint8, device=self.device)
+        if grad is None:
+            grad = Gaussians.empty(self.n, self.n_models, self.device)
+            grad.model_id = None
+        gs = g.struct(tensors)
+        gr = grad.struct()
+        p, b = self.projected_struct(), self.bins_struct()
+        N.ivrgs_render_backward(C.byref(gs), _vp(edit_table), C.byref(p), C.byref(b), self.cam_arr, self.V,
+                                self.lowpass, self.bg, _vp(self.final_T), _vp(self.last), _vp(dL_drgba),
+                                _vp(self.ws_bwd), self.ws_bwd_bytes, C.byref(gr), _vp(self.edit_grad),
+                                _stream(stream))
+        return grad, self.edit_grad
+
+    # -- views of the packed image
+    def view_image(self, v: int, t: Optional[torch.Tensor] = None) -> torch.Tensor:
+        t = self.rgba if t is None else t
+        c = self.cams[v]
+        off = self.cam_arr[v].pix_offset
+        return t[off:off + c.W * c.H].view(c.H, c.W, *t.shape[1:])
+
+
+# ----------------------------------------------------------------------------------------
+class RenderFunction(torch.autograd.Function):
+    """rgba = render(Gaussian attributes, edit table); backward through ivrgs_render_backward.
+
+    The forward keeps only the projected records, the bins, the final transmittance and the
+    last-contributor index per pixel (inside the Rasterizer); the per-pixel transmittance
+    of every contributor is recomputed in the backward, not stored.
+    """
+
+    @staticmethod
+    def forward(ctx, rast: Rasterizer, g: Gaussians, edit_table, *attrs):
+        rast.forward(g, edit_table.detach(), tensors=[a.detach() for a in attrs])
+        ctx.rast, ctx.g = rast, g
+        ctx.save_for_backward(edit_table, *attrs)
+        return rast.rgba.clone()
+
+    @staticmethod
+    def backward(ctx, d_rgba):
+        edit_table, *attrs = ctx.saved_tensors
+        rast: Rasterizer = ctx.rast
+        grad, egrad = rast.backward(ctx.g, edit_table.detach(), d_rgba.contiguous(),
+                                    tensors=[a.detach() for a in attrs])
+        ne = edit_table.numel()
+        rast.light_grad = egrad[ne:].view(rast.V, 4)[:, :3].clone()
+        outs = [getattr(grad, k).view_as(a) for k, a in zip(ATTRS, attrs)]
+        return (None, None, egrad[:ne].clone(), *outs)
+
+
+def render(rast: Rasterizer, g: Gaussians, edit_table: torch.Tensor, params: Optional[Sequence[torch.Tensor]] = None):
+    """Differentiable render of all views; returns the packed [n_pix, 4] RGBA tensor."""
+    attrs = [getattr(g, k) for k in ATTRS] if params is None else list(params)
+    return RenderFunction.apply(rast, g, edit_table, *attrs)

@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, exports every entry point
+include/ivrgs.h declares, and rejects bad arguments on the host before touching the device."""
+import ctypes as C
+import shutil
+
+import pytest
+
+from paper_2504_17954_gb300 import _native as N
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") or __import__("os").path.exists("/usr/local/cuda/bin/nvcc"):
+        from paper_2504_17954_gb300 import build
+        build.build()
+    return N.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = N.declared_symbols()
+    assert {"ivrgs_compose_edit", "ivrgs_project", "ivrgs_bin", "ivrgs_render", "ivrgs_render_backward"} <= set(syms)
+    for s in syms:
+        assert hasattr(lib, s), s
+
+
+def test_host_side_argument_checks(lib):
+    assert lib.ivrgs_version() >= 100
+    assert lib.ivrgs_edit_table_floats(5) == 48
+    st = lib.ivrgs_project(None, None, None, 1, 0.3, None, None)
+    assert st == N.IVRGS_ERR_INVALID_ARG and "NULL" in N.last_error()
+    cams = (N.ivrgs_camera * 2)()
+    for c in cams:
+        c.W = c.H = 32
+        c.fx = c.fy = 40.0
+        c.headlight = 1
+    cams[1].pix_offset = 100  # overlaps view 0 (1024 pixels)
+    b = C.c_size_t(0)
+    st = lib.ivrgs_bin_workspace(10, 2, cams, 16, 16, 1000, C.byref(b))
+    assert st == N.IVRGS_ERR_INVALID_ARG and "overlap" in N.last_error()
+    cams[1].pix_offset = 1024
+    assert lib.ivrgs_bin_workspace(10, 2, cams, 16, 16, 1000, C.byref(b)) == N.IVRGS_OK and b.value > 0
+    assert lib.ivrgs_bin_workspace(10, 2, cams, 8, 8, 1000, C.byref(b)) == N.IVRGS_ERR_UNSUPPORTED
+    assert lib.ivrgs_bin_workspace(10, 0, cams, 16, 16, 1000, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
+    assert lib.ivrgs_bin_workspace(10, 2, cams, 16, 16, 1 << 30, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
+    cams[0].headlight = 0  # orbital light with a zero direction
+    assert lib.ivrgs_bin_workspace(10, 2, cams, 16, 16, 1000, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
+    assert lib.ivrgs_render_backward_workspace(10, 2, C.byref(b)) == N.IVRGS_OK and b.value >= 10 * 2 * 36
+    ed = (N.ivrgs_model_edit * 1)()
+    li = N.ivrgs_light()
+    assert lib.ivrgs_compose_edit(None, 0, ed, C.byref(li), None, None, None) == N.IVRGS_ERR_INVALID_ARG
+
+
+def test_product_does_not_import_oracle():
+    import pathlib
+    root = pathlib.Path(N.__file__).parent
+    for p in list(root.glob("*.py")) + list(root.glob("csrc/*")):
+        text = p.read_text()
+        assert "import oracle" not in text and "from oracle" not in text and "ivrgs_oracle" not in text, p
