@@ -235,9 +235,10 @@ ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit
    Must be off while a stream is being captured into a CUDA graph. */
 void ivrgs_prof_enable(int32_t on);
 
-/* Synchronises on the recorded events and writes one line "kernel launches total_ms" per
-   kernel launched since the previous report into buf (NUL-terminated, truncated to len);
-   returns the full length of the report. */
+/* Synchronises on the recorded events and returns the length of a report with one line
+   "kernel launches total_ms" per kernel launched since the last delivered report. If buf
+   holds more than that many bytes (len > length) the report is copied there, NUL-terminated,
+   and the totals are reset; otherwise nothing is copied and the totals are kept. */
 int64_t ivrgs_prof_report(char* buf, int64_t len);
 
 #ifdef __cplusplus

@@ -20,6 +20,12 @@ std::mutex g_mu;
 bool g_on = false;
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
+struct Acc {
+    std::string name;
+    long long count;
+    double ms;
+};
+std::vector<Acc> g_acc;
 
 cudaEvent_t take_event() {
     if (!g_pool.empty()) {
@@ -61,39 +67,35 @@ void ivrgs_prof_enable(int32_t on) {
 
 int64_t ivrgs_prof_report(char* buf, int64_t len) {
     std::lock_guard<std::mutex> lk(g_mu);
-    struct Acc {
-        std::string name;
-        long long count;
-        double ms;
-    };
-    std::vector<Acc> acc;
+    // drain finished records into the per-kernel totals
     for (const Rec& r : g_recs) {
         cudaEventSynchronize(r.b);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, r.a, r.b);
         bool found = false;
-        for (auto& x : acc)
+        for (auto& x : g_acc)
             if (x.name == r.name) {
                 x.count += 1;
                 x.ms += ms;
                 found = true;
                 break;
             }
-        if (!found) acc.push_back({r.name, 1, (double)ms});
+        if (!found) g_acc.push_back({r.name, 1, (double)ms});
         g_pool.push_back(r.a);
         g_pool.push_back(r.b);
     }
     g_recs.clear();
     std::string out;
-    for (auto& x : acc) {
+    for (auto& x : g_acc) {
         char line[256];
         snprintf(line, sizeof line, "%s %lld %.6f\n", x.name.c_str(), x.count, x.ms);
         out += line;
     }
-    if (buf && len > 0) {
-        const int64_t n = (int64_t)out.size() < len - 1 ? (int64_t)out.size() : len - 1;
-        memcpy(buf, out.data(), (size_t)n);
-        buf[n] = 0;
+    // the totals are handed out (and reset) only to a caller whose buffer holds them
+    if (buf && len > (int64_t)out.size()) {
+        memcpy(buf, out.data(), out.size());
+        buf[out.size()] = 0;
+        g_acc.clear();
     }
     return (int64_t)out.size();
 }
