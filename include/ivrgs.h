@@ -230,6 +230,32 @@ ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit
                                    const float* d_dL_drgba, void* d_workspace, size_t ws_bytes,
                                    ivrgs_gaussians* grad, float* d_edit_grad, void* stream);
 
+/* Bytes of the device array that ivrgs_render_backward_static uses as its scratch. */
+#define IVRGS_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
+
+/* ivrgs_render_backward without a workspace argument. The paper has no counterpart: this
+   entry point exists for callers that cannot call cudaMalloc, for example a plugin running
+   inside a host visualisation application that owns all device memory, or an interactive
+   editing loop that must not stall on the device-wide synchronisation an allocation can
+   cause. Its scratch is one array of IVRGS_STATIC_SCRATCH_BYTES bytes compiled into the
+   library; every GPU that loads the library holds it until the process exits.
+   Arguments, outputs and semantics are those of ivrgs_render_backward minus d_workspace and
+   ws_bytes; the caller still provides every input and output array. The call allocates
+   nothing (no cudaMalloc, cudaFree or allocating library routine).
+   Limit: the workspace ivrgs_render_backward_workspace(n, n_views) reports (36 bytes per
+   view-Gaussian record plus 256) must fit, i.e. n * n_views <= 932,060; a larger request
+   returns IVRGS_ERR_CAPACITY before anything is launched.
+   The first call on a device looks up the array's device address with that device current
+   and caches it, so make that first call before any stream capture. Every call uses the
+   same array and leaves its contents behind (each call clears what must start at zero);
+   calls that overlap on the GPU -- concurrent streams, host threads or processes sharing
+   the context -- race on the array, so the caller must serialise them. */
+ivrgs_status ivrgs_render_backward_static(const ivrgs_gaussians* g, const float* d_edit_table,
+                                          const ivrgs_projected* p, const ivrgs_bins* b, const ivrgs_camera* cams,
+                                          int32_t n_views, float lowpass, const float* bg, const float* d_final_T,
+                                          const uint32_t* d_last, const float* d_dL_drgba, ivrgs_gaussians* grad,
+                                          float* d_edit_grad, void* stream);
+
 /* Opt-in per-kernel timing (measurement support; the paper has no counterpart). With
    on != 0 every kernel launch of the library is bracketed by two CUDA events on its stream.
    Must be off while a stream is being captured into a CUDA graph. */
