@@ -127,16 +127,17 @@ typedef struct {
 } ivrgs_projected;
 
 /* Tile bins. Global tile ids run over all views: view v's tiles start at the sum of the
-   tile counts of views < v, row-major inside a view. keys [capacity] = (tile << 32) |
-   bits(float depth), sorted ascending, ties in (view, Gaussian) order; values [capacity] =
-   Gaussian index g of each key; ranges [n_tiles][2] = [start, end) of each tile's run in the
-   sorted arrays ((0, 0) for an empty tile). d_n_pairs: device uint64 scalar receiving the
+   tile counts of views < v, row-major inside a view. The pairs (tile, Gaussian) are ordered
+   by (tile, bits of the float depth), ties in (view, Gaussian) order -- i.e. ascending in the
+   64-bit key (tile << 32) | bits(depth). tiles [capacity] = global tile id of each sorted pair;
+   values [capacity] = Gaussian index g of each sorted pair; ranges [n_tiles][2] = [start, end)
+   of each tile's run ((0, 0) for an empty tile). d_n_pairs: device uint64 scalar receiving the
    number of pairs (in CAPACITY mode a value > capacity means the outputs are incomplete). */
 typedef struct {
     int32_t tile_w, tile_h; /* 16 x 16 in this build */
     int64_t n_tiles;
     int64_t capacity;
-    uint64_t* keys;
+    uint32_t* tiles;
     uint32_t* values;
     uint32_t* ranges;
     uint64_t* d_n_pairs;
@@ -181,11 +182,14 @@ ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera*
                                  int32_t tile_h, int64_t capacity, size_t* bytes);
 
 /* Tile binning by radix sort (the tile-based rasterisation of 3DGS that Sec. 3 builds on:
-   projected Gaussians are composited in depth order per screen tile). Per record: tile rectangle (half-open)
-   x0 = clamp(floor((u - r)/tile_w), 0, Gx), x1 = clamp(floor((u + r)/tile_w) + 1, 0, Gx)
-   (same for y) evaluated in float32; one (key, value) pair per covered tile; a stable LSD
-   radix sort (8-bit digits, onesweep with decoupled look-back) over the bits the keys use;
-   per-tile [start, end) ranges.
+   projected Gaussians are composited in depth order per screen tile). Per record: tile
+   rectangle (half-open) x0 = clamp(floor((u - r)/tile_w), 0, Gx),
+   x1 = clamp(floor((u + r)/tile_w) + 1, 0, Gx) (same for y) evaluated in float32; one pair per
+   covered tile. Ordering: the covered records are radix-sorted by the bits of their float
+   depth (stable, 4 passes of 8 bits), their pairs are emitted in that order and then
+   radix-sorted by tile id (stable, one pass per 8 bits of the largest tile id); both sorts
+   are onesweep LSD sorts with decoupled look-back. The result equals the stable sort of all
+   pairs by (tile << 32 | depth bits).
    mode IVRGS_BIN_EXACT: counts the pairs, copies the count to the host (synchronises the
    stream), returns IVRGS_ERR_CAPACITY with out->n_pairs = required count if it exceeds
    out->capacity, else finishes and sets out->n_pairs.

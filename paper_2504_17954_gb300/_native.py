@@ -58,7 +58,7 @@ class ivrgs_projected(C.Structure):
 
 class ivrgs_bins(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("n_tiles", C.c_int64), ("capacity", C.c_int64),
-                ("keys", C.c_void_p), ("values", C.c_void_p), ("ranges", C.c_void_p), ("d_n_pairs", C.c_void_p),
+                ("tiles", C.c_void_p), ("values", C.c_void_p), ("ranges", C.c_void_p), ("d_n_pairs", C.c_void_p),
                 ("n_pairs", C.c_int64)]
 
 

@@ -111,10 +111,10 @@ static ivrgs_status check_bins(const ivrgs_bins* b, const CamBatch& cb) {
         return invalid("bins: n_tiles = " + std::to_string(b->n_tiles) + " but the cameras have " +
                        std::to_string(cb.n_tiles) + " tiles");
     if (b->capacity < 0 || b->capacity >= IVRGS_MAX_PAIRS) return invalid("bins: capacity must be in [0, 2^30)");
-    if (!b->ranges || !b->d_n_pairs || (b->capacity > 0 && (!b->keys || !b->values)))
+    if (!b->ranges || !b->d_n_pairs || (b->capacity > 0 && (!b->tiles || !b->values)))
         return invalid("bins: NULL array");
-    if (!aligned(b->keys, 8) || !aligned(b->ranges, 8) || !aligned(b->d_n_pairs, 8))
-        return invalid("bins: keys, ranges and d_n_pairs must be 8-byte aligned");
+    if (!aligned(b->tiles, 4) || !aligned(b->values, 4) || !aligned(b->ranges, 8) || !aligned(b->d_n_pairs, 8))
+        return invalid("bins: misaligned array (tiles/values 4, ranges/d_n_pairs 8 bytes)");
     return IVRGS_OK;
 }
 

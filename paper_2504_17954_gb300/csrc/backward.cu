@@ -70,10 +70,17 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(
         const int e = b_end - 1 - (int)threadIdx.x;
         __syncthreads();
         if (e >= b_start) {
-            const long long gi = vbase + values[rg.x + e];
+            const unsigned g = values[rg.x + e];
+            long long gi = vbase + g;
             float4 sa, sb;
-            const float4 cd = rgbd[gi];
-            stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
+            float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < (unsigned long long)n) {
+                cd = rgbd[gi];
+                stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
+            } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
+                gi = vbase;
+                stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), cd, sa, sb);
+            }
             s_a[threadIdx.x] = sa;
             s_b[threadIdx.x] = sb;
             s_blue[threadIdx.x] = cd.z;

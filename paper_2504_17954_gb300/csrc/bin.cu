@@ -1,22 +1,31 @@
-// Tile binning and the (tile, depth) key sort (rows a3, a4 of the path).
+// Tile binning and ordering (rows a3, a4 of the path).
 //
-//   count:  per (view, Gaussian) record the number of covered tiles of its float32 rectangle,
-//           summed per block of 2048 records;
-//   scan:   exclusive scan of the block sums (one CTA) and the total pair count;
-//   emit:   block-level scan of the record counts in record order, one (key, value) pair per
-//           covered tile, and the 8-bit digit histograms of all sort passes;
-//   sort:   stable LSD radix sort, one onesweep kernel per 8-bit digit: each CTA ranks a tile
-//           of 3072 keys with warp match/popc, publishes its per-digit counts and resolves its
-//           per-digit offsets by decoupled look-back over its predecessors (bounded spin),
-//           then scatters through shared memory;
-//   ranges: [start, end) of each tile's run in the sorted keys.
+// The result is the stable sort of all (tile, Gaussian) pairs by (global tile, float depth
+// bits), ties in record order (view, Gaussian index). It is produced in two sorts instead of
+// one sort of 64-bit keys over all pairs:
+//
+//   count:    per (view, Gaussian) record the number of covered tiles of its float32
+//             rectangle; per block of 2048 records the number of covered records and pairs;
+//   compact:  the covered records, in record order, as (depth bits, record index);
+//   sort 1:   stable LSD radix sort of the covered records by depth bits (4 onesweep passes);
+//   count 2:  pair counts of the depth-ordered records, block sums, scan;
+//   emit:     warp-cooperative emission of one (tile id, Gaussian) pair per covered tile, in
+//             depth order, with the digit histograms of the tile ids;
+//   sort 2:   stable LSD radix sort of the pairs by tile id (one pass per 8 tile bits);
+//   ranges:   [start, end) of every tile's run.
+//
+// Because sort 2 is stable and its input is in (depth, view, Gaussian) order, the output
+// is ordered by (tile, depth, Gaussian) -- the same order as one stable sort by
+// (tile << 32 | depth bits). Each onesweep pass ranks a tile of 4096 keys per CTA with warp
+// ballots, publishes per-digit counts and resolves its offsets by decoupled look-back over
+// its predecessors (a bounded spin), then scatters through shared memory.
 #include "common.cuh"
 
 namespace ivrgs {
 
 constexpr int kScanThreads = 256, kScanItems = 8, kScanBlock = kScanThreads * kScanItems;
-constexpr int kSortThreads = 256, kSortItems = 12, kSortTile = kSortThreads * kSortItems;
-constexpr int kMaxPasses = 8;
+constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxTilePasses = 4, kRecPasses = 4;
 constexpr unsigned kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr long long kMaxSpin = 1ll << 22;
 
@@ -32,6 +41,7 @@ __device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
 __device__ __forceinline__ unsigned record_count(const float2* __restrict__ xy, const int* __restrict__ radius,
                                                  long long i, const CamDev& c, int& x0, int& x1, int& y0, int& y1) {
     const int r = radius[i];
+    x0 = x1 = y0 = y1 = 0;
     if (r <= 0) return 0u;
     const float2 p = xy[i];
     tile_rect(p.x, p.y, r, c.gx, c.gy, x0, x1, y0, y1);
@@ -67,41 +77,74 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned& excl, 
     return total;
 }
 
+__device__ __forceinline__ unsigned warp_incl_scan(unsigned x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ long long clamp_count(const unsigned long long* d_n, long long cap) {
+    const unsigned long long nn = *d_n;
+    return (long long)nn < cap ? (long long)nn : cap;
+}
+
 // ------------------------------------------------------------------------- count
+// block sums: [0, nb) covered records, [nb, 2 nb) pairs
 __global__ void __launch_bounds__(kScanThreads) k_count(const float2* __restrict__ xy, const int* __restrict__ radius,
                                                         long long n, const __grid_constant__ CamBatch cb,
-                                                        unsigned long long* __restrict__ block_sums) {
-    __shared__ unsigned s_red[kScanThreads / 32];
+                                                        unsigned long long* __restrict__ sums, long long nb) {
+    __shared__ unsigned s_red[2][kScanThreads / 32];
     const long long total = n * cb.n;
     const long long base = (long long)blockIdx.x * kScanBlock;
-    unsigned long long sum = 0;
+    unsigned vis = 0, pairs = 0;
     int x0, x1, y0, y1;
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long i = base + (long long)j * kScanThreads + threadIdx.x;
-        if (i < total) sum += record_count(xy, radius, i, cb.c[i / n], x0, x1, y0, y1);
+        if (i < total) {
+            const unsigned c = record_count(xy, radius, i, cb.c[i / n], x0, x1, y0, y1);
+            vis += c ? 1u : 0u;
+            pairs += c;
+        }
     }
-    unsigned s = (unsigned)sum;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+        vis += __shfl_xor_sync(0xffffffffu, vis, o);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_red[0][threadIdx.x >> 5] = vis;
+        s_red[1][threadIdx.x >> 5] = pairs;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long b = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) b += s_red[w];
-        block_sums[blockIdx.x] = b;
+        unsigned long long a = 0, b = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) {
+            a += s_red[0][w];
+            b += s_red[1][w];
+        }
+        sums[blockIdx.x] = a;
+        sums[nb + blockIdx.x] = b;
     }
 }
 
 // ------------------------------------------------------------------------- scan of block sums
+// exclusive scan of consecutive arrays of nb u64 (one CTA per array); array k's total goes to
+// d_total0 (k = 0) or d_total1 (k = 1)
 __global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* __restrict__ sums, long long nb,
-                                                    unsigned long long* __restrict__ d_total) {
+                                                    unsigned long long* __restrict__ d_total0,
+                                                    unsigned long long* __restrict__ d_total1) {
     __shared__ unsigned long long s_w[33];
+    unsigned long long* a = sums + (long long)blockIdx.x * nb;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long carry = 0;
     for (long long b0 = 0; b0 < nb; b0 += 1024) {
         const long long i = b0 + threadIdx.x;
-        const unsigned long long x = i < nb ? sums[i] : 0ull;
+        const unsigned long long x = i < nb ? a[i] : 0ull;
         unsigned long long inc = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -121,56 +164,150 @@ __global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* __restri
             if (lane == 31) s_w[32] = wi;
         }
         __syncthreads();
-        if (i < nb) sums[i] = carry + s_w[warp] + inc - x;
+        if (i < nb) a[i] = carry + s_w[warp] + inc - x;
         carry += s_w[32];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *d_total = carry;
+    if (threadIdx.x == 0) *(blockIdx.x == 0 ? d_total0 : d_total1) = carry;
 }
 
-// ------------------------------------------------------------------------- emit + histograms
-__global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict__ xy, const int* __restrict__ radius,
-                                                       const float4* __restrict__ rgbd, long long n,
-                                                       const __grid_constant__ CamBatch cb,
-                                                       const unsigned long long* __restrict__ block_off,
-                                                       unsigned long long* __restrict__ keys,
-                                                       unsigned* __restrict__ vals, long long cap, int n_passes,
-                                                       unsigned* __restrict__ hist) {
-    __shared__ unsigned s_hist[kMaxPasses * 256];
+// ------------------------------------------------------------------------- compact
+__global__ void __launch_bounds__(kScanThreads) k_compact(const float2* __restrict__ xy, const int* __restrict__ radius,
+                                                          const float4* __restrict__ rgbd, long long n,
+                                                          const __grid_constant__ CamBatch cb,
+                                                          const unsigned long long* __restrict__ vis_off,
+                                                          unsigned* __restrict__ rkey, unsigned* __restrict__ rval,
+                                                          unsigned* __restrict__ hist) {
+    __shared__ unsigned s_hist[kRecPasses * 256];
     __shared__ unsigned s_warp[kScanThreads / 32 + 1];
-    for (int k = threadIdx.x; k < n_passes * 256; k += kScanThreads) s_hist[k] = 0u;
+    for (int k = threadIdx.x; k < kRecPasses * 256; k += kScanThreads) s_hist[k] = 0u;
     __syncthreads();
     const long long total = n * cb.n;
     const long long base = (long long)blockIdx.x * kScanBlock;
-    unsigned long long off = block_off[blockIdx.x];
+    unsigned long long off = vis_off[blockIdx.x];
+    int x0, x1, y0, y1;
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long i = base + (long long)j * kScanThreads + threadIdx.x;
-        int x0 = 0, x1 = 0, y0 = 0, y1 = 0, v = 0;
-        unsigned c = 0;
-        if (i < total) {
-            v = (int)(i / n);
-            c = record_count(xy, radius, i, cb.c[v], x0, x1, y0, y1);
+        unsigned f = 0;
+        if (i < total) f = record_count(xy, radius, i, cb.c[i / n], x0, x1, y0, y1) ? 1u : 0u;
+        unsigned excl;
+        const unsigned tot = block_excl_scan(f, excl, s_warp);
+        if (f) {
+            const unsigned key = __float_as_uint(rgbd[i].w);
+            rkey[off + excl] = key;
+            rval[off + excl] = (unsigned)i;
+#pragma unroll
+            for (int p = 0; p < kRecPasses; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
+        }
+        off += tot;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kRecPasses * 256; k += kScanThreads)
+        if (s_hist[k]) atomicAdd(&hist[k], s_hist[k]);
+}
+
+// ------------------------------------------------------------------------- count of sorted records
+__global__ void __launch_bounds__(kScanThreads) k_count_sorted(const float2* __restrict__ xy,
+                                                               const int* __restrict__ radius, long long n,
+                                                               const __grid_constant__ CamBatch cb,
+                                                               const unsigned* __restrict__ rval,
+                                                               const unsigned long long* __restrict__ d_m,
+                                                               unsigned long long* __restrict__ sums) {
+    __shared__ unsigned s_red[kScanThreads / 32];
+    const long long m = (long long)*d_m;
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    unsigned pairs = 0;
+    int x0, x1, y0, y1;
+#pragma unroll 1
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long k = base + (long long)j * kScanThreads + threadIdx.x;
+        if (k < m) {
+            const long long i = rval[k];
+            if (i < n * cb.n) pairs += record_count(xy, radius, i, cb.c[i / n], x0, x1, y0, y1);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = pairs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) b += s_red[w];
+        sums[blockIdx.x] = b;
+    }
+}
+
+// ------------------------------------------------------------------------- emission
+// Each warp emits the pairs of its 32 records with its lanes striding over the warp's pairs, so
+// consecutive lanes write consecutive slots.
+__global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict__ xy, const int* __restrict__ radius,
+                                                       long long n, const __grid_constant__ CamBatch cb,
+                                                       const unsigned* __restrict__ rval,
+                                                       const unsigned long long* __restrict__ d_m,
+                                                       const unsigned long long* __restrict__ pair_off,
+                                                       unsigned* __restrict__ tiles, unsigned* __restrict__ vals,
+                                                       long long cap, int n_passes, unsigned* __restrict__ hist) {
+    __shared__ unsigned s_hist[kMaxTilePasses * 256];
+    __shared__ unsigned s_warp[kScanThreads / 32 + 1];
+    __shared__ unsigned s_start[kScanThreads / 32][33];
+    __shared__ int s_x0[kScanThreads], s_w[kScanThreads], s_y0[kScanThreads];
+    __shared__ unsigned s_g[kScanThreads], s_t0[kScanThreads], s_gx[kScanThreads];
+    for (int k = threadIdx.x; k < n_passes * 256; k += kScanThreads) s_hist[k] = 0u;
+    __syncthreads();
+    const long long m = (long long)*d_m;
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long off = pair_off[blockIdx.x];
+#pragma unroll 1
+    for (int j = 0; j < kScanItems; ++j) {
+        const long long k = base + (long long)j * kScanThreads + threadIdx.x;
+        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+        unsigned c = 0, g = 0;
+        int v = 0;
+        if (k < m) {
+            const long long i = rval[k];
+            if (i < n * cb.n) {  // always true unless a timed-out sort left a slot unwritten
+                v = (int)(i / n);
+                c = record_count(xy, radius, i, cb.c[v], x0, x1, y0, y1);
+                g = (unsigned)(i - (long long)v * n);
+            }
         }
         unsigned excl;
         const unsigned tot = block_excl_scan(c, excl, s_warp);
-        if (c) {
-            const CamDev& cam = cb.c[v];
-            const unsigned dbits = __float_as_uint(rgbd[i].w);
-            const unsigned g = (unsigned)(i - (long long)v * n);
-            unsigned long long o = off + excl;
-            for (int ty = y0; ty < y1; ++ty)
-                for (int tx = x0; tx < x1; ++tx, ++o) {
-                    const unsigned long long tile = (unsigned long long)(cam.tile0 + (long long)ty * cam.gx + tx);
-                    const unsigned long long key = (tile << 32) | dbits;
-                    if ((long long)o < cap) {
-                        keys[o] = key;
-                        vals[o] = g;
-                        for (int p = 0; p < n_passes; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255)], 1u);
-                    }
-                }
+        const unsigned winc = warp_incl_scan(c);
+        s_start[warp][lane + 1] = winc;
+        if (lane == 0) s_start[warp][0] = 0;
+        s_x0[threadIdx.x] = x0;
+        s_w[threadIdx.x] = x1 - x0;
+        s_y0[threadIdx.x] = y0;
+        s_g[threadIdx.x] = g;
+        s_t0[threadIdx.x] = (unsigned)cb.c[v].tile0;
+        s_gx[threadIdx.x] = (unsigned)cb.c[v].gx;
+        __syncwarp();
+        const unsigned wtot = __shfl_sync(0xffffffffu, winc, 31);
+        // absolute offset of this warp's first pair = block offset + exclusive offset of lane 0
+        const unsigned long long wbase = off + __shfl_sync(0xffffffffu, excl, 0);
+        for (unsigned s = lane; s < wtot; s += 32) {
+            // record r of the warp holding slot s: the largest r with start[r] <= s
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (s_start[warp][r + step] <= s) r += step;
+            const int ti = warp * 32 + r;
+            const unsigned q = s - s_start[warp][r];
+            const unsigned w = (unsigned)s_w[ti];
+            const unsigned ty = q / w, tx = q - ty * w;
+            const unsigned tile = s_t0[ti] + ((unsigned)s_y0[ti] + ty) * s_gx[ti] + (unsigned)s_x0[ti] + tx;
+            const unsigned long long o = wbase + s;
+            if ((long long)o < cap) {
+                tiles[o] = tile;
+                vals[o] = s_g[ti];
+                for (int p = 0; p < n_passes; ++p) atomicAdd(&s_hist[p * 256 + ((tile >> (8 * p)) & 255u)], 1u);
+            }
         }
         off += tot;
+        __syncwarp();
     }
     __syncthreads();
     for (int k = threadIdx.x; k < n_passes * 256; k += kScanThreads)
@@ -185,11 +322,10 @@ __global__ void k_hist_scan(const unsigned* __restrict__ hist, unsigned* __restr
     base[blockIdx.x * 256 + threadIdx.x] = excl;
 }
 
-// ------------------------------------------------------------------------- onesweep pass
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(const unsigned long long* __restrict__ kin,
+// ------------------------------------------------------------------------- onesweep pass (u32 keys)
+__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __restrict__ kin,
                                                            const unsigned* __restrict__ vin,
-                                                           unsigned long long* __restrict__ kout,
-                                                           unsigned* __restrict__ vout,
+                                                           unsigned* __restrict__ kout, unsigned* __restrict__ vout,
                                                            const unsigned long long* __restrict__ d_n, long long cap,
                                                            int shift, const unsigned* __restrict__ base,
                                                            unsigned* __restrict__ lookback,
@@ -200,41 +336,45 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const unsigned long l
     __shared__ unsigned s_local[256];
     __shared__ unsigned s_global[256];
     __shared__ unsigned s_warp[kSortThreads / 32 + 1];
-    __shared__ unsigned long long s_keys[kSortTile];
+    __shared__ unsigned s_keys[kSortTile];
     __shared__ unsigned s_vals[kSortTile];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     for (int k = tid; k < (kSortThreads / 32) * 256; k += kSortThreads) (&s_whist[0][0])[k] = 0u;
     __syncthreads();
     const long long tile = s_tile;
-    const unsigned long long nn = *d_n;
-    const long long n = (long long)nn < cap ? (long long)nn : cap;
+    const long long n = clamp_count(d_n, cap);
     const long long start = tile * kSortTile;
     if (start >= n) return;
 
-    unsigned long long k[kSortItems];
-    unsigned d[kSortItems], pos[kSortItems];
+    unsigned key[kSortItems], pos[kSortItems];
     const unsigned lt = (1u << lane) - 1u;
     const long long wbase = start + (long long)warp * 32 * kSortItems;
+    // digit of item j, 256 for the slots past the end
+#define IVRGS_DIGIT(j) ((wbase + (j) * 32 + lane) < n ? ((key[j] >> shift) & 255u) : 256u)
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const long long idx = wbase + j * 32 + lane;
-        const bool valid = idx < n;
-        k[j] = valid ? kin[idx] : 0ull;
-        d[j] = valid ? (unsigned)((k[j] >> shift) & 255u) : 256u;
+        key[j] = idx < n ? kin[idx] : 0u;
     }
-    // rank inside the warp, in (item, lane) order == index order
+    // stable rank inside the warp, in (item, lane) order == index order: peers by 9 ballots
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const unsigned peers = __match_any_sync(0xffffffffu, d[j]);
-        const unsigned before = d[j] < 256u ? s_whist[warp][d[j]] : 0u;
+        const unsigned dj = IVRGS_DIGIT(j);
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const bool bit = (dj >> b) & 1u;
+            const unsigned v = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? v : ~v;
+        }
+        const unsigned before = dj < 256u ? s_whist[warp][dj] : 0u;
         pos[j] = before + __popc(peers & lt);
         __syncwarp();
-        if (d[j] < 256u && lane == __ffs(peers) - 1) s_whist[warp][d[j]] = before + __popc(peers);
+        if (dj < 256u && lane == __ffs(peers) - 1) s_whist[warp][dj] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // per digit (thread = digit): prefix over warps and the tile's count
     const unsigned dg = (unsigned)tid;
     unsigned cnt = 0;
 #pragma unroll
@@ -249,7 +389,6 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const unsigned long l
     unsigned lexcl;
     block_excl_scan(cnt, lexcl, s_warp);
     s_local[dg] = lexcl;
-    // decoupled look-back
     unsigned prefix = 0;
     if (tile > 0) {
         long long t = tile - 1;
@@ -274,37 +413,40 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(const unsigned long l
     s_global[dg] = base[dg] + prefix;
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j)
-        if (d[j] < 256u) {
-            pos[j] += s_local[d[j]] + s_whist[warp][d[j]];
-            s_keys[pos[j]] = k[j];
+    for (int j = 0; j < kSortItems; ++j) {
+        const unsigned dj = IVRGS_DIGIT(j);
+        if (dj < 256u) {
+            pos[j] += s_local[dj] + s_whist[warp][dj];
+            s_keys[pos[j]] = key[j];
         }
+    }
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const long long idx = wbase + j * 32 + lane;
-        if (d[j] < 256u) s_vals[pos[j]] = vin[idx];
+        if (idx < n) s_vals[pos[j]] = vin[idx];
     }
+#undef IVRGS_DIGIT
     __syncthreads();
     const int nvalid = (int)((n - start) < kSortTile ? (n - start) : kSortTile);
     for (int i = tid; i < nvalid; i += kSortThreads) {
-        const unsigned long long key = s_keys[i];
-        const unsigned dd = (unsigned)((key >> shift) & 255u);
+        const unsigned k = s_keys[i];
+        const unsigned dd = (k >> shift) & 255u;
         const unsigned o = s_global[dd] + ((unsigned)i - s_local[dd]);
-        kout[o] = key;
+        kout[o] = k;
         vout[o] = s_vals[i];
     }
 }
 
 // ------------------------------------------------------------------------- ranges
-__global__ void k_ranges(const unsigned long long* __restrict__ keys, const unsigned long long* __restrict__ d_n,
-                         long long cap, unsigned* __restrict__ ranges) {
+__global__ void k_ranges(const unsigned* __restrict__ tiles, const unsigned long long* __restrict__ d_n, long long cap,
+                         long long n_tiles, unsigned* __restrict__ ranges) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned long long nn = *d_n;
-    const long long n = (long long)nn < cap ? (long long)nn : cap;
+    const long long n = clamp_count(d_n, cap);
     if (i >= n) return;
-    const unsigned long long t = keys[i] >> 32;
-    if (i == 0 || (keys[i - 1] >> 32) != t) ranges[2 * t] = (unsigned)i;
-    if (i == n - 1 || (keys[i + 1] >> 32) != t) ranges[2 * t + 1] = (unsigned)(i + 1);
+    const unsigned t = tiles[i];
+    if ((long long)t >= n_tiles) return;  // only after a timed-out sort
+    if (i == 0 || tiles[i - 1] != t) ranges[2ll * t] = (unsigned)i;
+    if (i == n - 1 || tiles[i + 1] != t) ranges[2ll * t + 1] = (unsigned)(i + 1);
 }
 
 // ------------------------------------------------------------------------- host side
@@ -314,44 +456,99 @@ BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity) {
     BinPlan p{};
     int tile_bits = 0;
     while (tile_bits < 32 && (1ll << tile_bits) < n_tiles) ++tile_bits;
-    p.key_bits = 32 + tile_bits;
-    p.n_passes = (p.key_bits + 7) / 8;
+    p.key_bits = tile_bits;
+    p.n_passes = (tile_bits + 7) / 8;
     p.n_records = n_records;
     p.n_scan_blocks = (n_records + kScanBlock - 1) / kScanBlock;
     p.capacity = capacity;
+    p.rec_tiles = (n_records + kSortTile - 1) / kSortTile;
     p.sort_tiles = (capacity + kSortTile - 1) / kSortTile;
-    // [flag | histograms | digit bases | pass counters | total] are cleared by every sort;
+    const size_t nb = (size_t)(p.n_scan_blocks > 0 ? p.n_scan_blocks : 1);
+    const size_t nr = (size_t)(n_records > 0 ? n_records : 1);
+    const size_t cp = (size_t)(capacity > 0 ? capacity : 1);
+    // [flag | histograms | digit bases | pass counters | totals] are cleared by every call;
     // the error flag stays at offset 0 so that ivrgs_bin_check can find it without the plan
     size_t o = 0;
-    p.off_flag = o;       o = align_up(o + 4);
-    p.off_hist = o;       o = align_up(o + 4 * kMaxPasses * 256);
-    p.off_base = o;       o = align_up(o + 4 * kMaxPasses * 256);
-    p.off_counter = o;    o = align_up(o + 4 * kMaxPasses);
-    p.off_total = o;      o = align_up(o + 8);
-    p.off_block_sums = o; o = align_up(o + 8 * (size_t)(p.n_scan_blocks > 0 ? p.n_scan_blocks : 1));
-    p.off_lookback = o;   o = align_up(o + 4 * 256 * (size_t)p.n_passes * (size_t)(p.sort_tiles > 0 ? p.sort_tiles : 1));
-    p.off_keys_alt = o;   o = align_up(o + 8 * (size_t)(capacity > 0 ? capacity : 1));
-    p.off_vals_alt = o;   o = align_up(o + 4 * (size_t)(capacity > 0 ? capacity : 1));
+    p.off_flag = o;         o = align_up(o + 4);
+    p.off_hist = o;         o = align_up(o + 4 * 256 * (kRecPasses + kMaxTilePasses));
+    p.off_base = o;         o = align_up(o + 4 * 256 * (kRecPasses + kMaxTilePasses));
+    p.off_counter = o;      o = align_up(o + 4 * (kRecPasses + kMaxTilePasses));
+    p.off_total = o;        o = align_up(o + 8 * 2);
+    p.clear_bytes = o;
+    p.off_block_sums = o;   o = align_up(o + 8 * 3 * nb);
+    p.off_rec = o;          o = align_up(o + 4 * 4 * nr);
+    p.off_lookback_rec = o; o = align_up(o + 4 * 256 * (size_t)kRecPasses * (size_t)(p.rec_tiles > 0 ? p.rec_tiles : 1));
+    p.off_lookback = o;     o = align_up(o + 4 * 256 * (size_t)(p.n_passes > 0 ? p.n_passes : 1) *
+                                         (size_t)(p.sort_tiles > 0 ? p.sort_tiles : 1));
+    p.off_keys_alt = o;     o = align_up(o + 4 * cp);
+    p.off_vals_alt = o;     o = align_up(o + 4 * cp);
     p.total_bytes = o;
     return p;
 }
 
-// the debug hook used by the failure-detection test: a look-back bound and a tile that skips
-// publishing (host-side injection; every wait stays bounded)
+// the debug hook used by the failure-detection test: a look-back bound and a radix tile that
+// skips publishing (host-side injection; every wait stays bounded)
 static long long g_max_spin = kMaxSpin;
 static long long g_skip_publish_tile = -1;
 
+struct BinBufs {
+    unsigned long long *sums, *d_m, *d_n;
+    unsigned *hist_rec, *hist_tile, *base_rec, *base_tile, *counter, *flag, *lb_rec, *lb_tile;
+    unsigned *rkey[2], *rval[2], *talt, *valt;
+};
+
+static BinBufs bufs(const BinPlan& plan, char* ws, ivrgs_bins* out) {
+    BinBufs b;
+    const size_t nr = (size_t)(plan.n_records > 0 ? plan.n_records : 1);
+    b.sums = reinterpret_cast<unsigned long long*>(ws + plan.off_block_sums);
+    b.hist_rec = reinterpret_cast<unsigned*>(ws + plan.off_hist);
+    b.hist_tile = b.hist_rec + 256 * kRecPasses;
+    b.base_rec = reinterpret_cast<unsigned*>(ws + plan.off_base);
+    b.base_tile = b.base_rec + 256 * kRecPasses;
+    b.counter = reinterpret_cast<unsigned*>(ws + plan.off_counter);
+    b.flag = reinterpret_cast<unsigned*>(ws + plan.off_flag);
+    b.d_m = reinterpret_cast<unsigned long long*>(ws + plan.off_total);
+    b.d_n = reinterpret_cast<unsigned long long*>(out->d_n_pairs);
+    unsigned* r = reinterpret_cast<unsigned*>(ws + plan.off_rec);
+    b.rkey[0] = r; b.rval[0] = r + nr; b.rkey[1] = r + 2 * nr; b.rval[1] = r + 3 * nr;
+    b.lb_rec = reinterpret_cast<unsigned*>(ws + plan.off_lookback_rec);
+    b.lb_tile = reinterpret_cast<unsigned*>(ws + plan.off_lookback);
+    b.talt = reinterpret_cast<unsigned*>(ws + plan.off_keys_alt);
+    b.valt = reinterpret_cast<unsigned*>(ws + plan.off_vals_alt);
+    return b;
+}
+
 cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
                              uint64_t* d_n_pairs, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ws, 0, plan.clear_bytes, s)) != cudaSuccess) return e;
     unsigned long long* sums = reinterpret_cast<unsigned long long*>(ws + plan.off_block_sums);
-    if (plan.n_scan_blocks > 0) {
+    unsigned long long* d_m = reinterpret_cast<unsigned long long*>(ws + plan.off_total);
+    const long long nb = plan.n_scan_blocks;
+    if (nb > 0) {
         IVRGS_PROF("k_count", s);
-        k_count<<<(unsigned)plan.n_scan_blocks, kScanThreads, 0, s>>>(
-            reinterpret_cast<const float2*>(p->xy), p->radius, p->n, cb, sums);
+        k_count<<<(unsigned)nb, kScanThreads, 0, s>>>(reinterpret_cast<const float2*>(p->xy), p->radius, p->n, cb,
+                                                      sums, nb);
     }
     {
         IVRGS_PROF("k_scan_sums", s);
-        k_scan_sums<<<1, 1024, 0, s>>>(sums, plan.n_scan_blocks, reinterpret_cast<unsigned long long*>(d_n_pairs));
+        k_scan_sums<<<2, 1024, 0, s>>>(sums, nb, d_m, reinterpret_cast<unsigned long long*>(d_n_pairs));
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1,
+                                   const unsigned long long* d_n, long long cap, const unsigned* base,
+                                   unsigned* lookback, long long tiles, unsigned* counter, unsigned* flag,
+                                   const char* name, cudaStream_t s) {
+    unsigned* kb[2] = {k0, k1};
+    unsigned* vb[2] = {v0, v1};
+    for (int ps = 0; ps < n_passes && tiles > 0; ++ps) {
+        const int src = ps & 1, dst = src ^ 1;
+        IVRGS_PROF(name, s);
+        k_onesweep<<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps,
+                                                            base + 256 * ps, lookback + (size_t)256 * ps * tiles,
+                                                            counter + ps, flag, g_max_spin, g_skip_publish_tile);
     }
     return cudaGetLastError();
 }
@@ -359,56 +556,66 @@ cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const
 cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
                             ivrgs_bins* out, long long exact_pairs, cudaStream_t s) {
     cudaError_t e;
-    unsigned long long* sums = reinterpret_cast<unsigned long long*>(ws + plan.off_block_sums);
-    unsigned* hist = reinterpret_cast<unsigned*>(ws + plan.off_hist);
-    unsigned* base = reinterpret_cast<unsigned*>(ws + plan.off_base);
-    unsigned* counter = reinterpret_cast<unsigned*>(ws + plan.off_counter);
-    unsigned* flag = reinterpret_cast<unsigned*>(ws + plan.off_flag);
-    unsigned* lookback = reinterpret_cast<unsigned*>(ws + plan.off_lookback);
-    unsigned long long* kalt = reinterpret_cast<unsigned long long*>(ws + plan.off_keys_alt);
-    unsigned* valt = reinterpret_cast<unsigned*>(ws + plan.off_vals_alt);
-    const unsigned long long* d_n = reinterpret_cast<const unsigned long long*>(out->d_n_pairs);
+    BinBufs b = bufs(plan, ws, out);
     const long long cap = out->capacity;
-    unsigned long long* out_keys = reinterpret_cast<unsigned long long*>(out->keys);
-    // tiles actually launched per pass: exact count when known, else the capacity bound
+    const long long nb = plan.n_scan_blocks;
+    const long long rec_tiles = plan.rec_tiles;
     const long long n_work = exact_pairs >= 0 ? (exact_pairs < cap ? exact_pairs : cap) : cap;
-    const long long sort_tiles = (n_work + kSortTile - 1) / kSortTile;
-    // clear histograms, counters, flag (contiguous) and the look-back words of the launched tiles
-    if ((e = cudaMemsetAsync(ws, 0, plan.off_block_sums, s)) != cudaSuccess) return e;
-    if (sort_tiles > 0 &&
-        (e = cudaMemsetAsync(lookback, 0, 4 * 256 * (size_t)plan.n_passes * (size_t)sort_tiles, s)) != cudaSuccess)
+    const long long pair_tiles = (n_work + kSortTile - 1) / kSortTile;
+    if (rec_tiles > 0 &&
+        (e = cudaMemsetAsync(b.lb_rec, 0, 4 * 256 * (size_t)kRecPasses * (size_t)rec_tiles, s)) != cudaSuccess)
+        return e;
+    if (pair_tiles > 0 && plan.n_passes > 0 &&
+        (e = cudaMemsetAsync(b.lb_tile, 0, 4 * 256 * (size_t)plan.n_passes * (size_t)pair_tiles, s)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(out->ranges, 0, 8 * (size_t)out->n_tiles, s)) != cudaSuccess) return e;
-    // ping-pong so that the last pass lands in the caller's arrays
-    unsigned long long* kb[2];
-    unsigned* vb[2];
-    if (plan.n_passes % 2 == 0) {
-        kb[0] = out_keys; vb[0] = out->values; kb[1] = kalt; vb[1] = valt;
-    } else {
-        kb[0] = kalt; vb[0] = valt; kb[1] = out_keys; vb[1] = out->values;
-    }
-    if (plan.n_scan_blocks > 0) {
-        IVRGS_PROF("k_emit", s);
-        k_emit<<<(unsigned)plan.n_scan_blocks, kScanThreads, 0, s>>>(
-            reinterpret_cast<const float2*>(p->xy), p->radius, reinterpret_cast<const float4*>(p->rgbd), p->n, cb,
-            sums, kb[0], vb[0], cap, plan.n_passes, hist);
+    const float2* xy = reinterpret_cast<const float2*>(p->xy);
+    // covered records in record order, then by depth
+    if (nb > 0) {
+        IVRGS_PROF("k_compact", s);
+        k_compact<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, p->radius, reinterpret_cast<const float4*>(p->rgbd), p->n,
+                                                        cb, b.sums, b.rkey[0], b.rval[0], b.hist_rec);
     }
     {
         IVRGS_PROF("k_hist_scan", s);
-        k_hist_scan<<<plan.n_passes, 256, 0, s>>>(hist, base);
+        k_hist_scan<<<kRecPasses, 256, 0, s>>>(b.hist_rec, b.base_rec);
     }
-    for (int ps = 0; ps < plan.n_passes && sort_tiles > 0; ++ps) {
-        const int src = ps & 1, dst = src ^ 1;
-        {
-            IVRGS_PROF("k_onesweep", s);
-            k_onesweep<<<(unsigned)sort_tiles, kSortThreads, 0, s>>>(
-                kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps,
-                lookback + (size_t)256 * ps * sort_tiles, counter + ps, flag, g_max_spin, g_skip_publish_tile);
-        }
+    if ((e = onesweep_passes(kRecPasses, b.rkey[0], b.rval[0], b.rkey[1], b.rval[1], b.d_m, plan.n_records,
+                             b.base_rec, b.lb_rec, rec_tiles, b.counter, b.flag, "k_onesweep_rec", s)) != cudaSuccess)
+        return e;
+    // pair offsets of the depth-ordered records
+    unsigned long long* sums2 = b.sums + 2 * (nb > 0 ? nb : 1);
+    if (nb > 0) {
+        IVRGS_PROF("k_count_sorted", s);
+        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, p->radius, p->n, cb, b.rval[0], b.d_m, sums2);
     }
+    {
+        IVRGS_PROF("k_scan_sums", s);
+        k_scan_sums<<<1, 1024, 0, s>>>(sums2, nb, b.d_n, b.d_n);
+    }
+    // pairs in depth order, then stable by tile; the last pass lands in the caller's arrays
+    unsigned *t0, *v0, *t1, *v1;
+    if (plan.n_passes % 2 == 0) {
+        t0 = out->tiles; v0 = out->values; t1 = b.talt; v1 = b.valt;
+    } else {
+        t0 = b.talt; v0 = b.valt; t1 = out->tiles; v1 = out->values;
+    }
+    if (nb > 0) {
+        IVRGS_PROF("k_emit", s);
+        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, p->radius, p->n, cb, b.rval[0], b.d_m, sums2, t0, v0, cap,
+                                                     plan.n_passes, b.hist_tile);
+    }
+    if (plan.n_passes > 0) {
+        IVRGS_PROF("k_hist_scan", s);
+        k_hist_scan<<<plan.n_passes, 256, 0, s>>>(b.hist_tile, b.base_tile);
+    }
+    if ((e = onesweep_passes(plan.n_passes, t0, v0, t1, v1, b.d_n, cap, b.base_tile, b.lb_tile, pair_tiles,
+                             b.counter + kRecPasses, b.flag, "k_onesweep", s)) != cudaSuccess)
+        return e;
     if (n_work > 0) {
         IVRGS_PROF("k_ranges", s);
-        k_ranges<<<(unsigned)((n_work + 255) / 256), 256, 0, s>>>(out_keys, d_n, cap, out->ranges);
+        k_ranges<<<(unsigned)((n_work + 255) / 256), 256, 0, s>>>(out->tiles, b.d_n, cap, out->n_tiles,
+                                                                   out->ranges);
     }
     return cudaGetLastError();
 }

@@ -76,15 +76,16 @@ void set_error(const std::string& msg);
 ivrgs_status cuda_status(cudaError_t e, const char* what);
 
 struct BinPlan {
-    int n_passes;          // 8-bit digit passes over the key bits in use
-    int key_bits;
+    int n_passes;          // 8-bit digit passes of the tile-id sort
+    int key_bits;          // bits of the tile ids
     long long n_records;   // n * n_views
     long long n_scan_blocks;
     long long capacity;
-    long long sort_tiles;  // ceil(capacity / kSortTile)
-    // workspace layout (byte offsets)
-    size_t off_block_sums, off_hist, off_base, off_counter, off_lookback, off_keys_alt, off_vals_alt, off_flag,
-        off_total, total_bytes;
+    long long rec_tiles;   // radix tiles of the record sort
+    long long sort_tiles;  // radix tiles of the pair sort at full capacity
+    // workspace layout (byte offsets); [0, clear_bytes) is zeroed by every call
+    size_t off_flag, off_hist, off_base, off_counter, off_total, clear_bytes, off_block_sums, off_rec,
+        off_lookback_rec, off_lookback, off_keys_alt, off_vals_alt, total_bytes;
 };
 
 ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb);

@@ -39,12 +39,16 @@ __global__ void __launch_bounds__(kTilePix) k_render(const float2* __restrict__ 
         if (__syncthreads_count(done) == kTilePix) break;
         const int e = b0 + (int)threadIdx.x;
         if (e < len) {
-            const long long gi = vbase + values[rg.x + e];
-            const float2 m = xy[gi];
-            const float4 co = conic_o[gi];
-            const float4 cd = rgbd[gi];
+            const unsigned g = values[rg.x + e];
             float4 sa, sb;
-            stage_gaussian(m, co, cd, sa, sb);
+            float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < (unsigned long long)n) {
+                const long long gi = vbase + g;
+                cd = rgbd[gi];
+                stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
+            } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
+                stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), cd, sa, sb);
+            }
             s_a[threadIdx.x] = sa;
             s_b[threadIdx.x] = sb;
             s_blue[threadIdx.x] = cd.z;

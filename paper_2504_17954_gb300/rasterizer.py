@@ -166,7 +166,7 @@ class Rasterizer:
         self.ranges = torch.empty((self.n_tiles, 2), dtype=torch.int32, device=dev)
         self.d_n_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
         self.n_pairs = 0
-        self.keys = self.values = self.ws_bin = None
+        self.tiles = self.values = self.ws_bin = None
         self.capacity = 0
         self._ensure_capacity(int(capacity) if capacity else max(1024, 8 * VN))
         self.ws_bwd_bytes = N.ivrgs_render_backward_workspace(self.n, self.V)
@@ -180,7 +180,7 @@ class Rasterizer:
         if cap <= self.capacity:
             return
         self.capacity = cap
-        self.keys = torch.empty(cap, dtype=torch.int64, device=self.device)
+        self.tiles = torch.empty(cap, dtype=torch.int32, device=self.device)
         self.values = torch.empty(cap, dtype=torch.int32, device=self.device)
         self.ws_bin_bytes = N.ivrgs_bin_workspace(self.n, self.V, self.cam_arr, 16, 16, cap)
         self.ws_bin = torch.empty(self.ws_bin_bytes, dtype=torch.uint8, device=self.device)
@@ -196,7 +196,7 @@ class Rasterizer:
         b.tile_w = b.tile_h = 16
         b.n_tiles = self.n_tiles
         b.capacity = self.capacity
-        b.keys, b.values = self.keys.data_ptr(), self.values.data_ptr()
+        b.tiles, b.values = self.tiles.data_ptr(), self.values.data_ptr()
         b.ranges = self.ranges.data_ptr()
         b.d_n_pairs = self.d_n_pairs.data_ptr()
         b.n_pairs = self.n_pairs

@@ -88,10 +88,19 @@ def compare_image(gpu: np.ndarray, ref: np.ndarray, margins: np.ndarray, extra_e
 
 
 def gpu_keys(rast: Rasterizer):
+    """The GPU's sorted pairs as 64-bit keys (tile << 32 | depth bits), values and ranges.
+
+    The library returns sorted tile ids; the depth bits of each pair are read back from the
+    projected record it refers to, so the keys compare bit for bit with the oracle's."""
     n = rast.n_pairs
-    k = rast.keys[:n].cpu().numpy().view(np.uint64)
+    t = rast.tiles[:n].cpu().numpy().view(np.uint32).astype(np.uint64)
     v = rast.values[:n].cpu().numpy().view(np.uint32)
     r = rast.ranges.cpu().numpy().view(np.uint32)
+    toff = np.cumsum([0] + [((c.W + 15) // 16) * ((c.H + 15) // 16) for c in rast.cams])
+    view = np.searchsorted(toff, t.astype(np.int64), side="right") - 1
+    depth = rast.rgbd[:, 3].contiguous().cpu().numpy().view(np.uint32)
+    bits = depth[view * rast.n + v.astype(np.int64)].astype(np.uint64)
+    k = (t << np.uint64(32)) | bits
     return k, v, r
 
 
