@@ -76,8 +76,8 @@ def test_status_codes_for_bad_calls():
     # misaligned projected arrays
     b = rast.bins_struct()
     p.conic_o += 4
-    st = N.ivrgs_render(C.byref(p), C.byref(b), rast.cam_arr, rast.V, rast.bg, _vp(rast.rgba), _vp(rast.final_T),
-                        _vp(rast.last), _stream())
+    st = N.call("ivrgs_render", C.byref(p), C.byref(b), rast.cam_arr, rast.V, rast.bg, _vp(rast.rgba),
+                _vp(rast.final_T), _vp(rast.last), _stream(), allow=(N.IVRGS_ERR_INVALID_ARG,))
     assert st == N.IVRGS_ERR_INVALID_ARG and "misaligned" in N.last_error()
     # exact mode with a too-small pair buffer reports the required count
     p = rast.projected_struct()
