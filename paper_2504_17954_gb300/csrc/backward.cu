@@ -24,15 +24,48 @@ __device__ __forceinline__ float warp_sum(float x) {
     return x;
 }
 
-__global__ void __launch_bounds__(kTilePix) k_render_bwd(
+// Sum of v[0..7] over the warp in 9 shuffles (recursive halving): on return every lane holds
+// the warp total of value index (lane >> 2).
+__device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane) {
+    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+    float k1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b4 ? v[k] : v[4 + k];
+        const float r = __shfl_xor_sync(0xffffffffu, send, 16);
+        k1[k] = (b4 ? v[4 + k] : v[k]) + r;
+    }
+    float k2[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b3 ? k1[k] : k1[2 + k];
+        const float r = __shfl_xor_sync(0xffffffffu, send, 8);
+        k2[k] = (b3 ? k1[2 + k] : k1[k]) + r;
+    }
+    float x;
+    {
+        const float send = b2 ? k2[0] : k2[1];
+        const float r = __shfl_xor_sync(0xffffffffu, send, 4);
+        x = (b2 ? k2[1] : k2[0]) + r;
+    }
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    return x;
+}
+
+// Per tile, P pixels per thread (rows r and r + 16/P of one column).
+template <int P>
+__global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
     const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
     float3 bg, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
     const float4* __restrict__ dL, float4* __restrict__ g0, float4* __restrict__ g1, float* __restrict__ g2) {
-    __shared__ float4 s_a[kTilePix];
-    __shared__ float4 s_b[kTilePix];
-    __shared__ float s_blue[kTilePix];
-    __shared__ long long s_gi[kTilePix];
+    constexpr int NT = kTilePix / P;
+    constexpr int kBatch = 256;
+    __shared__ float4 s_a[kBatch];
+    __shared__ float4 s_b[kBatch];
+    __shared__ float s_blue[kBatch];
+    __shared__ long long s_gi[kBatch];
     __shared__ unsigned s_max;
     const long long tile = blockIdx.x;
     const int v = view_of_tile(cb, tile);
@@ -40,105 +73,136 @@ __global__ void __launch_bounds__(kTilePix) k_render_bwd(
     const int local = (int)(tile - cam.tile0);
     const int tx = local % cam.gx, ty = local / cam.gx;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (threadIdx.x / kTile);
-    const bool inside = px < cam.W && py < cam.H;
-    const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+    const int py0 = ty * kTile + (threadIdx.x / kTile);
+    const float fx = (float)px + 0.5f;
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
     const int lane = threadIdx.x & 31;
 
-    float Tf = 1.0f;
-    unsigned my_last = 0;
-    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (inside) {
-        const long long pix = cam.pix0 + (long long)py * cam.W + px;
-        Tf = final_T[pix];
-        my_last = last_in[pix];
-        d = dL[pix];
+    float fy[P], T[P], S0[P], S1[P], S2[P], dA_T[P];
+    float4 d[P];
+    unsigned my_last[P];
+    unsigned mx = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const int py = py0 + p * (kTile / P);
+        fy[p] = (float)py + 0.5f;
+        float Tf = 1.0f;
+        my_last[p] = 0;
+        d[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (px < cam.W && py < cam.H) {
+            const long long pix = cam.pix0 + (long long)py * cam.W + px;
+            Tf = final_T[pix];
+            my_last[p] = last_in[pix];
+            d[p] = dL[pix];
+        }
+        T[p] = Tf;
+        S0[p] = Tf * bg.x;
+        S1[p] = Tf * bg.y;
+        S2[p] = Tf * bg.z;
+        dA_T[p] = d[p].w * Tf;  // dL/dA * T_final
+        mx = max(mx, my_last[p]);
     }
     if (threadIdx.x == 0) s_max = 0u;
     __syncthreads();
-    atomicMax(&s_max, my_last);
+    atomicMax(&s_max, mx);
     __syncthreads();
     const int max_last = (int)s_max;
-    float T = Tf;
-    float S0 = Tf * bg.x, S1 = Tf * bg.y, S2 = Tf * bg.z;
-    const float dA_T = d.w * Tf;  // dL/dA * T_final
 
-    for (int b_end = max_last; b_end > 0; b_end -= kTilePix) {
-        const int b_start = max(0, b_end - kTilePix);
-        const int e = b_end - 1 - (int)threadIdx.x;
+    for (int b_end = max_last; b_end > 0; b_end -= kBatch) {
+        const int b_start = max(0, b_end - kBatch);
         __syncthreads();
-        if (e >= b_start) {
-            const unsigned g = values[rg.x + e];
-            long long gi = vbase + g;
-            float4 sa, sb;
-            float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (g < (unsigned long long)n) {
-                cd = rgbd[gi];
-                stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
-            } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
-                gi = vbase;
-                stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), cd, sa, sb);
+#pragma unroll
+        for (int q = 0; q < kBatch / NT; ++q) {
+            const int slot = threadIdx.x + q * NT;
+            const int e = b_end - 1 - slot;
+            if (e >= b_start) {
+                const unsigned g = values[rg.x + e];
+                long long gi = vbase + g;
+                float4 sa, sb;
+                float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (g < (unsigned long long)n) {
+                    cd = rgbd[gi];
+                    stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
+                } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
+                    gi = vbase;
+                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), cd, sa, sb);
+                }
+                s_a[slot] = sa;
+                s_b[slot] = sb;
+                s_blue[slot] = cd.z;
+                s_gi[slot] = gi;
             }
-            s_a[threadIdx.x] = sa;
-            s_b[threadIdx.x] = sb;
-            s_blue[threadIdx.x] = cd.z;
-            s_gi[threadIdx.x] = gi;
         }
         __syncthreads();
         const int cnt = b_end - b_start;
         for (int j = 0; j < cnt; ++j) {
             const int ee = b_end - 1 - j;
-            float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
+            const float4 a = s_a[j];
+            const float4 bb = s_b[j];
+            const float blue = s_blue[j];
+            // v[0..7] = d(u, v, a, b, c, o', r, g), vb = d(blue): summed over this thread's pixels
+            float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float vb = 0.f;
             bool contrib = false;
-            if (ee < (int)my_last) {
-                const float4 a = s_a[j];
-                const float4 bb = s_b[j];
-                float dx, dy;
-                const float p2 = blend_p2(a, bb, fx, fy, dx, dy);
-                if (p2 <= 0.0f) {
-                    const float G = fast_ex2(p2);
-                    const float raw = bb.y * G;
-                    const float alpha = fminf(kAlphaMax, raw);
-                    if (alpha >= kAlphaMin) {
-                        contrib = true;
-                        const float om = 1.0f - alpha;
-                        const float Ti = T / om;
-                        const float blue = s_blue[j];
-                        const float w = Ti * alpha;
-                        gr = w * d.x;
-                        gg = w * d.y;
-                        gbl = w * d.z;
-                        const float dalpha = (d.x * (Ti * bb.z) + d.y * (Ti * bb.w) + d.z * (Ti * blue)) -
-                                             (d.x * S0 + d.y * S1 + d.z * S2 - dA_T) / om;
-                        S0 = fmaf(w, bb.z, S0);
-                        S1 = fmaf(w, bb.w, S1);
-                        S2 = fmaf(w, blue, S2);
-                        T = Ti;
-                        if (raw < kAlphaMax) {
-                            const float dP = dalpha * raw;  // dalpha/dP = o' G
-                            go = dalpha * G;
-                            // P = p2 / log2(e): dP/du = (2A' dx + B' dy)/log2e, dP/dv = (B' dx + 2C' dy)/log2e
-                            const float il = 1.0f / kLog2e;
-                            gu = dP * (2.0f * a.z * dx + a.w * dy) * il;
-                            gv = dP * (a.w * dx + 2.0f * bb.x * dy) * il;
-                            ga = dP * (-0.5f * dx * dx);
-                            gb = dP * (-dx * dy);
-                            gc = dP * (-0.5f * dy * dy);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (ee < (int)my_last[p]) {
+                    float dx, dy;
+                    const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
+                    if (p2 <= 0.0f) {
+                        const float G = fast_ex2(p2);
+                        const float raw = bb.y * G;
+                        const float alpha = fminf(kAlphaMax, raw);
+                        if (alpha >= kAlphaMin) {
+                            contrib = true;
+                            const float om = 1.0f - alpha;
+                            const float Ti = T[p] / om;
+                            const float w = Ti * alpha;
+                            const float4 dd = d[p];
+                            vv[6] += w * dd.x;
+                            vv[7] += w * dd.y;
+                            vb += w * dd.z;
+                            const float dalpha = Ti * (dd.x * bb.z + dd.y * bb.w + dd.z * blue) -
+                                                 (dd.x * S0[p] + dd.y * S1[p] + dd.z * S2[p] - dA_T[p]) / om;
+                            S0[p] = fmaf(w, bb.z, S0[p]);
+                            S1[p] = fmaf(w, bb.w, S1[p]);
+                            S2[p] = fmaf(w, blue, S2[p]);
+                            T[p] = Ti;
+                            if (raw < kAlphaMax) {
+                                const float dP = dalpha * raw;  // dalpha/dP = o' G
+                                vv[5] += dalpha * G;
+                                // P = p2 / log2(e): dP/du = (2A' dx + B' dy)/log2e, dP/dv = (B' dx + 2C' dy)/log2e
+                                const float dPl = dP * (1.0f / kLog2e);
+                                vv[0] += dPl * (2.0f * a.z * dx + a.w * dy);
+                                vv[1] += dPl * (a.w * dx + 2.0f * bb.x * dy);
+                                vv[2] += dP * (-0.5f * dx * dx);
+                                vv[3] += dP * (-dx * dy);
+                                vv[4] += dP * (-0.5f * dy * dy);
+                            }
                         }
                     }
                 }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga); gb = warp_sum(gb); gc = warp_sum(gc);
-                go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl);
-                if (lane == 0) {
-                    const long long gi = s_gi[j];
-                    atomicAdd(&g0[gi], make_float4(gu, gv, ga, gb));
-                    atomicAdd(&g1[gi], make_float4(gc, go, gr, gg));
-                    atomicAdd(&g2[gi], gbl);
+            const unsigned m = __ballot_sync(0xffffffffu, contrib);
+            if (m == 0u) continue;
+            const long long gi = s_gi[j];
+            float* t0 = reinterpret_cast<float*>(g0 + gi);
+            float* t1 = reinterpret_cast<float*>(g1 + gi);
+            if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction
+                if (contrib) {
+                    atomicAdd(reinterpret_cast<float4*>(t0), make_float4(vv[0], vv[1], vv[2], vv[3]));
+                    atomicAdd(reinterpret_cast<float4*>(t1), make_float4(vv[4], vv[5], vv[6], vv[7]));
+                    atomicAdd(&g2[gi], vb);
                 }
+            } else {
+                const float x = warp_sum8_transposed(vv, lane);
+                vb = warp_sum(vb);
+                if ((lane & 3) == 0) {
+                    const int idx = lane >> 2;
+                    atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
+                }
+                if (lane == 0) atomicAdd(&g2[gi], vb);
             }
         }
     }
@@ -397,7 +461,7 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
     if ((e = cudaMemsetAsync(edit_grad, 0, sizeof(float) * (size_t)ne, s)) != cudaSuccess) return e;
     if (cb.n_tiles > 0) {
         IVRGS_PROF("k_render_bwd", s);
-        k_render_bwd<<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(
+        k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(
             reinterpret_cast<const float2*>(p->xy), reinterpret_cast<const float4*>(p->conic_o),
             reinterpret_cast<const float4*>(p->rgbd), p->n, b->values, reinterpret_cast<const uint2*>(b->ranges), cb,
             make_float3(bg[0], bg[1], bg[2]), final_T, last, reinterpret_cast<const float4*>(dL), g0, g1, g2);

@@ -303,7 +303,14 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict_
             if ((long long)o < cap) {
                 tiles[o] = tile;
                 vals[o] = s_g[ti];
-                for (int p = 0; p < n_passes; ++p) atomicAdd(&s_hist[p * 256 + ((tile >> (8 * p)) & 255u)], 1u);
+                atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
+            }
+            // higher bytes repeat along a warp's slots: one aggregated add per distinct digit
+            const unsigned act = __activemask();
+            for (int p = 1; p < n_passes; ++p) {
+                const unsigned dg = (long long)o < cap ? ((tile >> (8 * p)) & 255u) : 256u;
+                const unsigned peers = __match_any_sync(act, dg);
+                if (dg < 256u && lane == __ffs(peers) - 1) atomicAdd(&s_hist[p * 256 + dg], (unsigned)__popc(peers));
             }
         }
         off += tot;
@@ -438,15 +445,20 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
 }
 
 // ------------------------------------------------------------------------- ranges
-__global__ void k_ranges(const unsigned* __restrict__ tiles, const unsigned long long* __restrict__ d_n, long long cap,
-                         long long n_tiles, unsigned* __restrict__ ranges) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_ranges(const unsigned* __restrict__ tiles,
+                                                const unsigned long long* __restrict__ d_n, long long cap,
+                                                long long n_tiles, unsigned* __restrict__ ranges) {
     const long long n = clamp_count(d_n, cap);
-    if (i >= n) return;
-    const unsigned t = tiles[i];
-    if ((long long)t >= n_tiles) return;  // only after a timed-out sort
-    if (i == 0 || tiles[i - 1] != t) ranges[2ll * t] = (unsigned)i;
-    if (i == n - 1 || tiles[i + 1] != t) ranges[2ll * t + 1] = (unsigned)(i + 1);
+    const long long base = (long long)blockIdx.x * 2048;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long i = base + j * 256 + threadIdx.x;
+        if (i >= n) return;
+        const unsigned t = tiles[i];
+        if ((long long)t >= n_tiles) continue;  // only after a timed-out sort
+        if (i == 0 || tiles[i - 1] != t) ranges[2ll * t] = (unsigned)i;
+        if (i == n - 1 || tiles[i + 1] != t) ranges[2ll * t + 1] = (unsigned)(i + 1);
+    }
 }
 
 // ------------------------------------------------------------------------- host side
@@ -614,7 +626,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         return e;
     if (n_work > 0) {
         IVRGS_PROF("k_ranges", s);
-        k_ranges<<<(unsigned)((n_work + 255) / 256), 256, 0, s>>>(out->tiles, b.d_n, cap, out->n_tiles,
+        k_ranges<<<(unsigned)((n_work + 2047) / 2048), 256, 0, s>>>(out->tiles, b.d_n, cap, out->n_tiles,
                                                                    out->ranges);
     }
     return cudaGetLastError();
