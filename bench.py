@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="run warmup + 2 steps, print nothing else")
+    ap.add_argument("--opt", action="append", default=[], help="library option name=value (launch shapes)")
     return ap.parse_args()
 
 
@@ -147,6 +148,12 @@ def run_gpu(args, rank, world):
     from paper_2504_17954_gb300 import Gaussians, Rasterizer, compose_edit
 
     B.build()
+    opts = {}
+    for kv in args.opt:
+        k, v = kv.split("=")
+        N.ivrgs_set_option(k, int(v))
+    for k in ("render_pixels_per_thread", "render_bwd_pixels_per_thread"):
+        opts[k] = N.ivrgs_get_option(k)
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     w = workload(args.workload)
@@ -258,6 +265,7 @@ def run_gpu(args, rank, world):
            "dtype": "f32", "data": "synthetic (seeded volume-band Gaussians; no paper datasets)",
            "config": {"workload": w.name, "gaussians": comp.n, "models": len(w.models), "views": len(w.cameras),
                       "pixels_per_replica": rast.n_pix, "pairs": n_pairs, "l2": "flushed between timed steps",
+                      "options": opts,
                       "parallelism": f"replicas x{world}"},
            "fwd_mpix_s": fwd_value, "fwd_ms_per_step": ms_fwd_total / K,
            "roofline": roof, "kernels": kern_table, "clocks": clocks,

@@ -150,6 +150,13 @@ const char* ivrgs_last_error(void);
 /* Library version (major * 10000 + minor * 100 + patch). */
 int32_t ivrgs_version(void);
 
+/* Launch-shape options (process-wide; measurement-driven tuning, the paper has no counterpart):
+   "render_pixels_per_thread" and "render_bwd_pixels_per_thread" (1 or 2): pixels each thread
+   of the forward / backward blend owns. Results are identical for every setting.
+   Returns IVRGS_ERR_INVALID_ARG for an unknown name or value. */
+ivrgs_status ivrgs_set_option(const char* name, int64_t value);
+ivrgs_status ivrgs_get_option(const char* name, int64_t* value);
+
 /* Number of floats in an edit table for n_models models: IVRGS_EDIT_STRIDE * n_models + 8.
    Layout: per model m, [c_p(3), opacity scale, visible (0/1), 0, 0, 0]; then lambda(4), b(4).
    The edit-gradient buffer of ivrgs_render_backward has the same layout followed by

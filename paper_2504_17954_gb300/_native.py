@@ -66,6 +66,8 @@ _P = C.POINTER
 _SIGNATURES = {
     "ivrgs_last_error": (C.c_char_p, []),
     "ivrgs_version": (C.c_int32, []),
+    "ivrgs_set_option": (C.c_int32, [C.c_char_p, C.c_int64]),
+    "ivrgs_get_option": (C.c_int32, [C.c_char_p, _P(C.c_int64)]),
     "ivrgs_edit_table_floats": (C.c_int64, [C.c_int32]),
     "ivrgs_compose_edit": (C.c_int32, [_P(ivrgs_gaussians), C.c_int32, _P(ivrgs_model_edit), _P(ivrgs_light),
                                        _P(ivrgs_gaussians), C.c_void_p, C.c_void_p]),
@@ -186,6 +188,16 @@ def ivrgs_render_backward_static(g, d_edit_table, p, b, cams, n_views, lowpass, 
 
 
 IVRGS_STATIC_SCRATCH_BYTES = 32 << 20
+
+
+def ivrgs_set_option(name: str, value: int):
+    return call("ivrgs_set_option", name.encode(), int(value))
+
+
+def ivrgs_get_option(name: str) -> int:
+    v = C.c_int64(0)
+    call("ivrgs_get_option", name.encode(), C.byref(v))
+    return int(v.value)
 
 
 def prof_enable(on: bool):

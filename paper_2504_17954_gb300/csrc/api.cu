@@ -10,6 +10,11 @@ namespace ivrgs {
 
 static thread_local std::string g_last_error;
 
+Options& options() {
+    static Options o;
+    return o;
+}
+
 void set_error(const std::string& msg) { g_last_error = msg; }
 
 ivrgs_status cuda_status(cudaError_t e, const char* what) {
@@ -127,6 +132,28 @@ extern "C" {
 const char* ivrgs_last_error(void) { return g_last_error.c_str(); }
 
 int32_t ivrgs_version(void) { return 100; }
+
+ivrgs_status ivrgs_set_option(const char* name, int64_t value) {
+    set_error("");
+    if (!name) return invalid("name is NULL");
+    const std::string k(name);
+    if (k == "render_pixels_per_thread" || k == "render_bwd_pixels_per_thread") {
+        if (value != 1 && value != 2) return invalid(k + " must be 1 or 2");
+        (k == "render_pixels_per_thread" ? options().render_ppt : options().render_bwd_ppt) = (int)value;
+        return IVRGS_OK;
+    }
+    return invalid("unknown option '" + k + "'");
+}
+
+ivrgs_status ivrgs_get_option(const char* name, int64_t* value) {
+    set_error("");
+    if (!name || !value) return invalid("NULL argument");
+    const std::string k(name);
+    if (k == "render_pixels_per_thread") *value = options().render_ppt;
+    else if (k == "render_bwd_pixels_per_thread") *value = options().render_bwd_ppt;
+    else return invalid("unknown option '" + k + "'");
+    return IVRGS_OK;
+}
 
 int64_t ivrgs_edit_table_floats(int32_t n_models) { return (int64_t)IVRGS_EDIT_STRIDE * n_models + 8; }
 

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     constexpr int kBatch = 256;
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
-    __shared__ float s_blue[kBatch];
+    __shared__ float2 s_c[kBatch];
     __shared__ long long s_gi[kBatch];
     __shared__ unsigned s_max;
     const long long tile = blockIdx.x;
@@ -120,17 +120,17 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
                 const unsigned g = values[rg.x + e];
                 long long gi = vbase + g;
                 float4 sa, sb;
-                float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 sc;
                 if (g < (unsigned long long)n) {
-                    cd = rgbd[gi];
-                    stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
+                    stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
                 } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
                     gi = vbase;
-                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), cd, sa, sb);
+                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                                   sa, sb, sc);
                 }
                 s_a[slot] = sa;
                 s_b[slot] = sb;
-                s_blue[slot] = cd.z;
+                s_c[slot] = sc;
                 s_gi[slot] = gi;
             }
         }
@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             const int ee = b_end - 1 - j;
             const float4 a = s_a[j];
             const float4 bb = s_b[j];
-            const float blue = s_blue[j];
+            const float2 cc = s_c[j];
+            const float blue = cc.x;
             // v[0..7] = d(u, v, a, b, c, o', r, g), vb = d(blue): summed over this thread's pixels
             float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float vb = 0.f;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
                 if (ee < (int)my_last[p]) {
                     float dx, dy;
                     const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
-                    if (p2 <= 0.0f) {
+                    if (p2 <= 0.0f && p2 >= cc.y) {
                         const float G = fast_ex2(p2);
                         const float raw = bb.y * G;
                         const float alpha = fminf(kAlphaMax, raw);
@@ -461,10 +462,18 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
     if ((e = cudaMemsetAsync(edit_grad, 0, sizeof(float) * (size_t)ne, s)) != cudaSuccess) return e;
     if (cb.n_tiles > 0) {
         IVRGS_PROF("k_render_bwd", s);
-        k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(
-            reinterpret_cast<const float2*>(p->xy), reinterpret_cast<const float4*>(p->conic_o),
-            reinterpret_cast<const float4*>(p->rgbd), p->n, b->values, reinterpret_cast<const uint2*>(b->ranges), cb,
-            make_float3(bg[0], bg[1], bg[2]), final_T, last, reinterpret_cast<const float4*>(dL), g0, g1, g2);
+        const float2* xy = reinterpret_cast<const float2*>(p->xy);
+        const float4* co = reinterpret_cast<const float4*>(p->conic_o);
+        const float4* cd = reinterpret_cast<const float4*>(p->rgbd);
+        const uint2* rg = reinterpret_cast<const uint2*>(b->ranges);
+        const float3 bgc = make_float3(bg[0], bg[1], bg[2]);
+        const float4* dl = reinterpret_cast<const float4*>(dL);
+        if (options().render_bwd_ppt == 1)
+            k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, final_T,
+                                                                     last, dl, g0, g1, g2);
+        else
+            k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
+                                                                         final_T, last, dl, g0, g1, g2);
     }
     if (g->n > 0) {
         IVRGS_PROF("k_project_bwd", s);

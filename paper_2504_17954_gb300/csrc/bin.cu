@@ -87,9 +87,11 @@ __device__ __forceinline__ unsigned warp_incl_scan(unsigned x) {
     return x;
 }
 
-__device__ __forceinline__ long long clamp_count(const unsigned long long* d_n, long long cap) {
+// number of items a sort/ranges kernel works on: the count, or 0 if it exceeds the buffer (an
+// overflowing CAPACITY-mode call leaves the outputs unsorted; the caller sees the count)
+__device__ __forceinline__ long long sort_count(const unsigned long long* d_n, long long cap) {
     const unsigned long long nn = *d_n;
-    return (long long)nn < cap ? (long long)nn : cap;
+    return (long long)nn <= cap ? (long long)nn : 0;
 }
 
 // ------------------------------------------------------------------------- count
@@ -273,6 +275,24 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict_
                 g = (unsigned)(i - (long long)v * n);
             }
         }
+        // digits above the lowest byte: each row of the rectangle is a contiguous run of tile ids
+        // (narrower than 256), so it adds to at most two digits per higher byte
+        if (c) {
+            const unsigned t0 = (unsigned)cb.c[v].tile0, gxv = (unsigned)cb.c[v].gx, w = (unsigned)(x1 - x0);
+            for (int row = y0; row < y1; ++row) {
+                const unsigned a = t0 + (unsigned)row * gxv + (unsigned)x0, e = a + w;
+                for (int p = 1; p < n_passes; ++p) {
+                    const unsigned sh = 8u * p, d0 = a >> sh, d1 = (e - 1u) >> sh;
+                    if (d0 == d1) {
+                        atomicAdd(&s_hist[p * 256 + (d0 & 255u)], w);
+                    } else {
+                        const unsigned B = d1 << sh;
+                        atomicAdd(&s_hist[p * 256 + (d0 & 255u)], B - a);
+                        atomicAdd(&s_hist[p * 256 + (d1 & 255u)], e - B);
+                    }
+                }
+            }
+        }
         unsigned excl;
         const unsigned tot = block_excl_scan(c, excl, s_warp);
         const unsigned winc = warp_incl_scan(c);
@@ -304,13 +324,6 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict_
                 tiles[o] = tile;
                 vals[o] = s_g[ti];
                 atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
-            }
-            // higher bytes repeat along a warp's slots: one aggregated add per distinct digit
-            const unsigned act = __activemask();
-            for (int p = 1; p < n_passes; ++p) {
-                const unsigned dg = (long long)o < cap ? ((tile >> (8 * p)) & 255u) : 256u;
-                const unsigned peers = __match_any_sync(act, dg);
-                if (dg < 256u && lane == __ffs(peers) - 1) atomicAdd(&s_hist[p * 256 + dg], (unsigned)__popc(peers));
             }
         }
         off += tot;
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
     for (int k = tid; k < (kSortThreads / 32) * 256; k += kSortThreads) (&s_whist[0][0])[k] = 0u;
     __syncthreads();
     const long long tile = s_tile;
-    const long long n = clamp_count(d_n, cap);
+    const long long n = sort_count(d_n, cap);
     const long long start = tile * kSortTile;
     if (start >= n) return;
 
@@ -359,10 +372,12 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
     const long long wbase = start + (long long)warp * 32 * kSortItems;
     // digit of item j, 256 for the slots past the end
 #define IVRGS_DIGIT(j) ((wbase + (j) * 32 + lane) < n ? ((key[j] >> shift) & 255u) : 256u)
+    unsigned val[kSortItems];
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const long long idx = wbase + j * 32 + lane;
         key[j] = idx < n ? kin[idx] : 0u;
+        val[j] = idx < n ? vin[idx] : 0u;
     }
     // stable rank inside the warp, in (item, lane) order == index order: peers by 9 ballots
 #pragma unroll
@@ -396,24 +411,37 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
     unsigned lexcl;
     block_excl_scan(cnt, lexcl, s_warp);
     s_local[dg] = lexcl;
+    // decoupled look-back: read the status words of up to 8 predecessors at once, add their
+    // counts nearest-first until one carries an inclusive prefix; wait (bounded) on a
+    // predecessor that has not published yet
     unsigned prefix = 0;
     if (tile > 0) {
-        long long t = tile - 1;
+        long long t = tile - 1;  // nearest predecessor not yet accounted for
         long long spins = 0;
-        while (true) {
-            const unsigned s = ld_relaxed(lookback + t * 256 + dg);
-            const unsigned f = s >> 30;
-            if (f == 0u) {
+        bool done_lb = false;
+        while (!done_lb) {
+            unsigned st[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) st[w] = (t - w >= 0) ? ld_relaxed(lookback + (t - w) * 256 + dg) : (kFlagPre);
+            int w = 0;
+            for (; w < 8; ++w) {
+                const unsigned f = st[w] >> 30;
+                if (f == 0u) break;  // not published yet: re-read from this tile
+                prefix += st[w] & kValMask;
+                if (f == 2u || t - w == 0) {
+                    done_lb = true;
+                    break;
+                }
+            }
+            if (done_lb) break;
+            t -= w;
+            if (w == 0) {
                 if (++spins > max_spin) {
                     atomicOr(flag, 1u);
                     break;
                 }
                 if (spins > 64) __nanosleep(64);
-                continue;
             }
-            prefix += s & kValMask;
-            if (f == 2u || t == 0) break;
-            --t;
         }
         if (publish) st_relaxed(my_status, kFlagPre | ((prefix + cnt) & kValMask));
     }
@@ -430,7 +458,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const long long idx = wbase + j * 32 + lane;
-        if (idx < n) s_vals[pos[j]] = vin[idx];
+        if (idx < n) s_vals[pos[j]] = val[j];
     }
 #undef IVRGS_DIGIT
     __syncthreads();
@@ -448,7 +476,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
 __global__ void __launch_bounds__(256) k_ranges(const unsigned* __restrict__ tiles,
                                                 const unsigned long long* __restrict__ d_n, long long cap,
                                                 long long n_tiles, unsigned* __restrict__ ranges) {
-    const long long n = clamp_count(d_n, cap);
+    const long long n = sort_count(d_n, cap);
     const long long base = (long long)blockIdx.x * 2048;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {

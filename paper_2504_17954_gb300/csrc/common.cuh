@@ -89,6 +89,13 @@ struct BinPlan {
 };
 
 ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb);
+
+// tunable launch shapes (set through ivrgs_set_option; read by the launchers)
+struct Options {
+    int render_ppt = 2;      // pixels per thread of the forward blend (1 or 2)
+    int render_bwd_ppt = 2;  // pixels per thread of the backward blend (1 or 2)
+};
+Options& options();
 BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity);
 
 // launchers (each returns cudaGetLastError() of its launches)

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     constexpr int NT = kTilePix / P;
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
-    __shared__ float s_blue[kBatch];
+    __shared__ float2 s_c[kBatch];
     const long long tile = blockIdx.x;
     const int v = view_of_tile(cb, tile);
     const CamDev& cam = cb.c[v];
@@ -62,17 +62,17 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
             if (e < len) {
                 const unsigned g = values[rg.x + e];
                 float4 sa, sb;
-                float4 cd = make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 sc;
                 if (g < (unsigned long long)n) {
                     const long long gi = vbase + g;
-                    cd = rgbd[gi];
-                    stage_gaussian(xy[gi], conic_o[gi], cd, sa, sb);
+                    stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
                 } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
-                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), cd, sa, sb);
+                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                                   sa, sb, sc);
                 }
                 s_a[slot] = sa;
                 s_b[slot] = sb;
-                s_blue[slot] = cd.z;
+                s_c[slot] = sc;
             }
         }
         __syncthreads();
@@ -81,14 +81,15 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
         for (int j = 0; j < cnt; ++j) {
             const float4 a = s_a[j];
             const float4 bb = s_b[j];
+            const float2 cc = s_c[j];
             bool alldone = true;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                if (!done[p]) {
-                    float dx, dy;
-                    const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
+                float dx, dy;
+                const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
+                if (!done[p] && p2 <= 0.0f && p2 >= cc.y) {
                     const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
-                    if (p2 <= 0.0f && alpha >= kAlphaMin) {
+                    if (alpha >= kAlphaMin) {
                         const float Tn = T[p] * (1.0f - alpha);
                         if (Tn < kTMin) {
                             done[p] = true;
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
                             const float w = alpha * T[p];
                             C0[p] = fmaf(w, bb.z, C0[p]);
                             C1[p] = fmaf(w, bb.w, C1[p]);
-                            C2[p] = fmaf(w, s_blue[j], C2[p]);
+                            C2[p] = fmaf(w, cc.x, C2[p]);
                             T[p] = Tn;
                             last[p] = (unsigned)(b0 + j + 1);
                         }
@@ -121,12 +122,19 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
 cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const CamBatch& cb, const float* bg,
                           float* rgba, float* final_T, uint32_t* last, cudaStream_t s) {
     if (cb.n_tiles == 0) return cudaSuccess;
-    constexpr int P = 2;
     IVRGS_PROF("k_render", s);
-    k_render<P><<<(unsigned)cb.n_tiles, kTilePix / P, 0, s>>>(
-        reinterpret_cast<const float2*>(p->xy), reinterpret_cast<const float4*>(p->conic_o),
-        reinterpret_cast<const float4*>(p->rgbd), p->n, b->values, reinterpret_cast<const uint2*>(b->ranges), cb,
-        make_float3(bg[0], bg[1], bg[2]), reinterpret_cast<float4*>(rgba), final_T, last);
+    const float2* xy = reinterpret_cast<const float2*>(p->xy);
+    const float4* co = reinterpret_cast<const float4*>(p->conic_o);
+    const float4* cd = reinterpret_cast<const float4*>(p->rgbd);
+    const uint2* rg = reinterpret_cast<const uint2*>(b->ranges);
+    const float3 bgc = make_float3(bg[0], bg[1], bg[2]);
+    float4* out = reinterpret_cast<float4*>(rgba);
+    if (options().render_ppt == 1)
+        k_render<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out, final_T,
+                                                             last);
+    else
+        k_render<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
+                                                                 final_T, last);
     return cudaGetLastError();
 }
 

@@ -192,8 +192,19 @@ def test_render_only_matches_oracle_on_shared_records(which):
 
 
 # ------------------------------------------------------------------ end to end forward
+@pytest.fixture(params=[1, 2], ids=["ppt1", "ppt2"])
+def pixels_per_thread(request):
+    from paper_2504_17954_gb300 import _native as N
+    old = (N.ivrgs_get_option("render_pixels_per_thread"), N.ivrgs_get_option("render_bwd_pixels_per_thread"))
+    N.ivrgs_set_option("render_pixels_per_thread", request.param)
+    N.ivrgs_set_option("render_bwd_pixels_per_thread", request.param)
+    yield request.param
+    N.ivrgs_set_option("render_pixels_per_thread", old[0])
+    N.ivrgs_set_option("render_bwd_pixels_per_thread", old[1])
+
+
 @pytest.mark.parametrize("which", ["cfg1", "multi"])
-def test_forward_end_to_end(which):
+def test_forward_end_to_end(which, pixels_per_thread):
     w = sg.config1() if which == "cfg1" else _multi_view_scene(seed=25)
     rast, comp, table = _gpu.setup(w)
     rast.forward(comp, table)
@@ -224,7 +235,7 @@ def test_forward_end_to_end(which):
 
 # ------------------------------------------------------------------ backward
 @pytest.mark.parametrize("which", ["fd", "fd_orbital", "multi"])
-def test_backward_matches_oracle(which):
+def test_backward_matches_oracle(which, pixels_per_thread):
     if which.startswith("fd"):
         from tests.test_oracle_grad_fd import _scene
         models, ed, cams = _scene(which == "fd_orbital")
