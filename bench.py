@@ -35,7 +35,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ivrgs", choices=["ivrgs", "reference"])
-    ap.add_argument("--workload", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--workload", default="cfg4", choices=["cfg1", "cfg2", "cfg3", "cfg4", "cfg4-2v"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true", help="run warmup + 2 steps, print nothing else")
@@ -45,7 +45,8 @@ def parse():
 
 def workload(name):
     import scenegen as sg
-    return {"cfg1": sg.config1, "cfg2": sg.config2, "cfg3": sg.config3, "cfg4": sg.config4}[name]()
+    return {"cfg1": sg.config1, "cfg2": sg.config2, "cfg3": sg.config3, "cfg4": sg.config4,
+            "cfg4-2v": sg.config4_two_views}[name]()
 
 
 # ------------------------------------------------------------------------------------ clocks

@@ -151,7 +151,7 @@ const char* ivrgs_last_error(void);
 int32_t ivrgs_version(void);
 
 /* Launch-shape options (process-wide; measurement-driven tuning, the paper has no counterpart):
-   "render_pixels_per_thread" and "render_bwd_pixels_per_thread" (1 or 2): pixels each thread
+   "render_pixels_per_thread" and "render_bwd_pixels_per_thread" (1, 2 or 4): pixels each thread
    of the forward / backward blend owns. Results are identical for every setting.
    Returns IVRGS_ERR_INVALID_ARG for an unknown name or value. */
 ivrgs_status ivrgs_set_option(const char* name, int64_t value);

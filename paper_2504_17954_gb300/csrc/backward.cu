@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     atomicMax(&s_max, mx);
     __syncthreads();
     const int max_last = (int)s_max;
+    const int warp_last = (int)__reduce_max_sync(0xffffffffu, mx);
 
     for (int b_end = max_last; b_end > 0; b_end -= kBatch) {
         const int b_start = max(0, b_end - kBatch);
@@ -135,8 +136,10 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             }
         }
         __syncthreads();
+        // entries at or beyond every lane's last contributor are skipped by the whole warp
+        const int j0 = max(0, b_end - warp_last);
         const int cnt = b_end - b_start;
-        for (int j = 0; j < cnt; ++j) {
+        for (int j = j0; j < cnt; ++j) {
             const int ee = b_end - 1 - j;
             const float4 a = s_a[j];
             const float4 bb = s_b[j];
@@ -471,6 +474,9 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
         if (options().render_bwd_ppt == 1)
             k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, final_T,
                                                                      last, dl, g0, g1, g2);
+        else if (options().render_bwd_ppt == 4)
+            k_render_bwd<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
+                                                                         final_T, last, dl, g0, g1, g2);
         else
             k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
                                                                          final_T, last, dl, g0, g1, g2);

@@ -132,6 +132,9 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
     if (options().render_ppt == 1)
         k_render<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out, final_T,
                                                              last);
+    else if (options().render_ppt == 4)
+        k_render<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
+                                                                 final_T, last);
     else
         k_render<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
                                                                  final_T, last);

@@ -352,6 +352,15 @@ def config4(seed: int = 0, n_views: int = 8) -> Workload:
                     identity_edits(models))
 
 
+def config4_two_views(seed: int = 0) -> Workload:
+    """The 1M-Gaussian scene of config4 seen by its first two views (512^2, 800^2): a profiling
+    case whose buffers stay around 1 GB while its pair arrays exceed the L2 cache."""
+    w = config4(seed)
+    w.cameras = w.cameras[:2]
+    w.name = "cfg4-2v: 1M Gaussians / 4 models, 2 views 512^2 + 800^2"
+    return w
+
+
 def config5(seed: int = 0, n_views: int = 64) -> Workload:
     """8 composed models (3M, counts 1:2:..:8), 64 views with sides ~ U{512..2048}."""
     w = np.arange(1, 9)
