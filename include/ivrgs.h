@@ -152,7 +152,8 @@ int32_t ivrgs_version(void);
 
 /* Launch-shape options (process-wide; measurement-driven tuning, the paper has no counterpart):
    "render_pixels_per_thread" and "render_bwd_pixels_per_thread" (1, 2 or 4): pixels each thread
-   of the forward / backward blend owns. Results are identical for every setting.
+   of the forward / backward blend owns; "sort_match" (0 or 1): rank radix digits with warp
+   ballots (0) or match.any (1). Results are identical for every setting.
    Returns IVRGS_ERR_INVALID_ARG for an unknown name or value. */
 ivrgs_status ivrgs_set_option(const char* name, int64_t value);
 ivrgs_status ivrgs_get_option(const char* name, int64_t* value);

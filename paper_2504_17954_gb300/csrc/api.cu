@@ -142,6 +142,11 @@ ivrgs_status ivrgs_set_option(const char* name, int64_t value) {
         (k == "render_pixels_per_thread" ? options().render_ppt : options().render_bwd_ppt) = (int)value;
         return IVRGS_OK;
     }
+    if (k == "sort_match") {
+        if (value != 0 && value != 1) return invalid(k + " must be 0 or 1");
+        options().sort_match = (int)value;
+        return IVRGS_OK;
+    }
     return invalid("unknown option '" + k + "'");
 }
 
@@ -151,6 +156,7 @@ ivrgs_status ivrgs_get_option(const char* name, int64_t* value) {
     const std::string k(name);
     if (k == "render_pixels_per_thread") *value = options().render_ppt;
     else if (k == "render_bwd_pixels_per_thread") *value = options().render_bwd_ppt;
+    else if (k == "sort_match") *value = options().sort_match;
     else return invalid("unknown option '" + k + "'");
     return IVRGS_OK;
 }

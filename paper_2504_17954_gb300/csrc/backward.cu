@@ -145,47 +145,44 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             const float4 bb = s_b[j];
             const float2 cc = s_c[j];
             const float blue = cc.x;
-            // v[0..7] = d(u, v, a, b, c, o', r, g), vb = d(blue): summed over this thread's pixels
+            // per-thread sums over its pixels: vv = (m1, m2, m3, m4, m5, d o', d r, d g) with the
+            // moments m1 = sum dP dx, m2 = sum dP dy, m3 = sum dP dx^2, m4 = sum dP dx dy,
+            // m5 = sum dP dy^2 (the conic and mean gradients are linear in them); vb = d blue
             float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float vb = 0.f;
             bool contrib = false;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                if (ee < (int)my_last[p]) {
-                    float dx, dy;
-                    const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
-                    if (p2 <= 0.0f && p2 >= cc.y) {
-                        const float G = fast_ex2(p2);
-                        const float raw = bb.y * G;
-                        const float alpha = fminf(kAlphaMax, raw);
-                        if (alpha >= kAlphaMin) {
-                            contrib = true;
-                            const float om = 1.0f - alpha;
-                            const float Ti = T[p] / om;
-                            const float w = Ti * alpha;
-                            const float4 dd = d[p];
-                            vv[6] += w * dd.x;
-                            vv[7] += w * dd.y;
-                            vb += w * dd.z;
-                            const float dalpha = Ti * (dd.x * bb.z + dd.y * bb.w + dd.z * blue) -
-                                                 (dd.x * S0[p] + dd.y * S1[p] + dd.z * S2[p] - dA_T[p]) / om;
-                            S0[p] = fmaf(w, bb.z, S0[p]);
-                            S1[p] = fmaf(w, bb.w, S1[p]);
-                            S2[p] = fmaf(w, blue, S2[p]);
-                            T[p] = Ti;
-                            if (raw < kAlphaMax) {
-                                const float dP = dalpha * raw;  // dalpha/dP = o' G
-                                vv[5] += dalpha * G;
-                                // P = p2 / log2(e): dP/du = (2A' dx + B' dy)/log2e, dP/dv = (B' dx + 2C' dy)/log2e
-                                const float dPl = dP * (1.0f / kLog2e);
-                                vv[0] += dPl * (2.0f * a.z * dx + a.w * dy);
-                                vv[1] += dPl * (a.w * dx + 2.0f * bb.x * dy);
-                                vv[2] += dP * (-0.5f * dx * dx);
-                                vv[3] += dP * (-dx * dy);
-                                vv[4] += dP * (-0.5f * dy * dy);
-                            }
-                        }
-                    }
+                float dx, dy;
+                const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
+                const float G = fast_ex2(p2);
+                const float raw = bb.y * G;
+                const float alpha = fminf(kAlphaMax, raw);
+                const bool ok = ee < (int)my_last[p] && p2 <= 0.0f && p2 >= cc.y && alpha >= kAlphaMin;
+                if (ok) {
+                    contrib = true;
+                    const float r = __frcp_rn(1.0f - alpha);
+                    const float Ti = T[p] * r;
+                    const float w = Ti * alpha;
+                    const float4 dd = d[p];
+                    vv[6] = fmaf(w, dd.x, vv[6]);
+                    vv[7] = fmaf(w, dd.y, vv[7]);
+                    vb = fmaf(w, dd.z, vb);
+                    const float dalpha = Ti * (dd.x * bb.z + dd.y * bb.w + dd.z * blue) -
+                                         (dd.x * S0[p] + dd.y * S1[p] + dd.z * S2[p] - dA_T[p]) * r;
+                    S0[p] = fmaf(w, bb.z, S0[p]);
+                    S1[p] = fmaf(w, bb.w, S1[p]);
+                    S2[p] = fmaf(w, blue, S2[p]);
+                    T[p] = Ti;
+                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp
+                    const float dP = raw < kAlphaMax ? dalpha * raw : 0.0f;
+                    vv[5] = fmaf(raw < kAlphaMax ? dalpha : 0.0f, G, vv[5]);
+                    const float px_ = dP * dx, py_ = dP * dy;
+                    vv[0] += px_;
+                    vv[1] += py_;
+                    vv[2] = fmaf(px_, dx, vv[2]);
+                    vv[3] = fmaf(px_, dy, vv[3]);
+                    vv[4] = fmaf(py_, dy, vv[4]);
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, contrib);
@@ -193,19 +190,29 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             const long long gi = s_gi[j];
             float* t0 = reinterpret_cast<float*>(g0 + gi);
             float* t1 = reinterpret_cast<float*>(g1 + gi);
+            // moments -> (du, dv, da, db, dc): P = p2 / log2(e), p2 = A' dx^2 + B' dx dy + C' dy^2
+            //   du = (2 A' m1 + B' m2)/log2e, dv = (B' m1 + 2 C' m2)/log2e,
+            //   da = -m3/2, db = -m4, dc = -m5/2
+            const float il = 1.0f / kLog2e;
             if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction
                 if (contrib) {
-                    atomicAdd(reinterpret_cast<float4*>(t0), make_float4(vv[0], vv[1], vv[2], vv[3]));
-                    atomicAdd(reinterpret_cast<float4*>(t1), make_float4(vv[4], vv[5], vv[6], vv[7]));
+                    const float du = (2.0f * a.z * vv[0] + a.w * vv[1]) * il;
+                    const float dv = (a.w * vv[0] + 2.0f * bb.x * vv[1]) * il;
+                    atomicAdd(reinterpret_cast<float4*>(t0), make_float4(du, dv, -0.5f * vv[2], -vv[3]));
+                    atomicAdd(reinterpret_cast<float4*>(t1), make_float4(-0.5f * vv[4], vv[5], vv[6], vv[7]));
                     atomicAdd(&g2[gi], vb);
                 }
             } else {
-                const float x = warp_sum8_transposed(vv, lane);
+                float x = warp_sum8_transposed(vv, lane);  // lane holds the total of index lane >> 2
                 vb = warp_sum(vb);
-                if ((lane & 3) == 0) {
-                    const int idx = lane >> 2;
-                    atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
-                }
+                const int idx = lane >> 2;
+                const float other = __shfl_xor_sync(0xffffffffu, x, 4);  // m1 <-> m2 between idx 0 and 1
+                if (idx == 0) x = (2.0f * a.z * x + a.w * other) * il;
+                else if (idx == 1) x = (a.w * other + 2.0f * bb.x * x) * il;
+                else if (idx == 2) x = -0.5f * x;
+                else if (idx == 3) x = -x;
+                else if (idx == 4) x = -0.5f * x;
+                if ((lane & 3) == 0) atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
                 if (lane == 0) atomicAdd(&g2[gi], vb);
             }
         }

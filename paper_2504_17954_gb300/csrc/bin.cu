@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
                                                            int shift, const unsigned* __restrict__ base,
                                                            unsigned* __restrict__ lookback,
                                                            unsigned* __restrict__ counter, unsigned* __restrict__ flag,
-                                                           long long max_spin, long long skip_publish_tile) {
+                                                           long long max_spin, long long skip_publish_tile,
+                                                           int use_match) {
     __shared__ unsigned s_tile;
     __shared__ unsigned s_whist[kSortThreads / 32][256];
     __shared__ unsigned s_local[256];
@@ -369,31 +370,38 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
 
     unsigned key[kSortItems], pos[kSortItems];
     const unsigned lt = (1u << lane) - 1u;
-    const long long wbase = start + (long long)warp * 32 * kSortItems;
-    // digit of item j, 256 for the slots past the end
-#define IVRGS_DIGIT(j) ((wbase + (j) * 32 + lane) < n ? ((key[j] >> shift) & 255u) : 256u)
-    unsigned val[kSortItems];
+    // 32-bit offsets inside the radix tile; slots past the end hold the key 0xffffffff, whose
+    // digit (255) ranks them after every real key of the tile (they are never written out)
+    const int nvalid = (int)((n - start) < kSortTile ? (n - start) : kSortTile);
+    const int wofs = warp * 32 * kSortItems + lane;
+    const unsigned* kin_t = kin + start;
+    const unsigned* vin_t = vin + start;
+    // values wait in shared memory, in input order, until their destinations are known
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const long long idx = wbase + j * 32 + lane;
-        key[j] = idx < n ? kin[idx] : 0u;
-        val[j] = idx < n ? vin[idx] : 0u;
+        const int li = wofs + j * 32;
+        key[j] = li < nvalid ? kin_t[li] : 0xffffffffu;
+        s_vals[li] = li < nvalid ? vin_t[li] : 0u;
     }
-    // stable rank inside the warp, in (item, lane) order == index order: peers by 9 ballots
+    // stable rank inside the warp, in (item, lane) order == index order
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const unsigned dj = IVRGS_DIGIT(j);
-        unsigned peers = 0xffffffffu;
+        const unsigned dj = (key[j] >> shift) & 255u;
+        unsigned peers;
+        if (use_match) {
+            peers = __match_any_sync(0xffffffffu, dj);
+        } else {
+            peers = 0xffffffffu;
 #pragma unroll
-        for (int b = 0; b < 9; ++b) {
-            const bool bit = (dj >> b) & 1u;
-            const unsigned v = __ballot_sync(0xffffffffu, bit);
-            peers &= bit ? v : ~v;
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bit = (dj >> b) & 1u;
+                peers &= __ballot_sync(0xffffffffu, bit) ^ (bit - 1u);
+            }
         }
-        const unsigned before = dj < 256u ? s_whist[warp][dj] : 0u;
+        const unsigned before = s_whist[warp][dj];
         pos[j] = before + __popc(peers & lt);
         __syncwarp();
-        if (dj < 256u && lane == __ffs(peers) - 1) s_whist[warp][dj] = before + __popc(peers);
+        if (lane == __ffs(peers) - 1) s_whist[warp][dj] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -447,22 +455,18 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
     }
     s_global[dg] = base[dg] + prefix;
     __syncthreads();
+    unsigned val[kSortItems];
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const unsigned dj = IVRGS_DIGIT(j);
-        if (dj < 256u) {
-            pos[j] += s_local[dj] + s_whist[warp][dj];
-            s_keys[pos[j]] = key[j];
-        }
+        const unsigned dj = (key[j] >> shift) & 255u;
+        pos[j] += s_local[dj] + s_whist[warp][dj];
+        s_keys[pos[j]] = key[j];
+        val[j] = s_vals[wofs + j * 32];
     }
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const long long idx = wbase + j * 32 + lane;
-        if (idx < n) s_vals[pos[j]] = val[j];
-    }
-#undef IVRGS_DIGIT
     __syncthreads();
-    const int nvalid = (int)((n - start) < kSortTile ? (n - start) : kSortTile);
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) s_vals[pos[j]] = val[j];
+    __syncthreads();
     for (int i = tid; i < nvalid; i += kSortThreads) {
         const unsigned k = s_keys[i];
         const unsigned dd = (k >> shift) & 255u;
@@ -588,7 +592,8 @@ static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, uns
         IVRGS_PROF(name, s);
         k_onesweep<<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps,
                                                             base + 256 * ps, lookback + (size_t)256 * ps * tiles,
-                                                            counter + ps, flag, g_max_spin, g_skip_publish_tile);
+                                                            counter + ps, flag, g_max_spin, g_skip_publish_tile,
+                                                            options().sort_match);
     }
     return cudaGetLastError();
 }
