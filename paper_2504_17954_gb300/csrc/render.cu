@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
             }
         }
         __syncthreads();
-        if (all) continue;
+        // the walk below holds warp-wide votes, so a warp skips it only as a whole
+        if (__all_sync(0xffffffffu, all)) continue;
         const int cnt = min(kBatch, len - b0);
         // branch-free walk: every decision of the compositing is a predicate on the update
 #pragma unroll 2
