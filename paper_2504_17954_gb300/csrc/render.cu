@@ -76,39 +76,37 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
             }
         }
         __syncthreads();
-        // the walk below holds warp-wide votes, so a warp skips it only as a whole
-        if (__all_sync(0xffffffffu, all)) continue;
+        if (all) continue;
         const int cnt = min(kBatch, len - b0);
-        // branch-free walk: every decision of the compositing is a predicate on the update
-#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const float4 a = s_a[j];
             const float4 bb = s_b[j];
             const float2 cc = s_c[j];
-            const unsigned idx = (unsigned)(b0 + j + 1);
+            bool alldone = true;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 float dx, dy;
                 const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
-                const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
-                const bool ok = !done[p] && p2 <= 0.0f && p2 >= cc.y && alpha >= kAlphaMin;
-                const float Tn = T[p] * (1.0f - alpha);
-                const bool stop = ok && Tn < kTMin;
-                const bool add = ok && !stop;
-                const float w = add ? alpha * T[p] : 0.0f;
-                C0[p] = fmaf(w, bb.z, C0[p]);
-                C1[p] = fmaf(w, bb.w, C1[p]);
-                C2[p] = fmaf(w, cc.x, C2[p]);
-                T[p] = add ? Tn : T[p];
-                last[p] = add ? idx : last[p];
-                done[p] = done[p] || stop;
+                // a warp takes the update only if one of its pixels passes the cut-off tests
+                if (!done[p] && p2 <= 0.0f && p2 >= cc.y) {
+                    const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
+                    if (alpha >= kAlphaMin) {
+                        const float Tn = T[p] * (1.0f - alpha);
+                        if (Tn < kTMin) {
+                            done[p] = true;
+                        } else {
+                            const float w = alpha * T[p];
+                            C0[p] = fmaf(w, bb.z, C0[p]);
+                            C1[p] = fmaf(w, bb.w, C1[p]);
+                            C2[p] = fmaf(w, cc.x, C2[p]);
+                            T[p] = Tn;
+                            last[p] = (unsigned)(b0 + j + 1);
+                        }
+                    }
+                }
+                alldone = alldone && done[p];
             }
-            if ((j & 7) == 7) {
-                bool mine = true;
-#pragma unroll
-                for (int p = 0; p < P; ++p) mine = mine && done[p];
-                if (__all_sync(0xffffffffu, mine)) break;
-            }
+            if (alldone) break;  // per thread: no warp-wide operation inside this walk
         }
     }
 #pragma unroll
