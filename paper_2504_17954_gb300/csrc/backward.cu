@@ -53,7 +53,7 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
     return x;
 }
 
-// Per tile, P pixels per thread (rows r and r + 16/P of one column).
+// Per tile, P vertically adjacent pixels per thread; each warp covers a compact band of rows.
 template <int P>
 __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     const int local = (int)(tile - cam.tile0);
     const int tx = local % cam.gx, ty = local / cam.gx;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile);
+    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
     const float fx = (float)px + 0.5f;
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     unsigned mx = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const int py = py0 + p * (kTile / P);
+        const int py = py0 + p;
         fy[p] = (float)py + 0.5f;
         float Tf = 1.0f;
         my_last[p] = 0;

@@ -1,8 +1,9 @@
 // Per-tile front-to-back compositing (row a5; Sec. 3 second equation).
 //
-// One CTA per 16x16 tile; each of its 256/P threads owns P pixels of one column (rows r and
-// r + 16/P), so every Gaussian staged in shared memory is read once per P pixels and the P
-// transmittance chains run interleaved. The tile's sorted run is walked in batches of 256
+// One CTA per 16x16 tile; each of its 256/P threads owns P vertically adjacent pixels of one
+// column, so every Gaussian staged in shared memory is read once per P pixels and the P
+// transmittance chains run interleaved; a warp covers a compact band of 32P/16 rows, so a
+// Gaussian that misses the band lets the whole warp skip it. The tile's sorted run is walked in batches of 256
 // Gaussians: the CTA stages each batch (mean, conic pre-scaled by -log2(e)/2 so that the
 // exponent is one FMA chain, opacity, colour), then every pixel walks it. The CTA leaves as
 // soon as every pixel has reached T < 1e-4 (barrier count).
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     const int local = (int)(tile - cam.tile0);
     const int tx = local % cam.gx, ty = local / cam.gx;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile);
+    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
     const float fx = (float)px + 0.5f;
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     bool done[P], inside[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const int py = py0 + p * (kTile / P);
+        const int py = py0 + p;
         inside[p] = px < cam.W && py < cam.H;
         fy[p] = (float)py + 0.5f;
         C0[p] = C1[p] = C2[p] = 0.f;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
 #pragma unroll
     for (int p = 0; p < P; ++p)
         if (inside[p]) {
-            const int py = py0 + p * (kTile / P);
+            const int py = py0 + p;
             const long long pix = cam.pix0 + (long long)py * cam.W + px;
             rgba[pix] = make_float4(C0[p] + T[p] * bg.x, C1[p] + T[p] * bg.y, C2[p] + T[p] * bg.z, 1.0f - T[p]);
             final_T[pix] = T[p];
