@@ -150,40 +150,49 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             // m5 = sum dP dy^2 (the conic and mean gradients are linear in them); vb = d blue
             float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float vb = 0.f;
-            bool contrib = false;
+            float p2[P], dxs[P], dys[P];
+            bool ok0[P];
+            bool any = false;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float dx, dy;
-                const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
-                const float G = fast_ex2(p2);
+                p2[p] = blend_p2(a, bb, fx, fy[p], dxs[p], dys[p]);
+                ok0[p] = ee < (int)my_last[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
+                any = any || ok0[p];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            bool contrib = false;
+            // the P pixels update independently (predicated, no branches) so they interleave
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float G = fast_ex2(p2[p]);
                 const float raw = bb.y * G;
                 const float alpha = fminf(kAlphaMax, raw);
-                const bool ok = ee < (int)my_last[p] && p2 <= 0.0f && p2 >= cc.y && alpha >= kAlphaMin;
-                if (ok) {
-                    contrib = true;
-                    const float r = __frcp_rn(1.0f - alpha);
-                    const float Ti = T[p] * r;
-                    const float w = Ti * alpha;
-                    const float4 dd = d[p];
-                    vv[6] = fmaf(w, dd.x, vv[6]);
-                    vv[7] = fmaf(w, dd.y, vv[7]);
-                    vb = fmaf(w, dd.z, vb);
-                    const float dalpha = Ti * (dd.x * bb.z + dd.y * bb.w + dd.z * blue) -
-                                         (dd.x * S0[p] + dd.y * S1[p] + dd.z * S2[p] - dA_T[p]) * r;
-                    S0[p] = fmaf(w, bb.z, S0[p]);
-                    S1[p] = fmaf(w, bb.w, S1[p]);
-                    S2[p] = fmaf(w, blue, S2[p]);
-                    T[p] = Ti;
-                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp
-                    const float dP = raw < kAlphaMax ? dalpha * raw : 0.0f;
-                    vv[5] = fmaf(raw < kAlphaMax ? dalpha : 0.0f, G, vv[5]);
-                    const float px_ = dP * dx, py_ = dP * dy;
-                    vv[0] += px_;
-                    vv[1] += py_;
-                    vv[2] = fmaf(px_, dx, vv[2]);
-                    vv[3] = fmaf(px_, dy, vv[3]);
-                    vv[4] = fmaf(py_, dy, vv[4]);
-                }
+                const bool ok = ok0[p] && alpha >= kAlphaMin;
+                contrib = contrib || ok;
+                const float r = __frcp_rn(1.0f - alpha);
+                const float Ti = T[p] * r;
+                const float w = ok ? Ti * alpha : 0.0f;
+                const float4 dd = d[p];
+                vv[6] = fmaf(w, dd.x, vv[6]);
+                vv[7] = fmaf(w, dd.y, vv[7]);
+                vb = fmaf(w, dd.z, vb);
+                const float dalpha = Ti * (dd.x * bb.z + dd.y * bb.w + dd.z * blue) -
+                                     (dd.x * S0[p] + dd.y * S1[p] + dd.z * S2[p] - dA_T[p]) * r;
+                S0[p] = fmaf(w, bb.z, S0[p]);
+                S1[p] = fmaf(w, bb.w, S1[p]);
+                S2[p] = fmaf(w, blue, S2[p]);
+                T[p] = ok ? Ti : T[p];
+                // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
+                // selected rather than multiplied so that an infinite G never reaches the sums)
+                const bool live = ok && raw < kAlphaMax;
+                const float dP = live ? dalpha * raw : 0.0f;
+                vv[5] += live ? dalpha * G : 0.0f;
+                const float px_ = dP * dxs[p], py_ = dP * dys[p];
+                vv[0] += px_;
+                vv[1] += py_;
+                vv[2] = fmaf(px_, dxs[p], vv[2]);
+                vv[3] = fmaf(px_, dys[p], vv[3]);
+                vv[4] = fmaf(py_, dys[p], vv[4]);
             }
             const unsigned m = __ballot_sync(0xffffffffu, contrib);
             if (m == 0u) continue;

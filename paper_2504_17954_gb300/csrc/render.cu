@@ -77,37 +77,48 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
             }
         }
         __syncthreads();
-        if (all) continue;
+        // the walk below holds warp-wide votes: a warp skips or leaves it only as a whole
+        if (__all_sync(0xffffffffu, all)) continue;
         const int cnt = min(kBatch, len - b0);
         for (int j = 0; j < cnt; ++j) {
             const float4 a = s_a[j];
             const float4 bb = s_b[j];
             const float2 cc = s_c[j];
-            bool alldone = true;
+            float p2[P];
+            bool ok[P];
+            bool any = false;
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 float dx, dy;
-                const float p2 = blend_p2(a, bb, fx, fy[p], dx, dy);
-                // a warp takes the update only if one of its pixels passes the cut-off tests
-                if (!done[p] && p2 <= 0.0f && p2 >= cc.y) {
-                    const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
-                    if (alpha >= kAlphaMin) {
-                        const float Tn = T[p] * (1.0f - alpha);
-                        if (Tn < kTMin) {
-                            done[p] = true;
-                        } else {
-                            const float w = alpha * T[p];
-                            C0[p] = fmaf(w, bb.z, C0[p]);
-                            C1[p] = fmaf(w, bb.w, C1[p]);
-                            C2[p] = fmaf(w, cc.x, C2[p]);
-                            T[p] = Tn;
-                            last[p] = (unsigned)(b0 + j + 1);
-                        }
-                    }
-                }
-                alldone = alldone && done[p];
+                p2[p] = blend_p2(a, bb, fx, fy[p], dx, dy);
+                ok[p] = !done[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
+                any = any || ok[p];
             }
-            if (alldone) break;  // per thread: no warp-wide operation inside this walk
+            if (__any_sync(0xffffffffu, any)) {
+                const unsigned idx = (unsigned)(b0 + j + 1);
+                // the P pixels update independently (predicated, no branches) so they interleave
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2[p]));
+                    const bool okp = ok[p] && alpha >= kAlphaMin;
+                    const float Tn = T[p] * (1.0f - alpha);
+                    const bool stop = okp && Tn < kTMin;
+                    const bool add = okp && !stop;
+                    const float w = add ? alpha * T[p] : 0.0f;
+                    C0[p] = fmaf(w, bb.z, C0[p]);
+                    C1[p] = fmaf(w, bb.w, C1[p]);
+                    C2[p] = fmaf(w, cc.x, C2[p]);
+                    T[p] = add ? Tn : T[p];
+                    last[p] = add ? idx : last[p];
+                    done[p] = done[p] || stop;
+                }
+            }
+            if ((j & 7) == 7) {
+                bool mine = true;
+#pragma unroll
+                for (int p = 0; p < P; ++p) mine = mine && done[p];
+                if (__all_sync(0xffffffffu, mine)) break;
+            }
         }
     }
 #pragma unroll
