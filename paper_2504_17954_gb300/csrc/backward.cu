@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
 }
 
 // ------------------------------------------------------------------------- a7
-__global__ void __launch_bounds__(256) k_project_bwd(const ivrgs_gaussians g, const float* __restrict__ table,
+__global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g, const float* __restrict__ table,
                                                      const __grid_constant__ CamBatch cb, float lowpass,
                                                      const float4* __restrict__ g0, const float4* __restrict__ g1,
                                                      const float* __restrict__ g2, const ivrgs_gaussians grad,

@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict_
     __shared__ unsigned s_start[kScanThreads / 32][33];
     __shared__ int s_x0[kScanThreads], s_w[kScanThreads], s_y0[kScanThreads];
     __shared__ unsigned s_g[kScanThreads], s_t0[kScanThreads], s_gx[kScanThreads];
+    __shared__ float s_rw[kScanThreads];
     for (int k = threadIdx.x; k < n_passes * 256; k += kScanThreads) s_hist[k] = 0u;
     __syncthreads();
     const long long m = (long long)*d_m;
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict_
         if (lane == 0) s_start[warp][0] = 0;
         s_x0[threadIdx.x] = x0;
         s_w[threadIdx.x] = x1 - x0;
+        s_rw[threadIdx.x] = x1 > x0 ? 1.0f / (float)(x1 - x0) : 0.0f;
         s_y0[threadIdx.x] = y0;
         s_g[threadIdx.x] = g;
         s_t0[threadIdx.x] = (unsigned)cb.c[v].tile0;
@@ -317,7 +319,12 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict_
             const int ti = warp * 32 + r;
             const unsigned q = s - s_start[warp][r];
             const unsigned w = (unsigned)s_w[ti];
-            const unsigned ty = q / w, tx = q - ty * w;
+            // q / w by a float reciprocal (q < 2^24), then one exact correction step each way
+            unsigned ty = (unsigned)((float)q * s_rw[ti]);
+            int txs = (int)q - (int)(ty * w);
+            if (txs < 0) { --ty; txs += (int)w; }
+            if (txs >= (int)w) { ++ty; txs -= (int)w; }
+            const unsigned tx = (unsigned)txs;
             const unsigned tile = s_t0[ti] + ((unsigned)s_y0[ti] + ty) * s_gx[ti] + (unsigned)s_x0[ti] + tx;
             const unsigned long long o = wbase + s;
             if ((long long)o < cap) {
@@ -481,15 +488,28 @@ __global__ void __launch_bounds__(256) k_ranges(const unsigned* __restrict__ til
                                                 const unsigned long long* __restrict__ d_n, long long cap,
                                                 long long n_tiles, unsigned* __restrict__ ranges) {
     const long long n = sort_count(d_n, cap);
-    const long long base = (long long)blockIdx.x * 2048;
+    const long long i0 = ((long long)blockIdx.x * 256 + threadIdx.x) * 4;  // four consecutive pairs
+    if (i0 >= n) return;
+    unsigned t[4];
+    if (i0 + 4 <= n) {
+        const uint4 q = *reinterpret_cast<const uint4*>(tiles + i0);  // 16-byte aligned: i0 % 4 == 0
+        t[0] = q.x; t[1] = q.y; t[2] = q.z; t[3] = q.w;
+    } else {
+        for (int k = 0; k < 4; ++k) t[k] = i0 + k < n ? tiles[i0 + k] : 0xffffffffu;
+    }
+    unsigned prev = i0 > 0 ? tiles[i0 - 1] : 0xffffffffu;
+    const unsigned next = i0 + 4 < n ? tiles[i0 + 4] : 0xffffffffu;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const long long i = base + j * 256 + threadIdx.x;
-        if (i >= n) return;
-        const unsigned t = tiles[i];
-        if ((long long)t >= n_tiles) continue;  // only after a timed-out sort
-        if (i == 0 || tiles[i - 1] != t) ranges[2ll * t] = (unsigned)i;
-        if (i == n - 1 || tiles[i + 1] != t) ranges[2ll * t + 1] = (unsigned)(i + 1);
+    for (int k = 0; k < 4; ++k) {
+        const long long i = i0 + k;
+        if (i >= n) break;
+        const unsigned tk = t[k];
+        const unsigned nx = k < 3 ? t[k + 1] : next;
+        if ((long long)tk < n_tiles) {  // always, unless a timed-out sort left a slot unwritten
+            if (i == 0 || prev != tk) ranges[2ll * tk] = (unsigned)i;
+            if (i == n - 1 || nx != tk) ranges[2ll * tk + 1] = (unsigned)(i + 1);
+        }
+        prev = tk;
     }
 }
 
@@ -659,7 +679,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         return e;
     if (n_work > 0) {
         IVRGS_PROF("k_ranges", s);
-        k_ranges<<<(unsigned)((n_work + 2047) / 2048), 256, 0, s>>>(out->tiles, b.d_n, cap, out->n_tiles,
+        k_ranges<<<(unsigned)((n_work + 1023) / 1024), 256, 0, s>>>(out->tiles, b.d_n, cap, out->n_tiles,
                                                                    out->ranges);
     }
     return cudaGetLastError();

@@ -149,7 +149,7 @@ __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& 
     V.nl = fabsf(V.ndl);
     V.nh = fabsf(V.ndh);
     V.gate = (V.nl > 0.0f) && (V.nh > 0.0f);
-    V.spow = V.gate ? powf(V.nh, G.kp[3]) : 0.0f;
+    V.spow = V.gate ? __powf(V.nh, G.kp[3]) : 0.0f;  // nh in (0, 1]: exp2(beta log2 nh) on the MUFU
     const float spec = V.gate ? G.kp[2] * V.spow : 0.0f;
     const float diff = G.kp[0] + G.kp[1] * V.nl;
     for (int k = 0; k < 3; ++k) V.rgb[k] = diff * G.cv[k] + spec;
