@@ -255,6 +255,40 @@ class Rasterizer:
                                 _stream(stream))
         return grad, self.edit_grad
 
+    # -- CUDA graphs
+    def capture(self, g: Gaussians, edit_table: torch.Tensor, dL_drgba: Optional[torch.Tensor] = None,
+                grad: Optional[Gaussians] = None, warmup: int = 2) -> "torch.cuda.CUDAGraph":
+        """Capture one step (projection, CAPACITY-mode binning, compositing and, if dL_drgba is
+        given, the backward into ``grad``) as a CUDA graph; ``graph.replay()`` reruns it on the
+        current contents of the Gaussian, edit-table and dL buffers.
+
+        The pair buffer must already hold the step's pairs (run ``forward(mode="exact")`` once);
+        after a replay, ``d_n_pairs > capacity`` means the step overflowed and must be rerun
+        with a larger capacity."""
+        if dL_drgba is not None:
+            _check_cuda(dL_drgba, "dL_drgba")
+            if self.ws_bwd is None:
+                self.ws_bwd = torch.empty(self.ws_bwd_bytes, dtype=torch.uint8, device=self.device)
+            if grad is None:
+                grad = Gaussians.empty(self.n, self.n_models, self.device)
+                grad.model_id = None
+        self.graph_grad = grad
+        N.prof_enable(False)
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):  # warm-up outside capture (lazy module loading etc.)
+            for _ in range(warmup):
+                self.forward(g, edit_table, mode="capacity")
+                if dL_drgba is not None:
+                    self.backward(g, edit_table, dL_drgba, grad=grad)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.forward(g, edit_table, mode="capacity")
+            if dL_drgba is not None:
+                self.backward(g, edit_table, dL_drgba, grad=grad)
+        return graph
+
     # -- views of the packed image
     def view_image(self, v: int, t: Optional[torch.Tensor] = None) -> torch.Tensor:
         t = self.rgba if t is None else t
