@@ -75,18 +75,21 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
     const float fx = (float)px + 0.5f;
+    const int q0 = py0 & 3;                               // offset of this thread's first row in its group
+    const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
     const int lane = threadIdx.x & 31;
 
-    float fy[P], T[P], S0[P], S1[P], S2[P], dA_T[P];
+    // per pixel: T (recovered walking back) and DS = dL/dC . S - dL/dA T_final with
+    // S = sum over the contributors behind the current one of T_j alpha_j c_j + T_final bg
+    float T[P], DS[P];
     float4 d[P];
     unsigned my_last[P];
     unsigned mx = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int py = py0 + p;
-        fy[p] = (float)py + 0.5f;
         float Tf = 1.0f;
         my_last[p] = 0;
         d[p] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -97,10 +100,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             d[p] = dL[pix];
         }
         T[p] = Tf;
-        S0[p] = Tf * bg.x;
-        S1[p] = Tf * bg.y;
-        S2[p] = Tf * bg.z;
-        dA_T[p] = d[p].w * Tf;  // dL/dA * T_final
+        DS[p] = Tf * (d[p].x * bg.x + d[p].y * bg.y + d[p].z * bg.z - d[p].w);
         mx = max(mx, my_last[p]);
     }
     if (threadIdx.x == 0) s_max = 0u;
@@ -150,12 +150,13 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             // m5 = sum dP dy^2 (the conic and mean gradients are linear in them); vb = d blue
             float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float vb = 0.f;
-            float p2[P], dxs[P], dys[P];
+            float p2[P];
             bool ok0[P];
             bool any = false;
+            const RowGroup rgp = row_group(a, bb, fx, fyg);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                p2[p] = blend_p2(a, bb, fx, fy[p], dxs[p], dys[p]);
+                p2[p] = row_p2(rgp, bb, q0 + p);
                 ok0[p] = ee < (int)my_last[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
                 any = any || ok0[p];
             }
@@ -169,30 +170,29 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
                 const float alpha = fminf(kAlphaMax, raw);
                 const bool ok = ok0[p] && alpha >= kAlphaMin;
                 contrib = contrib || ok;
-                const float r = __frcp_rn(1.0f - alpha);
+                const float r = fast_rcp(1.0f - alpha);
                 const float Ti = T[p] * r;
                 const float w = ok ? Ti * alpha : 0.0f;
                 const float4 dd = d[p];
                 vv[6] = fmaf(w, dd.x, vv[6]);
                 vv[7] = fmaf(w, dd.y, vv[7]);
                 vb = fmaf(w, dd.z, vb);
-                const float dalpha = Ti * (dd.x * bb.z + dd.y * bb.w + dd.z * blue) -
-                                     (dd.x * S0[p] + dd.y * S1[p] + dd.z * S2[p] - dA_T[p]) * r;
-                S0[p] = fmaf(w, bb.z, S0[p]);
-                S1[p] = fmaf(w, bb.w, S1[p]);
-                S2[p] = fmaf(w, blue, S2[p]);
+                const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
+                const float dalpha = Ti * dc - DS[p] * r;
+                DS[p] = fmaf(w, dc, DS[p]);
                 T[p] = ok ? Ti : T[p];
                 // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
                 // selected rather than multiplied so that an infinite G never reaches the sums)
                 const bool live = ok && raw < kAlphaMax;
                 const float dP = live ? dalpha * raw : 0.0f;
                 vv[5] += live ? dalpha * G : 0.0f;
-                const float px_ = dP * dxs[p], py_ = dP * dys[p];
+                const float dxp = rgp.dx, dyp = rgp.dy0 - (float)(q0 + p);
+                const float px_ = dP * dxp, py_ = dP * dyp;
                 vv[0] += px_;
                 vv[1] += py_;
-                vv[2] = fmaf(px_, dxs[p], vv[2]);
-                vv[3] = fmaf(px_, dys[p], vv[3]);
-                vv[4] = fmaf(py_, dys[p], vv[4]);
+                vv[2] = fmaf(px_, dxp, vv[2]);
+                vv[3] = fmaf(px_, dyp, vv[3]);
+                vv[4] = fmaf(py_, dyp, vv[4]);
             }
             const unsigned m = __ballot_sync(0xffffffffu, contrib);
             if (m == 0u) continue;

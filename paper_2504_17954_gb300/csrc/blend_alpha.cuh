@@ -19,12 +19,32 @@ __device__ __forceinline__ void stage_gaussian(const float2 m, const float4 co, 
     sc = make_float2(cd.z, co.w > 0.0f ? thr : INFINITY);
 }
 
-// returns p2 = log2(e) * P and writes dx = u - px, dy = v - py
-__device__ __forceinline__ float blend_p2(const float4& sa, const float4& sb, float fx, float fy, float& dx,
-                                          float& dy) {
-    dx = sa.x - fx;
-    dy = sa.y - fy;
-    return fmaf(sa.z * dx, dx, fmaf(sa.w * dx, dy, sb.x * dy * dy));
+// p2 = log2(e) * P over an aligned group of 4 pixel rows of one column. With dx = u - px and
+// dy0 = v - py0 at the group's first row, row py0 + p has dy = dy0 - p and
+//   p2(p) = base - p k1 + p^2 C',  base = A' dx^2 + B' dx dy0 + C' dy0^2,  k1 = B' dx + 2 C' dy0.
+// Forward and backward evaluate exactly these fused operations for every pixel, whatever the
+// number of pixels per thread, so their float32 decisions agree bit for bit.
+struct RowGroup {
+    float dx, dy0, base, k1;
+};
+
+__device__ __forceinline__ RowGroup row_group(const float4& sa, const float4& sb, float fx, float fy0) {
+    RowGroup q;
+    q.dx = sa.x - fx;
+    q.dy0 = sa.y - fy0;
+    q.base = fmaf(sa.z * q.dx, q.dx, fmaf(sa.w * q.dx, q.dy0, sb.x * q.dy0 * q.dy0));
+    q.k1 = fmaf(2.0f * sb.x, q.dy0, sa.w * q.dx);
+    return q;
+}
+
+__device__ __forceinline__ float row_p2(const RowGroup& q, const float4& sb, int p) {
+    return fmaf(sb.x, (float)(p * p), fmaf(-(float)p, q.k1, q.base));
+}
+
+__device__ __forceinline__ float fast_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 }  // namespace ivrgs

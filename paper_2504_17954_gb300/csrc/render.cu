@@ -34,17 +34,18 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
     const float fx = (float)px + 0.5f;
+    const int q0 = py0 & 3;                               // offset of this thread's first row in its group
+    const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
 
-    float C0[P], C1[P], C2[P], T[P], fy[P];
+    float C0[P], C1[P], C2[P], T[P];
     unsigned last[P];
     bool done[P], inside[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int py = py0 + p;
         inside[p] = px < cam.W && py < cam.H;
-        fy[p] = (float)py + 0.5f;
         C0[p] = C1[p] = C2[p] = 0.f;
         T[p] = 1.f;
         last[p] = 0;
@@ -87,10 +88,10 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
             float p2[P];
             bool ok[P];
             bool any = false;
+            const RowGroup rgp = row_group(a, bb, fx, fyg);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                float dx, dy;
-                p2[p] = blend_p2(a, bb, fx, fy[p], dx, dy);
+                p2[p] = row_p2(rgp, bb, q0 + p);
                 ok[p] = !done[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
                 any = any || ok[p];
             }
