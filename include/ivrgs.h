@@ -59,7 +59,8 @@ enum {
 #define IVRGS_EDIT_STRIDE 8    /* floats per model in the edit table */
 #define IVRGS_MAX_PAIRS ((int64_t)1 << 30) /* (tile, Gaussian) pairs per ivrgs_bin call */
 
-enum { IVRGS_FP32 = 0 };
+enum { IVRGS_FP32 = 0, IVRGS_MIXED = 1 };
+#define IVRGS_ANCHOR_CHUNK 256 /* Gaussians per float32 position anchor in IVRGS_MIXED storage */
 enum { IVRGS_BIN_EXACT = 0, IVRGS_BIN_CAPACITY = 1 };
 
 /* One pinhole view. light_dir is the direction towards an orbital (directional) light in
@@ -94,22 +95,30 @@ typedef struct {
 } ivrgs_light;
 
 /* Editable Gaussians (Sec. 4.3 attribute set), structure of arrays, n entries.
-   mean [n][3], log_scale [n][3], quat [n][4] as (w, x, y, z) (need not be normalised),
-   opacity_logit [n], dcolor [n][3] (offset colour dc, c_v = c_p + dc), normal [n][3] (need
-   not be normalised), kads [n][4] = (k_a, k_d, k_s, beta), model_id [n] (basic model of
-   each Gaussian, < n_models). */
+   precision IVRGS_FP32: float32 arrays mean [n][3], log_scale [n][3], quat [n][4] as
+   (w, x, y, z) (need not be normalised), opacity_logit [n], dcolor [n][3] (offset colour dc,
+   c_v = c_p + dc), normal [n][3] (need not be normalised), kads [n][4] = (k_a, k_d, k_s,
+   beta); anchor unused.
+   precision IVRGS_MIXED (16-bit storage, float32 arithmetic): mean FP16 [n][3] offsets, with
+   the stored mean defined as the float32 sum anchor[g / IVRGS_ANCHOR_CHUNK] + offset
+   (anchor: float32 [ceil(n / 256)][3]); log_scale BF16 [n][3]; quat FP16 [n][4]; opacity_logit
+   FP16 [n]; dcolor BF16 [n][3]; normal BF16 [n][3]; kads FP16 [n][4]. ivrgs_pack_mixed
+   writes this layout.
+   model_id [n] (basic model of each Gaussian, < n_models) in both. Gradients are always
+   float32 with the FP32 layout (w.r.t. the decoded values for IVRGS_MIXED). */
 typedef struct {
     int64_t n;
-    int32_t precision; /* IVRGS_FP32 */
+    int32_t precision; /* IVRGS_FP32 or IVRGS_MIXED */
     int32_t n_models;
-    float* mean;
-    float* log_scale;
-    float* quat;
-    float* opacity_logit;
-    float* dcolor;
-    float* normal;
-    float* kads;
+    void* mean;
+    void* log_scale;
+    void* quat;
+    void* opacity_logit;
+    void* dcolor;
+    void* normal;
+    void* kads;
     uint16_t* model_id;
+    float* anchor; /* IVRGS_MIXED: float32 [ceil(n / 256)][3]; NULL for IVRGS_FP32 */
 } ivrgs_gaussians;
 
 /* Projected Gaussians, one record per (view v, Gaussian g) at index v * n + g.
@@ -241,6 +250,23 @@ ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit
                                    const float* bg, const float* d_final_T, const uint32_t* d_last,
                                    const float* d_dL_drgba, void* d_workspace, size_t ws_bytes,
                                    ivrgs_gaussians* grad, float* d_edit_grad, void* stream);
+
+/* Spatial ordering keys for packing (precision pattern; a storage-layout helper with no
+   counterpart in the paper): d_keys[g] = (model_id[g] << 30) | Morton code (10 bits per axis)
+   of mean[g] quantised inside the box [lo, hi] (host float[3] each). Sorting the keys
+   (stable, any sort) and passing the permutation to ivrgs_pack_mixed keeps each model
+   contiguous and makes every 256-Gaussian chunk spatially compact, so the FP16 offsets from
+   its anchor are small. g must be IVRGS_FP32. */
+ivrgs_status ivrgs_morton_keys(const ivrgs_gaussians* g, const float* lo, const float* hi, uint64_t* d_keys,
+                               void* stream);
+
+/* Packs float32 Gaussians into IVRGS_MIXED storage (Sec. 4.3 attributes, 16-bit floats,
+   round to nearest): out[k] = in[d_order[k]] (d_order: device uint32 [n], a permutation; NULL
+   for the identity). Each chunk of 256 output Gaussians gets the float32 anchor at the centre
+   of its means' bounding box and FP16 offsets from it. out->n must equal in->n; out's arrays
+   are caller-owned with the IVRGS_MIXED layout, out->anchor included. */
+ivrgs_status ivrgs_pack_mixed(const ivrgs_gaussians* in, const uint32_t* d_order, ivrgs_gaussians* out,
+                              void* stream);
 
 /* Bytes of the device array that ivrgs_render_backward_static uses as its scratch. */
 #define IVRGS_STATIC_SCRATCH_BYTES ((size_t)32 << 20)

@@ -24,6 +24,8 @@ IVRGS_MAX_MODELS = 1024
 IVRGS_EDIT_STRIDE = 8
 IVRGS_MAX_PAIRS = 1 << 30
 IVRGS_FP32 = 0
+IVRGS_MIXED = 1
+IVRGS_ANCHOR_CHUNK = 256
 IVRGS_BIN_EXACT = 0
 IVRGS_BIN_CAPACITY = 1
 
@@ -48,7 +50,8 @@ class ivrgs_light(C.Structure):
 class ivrgs_gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("precision", C.c_int32), ("n_models", C.c_int32), ("mean", C.c_void_p),
                 ("log_scale", C.c_void_p), ("quat", C.c_void_p), ("opacity_logit", C.c_void_p),
-                ("dcolor", C.c_void_p), ("normal", C.c_void_p), ("kads", C.c_void_p), ("model_id", C.c_void_p)]
+                ("dcolor", C.c_void_p), ("normal", C.c_void_p), ("kads", C.c_void_p), ("model_id", C.c_void_p),
+                ("anchor", C.c_void_p)]
 
 
 class ivrgs_projected(C.Structure):
@@ -73,6 +76,8 @@ _SIGNATURES = {
                                        _P(ivrgs_gaussians), C.c_void_p, C.c_void_p]),
     "ivrgs_project": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_camera), C.c_int32, C.c_float,
                                   _P(ivrgs_projected), C.c_void_p]),
+    "ivrgs_morton_keys": (C.c_int32, [_P(ivrgs_gaussians), _P(C.c_float), _P(C.c_float), C.c_void_p, C.c_void_p]),
+    "ivrgs_pack_mixed": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_gaussians), C.c_void_p]),
     "ivrgs_bin_workspace": (C.c_int32, [C.c_int64, C.c_int32, _P(ivrgs_camera), C.c_int32, C.c_int32, C.c_int64,
                                         _P(C.c_size_t)]),
     "ivrgs_bin": (C.c_int32, [_P(ivrgs_projected), _P(ivrgs_camera), C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
@@ -149,6 +154,14 @@ def ivrgs_compose_edit(models, n_models, edits, light, composed, d_edit_table, s
 
 def ivrgs_project(g, d_edit_table, cams, n_views, lowpass, out, stream):
     return call("ivrgs_project", g, d_edit_table, cams, n_views, lowpass, out, stream)
+
+
+def ivrgs_morton_keys(g, lo, hi, d_keys, stream):
+    return call("ivrgs_morton_keys", g, lo, hi, d_keys, stream)
+
+
+def ivrgs_pack_mixed(g_in, d_order, g_out, stream):
+    return call("ivrgs_pack_mixed", g_in, d_order, g_out, stream)
 
 
 def ivrgs_bin_workspace(n, n_views, cams, tile_w, tile_h, capacity) -> int:

@@ -77,22 +77,35 @@ ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch*
     return IVRGS_OK;
 }
 
-static ivrgs_status check_gaussians(const ivrgs_gaussians* g, const char* name, bool need_model_id) {
+static ivrgs_status check_gaussians(const ivrgs_gaussians* g, const char* name, bool need_model_id,
+                                    bool allow_mixed = false) {
     if (!g) return invalid(std::string(name) + " is NULL");
     if (g->n < 0) return invalid(std::string(name) + ": negative n");
-    if (g->precision != IVRGS_FP32) {
-        set_error(std::string(name) + ": only IVRGS_FP32 storage is implemented");
+    if (g->precision != IVRGS_FP32 && g->precision != IVRGS_MIXED)
+        return invalid(std::string(name) + ": unknown precision");
+    if (g->precision == IVRGS_MIXED && !allow_mixed) {
+        set_error(std::string(name) + ": this call takes IVRGS_FP32 storage");
         return IVRGS_ERR_UNSUPPORTED;
     }
     if (g->n == 0) return IVRGS_OK;
     if (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->dcolor || !g->normal || !g->kads ||
         (need_model_id && !g->model_id))
         return invalid(std::string(name) + ": NULL attribute array");
-    if (!aligned(g->quat, 16) || !aligned(g->kads, 16))
-        return invalid(std::string(name) + ": quat and kads must be 16-byte aligned");
-    if (!aligned(g->mean, 4) || !aligned(g->log_scale, 4) || !aligned(g->dcolor, 4) || !aligned(g->normal, 4) ||
-        !aligned(g->opacity_logit, 4) || (need_model_id && !aligned(g->model_id, 2)))
-        return invalid(std::string(name) + ": misaligned attribute array");
+    if (g->precision == IVRGS_FP32) {
+        if (!aligned(g->quat, 16) || !aligned(g->kads, 16))
+            return invalid(std::string(name) + ": quat and kads must be 16-byte aligned");
+        if (!aligned(g->mean, 4) || !aligned(g->log_scale, 4) || !aligned(g->dcolor, 4) || !aligned(g->normal, 4) ||
+            !aligned(g->opacity_logit, 4))
+            return invalid(std::string(name) + ": misaligned attribute array");
+    } else {
+        if (!g->anchor) return invalid(std::string(name) + ": IVRGS_MIXED needs the anchor array");
+        if (!aligned(g->quat, 8) || !aligned(g->kads, 8))
+            return invalid(std::string(name) + ": IVRGS_MIXED quat and kads must be 8-byte aligned");
+        if (!aligned(g->mean, 2) || !aligned(g->log_scale, 2) || !aligned(g->dcolor, 2) || !aligned(g->normal, 2) ||
+            !aligned(g->opacity_logit, 2) || !aligned(g->anchor, 4))
+            return invalid(std::string(name) + ": misaligned attribute array");
+    }
+    if (need_model_id && !aligned(g->model_id, 2)) return invalid(std::string(name) + ": misaligned model_id");
     return IVRGS_OK;
 }
 
@@ -195,7 +208,7 @@ ivrgs_status ivrgs_compose_edit(const ivrgs_gaussians* models, int32_t n_models,
 ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_camera* cams,
                            int32_t n_views, float lowpass, ivrgs_projected* out, void* stream) {
     set_error("");
-    ivrgs_status st = check_gaussians(g, "g", true);
+    ivrgs_status st = check_gaussians(g, "g", true, true);
     if (st) return st;
     if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
     if (!d_edit_table) return invalid("d_edit_table is NULL");
@@ -204,6 +217,31 @@ ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, 
     if ((st = make_cam_batch(cams, n_views, &cb))) return st;
     if ((st = check_projected(out, g->n, n_views))) return st;
     return cuda_status(launch_project(g, d_edit_table, cb, lowpass, out, (cudaStream_t)stream), "ivrgs_project");
+}
+
+ivrgs_status ivrgs_morton_keys(const ivrgs_gaussians* g, const float* lo, const float* hi, uint64_t* d_keys,
+                               void* stream) {
+    set_error("");
+    ivrgs_status st = check_gaussians(g, "g", true);
+    if (st) return st;
+    if (!lo || !hi || (!d_keys && g->n > 0)) return invalid("lo, hi and d_keys must be non-NULL");
+    for (int k = 0; k < 3; ++k)
+        if (!(hi[k] > lo[k]) || !isfinite(lo[k]) || !isfinite(hi[k])) return invalid("the box needs lo < hi, finite");
+    if (!aligned(d_keys, 8)) return invalid("d_keys must be 8-byte aligned");
+    return cuda_status(launch_morton(g, lo, hi, d_keys, (cudaStream_t)stream), "ivrgs_morton_keys");
+}
+
+ivrgs_status ivrgs_pack_mixed(const ivrgs_gaussians* in, const uint32_t* d_order, ivrgs_gaussians* out,
+                              void* stream) {
+    set_error("");
+    ivrgs_status st = check_gaussians(in, "in", true);
+    if (st) return st;
+    if (!out) return invalid("out is NULL");
+    if (out->precision != IVRGS_MIXED) return invalid("out->precision must be IVRGS_MIXED");
+    if ((st = check_gaussians(out, "out", true, true))) return st;
+    if (out->n != in->n) return invalid("out->n must equal in->n");
+    if (d_order && !aligned(d_order, 4)) return invalid("d_order misaligned");
+    return cuda_status(launch_pack_mixed(in, d_order, out, (cudaStream_t)stream), "ivrgs_pack_mixed");
 }
 
 ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera* cams, int32_t tile_w,
@@ -312,7 +350,7 @@ ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit
                                    const float* d_dL_drgba, void* d_workspace, size_t ws_bytes,
                                    ivrgs_gaussians* grad, float* d_edit_grad, void* stream) {
     set_error("");
-    ivrgs_status st = check_gaussians(g, "g", true);
+    ivrgs_status st = check_gaussians(g, "g", true, true);
     if (st) return st;
     if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
     if ((st = check_gaussians(grad, "grad", false))) return st;

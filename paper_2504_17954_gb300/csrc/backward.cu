@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
 }
 
 // ------------------------------------------------------------------------- a7
+template <int PREC>
 __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g, const float* __restrict__ table,
                                                      const __grid_constant__ CamBatch cb, float lowpass,
                                                      const float4* __restrict__ g0, const float4* __restrict__ g1,
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int M = g.n_models;
     GaussLocal G;
-    if (active) load_gauss(g, table, M, i, G);
+    if (active) load_gauss<PREC>(g, table, M, i, G);
     else G.visible = false;
     float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float dcv[3] = {0.f, 0.f, 0.f}, dkp[4] = {0.f, 0.f, 0.f, 0.f}, dnn[3] = {0.f, 0.f, 0.f}, dop = 0.f;
@@ -421,14 +422,14 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
             }
         }
         for (int k = 0; k < 3; ++k) {
-            grad.mean[3 * i + k] = gm[k];
-            grad.log_scale[3 * i + k] = gls[k];
-            grad.dcolor[3 * i + k] = gdc[k];
-            grad.normal[3 * i + k] = gn[k];
+            static_cast<float*>(grad.mean)[3 * i + k] = gm[k];
+            static_cast<float*>(grad.log_scale)[3 * i + k] = gls[k];
+            static_cast<float*>(grad.dcolor)[3 * i + k] = gdc[k];
+            static_cast<float*>(grad.normal)[3 * i + k] = gn[k];
         }
-        reinterpret_cast<float4*>(grad.quat)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-        reinterpret_cast<float4*>(grad.kads)[i] = make_float4(gk[0], gk[1], gk[2], gk[3]);
-        grad.opacity_logit[i] = glogit;
+        static_cast<float4*>(grad.quat)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        static_cast<float4*>(grad.kads)[i] = make_float4(gk[0], gk[1], gk[2], gk[3]);
+        static_cast<float*>(grad.opacity_logit)[i] = glogit;
     }
     // ---- edit gradients: global lambda, b block-reduced; per-model terms warp-reduced when the warp is
     // uniform in its model (composed models are contiguous), else per lane
@@ -499,8 +500,12 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
     }
     if (g->n > 0) {
         IVRGS_PROF("k_project_bwd", s);
-        k_project_bwd<<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1, g2, *grad,
-                                                                     edit_grad);
+        if (g->precision == IVRGS_MIXED)
+            k_project_bwd<IVRGS_MIXED><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1,
+                                                                                    g2, *grad, edit_grad);
+        else
+            k_project_bwd<IVRGS_FP32><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1,
+                                                                                   g2, *grad, edit_grad);
     }
     return cudaGetLastError();
 }

@@ -104,6 +104,9 @@ cudaError_t launch_compose(const ivrgs_gaussians* models, int32_t n_models, ivrg
                            cudaStream_t s);
 cudaError_t launch_edit_table(const ivrgs_model_edit* edits, int32_t n_models, const ivrgs_light* light,
                               float* table, cudaStream_t s);
+cudaError_t launch_morton(const ivrgs_gaussians* g, const float* lo, const float* hi, uint64_t* keys, cudaStream_t s);
+cudaError_t launch_pack_mixed(const ivrgs_gaussians* in, const uint32_t* order, ivrgs_gaussians* out,
+                              cudaStream_t s);
 cudaError_t launch_project(const ivrgs_gaussians* g, const float* table, const CamBatch& cb, float lowpass,
                            ivrgs_projected* out, cudaStream_t s);
 cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,

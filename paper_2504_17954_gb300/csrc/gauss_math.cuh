@@ -5,6 +5,9 @@
 //   Sec. 4.3: c_v = c_p + dc.  Sec. 4.5/4.6: o' = s_m sigmoid(logit), k' = lambda k + b.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace ivrgs {
@@ -25,13 +28,55 @@ struct GaussLocal {
     bool visible;
 };
 
+// attribute loads: float32 storage, or the 16-bit IVRGS_MIXED storage decoded to float32
+template <int PREC>
+__device__ __forceinline__ void load_attrs(const ivrgs_gaussians& g, long long i, float mu[3], float4& q, float ls[3],
+                                           float& logit, float dc[3], float nrm[3], float4& kk) {
+    if constexpr (PREC == IVRGS_FP32) {
+        const float* m = static_cast<const float*>(g.mean);
+        const float* s = static_cast<const float*>(g.log_scale);
+        const float* c = static_cast<const float*>(g.dcolor);
+        const float* n = static_cast<const float*>(g.normal);
+        for (int k = 0; k < 3; ++k) {
+            mu[k] = m[3 * i + k];
+            ls[k] = s[3 * i + k];
+            dc[k] = c[3 * i + k];
+            nrm[k] = n[3 * i + k];
+        }
+        q = static_cast<const float4*>(g.quat)[i];
+        kk = static_cast<const float4*>(g.kads)[i];
+        logit = static_cast<const float*>(g.opacity_logit)[i];
+    } else {
+        const __half* m = static_cast<const __half*>(g.mean);
+        const float* an = g.anchor + 3 * (i / IVRGS_ANCHOR_CHUNK);
+        const __nv_bfloat16* s = static_cast<const __nv_bfloat16*>(g.log_scale);
+        const __nv_bfloat16* c = static_cast<const __nv_bfloat16*>(g.dcolor);
+        const __nv_bfloat16* n = static_cast<const __nv_bfloat16*>(g.normal);
+        for (int k = 0; k < 3; ++k) {
+            mu[k] = __fadd_rn(__ldg(an + k), __half2float(m[3 * i + k]));  // the stored mean: anchor + offset
+            ls[k] = __bfloat162float(s[3 * i + k]);
+            dc[k] = __bfloat162float(c[3 * i + k]);
+            nrm[k] = __bfloat162float(n[3 * i + k]);
+        }
+        const uint2 qb = static_cast<const uint2*>(g.quat)[i];
+        const __half2 q01 = *reinterpret_cast<const __half2*>(&qb.x), q23 = *reinterpret_cast<const __half2*>(&qb.y);
+        q = make_float4(__low2float(q01), __high2float(q01), __low2float(q23), __high2float(q23));
+        const uint2 kb = static_cast<const uint2*>(g.kads)[i];
+        const __half2 k01 = *reinterpret_cast<const __half2*>(&kb.x), k23 = *reinterpret_cast<const __half2*>(&kb.y);
+        kk = make_float4(__low2float(k01), __high2float(k01), __low2float(k23), __high2float(k23));
+        logit = __half2float(static_cast<const __half*>(g.opacity_logit)[i]);
+    }
+}
+
+template <int PREC>
 __device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float* __restrict__ table, int n_models,
                                            long long i, GaussLocal& G) {
     G.model = g.model_id[i];
     const float* me = table + (long long)G.model * IVRGS_EDIT_STRIDE;
     G.visible = __ldg(me + 4) != 0.0f;
-    G.mu[0] = g.mean[3 * i]; G.mu[1] = g.mean[3 * i + 1]; G.mu[2] = g.mean[3 * i + 2];
-    const float4 q = reinterpret_cast<const float4*>(g.quat)[i];
+    float ls[3], dcol[3], nrm[3], logit;
+    float4 q, kk;
+    load_attrs<PREC>(g, i, G.mu, q, ls, logit, dcol, nrm, kk);
     G.qlen = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     const float iq = 1.0f / G.qlen;
     const float w = q.x * iq, x = q.y * iq, y = q.z * iq, z = q.w * iq;
@@ -39,7 +84,7 @@ __device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float
     G.Rq[0] = 1.f - 2.f * (y * y + z * z); G.Rq[1] = 2.f * (x * y - w * z); G.Rq[2] = 2.f * (x * z + w * y);
     G.Rq[3] = 2.f * (x * y + w * z); G.Rq[4] = 1.f - 2.f * (x * x + z * z); G.Rq[5] = 2.f * (y * z - w * x);
     G.Rq[6] = 2.f * (x * z - w * y); G.Rq[7] = 2.f * (y * z + w * x); G.Rq[8] = 1.f - 2.f * (x * x + y * y);
-    for (int k = 0; k < 3; ++k) G.sc[k] = expf(g.log_scale[3 * i + k]);
+    for (int k = 0; k < 3; ++k) G.sc[k] = expf(ls[k]);
     float M[9];
     for (int r = 0; r < 3; ++r)
         for (int k = 0; k < 3; ++k) M[3 * r + k] = G.Rq[3 * r + k] * G.sc[k];
@@ -49,16 +94,14 @@ __device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float
     G.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
     G.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
     G.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-    const float n0 = g.normal[3 * i], n1 = g.normal[3 * i + 1], n2 = g.normal[3 * i + 2];
-    G.nlen = sqrtf(n0 * n0 + n1 * n1 + n2 * n2);
+    G.nlen = sqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
     const float inl = 1.0f / G.nlen;
-    G.nn[0] = n0 * inl; G.nn[1] = n1 * inl; G.nn[2] = n2 * inl;
-    for (int c = 0; c < 3; ++c) G.cv[c] = __ldg(me + c) + g.dcolor[3 * i + c];
-    const float4 kk = reinterpret_cast<const float4*>(g.kads)[i];
+    G.nn[0] = nrm[0] * inl; G.nn[1] = nrm[1] * inl; G.nn[2] = nrm[2] * inl;
+    for (int c = 0; c < 3; ++c) G.cv[c] = __ldg(me + c) + dcol[c];
     G.k[0] = kk.x; G.k[1] = kk.y; G.k[2] = kk.z; G.k[3] = kk.w;
     const float* lam = table + (long long)n_models * IVRGS_EDIT_STRIDE;
     for (int c = 0; c < 4; ++c) G.kp[c] = __ldg(lam + c) * G.k[c] + __ldg(lam + 4 + c);
-    G.sig = 1.0f / (1.0f + expf(-g.opacity_logit[i]));
+    G.sig = 1.0f / (1.0f + expf(-logit));
     G.sm = __ldg(me + 3);
     G.o = G.sm * G.sig;
 }

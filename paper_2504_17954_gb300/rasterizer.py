@@ -34,7 +34,10 @@ def _check_cuda(t: torch.Tensor, name: str, dtype=torch.float32):
 # ----------------------------------------------------------------------------------------
 @dataclass
 class Gaussians:
-    """Editable Gaussians on the device, structure of arrays (Sec. 4.3 attribute set)."""
+    """Editable Gaussians on the device, structure of arrays (Sec. 4.3 attribute set).
+
+    precision 0 (float32) or 1 (16-bit storage, see ``pack_mixed``); ``anchor`` holds the
+    float32 position anchors of the 16-bit storage."""
     mean: torch.Tensor
     log_scale: torch.Tensor
     quat: torch.Tensor
@@ -44,6 +47,8 @@ class Gaussians:
     kads: torch.Tensor
     model_id: Optional[torch.Tensor]
     n_models: int
+    precision: int = 0
+    anchor: Optional[torch.Tensor] = None
 
     @property
     def n(self) -> int:
@@ -53,11 +58,12 @@ class Gaussians:
         ts = [getattr(self, k) for k in ATTRS] if tensors is None else list(tensors)
         s = N.ivrgs_gaussians()
         s.n = self.n
-        s.precision = N.IVRGS_FP32
+        s.precision = self.precision
         s.n_models = self.n_models
         for k, t in zip(ATTRS, ts):
             setattr(s, k, t.data_ptr())
         s.model_id = self.model_id.data_ptr() if self.model_id is not None else None
+        s.anchor = self.anchor.data_ptr() if self.anchor is not None else None
         return s
 
     @staticmethod
@@ -67,9 +73,39 @@ class Gaussians:
                          n_models=n_models)
 
     @staticmethod
+    def empty_mixed(n: int, n_models: int, device="cuda") -> "Gaussians":
+        h = lambda w, dt: torch.empty((n, w) if w > 1 else (n,), dtype=dt, device=device)
+        n_chunks = (n + N.IVRGS_ANCHOR_CHUNK - 1) // N.IVRGS_ANCHOR_CHUNK
+        return Gaussians(mean=h(3, torch.float16), log_scale=h(3, torch.bfloat16), quat=h(4, torch.float16),
+                         opacity_logit=h(1, torch.float16), dcolor=h(3, torch.bfloat16), normal=h(3, torch.bfloat16),
+                         kads=h(4, torch.float16), model_id=torch.empty(n, dtype=torch.int16, device=device),
+                         n_models=n_models, precision=N.IVRGS_MIXED,
+                         anchor=torch.empty((max(n_chunks, 1), 3), dtype=torch.float32, device=device))
+
+    @staticmethod
     def from_arrays(arrs: dict, n_models: int = 1, device="cuda") -> "Gaussians":
         t = lambda a: torch.as_tensor(a, dtype=torch.float32).to(device).contiguous()
         return Gaussians(*(t(arrs[k]) for k in ATTRS), model_id=None, n_models=n_models)
+
+
+def pack_mixed(g: Gaussians, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), stream=None):
+    """16-bit storage of float32 Gaussians (ivrgs_morton_keys + ivrgs_pack_mixed).
+
+    The Gaussians are reordered by (model, Morton code inside the box [lo, hi]) so that every
+    chunk of 256 is spatially compact; the permutation (a one-time model preparation, sorted
+    with torch) is returned with the packed set: packed[k] = g[order[k]]."""
+    if g.precision != N.IVRGS_FP32:
+        raise ValueError("pack_mixed takes float32 Gaussians")
+    dev = g.mean.device
+    keys = torch.empty(g.n, dtype=torch.int64, device=dev)
+    lo_c, hi_c = (C.c_float * 3)(*lo), (C.c_float * 3)(*hi)
+    gs = g.struct()
+    N.ivrgs_morton_keys(C.byref(gs), lo_c, hi_c, _vp(keys), _stream(stream))
+    order = torch.argsort(keys, stable=True).to(torch.int32)
+    out = Gaussians.empty_mixed(g.n, g.n_models, dev)
+    os_ = out.struct()
+    N.ivrgs_pack_mixed(C.byref(gs), _vp(order), C.byref(os_), _stream(stream))
+    return out, order
 
 
 def edit_structs(palette, opacity_scale, visible, lam, bias):

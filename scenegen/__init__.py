@@ -431,3 +431,71 @@ def synthetic_projected(sizes, n: int, seed: int, tie_frac: float = 0.3, max_rad
         d[tie] = r.choice(np.array([1.0, 2.5, 3.0, 3.25]), tie.sum())
         depth[v] = d
     return xy, rad, depth
+
+
+# ----------------------------------------------------------------------------------------
+# 16-bit storage encoding (an input format, not a step of the rendering method)
+# ----------------------------------------------------------------------------------------
+ANCHOR_CHUNK = 256
+
+
+def _spread10(x):
+    x = x.astype(np.uint32) & np.uint32(0x3FF)
+    x = (x | (x << np.uint32(16))) & np.uint32(0x030000FF)
+    x = (x | (x << np.uint32(8))) & np.uint32(0x0300F00F)
+    x = (x | (x << np.uint32(4))) & np.uint32(0x030C30C3)
+    x = (x | (x << np.uint32(2))) & np.uint32(0x09249249)
+    return x
+
+
+def to_bf16_bits(a) -> np.ndarray:
+    """float32 -> bfloat16 bit patterns, round to nearest even (finite inputs)."""
+    b = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    r = (b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    return r.astype(np.uint16)
+
+
+def bf16_bits_to_f32(bits) -> np.ndarray:
+    return (np.asarray(bits, np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32)
+
+
+def pack_mixed_arrays(mean, log_scale, quat, opacity_logit, dcolor, normal, kads, model_id,
+                      lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0)):
+    """The 16-bit storage of concatenated float32 attributes: reorder by (model id, Morton code
+    of the mean in the box [lo, hi], index), one float32 anchor per chunk of 256 at the centre
+    of the chunk's bounding box, FP16 mean offsets, BF16 log-scale / colour offset / normal,
+    FP16 quaternion / opacity logit / k. Returns (dict of arrays, order)."""
+    f = lambda a: np.ascontiguousarray(a, np.float32)
+    mean, log_scale, quat, dcolor, normal, kads = map(f, (mean, log_scale, quat, dcolor, normal, kads))
+    opacity_logit = f(opacity_logit)
+    lo32, hi32 = np.asarray(lo, np.float32), np.asarray(hi, np.float32)
+    inv = (np.float32(1.0) / (hi32 - lo32)).astype(np.float32)
+    q = np.clip((mean - lo32) * inv * np.float32(1024.0), np.float32(0.0), np.float32(1023.0)).astype(np.uint32)
+    code = (_spread10(q[:, 0]) << np.uint32(2)) | (_spread10(q[:, 1]) << np.uint32(1)) | _spread10(q[:, 2])
+    key = (np.asarray(model_id).astype(np.uint64) << np.uint64(30)) | code.astype(np.uint64)
+    order = np.argsort(key, kind="stable")
+    n = len(order)
+    m = mean[order]
+    n_chunks = (n + ANCHOR_CHUNK - 1) // ANCHOR_CHUNK
+    anchor = np.zeros((max(n_chunks, 1), 3), np.float32)
+    off = np.zeros((n, 3), np.float16)
+    for c in range(n_chunks):
+        sl = slice(c * ANCHOR_CHUNK, min(n, (c + 1) * ANCHOR_CHUNK))
+        a = (np.float32(0.5) * (m[sl].min(0) + m[sl].max(0))).astype(np.float32)
+        anchor[c] = a
+        off[sl] = (m[sl] - a).astype(np.float32).astype(np.float16)
+    out = dict(mean=off, anchor=anchor, log_scale=to_bf16_bits(log_scale[order]), quat=quat[order].astype(np.float16),
+               opacity_logit=opacity_logit[order].astype(np.float16), dcolor=to_bf16_bits(dcolor[order]),
+               normal=to_bf16_bits(normal[order]), kads=kads[order].astype(np.float16),
+               model_id=np.asarray(model_id)[order].astype(np.int16))
+    return out, order
+
+
+def decode_mixed_arrays(p):
+    """Float32 values of the 16-bit storage: mean = float32(anchor + offset), the rest widened."""
+    n = p["mean"].shape[0]
+    anchor = np.repeat(p["anchor"], ANCHOR_CHUNK, 0)[:n]
+    return dict(mean=(anchor + p["mean"].astype(np.float32)).astype(np.float32),
+                log_scale=bf16_bits_to_f32(p["log_scale"]), quat=p["quat"].astype(np.float32),
+                opacity_logit=p["opacity_logit"].astype(np.float32), dcolor=bf16_bits_to_f32(p["dcolor"]),
+                normal=bf16_bits_to_f32(p["normal"]), kads=p["kads"].astype(np.float32))
