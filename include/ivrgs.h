@@ -268,6 +268,19 @@ ivrgs_status ivrgs_morton_keys(const ivrgs_gaussians* g, const float* lo, const 
 ivrgs_status ivrgs_pack_mixed(const ivrgs_gaussians* in, const uint32_t* d_order, ivrgs_gaussians* out,
                               void* stream);
 
+/* ivrgs_render_backward that ADDS its gradients to grad and to the first
+   ivrgs_edit_table_floats(n_models) floats of d_edit_grad (the per-view light gradients of
+   this call's cameras, which follow, are overwritten) instead of overwriting them: the
+   backward of a set of views rendered in several calls (view waves, when one call would
+   exceed IVRGS_MAX_PAIRS pairs or IVRGS_MAX_VIEWS views) is the sum of the calls' backwards
+   (Sec. 3 Eq. C is per pixel; the views share only the Gaussians). Same arguments otherwise. */
+ivrgs_status ivrgs_render_backward_accumulate(const ivrgs_gaussians* g, const float* d_edit_table,
+                                              const ivrgs_projected* p, const ivrgs_bins* b, const ivrgs_camera* cams,
+                                              int32_t n_views, float lowpass, const float* bg, const float* d_final_T,
+                                              const uint32_t* d_last, const float* d_dL_drgba, void* d_workspace,
+                                              size_t ws_bytes, ivrgs_gaussians* grad, float* d_edit_grad,
+                                              void* stream);
+
 /* Bytes of the device array that ivrgs_render_backward_static uses as its scratch. */
 #define IVRGS_STATIC_SCRATCH_BYTES ((size_t)32 << 20)
 

@@ -90,6 +90,10 @@ _SIGNATURES = {
                                           _P(ivrgs_camera), C.c_int32, C.c_float, _P(C.c_float), C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, _P(ivrgs_gaussians),
                                           C.c_void_p, C.c_void_p]),
+    "ivrgs_render_backward_accumulate": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_projected),
+                                                     _P(ivrgs_bins), _P(ivrgs_camera), C.c_int32, C.c_float,
+                                                     _P(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                     C.c_size_t, _P(ivrgs_gaussians), C.c_void_p, C.c_void_p]),
     "ivrgs_render_backward_static": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_projected),
                                                  _P(ivrgs_bins), _P(ivrgs_camera), C.c_int32, C.c_float,
                                                  _P(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p,
@@ -192,6 +196,12 @@ def ivrgs_render_backward(g, d_edit_table, p, b, cams, n_views, lowpass, bg, d_f
                           grad, d_edit_grad, stream):
     return call("ivrgs_render_backward", g, d_edit_table, p, b, cams, n_views, lowpass, bg, d_final_T, d_last, d_dL,
                 ws, ws_bytes, grad, d_edit_grad, stream)
+
+
+def ivrgs_render_backward_accumulate(g, d_edit_table, p, b, cams, n_views, lowpass, bg, d_final_T, d_last, d_dL,
+                                     ws, ws_bytes, grad, d_edit_grad, stream):
+    return call("ivrgs_render_backward_accumulate", g, d_edit_table, p, b, cams, n_views, lowpass, bg, d_final_T,
+                d_last, d_dL, ws, ws_bytes, grad, d_edit_grad, stream)
 
 
 def ivrgs_render_backward_static(g, d_edit_table, p, b, cams, n_views, lowpass, bg, d_final_T, d_last, d_dL, grad,

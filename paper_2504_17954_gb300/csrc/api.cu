@@ -344,7 +344,7 @@ ivrgs_status ivrgs_render_backward_workspace(int64_t n, int32_t n_views, size_t*
     return IVRGS_OK;
 }
 
-ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
+static ivrgs_status render_backward_impl(int accumulate, const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
                                    const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float lowpass,
                                    const float* bg, const float* d_final_T, const uint32_t* d_last,
                                    const float* d_dL_drgba, void* d_workspace, size_t ws_bytes,
@@ -371,9 +371,28 @@ ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit
     }
     if (!aligned(d_workspace, 256)) return invalid("workspace must be 256-byte aligned");
     return cuda_status(launch_render_backward(g, d_edit_table, p, b, cb, lowpass, bg, d_final_T, d_last, d_dL_drgba,
-                                              static_cast<char*>(d_workspace), grad, d_edit_grad,
+                                              static_cast<char*>(d_workspace), grad, d_edit_grad, accumulate,
                                               (cudaStream_t)stream),
                        "ivrgs_render_backward");
+}
+
+ivrgs_status ivrgs_render_backward(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
+                                   const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float lowpass,
+                                   const float* bg, const float* d_final_T, const uint32_t* d_last,
+                                   const float* d_dL_drgba, void* d_workspace, size_t ws_bytes,
+                                   ivrgs_gaussians* grad, float* d_edit_grad, void* stream) {
+    return render_backward_impl(0, g, d_edit_table, p, b, cams, n_views, lowpass, bg, d_final_T, d_last, d_dL_drgba,
+                                d_workspace, ws_bytes, grad, d_edit_grad, stream);
+}
+
+ivrgs_status ivrgs_render_backward_accumulate(const ivrgs_gaussians* g, const float* d_edit_table,
+                                              const ivrgs_projected* p, const ivrgs_bins* b, const ivrgs_camera* cams,
+                                              int32_t n_views, float lowpass, const float* bg, const float* d_final_T,
+                                              const uint32_t* d_last, const float* d_dL_drgba, void* d_workspace,
+                                              size_t ws_bytes, ivrgs_gaussians* grad, float* d_edit_grad,
+                                              void* stream) {
+    return render_backward_impl(1, g, d_edit_table, p, b, cams, n_views, lowpass, bg, d_final_T, d_last, d_dL_drgba,
+                                d_workspace, ws_bytes, grad, d_edit_grad, stream);
 }
 
 }  // extern "C"

@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
                                                      const __grid_constant__ CamBatch cb, float lowpass,
                                                      const float4* __restrict__ g0, const float4* __restrict__ g1,
                                                      const float* __restrict__ g2, const ivrgs_gaussians grad,
-                                                     float* __restrict__ egrad) {
+                                                     float* __restrict__ egrad, int accumulate) {
     __shared__ float s_red[8][8];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = g.n;
@@ -421,15 +421,34 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
                 dcp[k] = dcv[k];
             }
         }
-        for (int k = 0; k < 3; ++k) {
-            static_cast<float*>(grad.mean)[3 * i + k] = gm[k];
-            static_cast<float*>(grad.log_scale)[3 * i + k] = gls[k];
-            static_cast<float*>(grad.dcolor)[3 * i + k] = gdc[k];
-            static_cast<float*>(grad.normal)[3 * i + k] = gn[k];
+        float* gmn = static_cast<float*>(grad.mean);
+        float* gsc = static_cast<float*>(grad.log_scale);
+        float* gco = static_cast<float*>(grad.dcolor);
+        float* gno = static_cast<float*>(grad.normal);
+        float4* gqu = static_cast<float4*>(grad.quat);
+        float4* gka = static_cast<float4*>(grad.kads);
+        float* glo = static_cast<float*>(grad.opacity_logit);
+        if (accumulate) {  // add to the gradients of earlier view waves
+            for (int k = 0; k < 3; ++k) {
+                gm[k] += gmn[3 * i + k];
+                gls[k] += gsc[3 * i + k];
+                gdc[k] += gco[3 * i + k];
+                gn[k] += gno[3 * i + k];
+            }
+            const float4 a4 = gqu[i], b4 = gka[i];
+            gq[0] += a4.x; gq[1] += a4.y; gq[2] += a4.z; gq[3] += a4.w;
+            gk[0] += b4.x; gk[1] += b4.y; gk[2] += b4.z; gk[3] += b4.w;
+            glogit += glo[i];
         }
-        static_cast<float4*>(grad.quat)[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
-        static_cast<float4*>(grad.kads)[i] = make_float4(gk[0], gk[1], gk[2], gk[3]);
-        static_cast<float*>(grad.opacity_logit)[i] = glogit;
+        for (int k = 0; k < 3; ++k) {
+            gmn[3 * i + k] = gm[k];
+            gsc[3 * i + k] = gls[k];
+            gco[3 * i + k] = gdc[k];
+            gno[3 * i + k] = gn[k];
+        }
+        gqu[i] = make_float4(gq[0], gq[1], gq[2], gq[3]);
+        gka[i] = make_float4(gk[0], gk[1], gk[2], gk[3]);
+        glo[i] = glogit;
     }
     // ---- edit gradients: global lambda, b block-reduced; per-model terms warp-reduced when the warp is
     // uniform in its model (composed models are contiguous), else per lane
@@ -471,7 +490,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
 cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table, const ivrgs_projected* p,
                                    const ivrgs_bins* b, const CamBatch& cb, float lowpass, const float* bg,
                                    const float* final_T, const uint32_t* last, const float* dL, char* ws,
-                                   ivrgs_gaussians* grad, float* edit_grad, cudaStream_t s) {
+                                   ivrgs_gaussians* grad, float* edit_grad, int accumulate, cudaStream_t s) {
     const long long vn = p->n * (long long)cb.n;
     float4* g0 = reinterpret_cast<float4*>(ws);
     float4* g1 = g0 + vn;
@@ -479,7 +498,10 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
     cudaError_t e;
     if ((e = cudaMemsetAsync(ws, 0, (size_t)vn * 36, s)) != cudaSuccess) return e;
     const long long ne = (long long)g->n_models * IVRGS_EDIT_STRIDE + 8 + 4ll * cb.n;
-    if ((e = cudaMemsetAsync(edit_grad, 0, sizeof(float) * (size_t)ne, s)) != cudaSuccess) return e;
+    // the per-view light gradients (the tail) always start at zero; the edit gradients only
+    // when not accumulating over view waves
+    const long long ne0 = accumulate ? (long long)g->n_models * IVRGS_EDIT_STRIDE + 8 : 0;
+    if ((e = cudaMemsetAsync(edit_grad + ne0, 0, sizeof(float) * (size_t)(ne - ne0), s)) != cudaSuccess) return e;
     if (cb.n_tiles > 0) {
         IVRGS_PROF("k_render_bwd", s);
         const float2* xy = reinterpret_cast<const float2*>(p->xy);
@@ -502,10 +524,10 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
         IVRGS_PROF("k_project_bwd", s);
         if (g->precision == IVRGS_MIXED)
             k_project_bwd<IVRGS_MIXED><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1,
-                                                                                    g2, *grad, edit_grad);
+                                                                                    g2, *grad, edit_grad, accumulate);
         else
             k_project_bwd<IVRGS_FP32><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1,
-                                                                                   g2, *grad, edit_grad);
+                                                                                   g2, *grad, edit_grad, accumulate);
     }
     return cudaGetLastError();
 }

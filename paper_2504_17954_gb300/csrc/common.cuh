@@ -118,6 +118,6 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
 cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table, const ivrgs_projected* p,
                                    const ivrgs_bins* b, const CamBatch& cb, float lowpass, const float* bg,
                                    const float* final_T, const uint32_t* last, const float* dL, char* ws,
-                                   ivrgs_gaussians* grad, float* edit_grad, cudaStream_t s);
+                                   ivrgs_gaussians* grad, float* edit_grad, int accumulate, cudaStream_t s);
 
 }  // namespace ivrgs

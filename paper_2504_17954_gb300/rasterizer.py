@@ -275,7 +275,7 @@ class Rasterizer:
         return self.render(stream)
 
     def backward(self, g: Gaussians, edit_table: torch.Tensor, dL_drgba: torch.Tensor, grad: Optional[Gaussians] = None,
-                 stream=None, tensors=None):
+                 stream=None, tensors=None, accumulate: bool = False, edit_grad: Optional[torch.Tensor] = None):
         _check_cuda(dL_drgba, "dL_drgba")
         if self.ws_bwd is None:
             self.ws_bwd = torch.empty(self.ws_bwd_bytes, dtype=torch.uint8, device=self.device)
@@ -285,11 +285,12 @@ class Rasterizer:
         gs = g.struct(tensors)
         gr = grad.struct()
         p, b = self.projected_struct(), self.bins_struct()
-        N.ivrgs_render_backward(C.byref(gs), _vp(edit_table), C.byref(p), C.byref(b), self.cam_arr, self.V,
-                                self.lowpass, self.bg, _vp(self.final_T), _vp(self.last), _vp(dL_drgba),
-                                _vp(self.ws_bwd), self.ws_bwd_bytes, C.byref(gr), _vp(self.edit_grad),
-                                _stream(stream))
-        return grad, self.edit_grad
+        eg = self.edit_grad if edit_grad is None else edit_grad
+        fn = N.ivrgs_render_backward_accumulate if accumulate else N.ivrgs_render_backward
+        fn(C.byref(gs), _vp(edit_table), C.byref(p), C.byref(b), self.cam_arr, self.V, self.lowpass, self.bg,
+           _vp(self.final_T), _vp(self.last), _vp(dL_drgba), _vp(self.ws_bwd), self.ws_bwd_bytes, C.byref(gr),
+           _vp(eg), _stream(stream))
+        return grad, eg
 
     # -- CUDA graphs
     def capture(self, g: Gaussians, edit_table: torch.Tensor, dL_drgba: Optional[torch.Tensor] = None,
@@ -331,6 +332,54 @@ class Rasterizer:
         c = self.cams[v]
         off = self.cam_arr[v].pix_offset
         return t[off:off + c.W * c.H].view(c.H, c.W, *t.shape[1:])
+
+
+# ----------------------------------------------------------------------------------------
+class WaveRasterizer:
+    """Many views rendered in waves of at most ``max_views`` views and ``pixel_budget`` pixels
+    (so that no binning call exceeds the library's per-call pair limit); the backward sums the
+    waves' gradients with ivrgs_render_backward_accumulate. Each wave owns a Rasterizer."""
+
+    def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", lowpass: float = 0.3,
+                 bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20):
+        self.cams = list(cams)
+        self.waves: List[List[int]] = []
+        cur, pix = [], 0
+        for v, c in enumerate(self.cams):
+            if cur and (len(cur) >= max_views or pix + c.W * c.H > pixel_budget):
+                self.waves.append(cur)
+                cur, pix = [], 0
+            cur.append(v)
+            pix += c.W * c.H
+        if cur:
+            self.waves.append(cur)
+        self.rasts = [Rasterizer([self.cams[v] for v in wv], n_gaussians, n_models, device=device, lowpass=lowpass,
+                                 bg=bg) for wv in self.waves]
+        self.n_models = n_models
+        self.V = len(self.cams)
+
+    def forward(self, g: Gaussians, edit_table: torch.Tensor, mode: str = "exact"):
+        for r in self.rasts:
+            r.forward(g, edit_table, mode=mode)
+
+    def backward(self, g: Gaussians, edit_table: torch.Tensor, dL_per_wave: Sequence[torch.Tensor],
+                 grad: Optional[Gaussians] = None):
+        """dL_per_wave[k]: packed dL/dRGBA of wave k's views. Returns (grad, gradient of the
+        edit table, per-view light gradients [V, 3]); the waves' contributions are summed."""
+        ne = edit_table.numel()
+        dev = self.rasts[0].device
+        eg = torch.empty(ne + 4 * max(len(wv) for wv in self.waves), dtype=torch.float32, device=dev)
+        light = torch.zeros((self.V, 3), dtype=torch.float32, device=dev)
+        for k, (r, wv) in enumerate(zip(self.rasts, self.waves)):
+            grad, _ = r.backward(g, edit_table, dL_per_wave[k], grad=grad, accumulate=k > 0, edit_grad=eg)
+            light[wv] = eg[ne:ne + 4 * len(wv)].view(len(wv), 4)[:, :3]
+        return grad, eg[:ne], light
+
+    def view_image(self, v: int) -> torch.Tensor:
+        for r, wv in zip(self.rasts, self.waves):
+            if v in wv:
+                return r.view_image(wv.index(v))
+        raise IndexError(v)
 
 
 # ----------------------------------------------------------------------------------------
