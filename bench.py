@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--profile-only", action="store_true", help="run warmup + 2 steps, print nothing else")
     ap.add_argument("--opt", action="append", default=[], help="library option name=value (launch shapes)")
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of CUDA-graph replays")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage and single-view forms")
     ap.add_argument("--autotune", action="store_true", help="pick launch shapes by timing (cached per GPU)")
     return ap.parse_args()
 
@@ -142,13 +143,127 @@ def kernel_work(name, w, stats):
 
 
 # ------------------------------------------------------------------------------------ GPU arm
+class Harness:
+    """Buffers, CUDA graphs and timing of the fwd+bwd step for one workload and one storage."""
+
+    def __init__(self, args, w, comp, table, dev, world, graphs=True):
+        import torch
+
+        from paper_2504_17954_gb300 import Gaussians, Rasterizer
+        self.args, self.w, self.comp, self.table, self.dev, self.world = args, w, comp, table, dev, world
+        self.ed = w.edits
+        self.rast = Rasterizer(w.cameras, comp.n, len(w.models), device=dev, lowpass=w.lowpass, bg=w.bg)
+        self.rast.forward(comp, table, mode="exact")  # sizes the pair buffer
+        torch.cuda.synchronize()
+        self.n_pairs = self.rast.n_pairs
+        self.rast._ensure_capacity(int(self.n_pairs * 1.1) + 4096)
+        gen = torch.Generator(device=dev).manual_seed(4)
+        self.dL = torch.randn((self.rast.n_pix, 4), generator=gen, device=dev, dtype=torch.float32) * 1e-3
+        self.grad = Gaussians.empty(comp.n, len(w.models), dev)
+        self.grad.model_id = None
+        self.flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        self.stream = torch.cuda.current_stream()
+        for _ in range(max(3, args.warmup)):
+            self.step()
+        torch.cuda.synchronize()
+        self.graphs = {}
+        if graphs and not args.eager:
+            self.graphs[True] = self.rast.capture(comp, table, self.dL, grad=self.grad)
+            self.graphs[False] = self.rast.capture(comp, table)
+
+    def edit(self):
+        from paper_2504_17954_gb300 import compose_edit
+        ed = self.ed
+        compose_edit(None, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias, device=self.dev,
+                     edit_table=self.table)
+
+    def step(self, backward=True):
+        """Eager: edit table, projection, binning (CAPACITY mode), compositing, backward."""
+        self.edit()
+        self.rast.forward(self.comp, self.table, mode="capacity")
+        if backward:
+            self.rast.backward(self.comp, self.table, self.dL, grad=self.grad)
+
+    def run_step(self, backward):
+        if self.graphs:
+            self.edit()
+            self.graphs[backward].replay()
+        else:
+            self.step(backward)
+
+    def timed(self, k, backward, prof=False):
+        """Device ms of k steps (L2 flushed between steps, outside the timed events), max over ranks."""
+        import torch
+
+        from paper_2504_17954_gb300 import _native as N
+        world = self.world
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        if prof:
+            N.prof_report()
+            N.prof_enable(True)
+        for _ in range(k):
+            self.flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            if prof:
+                self.step(backward)  # eager launches, each bracketed by the library's events
+            else:
+                self.run_step(backward)
+            b.record(self.stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        rep = {}
+        if prof:
+            N.prof_enable(False)
+            rep = N.prof_report()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        t = torch.tensor([ms], dtype=torch.float64, device=self.dev)
+        if world > 1:
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        if int(self.rast.d_n_pairs.item()) > self.rast.capacity:
+            raise RuntimeError("pair buffer overflow during the timed steps")
+        return float(t.item()), rep
+
+    def mpix(self, ms, k):
+        return self.rast.n_pix * self.world * k / (ms / 1e3) / 1e6
+
+
+def source_hash():
+    """Hash of the CUDA sources: ncu traffic figures are used only for the build they came from."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2504_17954_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it matches this build."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("traffic-json: "):
+            d = json.loads(line[len("traffic-json: "):])
+            if d.get("source_hash") == source_hash():
+                return d["kernels"].get(kernel)
+    return None
+
+
 def run_gpu(args, rank, world):
-    import numpy as np
     import torch
 
     from paper_2504_17954_gb300 import _native as N
     from paper_2504_17954_gb300 import build as B
-    from paper_2504_17954_gb300 import Gaussians, Rasterizer, compose_edit
+    from paper_2504_17954_gb300 import Gaussians, compose_edit, pack_mixed
 
     B.build()
     opts = {}
@@ -161,108 +276,61 @@ def run_gpu(args, rank, world):
     torch.cuda.set_device(dev)
     w = workload(args.workload)
     ed = w.edits
-    models = [Gaussians.from_arrays({k: getattr(m, k) for k in
-                                     ("mean", "log_scale", "quat", "opacity_logit", "dcolor", "normal", "kads")},
-                                    device=dev) for m in w.models]
+    attrs = ("mean", "log_scale", "quat", "opacity_logit", "dcolor", "normal", "kads")
+    models = [Gaussians.from_arrays({k: getattr(m, k) for k in attrs}, device=dev) for m in w.models]
     comp, table = compose_edit(models, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias, device=dev)
     del models
-    rast = Rasterizer(w.cameras, comp.n, len(w.models), device=dev, lowpass=w.lowpass, bg=w.bg)
-    rast.forward(comp, table, mode="exact")  # sizes the pair buffer
-    torch.cuda.synchronize()
-    n_pairs = rast.n_pairs
-    rast._ensure_capacity(int(n_pairs * 1.1) + 4096)
-    gen = torch.Generator(device=dev).manual_seed(4)
-    dL = torch.randn((rast.n_pix, 4), generator=gen, device=dev, dtype=torch.float32) * 1e-3
-    grad = Gaussians.empty(comp.n, len(w.models), dev)
-    grad.model_id = None
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def step(backward=True):
-        compose_edit(None, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias, device=dev,
-                     edit_table=table)
-        rast.forward(comp, table, mode="capacity")
-        if backward:
-            rast.backward(comp, table, dL, grad=grad)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
     if args.profile_only:  # a short run for profilers: warm-up plus one step, no report
-        step()
+        h = Harness(args, w, comp, table, dev, world, graphs=False)
+        h.step()
         torch.cuda.synchronize()
         return None
-    if int(rast.d_n_pairs.item()) > rast.capacity:
-        raise RuntimeError("pair buffer overflow")
+    h = Harness(args, w, comp, table, dev, world)
+    rast, n_pairs = h.rast, h.n_pairs
     evals = float(rast.last.double().sum().item())
-
     if args.autotune:
         from paper_2504_17954_gb300 import autotune
-        autotune.tune(lambda: step(True), f"{args.workload}|n={comp.n}|pairs~{n_pairs // 1000000}M")
+        autotune.tune(lambda: h.step(True), f"{args.workload}|n={comp.n}|pairs~{n_pairs // 1000000}M")
         for k in opts:
             opts[k] = N.ivrgs_get_option(k)
-    graphs = {}
-    if not args.eager:
-        graphs[True] = rast.capture(comp, table, dL, grad=grad)
-        graphs[False] = rast.capture(comp, table)
-
-    def run_step(backward):
-        compose_edit(None, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias, device=dev, edit_table=table)
-        if graphs:
-            graphs[backward].replay()
-        else:
-            rast.forward(comp, table, mode="capacity")
-            if backward:
-                rast.backward(comp, table, dL, grad=grad)
-
-    def timed(k, backward, prof=False):
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        evs = []
-        if prof:
-            N.prof_report()
-            N.prof_enable(True)
-        for _ in range(k):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            if prof:
-                step(backward)  # eager launches, each bracketed by the library's events
-            else:
-                run_step(backward)
-            b.record(stream)
-            evs.append((a, b))
-        torch.cuda.synchronize()
-        rep = {}
-        if prof:
-            N.prof_enable(False)
-            rep = N.prof_report()
-        if world > 1:
-            torch.distributed.barrier()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item()), rep
-
+        h = Harness(args, w, comp, table, dev, world)
+        rast = h.rast
     for _ in range(2):
-        run_step(True)
+        h.run_step(True)
+    K = args.steps
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
-    ms_total, _ = timed(args.steps, True)
-    ms_fwd_total, _ = timed(args.steps, False)
-    ms_eager, kernels = timed(args.steps, True, prof=True)
+    ms_total, _ = h.timed(K, True)
+    ms_fwd_total, _ = h.timed(K, False)
+    ms_eager, kernels = h.timed(K, True, prof=True)
     clocks = sampler.stop()
-    if int(rast.d_n_pairs.item()) > rast.capacity:
-        raise RuntimeError("pair buffer overflow during the timed steps")
-    K = args.steps
-    pix_all = rast.n_pix * world
-    value = pix_all * K / (ms_total / 1e3) / 1e6
-    fwd_value = pix_all * K / (ms_fwd_total / 1e3) / 1e6
+    value, fwd_value = h.mpix(ms_total, K), h.mpix(ms_fwd_total, K)
 
-    # roofline of the dominant kernel (largest share of device time in the timed steps)
+    # the batched form with 16-bit attribute storage, same workload
+    mixed = None
+    if not args.no_mixed:
+        packed, _ = pack_mixed(comp)
+        hm = Harness(args, w, packed, table, dev, world)
+        mm, _ = hm.timed(K, True)
+        mf, _ = hm.timed(K, False)
+        mixed = {"mpix_s": hm.mpix(mm, K), "fwd_mpix_s": hm.mpix(mf, K), "ms_per_step": mm / K,
+                 "storage": "FP16 mean offsets from per-256 FP32 anchors, BF16 log-scale/dc/normal, FP16 q/o/k",
+                 "bytes_per_gaussian": 44}
+        del hm, packed
+    # the plain single-view form (500k Gaussians, one 800x800 view, float32)
+    single = None
+    if not args.no_mixed and args.workload == "cfg4":
+        ws = workload("cfg2")
+        ms_ = [Gaussians.from_arrays({k: getattr(m, k) for k in attrs}, device=dev) for m in ws.models]
+        c2, t2 = compose_edit(ms_, ws.edits.palette, ws.edits.opacity_scale, ws.edits.visible, ws.edits.lam,
+                              ws.edits.bias, device=dev)
+        h2 = Harness(args, ws, c2, t2, dev, world)
+        sm, _ = h2.timed(K, True)
+        sf, _ = h2.timed(K, False)
+        single = {"workload": ws.name, "mpix_s": h2.mpix(sm, K), "fwd_mpix_s": h2.mpix(sf, K), "ms_per_step": sm / K}
+        del h2
+
+    # roofline of the dominant kernel (largest share of device time in the eager timed steps)
     pk = peaks()
     stats = {"n": comp.n, "V": len(w.cameras), "pairs": n_pairs, "evals": evals}
     kern_table = {}
@@ -273,23 +341,21 @@ def run_gpu(args, rank, world):
     per_launch_s = tot / cnt / 1e3
     wk = kernel_work(dom, w, stats)
     launches_per_step = sum(c for c, _ in kernels.values()) / K
-    if dom == "k_onesweep":
-        per_launch_s = tot / cnt / 1e3  # one launch = one 8-bit pass over all pairs
+    traffic = recorded_traffic(dom, args.workload)
     if wk is None:
         roof = {"bound": None, "kernel": dom}
     elif wk[0] == "hbm":
         ach = wk[1] / per_launch_s / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "peak_source": pk["source"], "traffic": None}
+                "frac": ach / pk["hbm_gbs"], "peak_source": pk["source"], "traffic": traffic}
     else:
         peak = N_SM * FP32_LANES * pk["sm_max_mhz"] * 1e6 / 1e12
         ach = wk[1] / per_launch_s / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "Top/s (FP32 lane ops)",
                 "frac": ach / peak, "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x {pk['sm_max_mhz']:.0f} MHz",
-                "traffic": None}
+                "traffic": traffic}
     roof["work_per_launch"] = wk[1] if wk else None
     roof["timing"] = "per-kernel CUDA events (library, launching stream) over K eager steps"
-
     roof["evaluated_entries_per_launch"] = evals
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -301,12 +367,13 @@ def run_gpu(args, rank, world):
                       "parallelism": f"replicas x{world}"},
            "fwd_mpix_s": fwd_value, "fwd_ms_per_step": ms_fwd_total / K,
            "launch": "eager" if args.eager else "cuda-graph replay",
-           "eager_mpix_s": pix_all * K / (ms_eager / 1e3) / 1e6,
+           "eager_mpix_s": h.mpix(ms_eager, K),
            "roofline": roof, "kernels": kern_table, "clocks": clocks,
+           "batched_mixed": mixed, "plain_single_view": single, "source_hash": source_hash(),
            "gpu_launches": int(round(launches_per_step * K))}
 
     if not args.no_e2e:
-        out["e2e"] = e2e(rast, comp, table, w, ed, dL, grad, K, dev, world)
+        out["e2e"] = e2e(rast, comp, table, w, ed, h.dL, h.grad, K, dev, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w)
     return out
