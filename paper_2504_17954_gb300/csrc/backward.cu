@@ -65,7 +65,6 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
-    __shared__ float4 s_box[kBatch];
     __shared__ long long s_gi[kBatch];
     __shared__ unsigned s_max;
     const long long tile = blockIdx.x;
@@ -78,11 +77,6 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     const float fx = (float)px + 0.5f;
     const int q0 = py0 & 3;                               // offset of this thread's first row in its group
     const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
-    // pixel-centre bounds of this warp's band: 16 columns x (32 P / 16) rows
-    const int band_rows = 32 * P / kTile;
-    const float wx0 = (float)(tx * kTile) + 0.5f, wx1 = wx0 + (float)(kTile - 1);
-    const float wy0 = (float)(ty * kTile + ((int)(threadIdx.x >> 5) * band_rows)) + 0.5f;
-    const float wy1 = wy0 + (float)(band_rows - 1);
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
     const int lane = threadIdx.x & 31;
@@ -128,22 +122,16 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
                 long long gi = vbase + g;
                 float4 sa, sb;
                 float2 sc;
-                float4 box;
                 if (g < (unsigned long long)n) {
-                    const float2 m = xy[gi];
-                    const float4 co = conic_o[gi];
-                    stage_gaussian(m, co, rgbd[gi], sa, sb, sc);
-                    box = cutoff_box(m, co);
+                    stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
                 } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
                     gi = vbase;
                     stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
                                    sa, sb, sc);
-                    box = make_float4(1.f, -1.f, 1.f, -1.f);
                 }
                 s_a[slot] = sa;
                 s_b[slot] = sb;
                 s_c[slot] = sc;
-                s_box[slot] = box;
                 s_gi[slot] = gi;
             }
         }
@@ -153,9 +141,6 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
         const int cnt = b_end - b_start;
         for (int j = j0; j < cnt; ++j) {
             const int ee = b_end - 1 - j;
-            const float4 bx = s_box[j];
-            // the whole warp skips a Gaussian whose cut-off box misses its pixel band
-            if (bx.y < wx0 || bx.x > wx1 || bx.w < wy0 || bx.z > wy1) continue;
             const float4 a = s_a[j];
             const float4 bb = s_b[j];
             const float2 cc = s_c[j];

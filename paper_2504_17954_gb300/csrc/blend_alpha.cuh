@@ -19,22 +19,6 @@ __device__ __forceinline__ void stage_gaussian(const float2 m, const float4 co, 
     sc = make_float2(cd.z, co.w > 0.0f ? thr : INFINITY);
 }
 
-// Axis-aligned box (x0, x1, y0, y1) outside which o' G < 1/255 for certain: the ellipse
-// d^T conic d <= 2 ln(255 o') has half-widths sqrt(2 ln(255 o') Sigma'_xx) and
-// sqrt(2 ln(255 o') Sigma'_yy), with Sigma' = conic^-1; the box is widened by 1% + 0.05 px so
-// that float32 rounding cannot make it miss a pixel that passes the cut-off. Empty (inverted)
-// when o' <= 1/255.
-__device__ __forceinline__ float4 cutoff_box(const float2 m, const float4 co) {
-    const float l = 2.0f * logf(255.0f * co.w);
-    if (!(l > 0.0f)) return make_float4(1.0f, -1.0f, 1.0f, -1.0f);
-    const float det = co.x * co.z - co.y * co.y;
-    // no cull unless the determinant is far from cancellation (relative to the products)
-    if (!(det > 1e-4f * co.x * co.z)) return make_float4(-INFINITY, INFINITY, -INFINITY, INFINITY);
-    const float ex = sqrtf(fmaxf(l * co.z / det, 0.0f)) * 1.01f + 0.05f;
-    const float ey = sqrtf(fmaxf(l * co.x / det, 0.0f)) * 1.01f + 0.05f;
-    return make_float4(m.x - ex, m.x + ex, m.y - ey, m.y + ey);
-}
-
 // p2 = log2(e) * P over an aligned group of 4 pixel rows of one column. With dx = u - px and
 // dy0 = v - py0 at the group's first row, row py0 + p has dy = dy0 - p and
 //   p2(p) = base - p k1 + p^2 C',  base = A' dx^2 + B' dx dy0 + C' dy0^2,  k1 = B' dx + 2 C' dy0.
