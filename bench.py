@@ -222,16 +222,29 @@ class Harness:
             rep = N.prof_report()
         if world > 1:
             torch.distributed.barrier()
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        t = torch.tensor([ms], dtype=torch.float64, device=self.dev)
-        if world > 1:
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), self.dev, world)
         if int(self.rast.d_n_pairs.item()) > self.rast.capacity:
             raise RuntimeError("pair buffer overflow during the timed steps")
-        return float(t.item()), rep
+        return ms, rep
 
     def mpix(self, ms, k):
-        return self.rast.n_pix * self.world * k / (ms / 1e3) / 1e6
+        return whole_job_mpix(self.rast.n_pix, self.world, k, ms)
+
+
+def max_over_ranks(ms: float, device, world: int) -> float:
+    """The slowest rank's time (replicas are timed between barriers; the job is as slow as its
+    slowest replica)."""
+    import torch
+    if world <= 1:
+        return float(ms)
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpix(pixels_per_replica: int, world: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: every replica renders its own copy of the workload."""
+    return pixels_per_replica * world * steps / (ms / 1e3) / 1e6
 
 
 def source_hash():
