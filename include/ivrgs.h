@@ -61,7 +61,7 @@ enum {
 
 enum { IVRGS_FP32 = 0, IVRGS_MIXED = 1 };
 #define IVRGS_ANCHOR_CHUNK 256 /* Gaussians per float32 position anchor in IVRGS_MIXED storage */
-enum { IVRGS_BIN_EXACT = 0, IVRGS_BIN_CAPACITY = 1 };
+enum { IVRGS_BIN_EXACT = 0, IVRGS_BIN_CAPACITY = 1, IVRGS_BIN_CULL = 2 };
 
 /* One pinhole view. light_dir is the direction towards an orbital (directional) light in
    world space, used when headlight == 0; with headlight != 0 the light sits at the camera
@@ -212,14 +212,23 @@ ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera*
    out->capacity, else finishes and sets out->n_pairs.
    mode IVRGS_BIN_CAPACITY: never synchronises (usable inside CUDA graph capture); works
    on min(count, capacity) pairs and leaves the true count in *out->d_n_pairs.
+   mode | IVRGS_BIN_CULL (no counterpart in the paper; a refinement that leaves every
+   composited value unchanged): a pair is emitted only if its tile meets the Gaussian's
+   opacity cut-off ellipse, q(e) = a e_x^2 + 2 b e_x e_y + c e_y^2 <= 2 ln(255 o') + 0.25 for
+   some point e of the box spanned by the tile's pixel centres (conic (a, b, c) and o' from
+   p->conic_o). Outside that
+   ellipse alpha < 1/255, so the compositing skips the Gaussian at every pixel of a dropped
+   tile. The lists are the rectangle lists above with those pairs removed, in the same order.
+   Conics with a c > 4096 (a c - b^2) keep their whole rectangle.
    A device-side wait of the sort that exceeds its iteration bound sets a flag in the
    workspace; EXACT mode reports it as IVRGS_ERR_TIMEOUT, CAPACITY mode via
-   ivrgs_bin_check(). */
+   ivrgs_bin_check(). An emission that disagrees with the count pass (never expected) is
+   reported the same way as IVRGS_ERR_CUDA. */
 ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32_t n_views, int32_t mode,
                        void* d_workspace, size_t ws_bytes, ivrgs_bins* out, void* stream);
 
 /* Reads (synchronously) the error flag a previous ivrgs_bin left in d_workspace:
-   IVRGS_OK or IVRGS_ERR_TIMEOUT. */
+   IVRGS_OK, IVRGS_ERR_TIMEOUT or IVRGS_ERR_CUDA (see ivrgs_bin). */
 ivrgs_status ivrgs_bin_check(const void* d_workspace, void* stream);
 
 /* Front-to-back alpha compositing per tile (Sec. 3 second equation, C = sum T_i alpha_i c_i,

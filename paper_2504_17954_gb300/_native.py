@@ -28,6 +28,7 @@ IVRGS_MIXED = 1
 IVRGS_ANCHOR_CHUNK = 256
 IVRGS_BIN_EXACT = 0
 IVRGS_BIN_CAPACITY = 1
+IVRGS_BIN_CULL = 2
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA_ERROR", 4: "TIMEOUT", 5: "UNSUPPORTED"}
 

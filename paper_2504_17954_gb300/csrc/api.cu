@@ -260,6 +260,20 @@ ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera*
     return IVRGS_OK;
 }
 
+// error flag of a bin workspace: bit 0 = a look-back wait gave up, bit 1 = the emission wrote a
+// different number of pairs than the count pass reported
+static ivrgs_status bin_flag_status(unsigned flag) {
+    if (flag & 1u) {
+        set_error("radix sort look-back wait exceeded its bound");
+        return IVRGS_ERR_TIMEOUT;
+    }
+    if (flag & 2u) {
+        set_error("tile emission disagreed with the pair count");
+        return IVRGS_ERR_CUDA;
+    }
+    return IVRGS_OK;
+}
+
 ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32_t n_views, int32_t mode,
                        void* d_workspace, size_t ws_bytes, ivrgs_bins* out, void* stream) {
     set_error("");
@@ -269,7 +283,10 @@ ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32
     if (!p) return invalid("projected is NULL");
     if ((st = check_projected(p, p->n, n_views))) return st;
     if ((st = check_bins(out, cb))) return st;
-    if (mode != IVRGS_BIN_EXACT && mode != IVRGS_BIN_CAPACITY) return invalid("mode must be EXACT or CAPACITY");
+    if (mode & ~(IVRGS_BIN_CAPACITY | IVRGS_BIN_CULL))
+        return invalid("mode must be IVRGS_BIN_EXACT or IVRGS_BIN_CAPACITY, optionally | IVRGS_BIN_CULL");
+    const int cull = (mode & IVRGS_BIN_CULL) ? 1 : 0;
+    const bool capacity_mode = (mode & IVRGS_BIN_CAPACITY) != 0;
     if (p->n * (long long)n_views >= (1ll << 40)) return invalid("too many records");
     const BinPlan plan = plan_bin(p->n * (long long)n_views, cb.n_tiles, out->capacity);
     if (!d_workspace || ws_bytes < plan.total_bytes) {
@@ -279,9 +296,9 @@ ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32
     if (!aligned(d_workspace, 256)) return invalid("workspace must be 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     char* ws = static_cast<char*>(d_workspace);
-    if ((st = cuda_status(launch_bin_count(p, cb, plan, ws, out->d_n_pairs, s), "ivrgs_bin count"))) return st;
+    if ((st = cuda_status(launch_bin_count(p, cb, plan, cull, ws, out->d_n_pairs, s), "ivrgs_bin count"))) return st;
     long long exact = -1;
-    if (mode == IVRGS_BIN_EXACT) {
+    if (!capacity_mode) {
         unsigned long long total = 0;
         if ((st = cuda_status(cudaMemcpyAsync(&total, out->d_n_pairs, 8, cudaMemcpyDeviceToHost, s), "ivrgs_bin")))
             return st;
@@ -293,16 +310,13 @@ ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32
         }
         exact = (long long)total;
     }
-    if ((st = cuda_status(launch_bin_sort(p, cb, plan, ws, out, exact, s), "ivrgs_bin sort"))) return st;
-    if (mode == IVRGS_BIN_EXACT) {
+    if ((st = cuda_status(launch_bin_sort(p, cb, plan, cull, ws, out, exact, s), "ivrgs_bin sort"))) return st;
+    if (!capacity_mode) {
         unsigned flag = 0;
         if ((st = cuda_status(cudaMemcpyAsync(&flag, ws + plan.off_flag, 4, cudaMemcpyDeviceToHost, s), "ivrgs_bin")))
             return st;
         if ((st = cuda_status(cudaStreamSynchronize(s), "ivrgs_bin"))) return st;
-        if (flag) {
-            set_error("radix sort look-back wait exceeded its bound");
-            return IVRGS_ERR_TIMEOUT;
-        }
+        return bin_flag_status(flag);
     }
     return IVRGS_OK;
 }
@@ -316,11 +330,7 @@ ivrgs_status ivrgs_bin_check(const void* d_workspace, void* stream) {
     if ((st = cuda_status(cudaMemcpyAsync(&flag, d_workspace, 4, cudaMemcpyDeviceToHost, s), "ivrgs_bin_check")))
         return st;
     if ((st = cuda_status(cudaStreamSynchronize(s), "ivrgs_bin_check"))) return st;
-    if (flag) {
-        set_error("radix sort look-back wait exceeded its bound");
-        return IVRGS_ERR_TIMEOUT;
-    }
-    return IVRGS_OK;
+    return bin_flag_status(flag);
 }
 
 ivrgs_status ivrgs_render(const ivrgs_projected* p, const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views,

@@ -5,21 +5,27 @@
 // one sort of 64-bit keys over all pairs:
 //
 //   count:    per (view, Gaussian) record the number of covered tiles of its float32
-//             rectangle; per block of 2048 records the number of covered records and pairs;
+//             rectangle (with IVRGS_BIN_CULL: of the rectangle's tiles that meet the
+//             opacity cut-off ellipse, tile_cull.cuh), stored per record; per block of 2048
+//             records the number of covered records and pairs;
 //   compact:  the covered records, in record order, as (depth bits, record index);
 //   sort 1:   stable LSD radix sort of the covered records by depth bits (4 onesweep passes);
 //   count 2:  pair counts of the depth-ordered records, block sums, scan;
 //   emit:     warp-cooperative emission of one (tile id, Gaussian) pair per covered tile, in
-//             depth order, with the digit histograms of the tile ids;
+//             depth order, with the digit histograms of the tile ids: the lanes of a warp
+//             first stride over the row runs of its 32 records (one culling evaluation per
+//             run), then over the pairs of 32 runs at a time, so stores stay coalesced;
 //   sort 2:   stable LSD radix sort of the pairs by tile id (one pass per 8 tile bits);
 //   ranges:   [start, end) of every tile's run.
 //
 // Because sort 2 is stable and its input is in (depth, view, Gaussian) order, the output
 // is ordered by (tile, depth, Gaussian) -- the same order as one stable sort by
 // (tile << 32 | depth bits). Each onesweep pass ranks a tile of 4096 keys per CTA with warp
-// ballots, publishes per-digit counts and resolves its offsets by decoupled look-back over
-// its predecessors (a bounded spin), then scatters through shared memory.
+// ballots, publishes per-digit counts, orders the tile by digit in shared memory, resolves its
+// global offsets by decoupled look-back over its predecessors (8 status words per round, a
+// bounded spin), then scatters.
 #include "common.cuh"
+#include "tile_cull.cuh"
 
 namespace ivrgs {
 
@@ -28,6 +34,7 @@ constexpr int kSortThreads = 256, kSortItems = 16, kSortTile = kSortThreads * kS
 constexpr int kMaxTilePasses = 4, kRecPasses = 4;
 constexpr unsigned kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr long long kMaxSpin = 1ll << 22;
+constexpr int kLookWindow = 8;  // predecessors whose status words one look-back round reads
 
 __device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
     unsigned v;
@@ -38,14 +45,57 @@ __device__ __forceinline__ void st_relaxed(unsigned* p, unsigned v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned record_count(const float2* __restrict__ xy, const int* __restrict__ radius,
-                                                 long long i, const CamDev& c, int& x0, int& x1, int& y0, int& y1) {
+// view of record i = v * n + g (32-bit division whenever the records fit 32 bits)
+__device__ __forceinline__ int view_of_record(long long i, long long n, long long total) {
+    return total <= 0xffffffffll ? (int)((unsigned)i / (unsigned)n) : (int)(i / n);
+}
+
+// rectangle of record i; false if the record covers no tile
+__device__ __forceinline__ bool record_rect(const float2* __restrict__ xy, const int* __restrict__ radius, long long i,
+                                            const CamDev& c, float2& p, int& x0, int& x1, int& y0, int& y1) {
     const int r = radius[i];
     x0 = x1 = y0 = y1 = 0;
-    if (r <= 0) return 0u;
-    const float2 p = xy[i];
+    if (r <= 0) return false;
+    p = xy[i];
     tile_rect(p.x, p.y, r, c.gx, c.gy, x0, x1, y0, y1);
-    return (unsigned)((x1 - x0) * (y1 - y0));
+    return x1 > x0 && y1 > y0;
+}
+
+// tile rows [ya, yb) of the rectangle whose band of pixel-centre rows [16 ty + 0.5, 16 ty + 15.5]
+// meets the ellipse's height [v - Y, v + Y] (the rows in it are still tested one by one)
+__device__ __forceinline__ void cull_rows(const CullEll& e, int y0, int y1, int& ya, int& yb) {
+    ya = y0;
+    yb = y1;
+    if (e.mode == 2) return;
+    if (e.mode == 0) {
+        yb = ya;
+        return;
+    }
+    const float inv = 1.0f / (float)kTile;
+    const float a = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(e.v, e.Y), (float)kTile - 0.5f), inv));
+    const float b = floorf(__fmul_rn(__fsub_rn(__fadd_rn(e.v, e.Y), 0.5f), inv)) + 1.0f;
+    ya = (int)fminf(fmaxf(a, (float)y0), (float)y1);
+    yb = (int)fminf(fmaxf(b, (float)ya), (float)y1);
+}
+
+// number of pairs of record i: every tile of its rectangle, or with culling the kept tiles
+__device__ __forceinline__ unsigned record_pairs(const float2* __restrict__ xy, const float4* __restrict__ conic_o,
+                                                 const int* __restrict__ radius, long long i, const CamDev& c,
+                                                 int cull) {
+    float2 p;
+    int x0, x1, y0, y1;
+    if (!record_rect(xy, radius, i, c, p, x0, x1, y0, y1)) return 0u;
+    if (!cull) return (unsigned)((x1 - x0) * (y1 - y0));
+    const CullEll e = cull_setup(p, conic_o[i], 1);
+    int ya, yb;
+    cull_rows(e, y0, y1, ya, yb);
+    unsigned tot = 0;
+    for (int ty = ya; ty < yb; ++ty) {
+        int lo, hi;
+        cull_row(e, ty, x0, x1, lo, hi);
+        tot += (unsigned)(hi - lo);
+    }
+    return tot;
 }
 
 // block-wide exclusive scan of one u32 per thread (256 threads); returns the block total
@@ -95,20 +145,23 @@ __device__ __forceinline__ long long sort_count(const unsigned long long* d_n, l
 }
 
 // ------------------------------------------------------------------------- count
-// block sums: [0, nb) covered records, [nb, 2 nb) pairs
-__global__ void __launch_bounds__(kScanThreads) k_count(const float2* __restrict__ xy, const int* __restrict__ radius,
-                                                        long long n, const __grid_constant__ CamBatch cb,
+// block sums: [0, nb) covered records, [nb, 2 nb) pairs; cnt[i] = pairs of record i
+__global__ void __launch_bounds__(kScanThreads) k_count(const float2* __restrict__ xy,
+                                                        const float4* __restrict__ conic_o,
+                                                        const int* __restrict__ radius, long long n,
+                                                        const __grid_constant__ CamBatch cb, int cull,
+                                                        unsigned* __restrict__ cnt,
                                                         unsigned long long* __restrict__ sums, long long nb) {
     __shared__ unsigned s_red[2][kScanThreads / 32];
     const long long total = n * cb.n;
     const long long base = (long long)blockIdx.x * kScanBlock;
     unsigned vis = 0, pairs = 0;
-    int x0, x1, y0, y1;
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long i = base + (long long)j * kScanThreads + threadIdx.x;
         if (i < total) {
-            const unsigned c = record_count(xy, radius, i, cb.c[i / n], x0, x1, y0, y1);
+            const unsigned c = record_pairs(xy, conic_o, radius, i, cb.c[view_of_record(i, n, total)], cull);
+            cnt[i] = c;
             vis += c ? 1u : 0u;
             pairs += c;
         }
@@ -174,9 +227,8 @@ __global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* __restri
 }
 
 // ------------------------------------------------------------------------- compact
-__global__ void __launch_bounds__(kScanThreads) k_compact(const float2* __restrict__ xy, const int* __restrict__ radius,
-                                                          const float4* __restrict__ rgbd, long long n,
-                                                          const __grid_constant__ CamBatch cb,
+__global__ void __launch_bounds__(kScanThreads) k_compact(const unsigned* __restrict__ cnt,
+                                                          const float4* __restrict__ rgbd, long long total,
                                                           const unsigned long long* __restrict__ vis_off,
                                                           unsigned* __restrict__ rkey, unsigned* __restrict__ rval,
                                                           unsigned* __restrict__ hist) {
@@ -184,15 +236,12 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const float2* __restri
     __shared__ unsigned s_warp[kScanThreads / 32 + 1];
     for (int k = threadIdx.x; k < kRecPasses * 256; k += kScanThreads) s_hist[k] = 0u;
     __syncthreads();
-    const long long total = n * cb.n;
     const long long base = (long long)blockIdx.x * kScanBlock;
     unsigned long long off = vis_off[blockIdx.x];
-    int x0, x1, y0, y1;
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long i = base + (long long)j * kScanThreads + threadIdx.x;
-        unsigned f = 0;
-        if (i < total) f = record_count(xy, radius, i, cb.c[i / n], x0, x1, y0, y1) ? 1u : 0u;
+        const unsigned f = (i < total && cnt[i]) ? 1u : 0u;
         unsigned excl;
         const unsigned tot = block_excl_scan(f, excl, s_warp);
         if (f) {
@@ -210,9 +259,7 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const float2* __restri
 }
 
 // ------------------------------------------------------------------------- count of sorted records
-__global__ void __launch_bounds__(kScanThreads) k_count_sorted(const float2* __restrict__ xy,
-                                                               const int* __restrict__ radius, long long n,
-                                                               const __grid_constant__ CamBatch cb,
+__global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* __restrict__ cnt, long long total,
                                                                const unsigned* __restrict__ rval,
                                                                const unsigned long long* __restrict__ d_m,
                                                                unsigned long long* __restrict__ sums) {
@@ -220,13 +267,12 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const float2* __r
     const long long m = (long long)*d_m;
     const long long base = (long long)blockIdx.x * kScanBlock;
     unsigned pairs = 0;
-    int x0, x1, y0, y1;
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long k = base + (long long)j * kScanThreads + threadIdx.x;
         if (k < m) {
             const long long i = rval[k];
-            if (i < n * cb.n) pairs += record_count(xy, radius, i, cb.c[i / n], x0, x1, y0, y1);
+            if (i < total) pairs += cnt[i];
         }
     }
 #pragma unroll
@@ -241,98 +287,135 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const float2* __r
 }
 
 // ------------------------------------------------------------------------- emission
-// Each warp emits the pairs of its 32 records with its lanes striding over the warp's pairs, so
-// consecutive lanes write consecutive slots.
-__global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict__ xy, const int* __restrict__ radius,
-                                                       long long n, const __grid_constant__ CamBatch cb,
+// Each warp emits the pairs of its 32 records. Round 1: its lanes stride over the records' tile
+// rows (row runs), evaluating each row's kept columns [lo, hi) once. Round 2, for every 32 row
+// runs: its lanes stride over those runs' pairs, so consecutive lanes write consecutive slots.
+// The pairs a warp writes must equal the sum of its records' counts from k_count (the same
+// rounded arithmetic decides both); a mismatch sets bit 1 of the error flag.
+__global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict__ xy,
+                                                       const float4* __restrict__ conic_o,
+                                                       const int* __restrict__ radius, long long n,
+                                                       const __grid_constant__ CamBatch cb, int cull,
                                                        const unsigned* __restrict__ rval,
+                                                       const unsigned* __restrict__ cnt,
                                                        const unsigned long long* __restrict__ d_m,
                                                        const unsigned long long* __restrict__ pair_off,
                                                        unsigned* __restrict__ tiles, unsigned* __restrict__ vals,
-                                                       long long cap, int n_passes, unsigned* __restrict__ hist) {
+                                                       long long cap, int n_passes, unsigned* __restrict__ hist,
+                                                       unsigned* __restrict__ flag) {
+    constexpr int kWarps = kScanThreads / 32;
     __shared__ unsigned s_hist[kMaxTilePasses * 256];
-    __shared__ unsigned s_warp[kScanThreads / 32 + 1];
-    __shared__ unsigned s_start[kScanThreads / 32][33];
-    __shared__ int s_x0[kScanThreads], s_w[kScanThreads], s_y0[kScanThreads];
+    __shared__ unsigned s_warp[kWarps + 1];
+    __shared__ unsigned s_rstart[kWarps][33];  // row-run prefix over the warp's records
+    __shared__ unsigned s_pstart[kWarps][33];  // pair prefix over the current 32 row runs
+    __shared__ unsigned s_rb[kWarps][32];      // tile id of each current run's first kept column
+    __shared__ unsigned s_rg[kWarps][32];      // Gaussian index of each current run
+    __shared__ CullEll s_e[kScanThreads];
+    __shared__ int s_x0[kScanThreads], s_x1[kScanThreads], s_ya[kScanThreads];
     __shared__ unsigned s_g[kScanThreads], s_t0[kScanThreads], s_gx[kScanThreads];
-    __shared__ float s_rw[kScanThreads];
     for (int k = threadIdx.x; k < n_passes * 256; k += kScanThreads) s_hist[k] = 0u;
     __syncthreads();
     const long long m = (long long)*d_m;
+    const long long total = n * cb.n;
     const long long base = (long long)blockIdx.x * kScanBlock;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long off = pair_off[blockIdx.x];
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long k = base + (long long)j * kScanThreads + threadIdx.x;
-        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-        unsigned c = 0, g = 0;
-        int v = 0;
-        if (k < m) {
-            const long long i = rval[k];
-            if (i < n * cb.n) {  // always true unless a timed-out sort left a slot unwritten
-                v = (int)(i / n);
-                c = record_count(xy, radius, i, cb.c[v], x0, x1, y0, y1);
-                g = (unsigned)(i - (long long)v * n);
-            }
-        }
-        // digits above the lowest byte: each row of the rectangle is a contiguous run of tile ids
-        // (narrower than 256), so it adds to at most two digits per higher byte
-        if (c) {
-            const unsigned t0 = (unsigned)cb.c[v].tile0, gxv = (unsigned)cb.c[v].gx, w = (unsigned)(x1 - x0);
-            for (int row = y0; row < y1; ++row) {
-                const unsigned a = t0 + (unsigned)row * gxv + (unsigned)x0, e = a + w;
-                for (int p = 1; p < n_passes; ++p) {
-                    const unsigned sh = 8u * p, d0 = a >> sh, d1 = (e - 1u) >> sh;
-                    if (d0 == d1) {
-                        atomicAdd(&s_hist[p * 256 + (d0 & 255u)], w);
-                    } else {
-                        const unsigned B = d1 << sh;
-                        atomicAdd(&s_hist[p * 256 + (d0 & 255u)], B - a);
-                        atomicAdd(&s_hist[p * 256 + (d1 & 255u)], e - B);
+        unsigned c = 0, rows = 0;
+        {
+            int x0 = 0, x1 = 0, y0 = 0, y1 = 0, ya = 0, yb = 0, v = 0;
+            unsigned g = 0;
+            CullEll e{};
+            if (k < m) {
+                const long long i = rval[k];
+                if (i < total) {  // always true unless a timed-out sort left a slot unwritten
+                    v = view_of_record(i, n, total);
+                    g = (unsigned)(i - (long long)v * n);
+                    c = cnt[i];
+                    float2 p;
+                    if (c && record_rect(xy, radius, i, cb.c[v], p, x0, x1, y0, y1)) {
+                        e = cull_setup(p, conic_o[i], cull);
+                        cull_rows(e, y0, y1, ya, yb);
+                        rows = (unsigned)(yb - ya);
                     }
                 }
             }
+            s_e[threadIdx.x] = e;
+            s_x0[threadIdx.x] = x0;
+            s_x1[threadIdx.x] = x1;
+            s_ya[threadIdx.x] = ya;
+            s_g[threadIdx.x] = g;
+            s_t0[threadIdx.x] = (unsigned)cb.c[v].tile0;
+            s_gx[threadIdx.x] = (unsigned)cb.c[v].gx;
         }
         unsigned excl;
         const unsigned tot = block_excl_scan(c, excl, s_warp);
-        const unsigned winc = warp_incl_scan(c);
-        s_start[warp][lane + 1] = winc;
-        if (lane == 0) s_start[warp][0] = 0;
-        s_x0[threadIdx.x] = x0;
-        s_w[threadIdx.x] = x1 - x0;
-        s_rw[threadIdx.x] = x1 > x0 ? 1.0f / (float)(x1 - x0) : 0.0f;
-        s_y0[threadIdx.x] = y0;
-        s_g[threadIdx.x] = g;
-        s_t0[threadIdx.x] = (unsigned)cb.c[v].tile0;
-        s_gx[threadIdx.x] = (unsigned)cb.c[v].gx;
+        const unsigned rinc = warp_incl_scan(rows);
+        s_rstart[warp][lane + 1] = rinc;
+        if (lane == 0) s_rstart[warp][0] = 0;
+        const unsigned cwarp = __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
         __syncwarp();
-        const unsigned wtot = __shfl_sync(0xffffffffu, winc, 31);
-        // absolute offset of this warp's first pair = block offset + exclusive offset of lane 0
+        const unsigned R = s_rstart[warp][32];
+        // absolute slot of the warp's first pair = block offset + exclusive offset of lane 0
         const unsigned long long wbase = off + __shfl_sync(0xffffffffu, excl, 0);
-        for (unsigned s = lane; s < wtot; s += 32) {
-            // record r of the warp holding slot s: the largest r with start[r] <= s
-            int r = 0;
+        unsigned done = 0;
+        for (unsigned r0 = 0; r0 < R; r0 += 32) {
+            const unsigned rr = r0 + lane;
+            int lo = 0, hi = 0;
+            unsigned rowbase = 0, g = 0;
+            if (rr < R) {
+                int r = 0;
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (s_start[warp][r + step] <= s) r += step;
-            const int ti = warp * 32 + r;
-            const unsigned q = s - s_start[warp][r];
-            const unsigned w = (unsigned)s_w[ti];
-            // q / w by a float reciprocal (q < 2^24), then one exact correction step each way
-            unsigned ty = (unsigned)((float)q * s_rw[ti]);
-            int txs = (int)q - (int)(ty * w);
-            if (txs < 0) { --ty; txs += (int)w; }
-            if (txs >= (int)w) { ++ty; txs -= (int)w; }
-            const unsigned tx = (unsigned)txs;
-            const unsigned tile = s_t0[ti] + ((unsigned)s_y0[ti] + ty) * s_gx[ti] + (unsigned)s_x0[ti] + tx;
-            const unsigned long long o = wbase + s;
-            if ((long long)o < cap) {
-                tiles[o] = tile;
-                vals[o] = s_g[ti];
-                atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
+                for (int step = 16; step > 0; step >>= 1)
+                    if (s_rstart[warp][r + step] <= rr) r += step;
+                const int ti = warp * 32 + r;
+                const int ty = s_ya[ti] + (int)(rr - s_rstart[warp][r]);
+                cull_row(s_e[ti], ty, s_x0[ti], s_x1[ti], lo, hi);
+                rowbase = s_t0[ti] + (unsigned)ty * s_gx[ti];
+                g = s_g[ti];
+                if (hi > lo) {
+                    // digits above the lowest byte: the run is contiguous in tile id (narrower
+                    // than 256), so it adds to at most two digits per higher byte
+                    const unsigned a = rowbase + (unsigned)lo, e = rowbase + (unsigned)hi;
+                    for (int p = 1; p < n_passes; ++p) {
+                        const unsigned sh = 8u * p, d0 = a >> sh, d1 = (e - 1u) >> sh;
+                        if (d0 == d1) {
+                            atomicAdd(&s_hist[p * 256 + (d0 & 255u)], e - a);
+                        } else {
+                            const unsigned B = d1 << sh;
+                            atomicAdd(&s_hist[p * 256 + (d0 & 255u)], B - a);
+                            atomicAdd(&s_hist[p * 256 + (d1 & 255u)], e - B);
+                        }
+                    }
+                }
             }
+            const unsigned w = (unsigned)(hi - lo);
+            const unsigned pinc = warp_incl_scan(w);
+            s_pstart[warp][lane + 1] = pinc;
+            if (lane == 0) s_pstart[warp][0] = 0;
+            s_rb[warp][lane] = rowbase + (unsigned)lo;
+            s_rg[warp][lane] = g;
+            __syncwarp();
+            const unsigned W = s_pstart[warp][32];
+            for (unsigned q = lane; q < W; q += 32) {
+                int l = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (s_pstart[warp][l + step] <= q) l += step;
+                const unsigned tile = s_rb[warp][l] + (q - s_pstart[warp][l]);
+                const unsigned long long o = wbase + done + q;
+                if ((long long)o < cap) {
+                    tiles[o] = tile;
+                    vals[o] = s_rg[warp][l];
+                    atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
+                }
+            }
+            done += W;
+            __syncwarp();
         }
+        if (lane == 0 && done != cwarp) atomicOr(flag, 2u);
         off += tot;
         __syncwarp();
     }
@@ -350,7 +433,7 @@ __global__ void k_hist_scan(const unsigned* __restrict__ hist, unsigned* __restr
 }
 
 // ------------------------------------------------------------------------- onesweep pass (u32 keys)
-__global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __restrict__ kin,
                                                            const unsigned* __restrict__ vin,
                                                            unsigned* __restrict__ kout, unsigned* __restrict__ vout,
                                                            const unsigned long long* __restrict__ d_n, long long cap,
@@ -426,8 +509,23 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
     unsigned lexcl;
     block_excl_scan(cnt, lexcl, s_warp);
     s_local[dg] = lexcl;
-    // decoupled look-back: read the status words of up to 8 predecessors at once, add their
-    // counts nearest-first until one carries an inclusive prefix; wait (bounded) on a
+    __syncthreads();
+    // local scatter into digit order first, so that keys and ranks are dead during the look-back
+    {
+        unsigned val[kSortItems];
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const unsigned dj = (key[j] >> shift) & 255u;
+            pos[j] += s_local[dj] + s_whist[warp][dj];
+            s_keys[pos[j]] = key[j];
+            val[j] = s_vals[wofs + j * 32];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) s_vals[pos[j]] = val[j];
+    }
+    // decoupled look-back: read the status words of up to kLookWindow predecessors at once, add
+    // their counts nearest-first until one carries an inclusive prefix; wait (bounded) on a
     // predecessor that has not published yet
     unsigned prefix = 0;
     if (tile > 0) {
@@ -435,11 +533,13 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
         long long spins = 0;
         bool done_lb = false;
         while (!done_lb) {
-            unsigned st[8];
+            unsigned st[kLookWindow];
 #pragma unroll
-            for (int w = 0; w < 8; ++w) st[w] = (t - w >= 0) ? ld_relaxed(lookback + (t - w) * 256 + dg) : (kFlagPre);
+            for (int w = 0; w < kLookWindow; ++w)
+                st[w] = (t - w >= 0) ? ld_relaxed(lookback + (t - w) * 256 + dg) : (kFlagPre);
             int w = 0;
-            for (; w < 8; ++w) {
+#pragma unroll
+            for (; w < kLookWindow; ++w) {
                 const unsigned f = st[w] >> 30;
                 if (f == 0u) break;  // not published yet: re-read from this tile
                 prefix += st[w] & kValMask;
@@ -461,18 +561,6 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_onesweep(const unsigned* __
         if (publish) st_relaxed(my_status, kFlagPre | ((prefix + cnt) & kValMask));
     }
     s_global[dg] = base[dg] + prefix;
-    __syncthreads();
-    unsigned val[kSortItems];
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const unsigned dj = (key[j] >> shift) & 255u;
-        pos[j] += s_local[dj] + s_whist[warp][dj];
-        s_keys[pos[j]] = key[j];
-        val[j] = s_vals[wofs + j * 32];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) s_vals[pos[j]] = val[j];
     __syncthreads();
     for (int i = tid; i < nvalid; i += kSortThreads) {
         const unsigned k = s_keys[i];
@@ -541,6 +629,7 @@ BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity) {
     p.clear_bytes = o;
     p.off_block_sums = o;   o = align_up(o + 8 * 3 * nb);
     p.off_rec = o;          o = align_up(o + 4 * 4 * nr);
+    p.off_cnt = o;          o = align_up(o + 4 * nr);
     p.off_lookback_rec = o; o = align_up(o + 4 * 256 * (size_t)kRecPasses * (size_t)(p.rec_tiles > 0 ? p.rec_tiles : 1));
     p.off_lookback = o;     o = align_up(o + 4 * 256 * (size_t)(p.n_passes > 0 ? p.n_passes : 1) *
                                          (size_t)(p.sort_tiles > 0 ? p.sort_tiles : 1));
@@ -558,7 +647,7 @@ static long long g_skip_publish_tile = -1;
 struct BinBufs {
     unsigned long long *sums, *d_m, *d_n;
     unsigned *hist_rec, *hist_tile, *base_rec, *base_tile, *counter, *flag, *lb_rec, *lb_tile;
-    unsigned *rkey[2], *rval[2], *talt, *valt;
+    unsigned *rkey[2], *rval[2], *talt, *valt, *cnt;
 };
 
 static BinBufs bufs(const BinPlan& plan, char* ws, ivrgs_bins* out) {
@@ -579,10 +668,11 @@ static BinBufs bufs(const BinPlan& plan, char* ws, ivrgs_bins* out) {
     b.lb_tile = reinterpret_cast<unsigned*>(ws + plan.off_lookback);
     b.talt = reinterpret_cast<unsigned*>(ws + plan.off_keys_alt);
     b.valt = reinterpret_cast<unsigned*>(ws + plan.off_vals_alt);
+    b.cnt = reinterpret_cast<unsigned*>(ws + plan.off_cnt);
     return b;
 }
 
-cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
+cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, int cull, char* ws,
                              uint64_t* d_n_pairs, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(ws, 0, plan.clear_bytes, s)) != cudaSuccess) return e;
@@ -591,8 +681,10 @@ cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const
     const long long nb = plan.n_scan_blocks;
     if (nb > 0) {
         IVRGS_PROF("k_count", s);
-        k_count<<<(unsigned)nb, kScanThreads, 0, s>>>(reinterpret_cast<const float2*>(p->xy), p->radius, p->n, cb,
-                                                      sums, nb);
+        k_count<<<(unsigned)nb, kScanThreads, 0, s>>>(reinterpret_cast<const float2*>(p->xy),
+                                                      reinterpret_cast<const float4*>(p->conic_o), p->radius, p->n,
+                                                      cb, cull, reinterpret_cast<unsigned*>(ws + plan.off_cnt), sums,
+                                                      nb);
     }
     {
         IVRGS_PROF("k_scan_sums", s);
@@ -618,7 +710,7 @@ static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, uns
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
+cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, int cull, char* ws,
                             ivrgs_bins* out, long long exact_pairs, cudaStream_t s) {
     cudaError_t e;
     BinBufs b = bufs(plan, ws, out);
@@ -638,8 +730,8 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     // covered records in record order, then by depth
     if (nb > 0) {
         IVRGS_PROF("k_compact", s);
-        k_compact<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, p->radius, reinterpret_cast<const float4*>(p->rgbd), p->n,
-                                                        cb, b.sums, b.rkey[0], b.rval[0], b.hist_rec);
+        k_compact<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt, reinterpret_cast<const float4*>(p->rgbd),
+                                                        plan.n_records, b.sums, b.rkey[0], b.rval[0], b.hist_rec);
     }
     {
         IVRGS_PROF("k_hist_scan", s);
@@ -652,7 +744,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     unsigned long long* sums2 = b.sums + 2 * (nb > 0 ? nb : 1);
     if (nb > 0) {
         IVRGS_PROF("k_count_sorted", s);
-        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, p->radius, p->n, cb, b.rval[0], b.d_m, sums2);
+        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt, plan.n_records, b.rval[0], b.d_m, sums2);
     }
     {
         IVRGS_PROF("k_scan_sums", s);
@@ -667,8 +759,9 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     }
     if (nb > 0) {
         IVRGS_PROF("k_emit", s);
-        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, p->radius, p->n, cb, b.rval[0], b.d_m, sums2, t0, v0, cap,
-                                                     plan.n_passes, b.hist_tile);
+        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, reinterpret_cast<const float4*>(p->conic_o), p->radius, p->n,
+                                                     cb, cull, b.rval[0], b.cnt, b.d_m, sums2, t0, v0, cap,
+                                                     plan.n_passes, b.hist_tile, b.flag);
     }
     if (plan.n_passes > 0) {
         IVRGS_PROF("k_hist_scan", s);

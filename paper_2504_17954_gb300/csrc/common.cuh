@@ -85,7 +85,7 @@ struct BinPlan {
     long long sort_tiles;  // radix tiles of the pair sort at full capacity
     // workspace layout (byte offsets); [0, clear_bytes) is zeroed by every call
     size_t off_flag, off_hist, off_base, off_counter, off_total, clear_bytes, off_block_sums, off_rec,
-        off_lookback_rec, off_lookback, off_keys_alt, off_vals_alt, total_bytes;
+        off_cnt, off_lookback_rec, off_lookback, off_keys_alt, off_vals_alt, total_bytes;
 };
 
 ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb);
@@ -109,9 +109,9 @@ cudaError_t launch_pack_mixed(const ivrgs_gaussians* in, const uint32_t* order, 
                               cudaStream_t s);
 cudaError_t launch_project(const ivrgs_gaussians* g, const float* table, const CamBatch& cb, float lowpass,
                            ivrgs_projected* out, cudaStream_t s);
-cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
+cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, int cull, char* ws,
                              uint64_t* d_n_pairs, cudaStream_t s);
-cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, char* ws,
+cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const BinPlan& plan, int cull, char* ws,
                             ivrgs_bins* out, long long exact_pairs, cudaStream_t s);
 cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const CamBatch& cb, const float* bg,
                           float* rgba, float* final_T, uint32_t* last, cudaStream_t s);

@@ -176,17 +176,20 @@ class Rasterizer:
     """Device buffers for one camera set and one scene size; forward and backward calls.
 
     ``capacity`` fixes the pair buffer (required for CUDA-graph capture, mode="capacity");
-    with mode="exact" the buffer grows to the exact pair count when needed.
+    with mode="exact" the buffer grows to the exact pair count when needed. ``cull`` drops the
+    pairs of tiles that the Gaussian's opacity cut-off ellipse misses (IVRGS_BIN_CULL): the same
+    images and gradients from shorter tile lists; ``cull=False`` gives the full rectangle lists.
     """
 
     def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", capacity: Optional[int] = None,
-                 lowpass: float = 0.3, bg=(0.0, 0.0, 0.0)):
+                 lowpass: float = 0.3, bg=(0.0, 0.0, 0.0), cull: bool = True):
         self.cams = list(cams)
         self.V = len(self.cams)
         self.n = int(n_gaussians)
         self.n_models = int(n_models)
         self.device = torch.device(device)
         self.lowpass = float(lowpass)
+        self.cull_flag = N.IVRGS_BIN_CULL if cull else 0
         self.cam_arr, self.n_pix = camera_structs(self.cams)
         self.bg = (C.c_float * 3)(*[float(x) for x in bg])
         self.n_tiles = n_tiles(self.cams)
@@ -249,8 +252,9 @@ class Rasterizer:
         if mode == "exact":
             while True:
                 b = self.bins_struct()
-                st = N.ivrgs_bin(C.byref(p), self.cam_arr, self.V, N.IVRGS_BIN_EXACT, _vp(self.ws_bin), self.ws_bin_bytes,
-                                 C.byref(b), _stream(stream), allow=(N.IVRGS_OK, N.IVRGS_ERR_CAPACITY))
+                st = N.ivrgs_bin(C.byref(p), self.cam_arr, self.V, N.IVRGS_BIN_EXACT | self.cull_flag, _vp(self.ws_bin),
+                                 self.ws_bin_bytes, C.byref(b), _stream(stream),
+                                 allow=(N.IVRGS_OK, N.IVRGS_ERR_CAPACITY))
                 if st == N.IVRGS_OK:
                     self.n_pairs = int(b.n_pairs)
                     return self.n_pairs
@@ -259,8 +263,8 @@ class Rasterizer:
                     raise N.IvrgsError("ivrgs_bin", st, f"{need} pairs exceed the per-call limit")
                 self._ensure_capacity(int(need * 1.25) + 1024)
         b = self.bins_struct()
-        N.ivrgs_bin(C.byref(p), self.cam_arr, self.V, N.IVRGS_BIN_CAPACITY, _vp(self.ws_bin), self.ws_bin_bytes,
-                    C.byref(b), _stream(stream))
+        N.ivrgs_bin(C.byref(p), self.cam_arr, self.V, N.IVRGS_BIN_CAPACITY | self.cull_flag, _vp(self.ws_bin),
+                    self.ws_bin_bytes, C.byref(b), _stream(stream))
         return -1
 
     def render(self, stream=None):
@@ -341,7 +345,7 @@ class WaveRasterizer:
     waves' gradients with ivrgs_render_backward_accumulate. Each wave owns a Rasterizer."""
 
     def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", lowpass: float = 0.3,
-                 bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20):
+                 bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20, cull: bool = True):
         self.cams = list(cams)
         self.waves: List[List[int]] = []
         cur, pix = [], 0
@@ -354,7 +358,7 @@ class WaveRasterizer:
         if cur:
             self.waves.append(cur)
         self.rasts = [Rasterizer([self.cams[v] for v in wv], n_gaussians, n_models, device=device, lowpass=lowpass,
-                                 bg=bg) for wv in self.waves]
+                                 bg=bg, cull=cull) for wv in self.waves]
         self.n_models = n_models
         self.V = len(self.cams)
 

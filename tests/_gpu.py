@@ -36,12 +36,37 @@ def device_models(models) -> List[Gaussians]:
     return out
 
 
-def setup(w: sg.Workload, capacity=None, edits=None):
+def setup(w: sg.Workload, capacity=None, edits=None, cull=True):
     ed = w.edits if edits is None else edits
     dm = device_models(w.models)
     comp, table = compose_edit(dm, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias)
-    rast = Rasterizer(w.cameras, comp.n, len(w.models), capacity=capacity, lowpass=w.lowpass, bg=w.bg)
+    rast = Rasterizer(w.cameras, comp.n, len(w.models), capacity=capacity, lowpass=w.lowpass, bg=w.bg, cull=cull)
     return rast, comp, table
+
+
+def last_gaussian(rast: Rasterizer, v: int, pix: np.ndarray) -> np.ndarray:
+    """Gaussian index of each sampled pixel's last contributor (-1 if none), from the GPU's
+    `last` (a position in the pixel's tile run) and its tile lists; unlike the position it does
+    not depend on which non-contributing entries a list holds."""
+    c = rast.cams[v]
+    gx = (c.W + 15) // 16
+    t0 = sum(((q.W + 15) // 16) * ((q.H + 15) // 16) for q in rast.cams[:v])
+    last = rast.view_image(v, rast.last).cpu().numpy()[pix[:, 1], pix[:, 0]].astype(np.int64)
+    tile = t0 + (pix[:, 1] // 16) * gx + pix[:, 0] // 16
+    start = rast.ranges.cpu().numpy().view(np.uint32)[tile, 0].astype(np.int64)
+    vals = rast.values.cpu().numpy().view(np.uint32).astype(np.int64)
+    out = np.full(len(pix), -1, np.int64)
+    has = last > 0
+    out[has] = vals[start[has] + last[has] - 1]
+    return out
+
+
+def oracle_last_gaussian(offs: np.ndarray, lists: np.ndarray, last: np.ndarray) -> np.ndarray:
+    """The same for the oracle's per-pixel lists (oracle.pixel_lists) and its `last`."""
+    out = np.full(len(last), -1, np.int64)
+    has = last > 0
+    out[has] = lists[offs[:-1][has] + last[has].astype(np.int64) - 1]
+    return out
 
 
 def uncertain_records(p: oracle.Projected, tile: int = 16) -> np.ndarray:

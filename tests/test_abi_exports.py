@@ -56,3 +56,17 @@ def test_product_does_not_import_oracle():
     for p in list(root.glob("*.py")) + list(root.glob("csrc/*")):
         text = p.read_text()
         assert "import oracle" not in text and "from oracle" not in text and "ivrgs_oracle" not in text, p
+
+
+def test_header_constants_match_binding():
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "ivrgs.h")).read()
+    pairs = re.findall(r"\b(IVRGS_[A-Z0-9_]+)\s*=\s*(\d+)", hdr)
+    pairs += re.findall(r"#define\s+(IVRGS_[A-Z0-9_]+)\s+\(?(\d+)", hdr)
+    checked = 0
+    for name, val in pairs:
+        if hasattr(N, name):
+            assert getattr(N, name) == int(val), name
+            checked += 1
+    assert checked >= 8 and N.IVRGS_BIN_CULL == 2

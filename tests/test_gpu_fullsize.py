@@ -53,8 +53,9 @@ def _check_pixels(rast, w, views, per_view, seed):
         assert bad == 0, (v, err)
         total_excused += excused
         safe = ~(_gpu.near_tie(mg) | tile_unc)
-        glast = rast.view_image(v, rast.last).cpu().numpy()[pix[:, 1], pix[:, 0]]
-        np.testing.assert_array_equal(glast[safe], last[safe].astype(np.int32))
+        offs, lists = oracle.pixel_lists(p, c, pix)
+        np.testing.assert_array_equal(_gpu.last_gaussian(rast, v, pix)[safe],
+                                      _gpu.oracle_last_gaussian(offs, lists, last)[safe])
         out.append((v, p, pix, safe))
     assert total_excused <= max(2, 0.002 * per_view * len(views))
     return out, comp, table

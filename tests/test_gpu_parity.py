@@ -73,7 +73,7 @@ def test_project_matches_oracle(which):
 def _gpu_bin_from(sizes, xy, rad, depth, mode="exact", capacity=None):
     V, n = rad.shape
     cams = [sg.look_at([3, 0, 0], W, H) for (W, H) in sizes]
-    rast = Rasterizer(cams, n, 1, capacity=capacity)
+    rast = Rasterizer(cams, n, 1, capacity=capacity, cull=False)  # the rectangle lists
     rast.xy.copy_(torch.as_tensor(xy.reshape(-1, 2)))
     rast.radius.copy_(torch.as_tensor(rad.reshape(-1)))
     d = np.zeros((V * n, 4), np.float32)
@@ -157,7 +157,7 @@ def test_render_only_matches_oracle_on_shared_records(which):
     projs = _shared_records(w)
     sizes = [(c.W, c.H) for c in w.cameras]
     n = projs[0].radius.shape[0]
-    rast = Rasterizer(w.cameras, n, len(w.models), bg=w.bg)
+    rast = Rasterizer(w.cameras, n, len(w.models), bg=w.bg, cull=False)  # lists compared with the oracle's
     rast.xy.copy_(torch.as_tensor(np.concatenate([p.uv for p in projs]).astype(np.float32)))
     rast.conic_o.copy_(torch.as_tensor(np.concatenate(
         [np.c_[p.conic, p.opacity] for p in projs]).astype(np.float32)))
@@ -206,7 +206,7 @@ def pixels_per_thread(request):
 @pytest.mark.parametrize("which", ["cfg1", "multi"])
 def test_forward_end_to_end(which, pixels_per_thread):
     w = sg.config1() if which == "cfg1" else _multi_view_scene(seed=25)
-    rast, comp, table = _gpu.setup(w)
+    rast, comp, table = _gpu.setup(w, cull=False)  # tile lists compared with the oracle's
     rast.forward(comp, table)
     torch.cuda.synchronize()
     ref = oracle.render(w.models, w.edits, w.cameras, bg=w.bg)
