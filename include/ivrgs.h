@@ -162,7 +162,9 @@ int32_t ivrgs_version(void);
 /* Launch-shape options (process-wide; measurement-driven tuning, the paper has no counterpart):
    "render_pixels_per_thread" and "render_bwd_pixels_per_thread" (1, 2 or 4): pixels each thread
    of the forward / backward blend owns; "sort_match" (0 or 1): rank radix digits with warp
-   ballots (0) or match.any (1). Results are identical for every setting.
+   ballots (0) or match.any (1); "sort_scan" (0 or 1): radix-pass offsets by decoupled
+   look-back (0, one kernel per pass) or reduce-then-scan (1: a histogram kernel, a per-digit
+   scan and the scatter; no device-side waits). Results are identical for every setting.
    Returns IVRGS_ERR_INVALID_ARG for an unknown name or value. */
 ivrgs_status ivrgs_set_option(const char* name, int64_t value);
 ivrgs_status ivrgs_get_option(const char* name, int64_t* value);
@@ -194,7 +196,8 @@ ivrgs_status ivrgs_compose_edit(const ivrgs_gaussians* models, int32_t n_models,
 ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_camera* cams,
                            int32_t n_views, float lowpass, ivrgs_projected* out, void* stream);
 
-/* Workspace bytes ivrgs_bin needs for p->n * n_views records and `capacity` pairs. */
+/* Workspace bytes ivrgs_bin needs for p->n * n_views records (below 2^32) and `capacity` pairs
+   (about 21 bytes per record plus 9 per pair). */
 ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera* cams, int32_t tile_w,
                                  int32_t tile_h, int64_t capacity, size_t* bytes);
 

@@ -20,6 +20,7 @@ SPACE = {
     "render_pixels_per_thread": (1, 2, 4),
     "render_bwd_pixels_per_thread": (1, 2, 4),
     "sort_match": (0, 1),
+    "sort_scan": (0, 1),
 }
 
 

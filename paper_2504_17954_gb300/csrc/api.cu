@@ -155,9 +155,9 @@ ivrgs_status ivrgs_set_option(const char* name, int64_t value) {
         (k == "render_pixels_per_thread" ? options().render_ppt : options().render_bwd_ppt) = (int)value;
         return IVRGS_OK;
     }
-    if (k == "sort_match") {
+    if (k == "sort_match" || k == "sort_scan") {
         if (value != 0 && value != 1) return invalid(k + " must be 0 or 1");
-        options().sort_match = (int)value;
+        (k == "sort_match" ? options().sort_match : options().sort_scan) = (int)value;
         return IVRGS_OK;
     }
     return invalid("unknown option '" + k + "'");
@@ -170,6 +170,7 @@ ivrgs_status ivrgs_get_option(const char* name, int64_t* value) {
     if (k == "render_pixels_per_thread") *value = options().render_ppt;
     else if (k == "render_bwd_pixels_per_thread") *value = options().render_bwd_ppt;
     else if (k == "sort_match") *value = options().sort_match;
+    else if (k == "sort_scan") *value = options().sort_scan;
     else return invalid("unknown option '" + k + "'");
     return IVRGS_OK;
 }
@@ -256,6 +257,7 @@ ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera*
     static thread_local CamBatch cb;
     ivrgs_status st = make_cam_batch(cams, n_views, &cb);
     if (st) return st;
+    if (n * (long long)n_views >= (1ll << 32)) return invalid("n * n_views must be below 2^32");
     *bytes = plan_bin(n * (long long)n_views, cb.n_tiles, capacity).total_bytes;
     return IVRGS_OK;
 }
@@ -287,7 +289,7 @@ ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32
         return invalid("mode must be IVRGS_BIN_EXACT or IVRGS_BIN_CAPACITY, optionally | IVRGS_BIN_CULL");
     const int cull = (mode & IVRGS_BIN_CULL) ? 1 : 0;
     const bool capacity_mode = (mode & IVRGS_BIN_CAPACITY) != 0;
-    if (p->n * (long long)n_views >= (1ll << 40)) return invalid("too many records");
+    if (p->n * (long long)n_views >= (1ll << 32)) return invalid("n * n_views must be below 2^32");
     const BinPlan plan = plan_bin(p->n * (long long)n_views, cb.n_tiles, out->capacity);
     if (!d_workspace || ws_bytes < plan.total_bytes) {
         set_error("workspace too small: need " + std::to_string(plan.total_bytes) + " bytes");

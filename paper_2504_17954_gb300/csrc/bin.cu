@@ -433,6 +433,11 @@ __global__ void k_hist_scan(const unsigned* __restrict__ hist, unsigned* __restr
 }
 
 // ------------------------------------------------------------------------- onesweep pass (u32 keys)
+// LOOKBACK = true: onesweep (tiles taken in launch order from `counter`, offsets by decoupled
+// look-back). LOOKBACK = false: the scatter of a reduce-then-scan pass (tile = block index,
+// offsets read from `lookback`, which then holds the scanned digit table of k_upsweep and
+// k_digit_scan: entry [d][tile] = first output slot of digit d in this tile).
+template <bool LOOKBACK>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __restrict__ kin,
                                                            const unsigned* __restrict__ vin,
                                                            unsigned* __restrict__ kout, unsigned* __restrict__ vout,
@@ -450,10 +455,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
     __shared__ unsigned s_keys[kSortTile];
     __shared__ unsigned s_vals[kSortTile];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    if (LOOKBACK && tid == 0) s_tile = atomicAdd(counter, 1u);
     for (int k = tid; k < (kSortThreads / 32) * 256; k += kSortThreads) (&s_whist[0][0])[k] = 0u;
     __syncthreads();
-    const long long tile = s_tile;
+    const long long tile = LOOKBACK ? (long long)s_tile : (long long)blockIdx.x;
     const long long n = sort_count(d_n, cap);
     const long long start = tile * kSortTile;
     if (start >= n) return;
@@ -505,7 +510,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
     }
     unsigned* my_status = lookback + tile * 256 + dg;
     const bool publish = tile != skip_publish_tile;
-    if (publish) st_relaxed(my_status, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+    if (LOOKBACK && publish) st_relaxed(my_status, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
     unsigned lexcl;
     block_excl_scan(cnt, lexcl, s_warp);
     s_local[dg] = lexcl;
@@ -524,43 +529,47 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) s_vals[pos[j]] = val[j];
     }
-    // decoupled look-back: read the status words of up to kLookWindow predecessors at once, add
-    // their counts nearest-first until one carries an inclusive prefix; wait (bounded) on a
-    // predecessor that has not published yet
-    unsigned prefix = 0;
-    if (tile > 0) {
-        long long t = tile - 1;  // nearest predecessor not yet accounted for
-        long long spins = 0;
-        bool done_lb = false;
-        while (!done_lb) {
-            unsigned st[kLookWindow];
-#pragma unroll
-            for (int w = 0; w < kLookWindow; ++w)
-                st[w] = (t - w >= 0) ? ld_relaxed(lookback + (t - w) * 256 + dg) : (kFlagPre);
-            int w = 0;
-#pragma unroll
-            for (; w < kLookWindow; ++w) {
-                const unsigned f = st[w] >> 30;
-                if (f == 0u) break;  // not published yet: re-read from this tile
-                prefix += st[w] & kValMask;
-                if (f == 2u || t - w == 0) {
-                    done_lb = true;
-                    break;
+    if constexpr (!LOOKBACK) {
+        s_global[dg] = lookback[(long long)dg * gridDim.x + tile];
+    } else {
+        // decoupled look-back: read the status words of up to kLookWindow predecessors at once, add
+        // their counts nearest-first until one carries an inclusive prefix; wait (bounded) on a
+        // predecessor that has not published yet
+        unsigned prefix = 0;
+        if (tile > 0) {
+            long long t = tile - 1;  // nearest predecessor not yet accounted for
+            long long spins = 0;
+            bool done_lb = false;
+            while (!done_lb) {
+                unsigned st[kLookWindow];
+    #pragma unroll
+                for (int w = 0; w < kLookWindow; ++w)
+                    st[w] = (t - w >= 0) ? ld_relaxed(lookback + (t - w) * 256 + dg) : (kFlagPre);
+                int w = 0;
+    #pragma unroll
+                for (; w < kLookWindow; ++w) {
+                    const unsigned f = st[w] >> 30;
+                    if (f == 0u) break;  // not published yet: re-read from this tile
+                    prefix += st[w] & kValMask;
+                    if (f == 2u || t - w == 0) {
+                        done_lb = true;
+                        break;
+                    }
+                }
+                if (done_lb) break;
+                t -= w;
+                if (w == 0) {
+                    if (++spins > max_spin) {
+                        atomicOr(flag, 1u);
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(64);
                 }
             }
-            if (done_lb) break;
-            t -= w;
-            if (w == 0) {
-                if (++spins > max_spin) {
-                    atomicOr(flag, 1u);
-                    break;
-                }
-                if (spins > 64) __nanosleep(64);
-            }
+            if (publish) st_relaxed(my_status, kFlagPre | ((prefix + cnt) & kValMask));
         }
-        if (publish) st_relaxed(my_status, kFlagPre | ((prefix + cnt) & kValMask));
+        s_global[dg] = base[dg] + prefix;
     }
-    s_global[dg] = base[dg] + prefix;
     __syncthreads();
     for (int i = tid; i < nvalid; i += kSortThreads) {
         const unsigned k = s_keys[i];
@@ -568,6 +577,67 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
         const unsigned o = s_global[dd] + ((unsigned)i - s_local[dd]);
         kout[o] = k;
         vout[o] = s_vals[i];
+    }
+}
+
+// ------------------------------------------------------------------------- reduce-then-scan
+// k_upsweep: digit histogram of radix tile blockIdx.x, written to table[d][tile] (zeros for a
+// tile past the end). k_digit_scan: one CTA per digit d turns row d into exclusive offsets
+// base[d] + sum of the row's earlier tiles.
+__global__ void __launch_bounds__(kSortThreads) k_upsweep(const unsigned* __restrict__ kin,
+                                                          const unsigned long long* __restrict__ d_n, long long cap,
+                                                          int shift, unsigned* __restrict__ table) {
+    __shared__ unsigned s_h[256];
+    const int tid = threadIdx.x;
+    s_h[tid] = 0u;
+    __syncthreads();
+    const long long n = sort_count(d_n, cap);
+    const long long start = (long long)blockIdx.x * kSortTile;
+    if (start < n) {
+        const int nvalid = (int)((n - start) < kSortTile ? (n - start) : kSortTile);
+        const unsigned* k = kin + start;
+#pragma unroll 4
+        for (int j = tid; j < nvalid; j += kSortThreads) atomicAdd(&s_h[(k[j] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    table[(long long)tid * gridDim.x + blockIdx.x] = s_h[tid];
+}
+
+constexpr int kDigitScanThreads = 1024, kDigitScanItems = 16;
+
+__global__ void __launch_bounds__(kDigitScanThreads) k_digit_scan(unsigned* __restrict__ table,
+                                                                  const unsigned* __restrict__ base, long long n_tiles) {
+    __shared__ unsigned s_w[kDigitScanThreads / 32 + 1];
+    unsigned* row = table + (long long)blockIdx.x * n_tiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned carry = base[blockIdx.x];
+    for (long long c0 = 0; c0 < n_tiles; c0 += (long long)kDigitScanThreads * kDigitScanItems) {
+        const long long t0 = c0 + (long long)threadIdx.x * kDigitScanItems;
+        unsigned v[kDigitScanItems], sum = 0;
+#pragma unroll
+        for (int k = 0; k < kDigitScanItems; ++k) {
+            v[k] = t0 + k < n_tiles ? row[t0 + k] : 0u;
+            sum += v[k];
+        }
+        unsigned inc = warp_incl_scan(sum);
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned w = s_w[lane];
+            const unsigned wi = warp_incl_scan(w);
+            s_w[lane] = wi - w;
+            if (lane == 31) s_w[32] = wi;
+        }
+        __syncthreads();
+        unsigned run = carry + s_w[warp] + inc - sum;
+#pragma unroll
+        for (int k = 0; k < kDigitScanItems; ++k)
+            if (t0 + k < n_tiles) {
+                row[t0 + k] = run;
+                run += v[k];
+            }
+        carry += s_w[32];
+        __syncthreads();
     }
 }
 
@@ -699,13 +769,24 @@ static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, uns
                                    const char* name, cudaStream_t s) {
     unsigned* kb[2] = {k0, k1};
     unsigned* vb[2] = {v0, v1};
+    const bool rts = options().sort_scan != 0;
     for (int ps = 0; ps < n_passes && tiles > 0; ++ps) {
         const int src = ps & 1, dst = src ^ 1;
+        unsigned* lb = lookback + (size_t)256 * ps * tiles;
         IVRGS_PROF(name, s);
-        k_onesweep<<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps,
-                                                            base + 256 * ps, lookback + (size_t)256 * ps * tiles,
-                                                            counter + ps, flag, g_max_spin, g_skip_publish_tile,
-                                                            options().sort_match);
+        if (rts) {
+            k_upsweep<<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], d_n, cap, 8 * ps, lb);
+            k_digit_scan<<<256, kDigitScanThreads, 0, s>>>(lb, base + 256 * ps, tiles);
+            k_onesweep<false><<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_n, cap,
+                                                                      8 * ps, base + 256 * ps, lb, counter + ps, flag,
+                                                                      g_max_spin, g_skip_publish_tile,
+                                                                      options().sort_match);
+        } else {
+            k_onesweep<true><<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_n, cap,
+                                                                     8 * ps, base + 256 * ps, lb, counter + ps, flag,
+                                                                     g_max_spin, g_skip_publish_tile,
+                                                                     options().sort_match);
+        }
     }
     return cudaGetLastError();
 }

@@ -95,6 +95,7 @@ struct Options {
     int render_ppt = 4;      // pixels per thread of the forward blend (1, 2 or 4)
     int render_bwd_ppt = 4;  // pixels per thread of the backward blend (1, 2 or 4)
     int sort_match = 0;      // radix ranking: 0 = warp ballots per digit bit, 1 = match.any
+    int sort_scan = 0;       // radix offsets: 0 = decoupled look-back (onesweep), 1 = reduce-then-scan
 };
 Options& options();
 BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity);

@@ -40,6 +40,8 @@ def test_lookback_timeout_is_reported_and_context_survives():
     rast.bin("exact")  # sizes the buffers
     torch.cuda.synchronize()
     L = N.lib()
+    old_scan = N.ivrgs_get_option("sort_scan")
+    N.ivrgs_set_option("sort_scan", 0)  # the passes with device-side waits
     L.ivrgs_debug_bin_hooks(2000, 0)
     try:
         p, b = rast.projected_struct(), rast.bins_struct()
@@ -50,6 +52,7 @@ def test_lookback_timeout_is_reported_and_context_survives():
         assert N.ivrgs_bin_check(_vp(rast.ws_bin), _stream(), allow=(N.IVRGS_ERR_TIMEOUT,)) == N.IVRGS_ERR_TIMEOUT
     finally:
         L.ivrgs_debug_bin_hooks(0, -1)
+        N.ivrgs_set_option("sort_scan", old_scan)
     # the context is healthy: a normal call is exact again and the flag is cleared
     rast.bin("exact")
     torch.cuda.synchronize()

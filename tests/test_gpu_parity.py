@@ -89,9 +89,18 @@ def _gpu_bin_from(sizes, xy, rad, depth, mode="exact", capacity=None):
     return rast
 
 
+@pytest.fixture(params=[0, 1], ids=["lookback", "rts"])
+def sort_scan(request):
+    from paper_2504_17954_gb300 import _native as N
+    old = N.ivrgs_get_option("sort_scan")
+    N.ivrgs_set_option("sort_scan", request.param)
+    yield request.param
+    N.ivrgs_set_option("sort_scan", old)
+
+
 @pytest.mark.parametrize("case", ["small", "ties", "ragged", "many", "single_tile", "empty"])
 @pytest.mark.parametrize("mode", ["exact", "capacity"])
-def test_bin_bit_exact(case, mode):
+def test_bin_bit_exact(case, mode, sort_scan):
     if case == "small":
         sizes, n, seed, kw = [(64, 48)], 500, 1, {}
     elif case == "ties":
