@@ -87,11 +87,15 @@ typedef struct {
     int32_t visible;
 } ivrgs_model_edit;
 
-/* Global light-magnitude edit (Sec. 4.5, Sec. 4.6): k' = lambda * k + bias for
-   k = (k_a, k_d, k_s, beta). */
+/* Global light edits (Sec. 4.5, Sec. 4.6): magnitude k' = lambda * k + bias for
+   k = (k_a, k_d, k_s, beta); with dir_on != 0 the direction dir (any non-zero length; dir / |dir|
+   is used) replaces the light_dir of every view that has an orbital light (Sec. 4.6 learns one
+   light direction for the composed model). */
 typedef struct {
     float lambda[4];
     float bias[4];
+    float dir[3];
+    int32_t dir_on;
 } ivrgs_light;
 
 /* Editable Gaussians (Sec. 4.3 attribute set), structure of arrays, n entries.
@@ -169,10 +173,11 @@ int32_t ivrgs_version(void);
 ivrgs_status ivrgs_set_option(const char* name, int64_t value);
 ivrgs_status ivrgs_get_option(const char* name, int64_t* value);
 
-/* Number of floats in an edit table for n_models models: IVRGS_EDIT_STRIDE * n_models + 8.
-   Layout: per model m, [c_p(3), opacity scale, visible (0/1), 0, 0, 0]; then lambda(4), b(4).
-   The edit-gradient buffer of ivrgs_render_backward has the same layout followed by
-   4 floats per view (d light_dir (3), 0). */
+/* Number of floats in an edit table for n_models models: IVRGS_EDIT_STRIDE * n_models + 12.
+   Layout: per model m, [c_p(3), opacity scale, visible (0/1), 0, 0, 0]; then lambda(4), b(4),
+   global light (dir(3), on (0/1)). The edit-gradient buffer of ivrgs_render_backward has the
+   same layout (the global light's slots receive d dir while it is on) followed by 4 floats per
+   view (d light_dir (3), 0; zero for views whose light the global one replaces). */
 int64_t ivrgs_edit_table_floats(int32_t n_models);
 
 /* Composition and edits (Sec. 4.5: the composed model is the concatenation of the basic
@@ -318,6 +323,50 @@ ivrgs_status ivrgs_render_backward_static(const ivrgs_gaussians* g, const float*
                                           int32_t n_views, float lowpass, const float* bg, const float* d_final_T,
                                           const uint32_t* d_last, const float* d_dL_drgba, ivrgs_gaussians* grad,
                                           float* d_edit_grad, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+   Inverse volume exploration (Sec. 4.6): all Gaussian attributes stay fixed; the per-model
+   palette colour c_p and opacity scale, the global lambda and b, and (orbital light) the global
+   light direction as polar and azimuthal angles are fitted to a reference image by gradient
+   steps on a combined L1 / SSIM loss (Sec. 5: learning rate 0.01, 1000 iterations).
+   --------------------------------------------------------------------------------------- */
+enum {
+    IVRGS_LEARN_COLOR = 1,           /* c_p of every model */
+    IVRGS_LEARN_OPACITY = 2,         /* opacity scale of every model */
+    IVRGS_LEARN_LIGHT_MAGNITUDE = 4, /* lambda and b */
+    IVRGS_LEARN_LIGHT_DIRECTION = 8  /* polar / azimuth of the edit table's global light (if on) */
+};
+
+/* Workspace bytes of ivrgs_image_loss for these views. */
+ivrgs_status ivrgs_image_loss_workspace(const ivrgs_camera* cams, int32_t n_views, size_t* bytes);
+
+/* Image loss of a rendering against a reference (the 3DGS loss that the paper's combination of
+   L1 and SSIM denotes): loss = (1 - lambda_ssim) L1 + lambda_ssim (1 - SSIM) over the R, G, B
+   channels of all views, L1 = mean |x - y|, SSIM = mean of the per-pixel, per-channel structural
+   similarity with an 11 x 11 Gaussian window (sigma 1.5, normalised), C1 = 0.01^2, C2 = 0.03^2,
+   zero padding at each view's border. d_rgba, d_target: packed images [.][4] (alpha ignored),
+   16-byte aligned. Writes d_loss[0..2] = (loss, L1, SSIM) and d_dL_drgba [.][4] = dloss/d(r, g,
+   b) with 0 for alpha, for the views' pixels only. Workspace: ivrgs_image_loss_workspace bytes,
+   256-byte aligned. */
+ivrgs_status ivrgs_image_loss(const float* d_rgba, const float* d_target, const ivrgs_camera* cams, int32_t n_views,
+                              float lambda_ssim, void* d_workspace, size_t ws_bytes, float* d_loss,
+                              float* d_dL_drgba, void* stream);
+
+/* Floats of the optimiser state for n_models models: 2 (4 n_models + 10) + 3 = first and second
+   moments of every learnable value, the light's (polar, azimuth) angles and the step count. */
+int64_t ivrgs_edit_adam_state_floats(int32_t n_models);
+
+/* Sets the moments and the step count to zero and the angles to those of the edit table's
+   global light (polar from +z, azimuth from +x). */
+ivrgs_status ivrgs_edit_adam_init(const float* d_edit_table, int32_t n_models, float* d_state, void* stream);
+
+/* One Adam step (Kingma and Ba; bias-corrected moments, step = lr m^ / (sqrt(v^) + eps)) on the
+   edit-table values selected by `learn` (IVRGS_LEARN_*), with d_edit_grad laid out as the
+   edit-gradient buffer of ivrgs_render_backward. The light direction is stepped through its
+   angles and written back to the table as a unit vector (only while the global light is on).
+   The step count lives in d_state, so a captured CUDA graph can replay whole iterations. */
+ivrgs_status ivrgs_edit_adam(float* d_edit_table, const float* d_edit_grad, int32_t n_models, float* d_state,
+                             int32_t learn, float lr, float beta1, float beta2, float eps, void* stream);
 
 /* Opt-in per-kernel timing (measurement support; the paper has no counterpart). With
    on != 0 every kernel launch of the library is bracketed by two CUDA events on its stream.

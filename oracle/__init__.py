@@ -9,7 +9,8 @@ passages of the paper each step follows); this module does the bookkeeping:
 
 * composition (Sec. 4.5): the basic models' attributes are concatenated in model order;
 * the edit table (Sec. 4.5, 4.6): per model [c_p(3), opacity scale, visible, 0, 0, 0], then
-  lambda(4) and b(4), with k' = lambda * (k_a, k_d, k_s, beta) + b;
+  lambda(4) and b(4), with k' = lambda * (k_a, k_d, k_s, beta) + b, then an optional global
+  orbital light direction (l(3), on) that replaces every view's own (Sec. 4.6);
 * per view: projection + shading, float32-decided binning, compositing, and the reverse
   mode of all of it.
 
@@ -102,13 +103,17 @@ def compose(models) -> Composed:
 
 def edit_table(edits) -> np.ndarray:
     M = len(edits.opacity_scale)
-    t = np.zeros(M * EDIT_STRIDE + 8, np.float64)
+    t = np.zeros(M * EDIT_STRIDE + 12, np.float64)
     for m in range(M):
         t[m * EDIT_STRIDE:m * EDIT_STRIDE + 3] = edits.palette[m]
         t[m * EDIT_STRIDE + 3] = edits.opacity_scale[m]
         t[m * EDIT_STRIDE + 4] = 1.0 if edits.visible[m] else 0.0
     t[M * EDIT_STRIDE:M * EDIT_STRIDE + 4] = edits.lam
     t[M * EDIT_STRIDE + 4:M * EDIT_STRIDE + 8] = edits.bias
+    ld = getattr(edits, "light_dir", None)
+    if ld is not None:  # one light direction for every orbital view (Sec. 4.6)
+        t[M * EDIT_STRIDE + 8:M * EDIT_STRIDE + 11] = ld
+        t[M * EDIT_STRIDE + 11] = 1.0
     return t
 
 

@@ -32,7 +32,9 @@
  * Gradients (reverse mode of all of the above) are taken w.r.t. the stored parameters:
  * mean, log-scale, unnormalised quaternion and normal, opacity logit, colour offset,
  * (k_a,k_d,k_s,beta), and the edit parameters {c_p, opacity scale} per model, {lambda, b}
- * global, and the orbital light direction per view.
+ * global, and the orbital light direction: per view, or the edit table's global light
+ * direction when that is switched on (Sec. 4.6 learns one light direction for the composed
+ * model, as polar and azimuthal angles).
  */
 #include <math.h>
 #include <stdint.h>
@@ -56,8 +58,15 @@ typedef struct {
     const int32_t* model_id;
 } orc_gaussians;
 
-/* edit table: per model m: [c_p(3), opacity scale, visible, 0, 0, 0]; then lambda(4), b(4) */
+/* edit table: per model m: [c_p(3), opacity scale, visible, 0, 0, 0]; then lambda(4), b(4),
+   global light (l_x, l_y, l_z, on): with on != 0 every view with an orbital light uses
+   l / |l| instead of its own light_dir */
 #define EDIT_STRIDE 8
+
+static const double* table_light(const double* edit, int32_t n_models) {
+    const double* L = edit + (int64_t)n_models * EDIT_STRIDE + 8;
+    return L[3] != 0.0 ? L : NULL;
+}
 
 static double sigmoid(double x) { return 1.0 / (1.0 + exp(-x)); }
 
@@ -203,8 +212,10 @@ static void project_one(const orc_gaussians* G, int64_t g, const double* edit, i
     if (cam->headlight) {
         for (int c = 0; c < 3; ++c) f->l[c] = f->vdir[c];
     } else {
-        double ll = norm3(cam->light_dir);
-        for (int c = 0; c < 3; ++c) f->l[c] = cam->light_dir[c] / ll;
+        const double* L = table_light(edit, n_models);
+        const double* ld = L ? L : cam->light_dir;
+        double ll = norm3(ld);
+        for (int c = 0; c < 3; ++c) f->l[c] = ld[c] / ll;
     }
     for (int c = 0; c < 3; ++c) f->hv[c] = f->vdir[c] + f->l[c];
     f->hlen = norm3(f->hv);
@@ -575,10 +586,14 @@ void orc_project_backward(int64_t n, const double* mean, const double* log_scale
         if (cam->headlight) {
             for (int c = 0; c < 3; ++c) dv[c] += dl[c];
         } else {
-            double ll = norm3(cam->light_dir);
-            double lh[3] = {cam->light_dir[0] / ll, cam->light_dir[1] / ll, cam->light_dir[2] / ll};
+            /* gradient w.r.t. the direction actually used: the table's or the view's */
+            const double* L = table_light(edit, n_models);
+            const double* lsrc = L ? L : cam->light_dir;
+            double* dst = L ? d_edit + (int64_t)n_models * EDIT_STRIDE + 8 : d_light;
+            double ll = norm3(lsrc);
+            double lh[3] = {lsrc[0] / ll, lsrc[1] / ll, lsrc[2] / ll};
             double ld = dot3(lh, dl);
-            for (int c = 0; c < 3; ++c) d_light[c] += (dl[c] - lh[c] * ld) / ll;
+            for (int c = 0; c < 3; ++c) dst[c] += (dl[c] - lh[c] * ld) / ll;
         }
         {
             double nd = dot3(f.nn, dnn);

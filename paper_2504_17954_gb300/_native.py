@@ -29,6 +29,10 @@ IVRGS_ANCHOR_CHUNK = 256
 IVRGS_BIN_EXACT = 0
 IVRGS_BIN_CAPACITY = 1
 IVRGS_BIN_CULL = 2
+IVRGS_LEARN_COLOR = 1
+IVRGS_LEARN_OPACITY = 2
+IVRGS_LEARN_LIGHT_MAGNITUDE = 4
+IVRGS_LEARN_LIGHT_DIRECTION = 8
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CAPACITY", 3: "CUDA_ERROR", 4: "TIMEOUT", 5: "UNSUPPORTED"}
 
@@ -45,7 +49,7 @@ class ivrgs_model_edit(C.Structure):
 
 
 class ivrgs_light(C.Structure):
-    _fields_ = [("lambda_", C.c_float * 4), ("bias", C.c_float * 4)]
+    _fields_ = [("lambda_", C.c_float * 4), ("bias", C.c_float * 4), ("dir", C.c_float * 3), ("dir_on", C.c_int32)]
 
 
 class ivrgs_gaussians(C.Structure):
@@ -99,6 +103,13 @@ _SIGNATURES = {
                                                  _P(ivrgs_bins), _P(ivrgs_camera), C.c_int32, C.c_float,
                                                  _P(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p,
                                                  _P(ivrgs_gaussians), C.c_void_p, C.c_void_p]),
+    "ivrgs_image_loss_workspace": (C.c_int32, [_P(ivrgs_camera), C.c_int32, _P(C.c_size_t)]),
+    "ivrgs_image_loss": (C.c_int32, [C.c_void_p, C.c_void_p, _P(ivrgs_camera), C.c_int32, C.c_float, C.c_void_p,
+                                     C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ivrgs_edit_adam_state_floats": (C.c_int64, [C.c_int32]),
+    "ivrgs_edit_adam_init": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "ivrgs_edit_adam": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_float, C.c_float,
+                                    C.c_float, C.c_float, C.c_void_p]),
     "ivrgs_debug_bin_hooks": (None, [C.c_longlong, C.c_longlong]),
     "ivrgs_prof_enable": (None, [C.c_int32]),
     "ivrgs_prof_report": (C.c_int64, [C.c_char_p, C.c_int64]),
@@ -238,3 +249,21 @@ def prof_report() -> dict:
         name, cnt, ms = line.split()
         out[name] = (int(cnt), float(ms))
     return out
+
+
+def ivrgs_image_loss_workspace(cams, n_views) -> int:
+    b = C.c_size_t(0)
+    call("ivrgs_image_loss_workspace", cams, n_views, C.byref(b))
+    return int(b.value)
+
+
+def ivrgs_image_loss(d_rgba, d_target, cams, n_views, lambda_ssim, ws, ws_bytes, d_loss, d_dL, stream):
+    return call("ivrgs_image_loss", d_rgba, d_target, cams, n_views, lambda_ssim, ws, ws_bytes, d_loss, d_dL, stream)
+
+
+def ivrgs_edit_adam_init(d_table, n_models, d_state, stream):
+    return call("ivrgs_edit_adam_init", d_table, n_models, d_state, stream)
+
+
+def ivrgs_edit_adam(d_table, d_egrad, n_models, d_state, learn, lr, beta1, beta2, eps, stream):
+    return call("ivrgs_edit_adam", d_table, d_egrad, n_models, d_state, learn, lr, beta1, beta2, eps, stream)

@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <string>
 
 #include "common.cuh"
@@ -175,7 +176,7 @@ ivrgs_status ivrgs_get_option(const char* name, int64_t* value) {
     return IVRGS_OK;
 }
 
-int64_t ivrgs_edit_table_floats(int32_t n_models) { return (int64_t)IVRGS_EDIT_STRIDE * n_models + 8; }
+int64_t ivrgs_edit_table_floats(int32_t n_models) { return (int64_t)IVRGS_EDIT_STRIDE * n_models + 12; }
 
 ivrgs_status ivrgs_compose_edit(const ivrgs_gaussians* models, int32_t n_models, const ivrgs_model_edit* edits,
                                 const ivrgs_light* light, ivrgs_gaussians* composed, float* d_edit_table,
@@ -408,3 +409,67 @@ ivrgs_status ivrgs_render_backward_accumulate(const ivrgs_gaussians* g, const fl
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------- inverse exploration
+static long long packed_pixels(const CamBatch& cb) {
+    long long n = 0;
+    for (int v = 0; v < cb.n; ++v) n = std::max(n, cb.c[v].pix0 + (long long)cb.c[v].W * cb.c[v].H);
+    return n;
+}
+
+ivrgs_status ivrgs_image_loss_workspace(const ivrgs_camera* cams, int32_t n_views, size_t* bytes) {
+    set_error("");
+    if (!bytes) return invalid("bytes is NULL");
+    static thread_local CamBatch cb;
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    if (st) return st;
+    *bytes = image_loss_workspace(cb, packed_pixels(cb));
+    return IVRGS_OK;
+}
+
+ivrgs_status ivrgs_image_loss(const float* d_rgba, const float* d_target, const ivrgs_camera* cams, int32_t n_views,
+                              float lambda_ssim, void* d_workspace, size_t ws_bytes, float* d_loss,
+                              float* d_dL_drgba, void* stream) {
+    set_error("");
+    static thread_local CamBatch cb;
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    if (st) return st;
+    if (!d_rgba || !d_target || !d_loss || !d_dL_drgba) return invalid("device arrays must be non-NULL");
+    if (!aligned(d_rgba, 16) || !aligned(d_target, 16) || !aligned(d_dL_drgba, 16))
+        return invalid("d_rgba, d_target and d_dL_drgba must be 16-byte aligned");
+    if (!(lambda_ssim >= 0.0f && lambda_ssim <= 1.0f)) return invalid("lambda_ssim must be in [0, 1]");
+    const long long n_pix = packed_pixels(cb);
+    const size_t need = image_loss_workspace(cb, n_pix);
+    if (!d_workspace || ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return IVRGS_ERR_CAPACITY;
+    }
+    if (!aligned(d_workspace, 256)) return invalid("workspace must be 256-byte aligned");
+    return cuda_status(launch_image_loss(d_rgba, d_target, cb, n_pix, lambda_ssim, static_cast<char*>(d_workspace),
+                                         d_loss, d_dL_drgba, (cudaStream_t)stream),
+                       "ivrgs_image_loss");
+}
+
+int64_t ivrgs_edit_adam_state_floats(int32_t n_models) { return 2ll * (4ll * n_models + 10) + 3; }
+
+ivrgs_status ivrgs_edit_adam_init(const float* d_edit_table, int32_t n_models, float* d_state, void* stream) {
+    set_error("");
+    if (n_models < 1 || n_models > IVRGS_MAX_MODELS) return invalid("n_models out of range");
+    if (!d_edit_table || !d_state) return invalid("device arrays must be non-NULL");
+    return cuda_status(launch_edit_adam_init(d_edit_table, n_models, d_state, (cudaStream_t)stream),
+                       "ivrgs_edit_adam_init");
+}
+
+ivrgs_status ivrgs_edit_adam(float* d_edit_table, const float* d_edit_grad, int32_t n_models, float* d_state,
+                             int32_t learn, float lr, float beta1, float beta2, float eps, void* stream) {
+    set_error("");
+    if (n_models < 1 || n_models > IVRGS_MAX_MODELS) return invalid("n_models out of range");
+    if (!d_edit_table || !d_edit_grad || !d_state) return invalid("device arrays must be non-NULL");
+    if (learn & ~(IVRGS_LEARN_COLOR | IVRGS_LEARN_OPACITY | IVRGS_LEARN_LIGHT_MAGNITUDE | IVRGS_LEARN_LIGHT_DIRECTION))
+        return invalid("unknown bits in learn");
+    if (!(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return invalid("need lr > 0, 0 <= beta1, beta2 < 1, eps > 0");
+    return cuda_status(launch_edit_adam(d_edit_table, d_edit_grad, n_models, d_state, learn, lr, beta1, beta2, eps,
+                                        (cudaStream_t)stream),
+                       "ivrgs_edit_adam");
+}

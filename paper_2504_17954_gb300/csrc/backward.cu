@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
     GaussLocal G;
     if (active) load_gauss<PREC>(g, table, M, i, G);
     else G.visible = false;
+    const bool tl_on = __ldg(table + (long long)M * IVRGS_EDIT_STRIDE + 11) != 0.0f;  // uniform
     float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float dcv[3] = {0.f, 0.f, 0.f}, dkp[4] = {0.f, 0.f, 0.f, 0.f}, dnn[3] = {0.f, 0.f, 0.f}, dop = 0.f;
     for (int v = 0; v < cb.n; ++v) {
@@ -293,9 +294,11 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
                 }
                 if (c.headlight) {
                     for (int k = 0; k < 3; ++k) dv[k] += dl[k];
-                } else {
-                    const float ld = c.light[0] * dl[0] + c.light[1] * dl[1] + c.light[2] * dl[2];
-                    for (int k = 0; k < 3; ++k) dlv[k] = (dl[k] - c.light[k] * ld) / c.light_len;
+                } else {  // gradient w.r.t. the direction used: the table's global light or the view's
+                    const float* lh = G.tl_on ? G.tl : c.light;
+                    const float ll = G.tl_on ? G.tl_len : c.light_len;
+                    const float ld = lh[0] * dl[0] + lh[1] * dl[1] + lh[2] * dl[2];
+                    for (int k = 0; k < 3; ++k) dlv[k] = (dl[k] - lh[k] * ld) / ll;
                 }
                 {
                     const float vd = V.vd[0] * dv[0] + V.vd[1] * dv[1] + V.vd[2] * dv[2];
@@ -366,7 +369,10 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
             if (threadIdx.x < 3) {
                 float t = 0.f;
                 for (int w = 0; w < 8; ++w) t += s_red[w][threadIdx.x];
-                if (t != 0.f) atomicAdd(&egrad[(long long)M * IVRGS_EDIT_STRIDE + 8 + 4 * v + threadIdx.x], t);
+                // the table's global light (its slot) or the view's light_dir (the per-view tail)
+                const long long slot = tl_on ? (long long)M * IVRGS_EDIT_STRIDE + 8
+                                             : (long long)M * IVRGS_EDIT_STRIDE + 12 + 4 * v;
+                if (t != 0.f) atomicAdd(&egrad[slot + threadIdx.x], t);
             }
         }
     }
@@ -497,10 +503,10 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
     float* g2 = reinterpret_cast<float*>(g1 + vn);
     cudaError_t e;
     if ((e = cudaMemsetAsync(ws, 0, (size_t)vn * 36, s)) != cudaSuccess) return e;
-    const long long ne = (long long)g->n_models * IVRGS_EDIT_STRIDE + 8 + 4ll * cb.n;
+    const long long ne = (long long)g->n_models * IVRGS_EDIT_STRIDE + 12 + 4ll * cb.n;
     // the per-view light gradients (the tail) always start at zero; the edit gradients only
     // when not accumulating over view waves
-    const long long ne0 = accumulate ? (long long)g->n_models * IVRGS_EDIT_STRIDE + 8 : 0;
+    const long long ne0 = accumulate ? (long long)g->n_models * IVRGS_EDIT_STRIDE + 12 : 0;
     if ((e = cudaMemsetAsync(edit_grad + ne0, 0, sizeof(float) * (size_t)(ne - ne0), s)) != cudaSuccess) return e;
     if (cb.n_tiles > 0) {
         IVRGS_PROF("k_render_bwd", s);

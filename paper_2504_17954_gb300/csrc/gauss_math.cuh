@@ -24,6 +24,8 @@ struct GaussLocal {
     float k[4], kp[4];      // stored k and edited k' = lambda k + b
     float sig, o;           // sigmoid(logit), o' = s_m sigmoid
     float sm;               // opacity scale of the model
+    float tl[3], tl_len;    // the edit table's global light, normalised, and its length
+    bool tl_on;             // the global light replaces every orbital view's light_dir
     int model;
     bool visible;
 };
@@ -101,6 +103,16 @@ __device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float
     G.k[0] = kk.x; G.k[1] = kk.y; G.k[2] = kk.z; G.k[3] = kk.w;
     const float* lam = table + (long long)n_models * IVRGS_EDIT_STRIDE;
     for (int c = 0; c < 4; ++c) G.kp[c] = __ldg(lam + c) * G.k[c] + __ldg(lam + 4 + c);
+    G.tl_on = __ldg(lam + 11) != 0.0f;
+    if (G.tl_on) {
+        const float l0 = __ldg(lam + 8), l1 = __ldg(lam + 9), l2 = __ldg(lam + 10);
+        G.tl_len = sqrtf(l0 * l0 + l1 * l1 + l2 * l2);
+        const float il = 1.0f / G.tl_len;
+        G.tl[0] = l0 * il; G.tl[1] = l1 * il; G.tl[2] = l2 * il;
+    } else {
+        G.tl[0] = G.tl[1] = G.tl[2] = 0.0f;
+        G.tl_len = 1.0f;
+    }
     G.sig = 1.0f / (1.0f + expf(-logit));
     G.sm = __ldg(me + 3);
     G.o = G.sm * G.sig;
@@ -181,7 +193,7 @@ __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& 
     if (c.headlight) {
         for (int k = 0; k < 3; ++k) V.l[k] = V.vd[k];
     } else {
-        for (int k = 0; k < 3; ++k) V.l[k] = c.light[k];
+        for (int k = 0; k < 3; ++k) V.l[k] = G.tl_on ? G.tl[k] : c.light[k];
     }
     float hv[3] = {V.vd[0] + V.l[0], V.vd[1] + V.l[1], V.vd[2] + V.l[2]};
     V.hlen = sqrtf(hv[0] * hv[0] + hv[1] * hv[1] + hv[2] * hv[2]);

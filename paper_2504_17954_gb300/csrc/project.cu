@@ -51,13 +51,13 @@ cudaError_t launch_compose(const ivrgs_gaussians* models, int32_t n_models, ivrg
 // ------------------------------------------------------------------------- edit table
 struct EditParams {
     int n_models;
-    float lam[4], bias[4];
+    float lam[4], bias[4], light[4];
     float e[IVRGS_MAX_MODELS][5];
 };
 
 __global__ void k_edit_table(const __grid_constant__ EditParams p, float* __restrict__ table) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int total = p.n_models * IVRGS_EDIT_STRIDE + 8;
+    const int total = p.n_models * IVRGS_EDIT_STRIDE + 12;
     if (i >= total) return;
     float v = 0.0f;
     if (i < p.n_models * IVRGS_EDIT_STRIDE) {
@@ -65,7 +65,7 @@ __global__ void k_edit_table(const __grid_constant__ EditParams p, float* __rest
         v = k < 5 ? p.e[m][k] : 0.0f;
     } else {
         const int k = i - p.n_models * IVRGS_EDIT_STRIDE;
-        v = k < 4 ? p.lam[k] : p.bias[k - 4];
+        v = k < 4 ? p.lam[k] : (k < 8 ? p.bias[k - 4] : p.light[k - 8]);
     }
     table[i] = v;
 }
@@ -78,6 +78,8 @@ cudaError_t launch_edit_table(const ivrgs_model_edit* edits, int32_t n_models, c
         p.lam[k] = light->lambda[k];
         p.bias[k] = light->bias[k];
     }
+    for (int k = 0; k < 3; ++k) p.light[k] = light->dir[k];
+    p.light[3] = light->dir_on ? 1.0f : 0.0f;
     for (int m = 0; m < n_models; ++m) {
         p.e[m][0] = edits[m].palette[0];
         p.e[m][1] = edits[m].palette[1];
@@ -85,7 +87,7 @@ cudaError_t launch_edit_table(const ivrgs_model_edit* edits, int32_t n_models, c
         p.e[m][3] = edits[m].opacity_scale;
         p.e[m][4] = edits[m].visible ? 1.0f : 0.0f;
     }
-    const int total = n_models * IVRGS_EDIT_STRIDE + 8;
+    const int total = n_models * IVRGS_EDIT_STRIDE + 12;
     {
         IVRGS_PROF("k_edit_table", s);
         k_edit_table<<<(total + 255) / 256, 256, 0, s>>>(p, table);

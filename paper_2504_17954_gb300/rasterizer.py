@@ -108,7 +108,7 @@ def pack_mixed(g: Gaussians, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), stream=N
     return out, order
 
 
-def edit_structs(palette, opacity_scale, visible, lam, bias):
+def edit_structs(palette, opacity_scale, visible, lam, bias, light_dir=None):
     M = len(opacity_scale)
     ed = (N.ivrgs_model_edit * M)()
     for m in range(M):
@@ -120,16 +120,22 @@ def edit_structs(palette, opacity_scale, visible, lam, bias):
     for k in range(4):
         li.lambda_[k] = float(lam[k])
         li.bias[k] = float(bias[k])
+    if light_dir is not None:
+        for k in range(3):
+            li.dir[k] = float(light_dir[k])
+        li.dir_on = 1
     return ed, li
 
 
 def compose_edit(models: Sequence[Gaussians], palette, opacity_scale, visible, lam, bias, device="cuda",
-                 composed: Optional[Gaussians] = None, edit_table: Optional[torch.Tensor] = None, stream=None):
+                 composed: Optional[Gaussians] = None, edit_table: Optional[torch.Tensor] = None, stream=None,
+                 light_dir=None):
     """Concatenate basic models on the device and write the edit table (ivrgs_compose_edit).
 
-    With ``models`` empty (or None) and ``composed`` None only the edit table is rewritten."""
+    With ``models`` empty (or None) and ``composed`` None only the edit table is rewritten.
+    ``light_dir`` (3 floats) switches on the global light that replaces every orbital view's."""
     M = len(opacity_scale)
-    ed, li = edit_structs(palette, opacity_scale, visible, lam, bias)
+    ed, li = edit_structs(palette, opacity_scale, visible, lam, bias, light_dir)
     if edit_table is None:
         edit_table = torch.empty(N.lib().ivrgs_edit_table_floats(M), dtype=torch.float32, device=device)
     comp_s = None

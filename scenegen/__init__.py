@@ -222,10 +222,12 @@ class Edits:
     visible: np.ndarray        # [M] int32
     lam: np.ndarray = field(default_factory=lambda: np.ones(4, np.float32))
     bias: np.ndarray = field(default_factory=lambda: np.zeros(4, np.float32))
+    light_dir: Optional[np.ndarray] = None  # one orbital light direction for every view, or None
 
     def copy(self) -> "Edits":
         return Edits(*(np.array(a, copy=True) for a in (self.palette, self.opacity_scale,
-                                                        self.visible, self.lam, self.bias)))
+                                                        self.visible, self.lam, self.bias)),
+                     light_dir=None if self.light_dir is None else np.array(self.light_dir, copy=True))
 
 
 def identity_edits(models: List[Model]) -> Edits:

@@ -39,7 +39,8 @@ def device_models(models) -> List[Gaussians]:
 def setup(w: sg.Workload, capacity=None, edits=None, cull=True):
     ed = w.edits if edits is None else edits
     dm = device_models(w.models)
-    comp, table = compose_edit(dm, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias)
+    comp, table = compose_edit(dm, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias,
+                               light_dir=getattr(ed, "light_dir", None))
     rast = Rasterizer(w.cameras, comp.n, len(w.models), capacity=capacity, lowpass=w.lowpass, bg=w.bg, cull=cull)
     return rast, comp, table
 

@@ -25,7 +25,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_side_argument_checks(lib):
     assert lib.ivrgs_version() >= 100
-    assert lib.ivrgs_edit_table_floats(5) == 48
+    assert lib.ivrgs_edit_table_floats(5) == 52
     st = lib.ivrgs_project(None, None, None, 1, 0.3, None, None)
     assert st == N.IVRGS_ERR_INVALID_ARG and "NULL" in N.last_error()
     cams = (N.ivrgs_camera * 2)()

@@ -243,11 +243,11 @@ def test_forward_end_to_end(which, pixels_per_thread):
 
 
 # ------------------------------------------------------------------ backward
-@pytest.mark.parametrize("which", ["fd", "fd_orbital", "multi"])
+@pytest.mark.parametrize("which", ["fd", "fd_orbital", "fd_table_light", "multi"])
 def test_backward_matches_oracle(which, pixels_per_thread):
     if which.startswith("fd"):
         from tests.test_oracle_grad_fd import _scene
-        models, ed, cams = _scene(which == "fd_orbital")
+        models, ed, cams = _scene(which != "fd", which == "fd_table_light")
         w = sg.Workload("fd", models, cams, ed, bg=np.array([0.2, 0.1, 0.3], np.float32))
     else:
         w = _multi_view_scene(seed=27)
@@ -271,6 +271,9 @@ def test_backward_matches_oracle(which, pixels_per_thread):
         sl = slice(8 * m, 8 * m + 4)
         assert _gpu.rel_l2(eg[sl], gref.edit[sl]) < 1e-3, (m, eg[sl], gref.edit[sl])
     assert _gpu.rel_l2(eg[8 * M:ne], gref.edit[8 * M:]) < 1e-3
+    if which == "fd_table_light":  # the global light's gradient on its own
+        assert _gpu.rel_l2(eg[8 * M + 8:8 * M + 11], gref.edit[8 * M + 8:8 * M + 11]) < 1e-3
+        assert np.abs(gref.edit[8 * M + 8:8 * M + 11]).max() > 0
     light = eg[ne:].reshape(len(w.cameras), 4)[:, :3]
     for v, c in enumerate(w.cameras):
         if c.headlight:

@@ -24,7 +24,7 @@ def _signature(r):
             tuple(l.tobytes() for l in r.last), tuple(m[..., 4:].tobytes() for m in r.margins))
 
 
-def _scene(orbital: bool):
+def _scene(orbital, table_light=False):
     w = sg.fd_subscene()
     if orbital:
         c = w.cameras[0]
@@ -40,12 +40,15 @@ def _scene(orbital: bool):
     ed.opacity_scale[:] = [0.8, 1.1]
     ed.lam = np.array([1.1, 0.9, 1.2, 0.8], np.float32)
     ed.bias = np.array([0.02, -0.01, 0.03, 1.0], np.float32)
+    if table_light:  # the global light of the edit table overrides the view's (Sec. 4.6)
+        ed.light_dir = np.array(sg.orbital_light(-50.0, 0.4), np.float64) * 1.7
     return models, ed, w.cameras
 
 
-@pytest.mark.parametrize("orbital", [False, True])
-def test_oracle_gradient_matches_central_fd(orbital):
-    models, ed, cams = _scene(orbital)
+@pytest.mark.parametrize("orbital,table_light", [(False, False), (True, False), (True, True)],
+                         ids=["headlight", "orbital", "table_light"])
+def test_oracle_gradient_matches_central_fd(orbital, table_light):
+    models, ed, cams = _scene(orbital, table_light)
     comp = oracle.compose(models)
     table = oracle.edit_table(ed)
     bg = np.array([0.2, 0.1, 0.3])
@@ -65,6 +68,8 @@ def test_oracle_gradient_matches_central_fd(orbital):
             j = int(rng.integers(0, arr.shape[1])) if arr.ndim == 2 else None
             return ("param", k, g, j)
         kind = rng.integers(0, 4 if not orbital else 5)
+        if kind == 4 and table_light:
+            return ("edit", M * 8 + 8 + int(rng.integers(0, 3)), None, None)
         if kind == 0:
             return ("edit", int(rng.integers(0, M)) * 8 + int(rng.integers(0, 3)), None, None)
         if kind == 1:
@@ -124,3 +129,28 @@ def test_oracle_gradient_matches_central_fd(orbital):
         assert tol(fd), (kind, a, b, c, fd, an)
     assert checked == 64 and flipped < checked and refined <= 8, (checked, flipped, refined)
     print(f"checked {checked}, flipped {flipped}, refined {refined}, max rel err {max(errs):.2e}")
+
+
+def test_table_light_replaces_the_view_light():
+    """The edit table's global light gives the image of a view whose own light_dir is that
+    direction (any length: only l / |l| is used), and leaves the view's light_dir without a
+    gradient; switched off (4th entry 0) it changes nothing."""
+    models, ed, cams = _scene(True)
+    bg = np.array([0.1, 0.2, 0.3])
+    ref = oracle.render(models, ed, cams, bg=bg)
+    ed2 = ed.copy()
+    ed2.light_dir = np.array(cams[0].light_dir, np.float64) * 3.0
+    cams2 = [sg.Camera(**{**c.__dict__, "light_dir": np.array([0.0, 0.0, 1.0])}) for c in cams]
+    r2 = oracle.render(models, ed2, cams2, bg=bg)
+    np.testing.assert_allclose(r2.images[0], ref.images[0], rtol=0, atol=1e-14)
+    wts = [np.ones((c.H, c.W, 4)) for c in cams]
+    g2 = oracle.render_backward(r2, cams2, wts, bg=bg)
+    assert np.all(g2.light == 0.0)
+    M = len(models)
+    g1 = oracle.render_backward(ref, cams, wts, bg=bg)
+    # d/dl of the table light (length 3) = d/dl of the view light (length 1) / 3
+    np.testing.assert_allclose(g2.edit[M * 8 + 8:M * 8 + 11] * 3.0, g1.light[0], rtol=1e-10, atol=1e-12)
+    t = oracle.edit_table(ed2)
+    t[M * 8 + 11] = 0.0
+    r3 = oracle.render(models, ed2, cams, bg=bg, table=t)
+    np.testing.assert_array_equal(r3.images[0], ref.images[0])
