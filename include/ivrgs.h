@@ -248,6 +248,18 @@ ivrgs_status ivrgs_render(const ivrgs_projected* p, const ivrgs_bins* b, const i
                           int32_t n_views, const float* bg, float* d_rgba, float* d_final_T, uint32_t* d_last,
                           void* stream);
 
+/* Auxiliary maps with the compositing weights of ivrgs_render (Sec. 4.2 first equation: depth
+   and normal maps D, N = sum_i T_i alpha_i {d_i, n_i}; Sec. 4.3: offset-colour and coefficient
+   maps sum_i T_i alpha_i {dc_i, k_i}; the attribute render modes of Sec. 4.7). Inputs: the
+   Gaussians g and edit table of the projection that produced p, and the bins b. Output per
+   packed pixel, d_aux [.][12] float (16-byte aligned): depth (camera z), normal (3, world,
+   unit per Gaussian), dc (3), k' = lambda k + b (4: k_a, k_d, k_s, beta), 1 - T. The walk takes
+   exactly the contributors and weights of ivrgs_render (the last channel equals its alpha).
+   No background term. */
+ivrgs_status ivrgs_render_aux(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
+                              const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float* d_aux,
+                              void* stream);
+
 /* Workspace bytes ivrgs_render_backward needs for n Gaussians and n_views views. */
 ivrgs_status ivrgs_render_backward_workspace(int64_t n, int32_t n_views, size_t* bytes);
 

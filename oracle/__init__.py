@@ -337,3 +337,34 @@ def pixels_backward(comp, table, cams, projs, pix_per_view, dL_per_view, bg=(0.0
             _project_backward(comp, table, c, lowpass, g, params, dedit, dlight[v])
         per_view.append(g)
     return Grads(params, dedit, dlight, per_view)
+
+
+# ----------------------------------------------------------------------------------------
+# Auxiliary maps (Sec. 4.2 depth / normal maps, Sec. 4.3 offset-colour and coefficient maps,
+# the attribute render modes of Sec. 4.7): the RGB blend weights T_i alpha_i applied to
+# per-Gaussian values instead of colours.
+# ----------------------------------------------------------------------------------------
+AUX_CHANNELS = ("depth", "nx", "ny", "nz", "dc_r", "dc_g", "dc_b", "ka", "kd", "ks", "beta")
+
+
+def aux_attributes(comp: Composed, table: np.ndarray, p: Projected) -> np.ndarray:
+    """[N, 11]: camera depth, unit normal (world), offset colour dc, edited k' = lambda k + b."""
+    M = comp.n_models
+    lam = table[M * EDIT_STRIDE:M * EDIT_STRIDE + 4]
+    bias = table[M * EDIT_STRIDE + 4:M * EDIT_STRIDE + 8]
+    nrm = comp.normal / np.linalg.norm(comp.normal, axis=1, keepdims=True)
+    return np.ascontiguousarray(np.c_[p.depth, nrm, comp.dcolor, comp.kads * lam + bias], np.float64)
+
+
+def render_aux(r: "Render", cams, tile=(16, 16)) -> List[np.ndarray]:
+    """Per view [H, W, 12]: the 11 auxiliary channels (AUX_CHANNELS) and 1 - T."""
+    out = []
+    for v, (c, p) in enumerate(zip(cams, r.projs)):
+        aux = aux_attributes(r.comp, r.table, p)
+        o = np.zeros((c.H, c.W, len(AUX_CHANNELS) + 1))
+        lib().orc_render_view_aux(_p(p.uv), _p(p.conic), _p(p.opacity), _p(p.rgb), _p(aux),
+                                  C.c_int32(len(AUX_CHANNELS)), _p(r.bins.values, C.c_uint32),
+                                  _p(r.bins.ranges, C.c_uint32), C.c_int64(int(r.bins.tile_offset[v])),
+                                  C.c_int32(c.W), C.c_int32(c.H), C.c_int32(tile[0]), C.c_int32(tile[1]), _p(o))
+        out.append(o)
+    return out

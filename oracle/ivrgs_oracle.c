@@ -419,6 +419,54 @@ void orc_render_view(const double* uv, const double* conic, const double* opacit
         }
 }
 
+/* Auxiliary maps (Sec. 4.2 first equation: D, N = sum_i T_i alpha_i {d_i, n_i}; Sec. 4.3: the
+   offset-colour and coefficient maps sum_i T_i alpha_i {dc_i, k_i}): per pixel of one view, the
+   contributors and their T_i from blend_pixel, alpha_i from the same formula, and
+   out[p][a] = sum_i T_i alpha_i aux[g_i][a] for a < na, then out[p][na] = 1 - T_final. */
+void orc_render_view_aux(const double* uv, const double* conic, const double* opacity, const double* rgb,
+                         const double* aux, int32_t na, const uint32_t* values, const uint32_t* ranges,
+                         int64_t tile0, int32_t W, int32_t H, int32_t tw, int32_t th, double* out) {
+    orc_view_proj P = {uv, conic, opacity, rgb};
+    int32_t gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int64_t maxlen = 1;
+    for (int64_t t = 0; t < (int64_t)gx * gy; ++t) {
+        int64_t l = (int64_t)ranges[2 * (tile0 + t) + 1] - ranges[2 * (tile0 + t)];
+        if (l > maxlen) maxlen = l;
+    }
+    int64_t* rk = (int64_t*)malloc(sizeof(int64_t) * (size_t)maxlen);
+    double* rT = (double*)malloc(sizeof(double) * (size_t)maxlen);
+    const double zero_bg[3] = {0.0, 0.0, 0.0};
+    for (int32_t ty = 0; ty < gy; ++ty)
+        for (int32_t tx = 0; tx < gx; ++tx) {
+            int64_t t = tile0 + (int64_t)ty * gx + tx;
+            uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+            for (int32_t j = ty * th; j < (ty + 1) * th && j < H; ++j)
+                for (int32_t i = tx * tw; i < (tx + 1) * tw && i < W; ++i) {
+                    int64_t p = (int64_t)j * W + i;
+                    double rgba[4], Tf, px = i + 0.5, py = j + 0.5;
+                    uint32_t last;
+                    int64_t nrec = 0;
+                    blend_pixel(&P, values + s, (int64_t)e - s, px, py, zero_bg, rgba, &Tf, &last, NULL, rk, rT,
+                                &nrec);
+                    double* o = out + (int64_t)(na + 1) * p;
+                    for (int a = 0; a <= na; ++a) o[a] = 0.0;
+                    for (int64_t r = 0; r < nrec; ++r) {
+                        uint32_t g = values[s + rk[r]];
+                        const double* cn = conic + 3 * (int64_t)g;
+                        double dx = uv[2 * (int64_t)g] - px, dy = uv[2 * (int64_t)g + 1] - py;
+                        double Pw = -0.5 * (cn[0] * dx * dx + cn[2] * dy * dy) - cn[1] * dx * dy;
+                        double raw = opacity[g] * exp(Pw);
+                        double alpha = raw < ALPHA_MAX ? raw : ALPHA_MAX;
+                        double w = rT[r] * alpha;
+                        for (int a = 0; a < na; ++a) o[a] += w * aux[(int64_t)na * g + a];
+                    }
+                    o[na] = 1.0 - Tf;
+                }
+        }
+    free(rk);
+    free(rT);
+}
+
 /* Composite a list of pixels, each with its own explicit ordered list (sampled checks). */
 void orc_render_pixels(const double* uv, const double* conic, const double* opacity, const double* rgb,
                        int64_t n_px, const double* pxy, const int64_t* list_off, const uint32_t* lists,

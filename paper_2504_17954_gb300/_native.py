@@ -90,6 +90,8 @@ _SIGNATURES = {
     "ivrgs_bin_check": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "ivrgs_render": (C.c_int32, [_P(ivrgs_projected), _P(ivrgs_bins), _P(ivrgs_camera), C.c_int32,
                                  _P(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ivrgs_render_aux": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_projected), _P(ivrgs_bins),
+                                     _P(ivrgs_camera), C.c_int32, C.c_void_p, C.c_void_p]),
     "ivrgs_render_backward_workspace": (C.c_int32, [C.c_int64, C.c_int32, _P(C.c_size_t)]),
     "ivrgs_render_backward": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_projected), _P(ivrgs_bins),
                                           _P(ivrgs_camera), C.c_int32, C.c_float, _P(C.c_float), C.c_void_p,
@@ -267,3 +269,7 @@ def ivrgs_edit_adam_init(d_table, n_models, d_state, stream):
 
 def ivrgs_edit_adam(d_table, d_egrad, n_models, d_state, learn, lr, beta1, beta2, eps, stream):
     return call("ivrgs_edit_adam", d_table, d_egrad, n_models, d_state, learn, lr, beta1, beta2, eps, stream)
+
+
+def ivrgs_render_aux(g, d_edit_table, p, b, cams, n_views, d_aux, stream):
+    return call("ivrgs_render_aux", g, d_edit_table, p, b, cams, n_views, d_aux, stream)

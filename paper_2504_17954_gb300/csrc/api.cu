@@ -350,6 +350,24 @@ ivrgs_status ivrgs_render(const ivrgs_projected* p, const ivrgs_bins* b, const i
     return cuda_status(launch_render(p, b, cb, bg, d_rgba, d_final_T, d_last, (cudaStream_t)stream), "ivrgs_render");
 }
 
+ivrgs_status ivrgs_render_aux(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
+                              const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float* d_aux,
+                              void* stream) {
+    set_error("");
+    static thread_local CamBatch cb;
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    if (st) return st;
+    if ((st = check_gaussians(g, "g", true, true))) return st;
+    if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
+    if (!p) return invalid("projected is NULL");
+    if (p->n != g->n) return invalid("p->n must equal g->n");
+    if ((st = check_projected(p, p->n, n_views))) return st;
+    if ((st = check_bins(b, cb))) return st;
+    if (!d_edit_table || !d_aux) return invalid("d_edit_table and d_aux must be non-NULL");
+    if (!aligned(d_aux, 16)) return invalid("d_aux must be 16-byte aligned");
+    return cuda_status(launch_render_aux(g, d_edit_table, p, b, cb, d_aux, (cudaStream_t)stream), "ivrgs_render_aux");
+}
+
 ivrgs_status ivrgs_render_backward_workspace(int64_t n, int32_t n_views, size_t* bytes) {
     set_error("");
     if (!bytes || n < 0 || n_views < 1 || n_views > IVRGS_MAX_VIEWS) return invalid("bad arguments");

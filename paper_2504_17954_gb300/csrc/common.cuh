@@ -116,6 +116,8 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
                             ivrgs_bins* out, long long exact_pairs, cudaStream_t s);
 cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const CamBatch& cb, const float* bg,
                           float* rgba, float* final_T, uint32_t* last, cudaStream_t s);
+cudaError_t launch_render_aux(const ivrgs_gaussians* g, const float* table, const ivrgs_projected* p,
+                              const ivrgs_bins* b, const CamBatch& cb, float* aux, cudaStream_t s);
 size_t image_loss_workspace(const CamBatch& cb, long long n_pix);
 cudaError_t launch_image_loss(const float* rgba, const float* target, const CamBatch& cb, long long n_pix,
                               float lambda, char* ws, float* loss, float* dL, cudaStream_t s);

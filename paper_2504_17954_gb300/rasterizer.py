@@ -284,6 +284,19 @@ class Rasterizer:
         self.bin(mode, stream)
         return self.render(stream)
 
+    AUX_CHANNELS = ("depth", "nx", "ny", "nz", "dc_r", "dc_g", "dc_b", "ka", "kd", "ks", "beta", "alpha")
+
+    def render_aux(self, g: Gaussians, edit_table: torch.Tensor, stream=None) -> torch.Tensor:
+        """Auxiliary maps of the last forward (ivrgs_render_aux): [n_pix, 12] with the channels
+        AUX_CHANNELS (depth, normal, offset colour, k', 1 - T)."""
+        if getattr(self, "aux", None) is None:
+            self.aux = torch.empty((self.n_pix, 12), dtype=torch.float32, device=self.device)
+        gs = g.struct()
+        p, b = self.projected_struct(), self.bins_struct()
+        N.ivrgs_render_aux(C.byref(gs), _vp(edit_table), C.byref(p), C.byref(b), self.cam_arr, self.V,
+                           _vp(self.aux), _stream(stream))
+        return self.aux
+
     def backward(self, g: Gaussians, edit_table: torch.Tensor, dL_drgba: torch.Tensor, grad: Optional[Gaussians] = None,
                  stream=None, tensors=None, accumulate: bool = False, edit_grad: Optional[torch.Tensor] = None):
         _check_cuda(dL_drgba, "dL_drgba")

@@ -372,3 +372,40 @@ def test_bin_matches_python_sort_with_ties():
             assert (s, e) == (idx[0], idx[-1] + 1)
         else:
             assert s == e == 0
+
+
+# ------------------------------------------------------------------ auxiliary maps (Sec. 4.2, 4.3)
+def test_aux_maps_reduce_to_alpha_and_colour():
+    """The auxiliary compositing applies the RGB blend weights T_i alpha_i: per-Gaussian values
+    (1, r, g, b) give (1 - T, C) of the colour render with a black background; a scene whose
+    normals all point one way gives N = n (1 - T); the last channel is 1 - T."""
+    import ctypes as C
+    w = sg.tiny_scene(600, 40, 32, 71, log_scale_mu=-3.0, n_models=2)
+    cams = w.cameras
+    r = oracle.render(w.models, w.edits, cams, bg=(0.0, 0.0, 0.0))
+    p = r.projs[0]
+    c = cams[0]
+    aux = np.ascontiguousarray(np.c_[np.ones(len(p.opacity)), p.rgb], np.float64)
+    o = np.zeros((c.H, c.W, 5))
+    oracle.lib().orc_render_view_aux(oracle._p(p.uv), oracle._p(p.conic), oracle._p(p.opacity), oracle._p(p.rgb),
+                                     oracle._p(aux), C.c_int32(4), oracle._p(r.bins.values, C.c_uint32),
+                                     oracle._p(r.bins.ranges, C.c_uint32), C.c_int64(0), C.c_int32(c.W),
+                                     C.c_int32(c.H), C.c_int32(16), C.c_int32(16), oracle._p(o))
+    img = r.images[0]
+    assert img[..., 3].max() > 0.3
+    np.testing.assert_allclose(o[..., 0], img[..., 3], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(o[..., 1:4], img[..., :3], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(o[..., 4], img[..., 3], rtol=0, atol=1e-15)
+    # one shared normal (any length: only its direction is used)
+    for m in w.models:
+        m.normal[:] = np.array([0.3, -2.0, 1.1], np.float32)
+    r2 = oracle.render(w.models, w.edits, cams)
+    maps = oracle.render_aux(r2, cams)[0]
+    n32 = np.array([0.3, -2.0, 1.1], np.float32).astype(np.float64)  # the stored (float32) normal
+    n = n32 / np.linalg.norm(n32)
+    np.testing.assert_allclose(maps[..., 1:4], maps[..., 11:12] * n, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(maps[..., 11], r2.images[0][..., 3], rtol=0, atol=1e-15)
+    # depth lies between the nearest and farthest contributor's depth, times the coverage
+    live = p.radius > 0
+    assert np.all(maps[..., 0] <= p.depth[live].max() * maps[..., 11] + 1e-12)
+    assert np.all(maps[..., 0] >= p.depth[live].min() * maps[..., 11] - 1e-12)
