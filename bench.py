@@ -331,6 +331,22 @@ def run_gpu(args, rank, world):
                  "storage": "FP16 mean offsets from per-256 FP32 anchors, BF16 log-scale/dc/normal, FP16 q/o/k",
                  "bytes_per_gaussian": 44}
         del hm, packed
+    # the vector-quantised storage (Sec. 4.4): k = 256 codebooks per model and attribute
+    vqd = None
+    if not args.no_mixed:
+        from paper_2504_17954_gb300 import vq_compress
+        ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ta.record()
+        q = vq_compress(comp, k=256, iters=16)
+        tb.record()
+        torch.cuda.synchronize()
+        hq = Harness(args, w, q, table, dev, world)
+        qm, _ = hq.timed(K, True)
+        qf, _ = hq.timed(K, False)
+        vqd = {"mpix_s": hq.mpix(qm, K), "fwd_mpix_s": hq.mpix(qf, K), "ms_per_step": qm / K,
+               "storage": "FP32 mean and normal, uint8 indices into per-model k=256 scalar codebooks",
+               "bytes_per_gaussian": 41, "codebook_build_ms": ta.elapsed_time(tb)}
+        del hq, q
     # the plain single-view form (500k Gaussians, one 800x800 view, float32)
     single = None
     if not args.no_mixed and args.workload == "cfg4":
@@ -387,7 +403,7 @@ def run_gpu(args, rank, world):
            "launch": "eager" if args.eager else "cuda-graph replay",
            "eager_mpix_s": h.mpix(ms_eager, K),
            "roofline": roof, "kernels": kern_table, "clocks": clocks,
-           "batched_mixed": mixed, "plain_single_view": single, "inverse_exploration": inverse,
+           "batched_mixed": mixed, "batched_vq": vqd, "plain_single_view": single, "inverse_exploration": inverse,
            "source_hash": source_hash(),
            "gpu_launches": int(round(launches_per_step * K))}
 

@@ -59,7 +59,9 @@ enum {
 #define IVRGS_EDIT_STRIDE 8    /* floats per model in the edit table */
 #define IVRGS_MAX_PAIRS ((int64_t)1 << 30) /* (tile, Gaussian) pairs per ivrgs_bin call */
 
-enum { IVRGS_FP32 = 0, IVRGS_MIXED = 1 };
+enum { IVRGS_FP32 = 0, IVRGS_MIXED = 1, IVRGS_VQ = 2 };
+#define IVRGS_VQ_ATTRS 8       /* codebooks per model: log_scale, quat, opacity_logit, dcolor, k_a, k_d, k_s, beta */
+#define IVRGS_VQ_MAX_K 256     /* codebook entries at most (u8 indices) */
 #define IVRGS_ANCHOR_CHUNK 256 /* Gaussians per float32 position anchor in IVRGS_MIXED storage */
 enum { IVRGS_BIN_EXACT = 0, IVRGS_BIN_CAPACITY = 1, IVRGS_BIN_CULL = 2 };
 
@@ -108,11 +110,18 @@ typedef struct {
    (anchor: float32 [ceil(n / 256)][3]); log_scale BF16 [n][3]; quat FP16 [n][4]; opacity_logit
    FP16 [n]; dcolor BF16 [n][3]; normal BF16 [n][3]; kads FP16 [n][4]. ivrgs_pack_mixed
    writes this layout.
-   model_id [n] (basic model of each Gaussian, < n_models) in both. Gradients are always
-   float32 with the FP32 layout (w.r.t. the decoded values for IVRGS_MIXED). */
+   precision IVRGS_VQ (Sec. 4.4: vector quantisation; mean and normal exact, every other
+   attribute an index into a scalar codebook shared by all components of that attribute
+   within one basic model): mean and normal float32 as in IVRGS_FP32; uint8 indices
+   log_scale [n][3], quat [n][4], opacity_logit [n], dcolor [n][3], kads [n][4]; codebook
+   float32 [n_models][IVRGS_VQ_ATTRS][vq_k], the attributes in the order log_scale, quat,
+   opacity_logit, dcolor, k_a, k_d, k_s, beta (kads component j uses codebook 4 + j).
+   ivrgs_vq_build writes this layout.
+   model_id [n] (basic model of each Gaussian, < n_models) in all. Gradients are always
+   float32 with the FP32 layout (w.r.t. the decoded values for IVRGS_MIXED and IVRGS_VQ). */
 typedef struct {
     int64_t n;
-    int32_t precision; /* IVRGS_FP32 or IVRGS_MIXED */
+    int32_t precision; /* IVRGS_FP32, IVRGS_MIXED or IVRGS_VQ */
     int32_t n_models;
     void* mean;
     void* log_scale;
@@ -122,7 +131,9 @@ typedef struct {
     void* normal;
     void* kads;
     uint16_t* model_id;
-    float* anchor; /* IVRGS_MIXED: float32 [ceil(n / 256)][3]; NULL for IVRGS_FP32 */
+    float* anchor;   /* IVRGS_MIXED: float32 [ceil(n / 256)][3]; unused otherwise */
+    float* codebook; /* IVRGS_VQ: float32 [n_models][IVRGS_VQ_ATTRS][vq_k]; unused otherwise */
+    int32_t vq_k;    /* IVRGS_VQ: codebook entries, 1..IVRGS_VQ_MAX_K */
 } ivrgs_gaussians;
 
 /* Projected Gaussians, one record per (view v, Gaussian g) at index v * n + g.
@@ -202,7 +213,7 @@ ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, 
                            int32_t n_views, float lowpass, ivrgs_projected* out, void* stream);
 
 /* Workspace bytes ivrgs_bin needs for p->n * n_views records (below 2^32) and `capacity` pairs
-   (about 21 bytes per record plus 9 per pair). */
+   (about 57 bytes per record plus 9 per pair). */
 ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera* cams, int32_t tile_w,
                                  int32_t tile_h, int64_t capacity, size_t* bytes);
 
@@ -379,6 +390,25 @@ ivrgs_status ivrgs_edit_adam_init(const float* d_edit_table, int32_t n_models, f
    The step count lives in d_state, so a captured CUDA graph can replay whole iterations. */
 ivrgs_status ivrgs_edit_adam(float* d_edit_table, const float* d_edit_grad, int32_t n_models, float* d_state,
                              int32_t learn, float lr, float beta1, float beta2, float eps, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+   Vector quantisation (Sec. 4.4): codebooks by k-means per basic model and attribute (all
+   attributes but the mean and the normal; one scalar codebook per attribute shared by its
+   components), one uint8 index per component.
+   --------------------------------------------------------------------------------------- */
+/* Workspace bytes of ivrgs_vq_build. */
+ivrgs_status ivrgs_vq_build_workspace(int32_t n_models, int32_t k, size_t* bytes);
+
+/* Builds the IVRGS_VQ storage of src (IVRGS_FP32 with model_id): for every (model, attribute)
+   k centroids initialised evenly over [min, max] of its values, then `iters` Lloyd iterations
+   (nearest centroid by midpoints of the sorted centroids, a value on a midpoint to the lower
+   one; each centroid moved to the mean of its values, an empty one kept; order kept by a
+   running maximum); then every component's index of its nearest centroid. Writes out's index
+   arrays and codebook ([n_models][IVRGS_VQ_ATTRS][k]); out->mean, normal and model_id are not
+   touched (they may share src's arrays). out: precision IVRGS_VQ, same n and n_models, vq_k = k.
+   Workspace 256-byte aligned, ivrgs_vq_build_workspace bytes. */
+ivrgs_status ivrgs_vq_build(const ivrgs_gaussians* src, int32_t k, int32_t iters, ivrgs_gaussians* out,
+                            void* d_workspace, size_t ws_bytes, void* stream);
 
 /* Opt-in per-kernel timing (measurement support; the paper has no counterpart). With
    on != 0 every kernel launch of the library is bracketed by two CUDA events on its stream.

@@ -25,6 +25,9 @@ IVRGS_EDIT_STRIDE = 8
 IVRGS_MAX_PAIRS = 1 << 30
 IVRGS_FP32 = 0
 IVRGS_MIXED = 1
+IVRGS_VQ = 2
+IVRGS_VQ_ATTRS = 8
+IVRGS_VQ_MAX_K = 256
 IVRGS_ANCHOR_CHUNK = 256
 IVRGS_BIN_EXACT = 0
 IVRGS_BIN_CAPACITY = 1
@@ -56,7 +59,7 @@ class ivrgs_gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("precision", C.c_int32), ("n_models", C.c_int32), ("mean", C.c_void_p),
                 ("log_scale", C.c_void_p), ("quat", C.c_void_p), ("opacity_logit", C.c_void_p),
                 ("dcolor", C.c_void_p), ("normal", C.c_void_p), ("kads", C.c_void_p), ("model_id", C.c_void_p),
-                ("anchor", C.c_void_p)]
+                ("anchor", C.c_void_p), ("codebook", C.c_void_p), ("vq_k", C.c_int32)]
 
 
 class ivrgs_projected(C.Structure):
@@ -112,6 +115,9 @@ _SIGNATURES = {
     "ivrgs_edit_adam_init": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ivrgs_edit_adam": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_float, C.c_float,
                                     C.c_float, C.c_float, C.c_void_p]),
+    "ivrgs_vq_build_workspace": (C.c_int32, [C.c_int32, C.c_int32, _P(C.c_size_t)]),
+    "ivrgs_vq_build": (C.c_int32, [_P(ivrgs_gaussians), C.c_int32, C.c_int32, _P(ivrgs_gaussians), C.c_void_p,
+                                   C.c_size_t, C.c_void_p]),
     "ivrgs_debug_bin_hooks": (None, [C.c_longlong, C.c_longlong]),
     "ivrgs_prof_enable": (None, [C.c_int32]),
     "ivrgs_prof_report": (C.c_int64, [C.c_char_p, C.c_int64]),
@@ -273,3 +279,13 @@ def ivrgs_edit_adam(d_table, d_egrad, n_models, d_state, learn, lr, beta1, beta2
 
 def ivrgs_render_aux(g, d_edit_table, p, b, cams, n_views, d_aux, stream):
     return call("ivrgs_render_aux", g, d_edit_table, p, b, cams, n_views, d_aux, stream)
+
+
+def ivrgs_vq_build_workspace(n_models, k) -> int:
+    b = C.c_size_t(0)
+    call("ivrgs_vq_build_workspace", n_models, k, C.byref(b))
+    return int(b.value)
+
+
+def ivrgs_vq_build(src, k, iters, out, ws, ws_bytes, stream):
+    return call("ivrgs_vq_build", src, k, iters, out, ws, ws_bytes, stream)

@@ -82,9 +82,9 @@ static ivrgs_status check_gaussians(const ivrgs_gaussians* g, const char* name, 
                                     bool allow_mixed = false) {
     if (!g) return invalid(std::string(name) + " is NULL");
     if (g->n < 0) return invalid(std::string(name) + ": negative n");
-    if (g->precision != IVRGS_FP32 && g->precision != IVRGS_MIXED)
+    if (g->precision != IVRGS_FP32 && g->precision != IVRGS_MIXED && g->precision != IVRGS_VQ)
         return invalid(std::string(name) + ": unknown precision");
-    if (g->precision == IVRGS_MIXED && !allow_mixed) {
+    if (g->precision != IVRGS_FP32 && !allow_mixed) {
         set_error(std::string(name) + ": this call takes IVRGS_FP32 storage");
         return IVRGS_ERR_UNSUPPORTED;
     }
@@ -98,6 +98,13 @@ static ivrgs_status check_gaussians(const ivrgs_gaussians* g, const char* name, 
         if (!aligned(g->mean, 4) || !aligned(g->log_scale, 4) || !aligned(g->dcolor, 4) || !aligned(g->normal, 4) ||
             !aligned(g->opacity_logit, 4))
             return invalid(std::string(name) + ": misaligned attribute array");
+    } else if (g->precision == IVRGS_VQ) {
+        if (!g->codebook) return invalid(std::string(name) + ": IVRGS_VQ needs the codebook array");
+        if (g->vq_k < 1 || g->vq_k > IVRGS_VQ_MAX_K) return invalid(std::string(name) + ": vq_k out of range");
+        if (!aligned(g->quat, 4) || !aligned(g->kads, 4) || !aligned(g->mean, 4) || !aligned(g->normal, 4) ||
+            !aligned(g->codebook, 4))
+            return invalid(std::string(name) + ": IVRGS_VQ quat/kads indices must be 4-byte aligned");
+        if (!g->model_id) return invalid(std::string(name) + ": IVRGS_VQ needs model_id");
     } else {
         if (!g->anchor) return invalid(std::string(name) + ": IVRGS_MIXED needs the anchor array");
         if (!aligned(g->quat, 8) || !aligned(g->kads, 8))
@@ -490,4 +497,40 @@ ivrgs_status ivrgs_edit_adam(float* d_edit_table, const float* d_edit_grad, int3
     return cuda_status(launch_edit_adam(d_edit_table, d_edit_grad, n_models, d_state, learn, lr, beta1, beta2, eps,
                                         (cudaStream_t)stream),
                        "ivrgs_edit_adam");
+}
+
+// ------------------------------------------------------------------------- vector quantisation
+ivrgs_status ivrgs_vq_build_workspace(int32_t n_models, int32_t k, size_t* bytes) {
+    set_error("");
+    if (!bytes) return invalid("bytes is NULL");
+    if (n_models < 1 || n_models > IVRGS_MAX_MODELS) return invalid("n_models out of range");
+    if (k < 1 || k > IVRGS_VQ_MAX_K) return invalid("k must be in [1, IVRGS_VQ_MAX_K]");
+    *bytes = vq_workspace(n_models, k);
+    return IVRGS_OK;
+}
+
+ivrgs_status ivrgs_vq_build(const ivrgs_gaussians* src, int32_t k, int32_t iters, ivrgs_gaussians* out,
+                            void* d_workspace, size_t ws_bytes, void* stream) {
+    set_error("");
+    ivrgs_status st = check_gaussians(src, "src", true);
+    if (st) return st;
+    if (src->n_models < 1 || src->n_models > IVRGS_MAX_MODELS) return invalid("src->n_models out of range");
+    if (k < 1 || k > IVRGS_VQ_MAX_K) return invalid("k must be in [1, IVRGS_VQ_MAX_K]");
+    if (iters < 0) return invalid("iters must be >= 0");
+    if (!out) return invalid("out is NULL");
+    if (out->precision != IVRGS_VQ || out->n != src->n || out->n_models != src->n_models || out->vq_k != k)
+        return invalid("out must be IVRGS_VQ with the n, n_models of src and vq_k = k");
+    if (src->n > 0 && (!out->log_scale || !out->quat || !out->opacity_logit || !out->dcolor || !out->kads))
+        return invalid("out: NULL index array");
+    if (!out->codebook || !aligned(out->codebook, 4)) return invalid("out: codebook NULL or misaligned");
+    if (src->n > 0 && (!aligned(out->quat, 4) || !aligned(out->kads, 4)))
+        return invalid("out: quat and kads index arrays must be 4-byte aligned");
+    const size_t need = vq_workspace(src->n_models, k);
+    if (!d_workspace || ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return IVRGS_ERR_CAPACITY;
+    }
+    if (!aligned(d_workspace, 256)) return invalid("workspace must be 256-byte aligned");
+    return cuda_status(launch_vq_build(src, k, iters, out, static_cast<char*>(d_workspace), (cudaStream_t)stream),
+                       "ivrgs_vq_build");
 }

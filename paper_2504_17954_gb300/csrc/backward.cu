@@ -528,7 +528,10 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
     }
     if (g->n > 0) {
         IVRGS_PROF("k_project_bwd", s);
-        if (g->precision == IVRGS_MIXED)
+        if (g->precision == IVRGS_VQ)
+            k_project_bwd<IVRGS_VQ><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1, g2,
+                                                                                 *grad, edit_grad, accumulate);
+        else if (g->precision == IVRGS_MIXED)
             k_project_bwd<IVRGS_MIXED><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1,
                                                                                     g2, *grad, edit_grad, accumulate);
         else

@@ -8,7 +8,8 @@
 //             rectangle (with IVRGS_BIN_CULL: of the rectangle's tiles that meet the
 //             opacity cut-off ellipse, tile_cull.cuh), stored per record; per block of 2048
 //             records the number of covered records and pairs;
-//   compact:  the covered records, in record order, as (depth bits, record index);
+//   compact:  the covered records, in record order, as (depth bits, compacted index), with
+//             their pair counts and a packed 32-byte copy of what the emission needs;
 //   sort 1:   stable LSD radix sort of the covered records by depth bits (4 onesweep passes);
 //   count 2:  pair counts of the depth-ordered records, block sums, scan;
 //   emit:     warp-cooperative emission of one (tile id, Gaussian) pair per covered tile, in
@@ -227,10 +228,17 @@ __global__ void __launch_bounds__(1024) k_scan_sums(unsigned long long* __restri
 }
 
 // ------------------------------------------------------------------------- compact
+// Per covered record, in compacted order k: (depth bits, k) for the record sort, its pair count
+// cnt2[k] and the packed record rec[2k..2k+1] = {(u, v, a, b), (c, o', record index, radius)}
+// that the emission gathers in depth order (one 32-byte read instead of four scattered ones).
 __global__ void __launch_bounds__(kScanThreads) k_compact(const unsigned* __restrict__ cnt,
+                                                          const float2* __restrict__ xy,
+                                                          const float4* __restrict__ conic_o,
+                                                          const int* __restrict__ radius,
                                                           const float4* __restrict__ rgbd, long long total,
                                                           const unsigned long long* __restrict__ vis_off,
                                                           unsigned* __restrict__ rkey, unsigned* __restrict__ rval,
+                                                          unsigned* __restrict__ cnt2, float4* __restrict__ rec,
                                                           unsigned* __restrict__ hist) {
     __shared__ unsigned s_hist[kRecPasses * 256];
     __shared__ unsigned s_warp[kScanThreads / 32 + 1];
@@ -241,15 +249,22 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const unsigned* __rest
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long i = base + (long long)j * kScanThreads + threadIdx.x;
-        const unsigned f = (i < total && cnt[i]) ? 1u : 0u;
+        const unsigned c = i < total ? cnt[i] : 0u;
+        const unsigned f = c ? 1u : 0u;
         unsigned excl;
         const unsigned tot = block_excl_scan(f, excl, s_warp);
         if (f) {
+            const unsigned long long k = off + excl;
             const unsigned key = __float_as_uint(rgbd[i].w);
-            rkey[off + excl] = key;
-            rval[off + excl] = (unsigned)i;
+            rkey[k] = key;
+            rval[k] = (unsigned)k;
+            cnt2[k] = c;
+            const float2 p = xy[i];
+            const float4 co = conic_o[i];
+            rec[2 * k] = make_float4(p.x, p.y, co.x, co.y);
+            rec[2 * k + 1] = make_float4(co.z, co.w, __uint_as_float((unsigned)i), __int_as_float(radius[i]));
 #pragma unroll
-            for (int p = 0; p < kRecPasses; ++p) atomicAdd(&s_hist[p * 256 + ((key >> (8 * p)) & 255u)], 1u);
+            for (int q = 0; q < kRecPasses; ++q) atomicAdd(&s_hist[q * 256 + ((key >> (8 * q)) & 255u)], 1u);
         }
         off += tot;
     }
@@ -259,7 +274,7 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const unsigned* __rest
 }
 
 // ------------------------------------------------------------------------- count of sorted records
-__global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* __restrict__ cnt, long long total,
+__global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* __restrict__ cnt2,
                                                                const unsigned* __restrict__ rval,
                                                                const unsigned long long* __restrict__ d_m,
                                                                unsigned long long* __restrict__ sums) {
@@ -271,8 +286,8 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* _
     for (int j = 0; j < kScanItems; ++j) {
         const long long k = base + (long long)j * kScanThreads + threadIdx.x;
         if (k < m) {
-            const long long i = rval[k];
-            if (i < total) pairs += cnt[i];
+            const long long kk = rval[k];
+            if (kk < m) pairs += cnt2[kk];  // always true unless a timed-out sort left a slot unwritten
         }
     }
 #pragma unroll
@@ -292,12 +307,10 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* _
 // runs: its lanes stride over those runs' pairs, so consecutive lanes write consecutive slots.
 // The pairs a warp writes must equal the sum of its records' counts from k_count (the same
 // rounded arithmetic decides both); a mismatch sets bit 1 of the error flag.
-__global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict__ xy,
-                                                       const float4* __restrict__ conic_o,
-                                                       const int* __restrict__ radius, long long n,
+__global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict__ rec,
+                                                       const unsigned* __restrict__ cnt2, long long n,
                                                        const __grid_constant__ CamBatch cb, int cull,
                                                        const unsigned* __restrict__ rval,
-                                                       const unsigned* __restrict__ cnt,
                                                        const unsigned long long* __restrict__ d_m,
                                                        const unsigned long long* __restrict__ pair_off,
                                                        unsigned* __restrict__ tiles, unsigned* __restrict__ vals,
@@ -329,14 +342,18 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float2* __restrict_
             unsigned g = 0;
             CullEll e{};
             if (k < m) {
-                const long long i = rval[k];
-                if (i < total) {  // always true unless a timed-out sort left a slot unwritten
+                const long long kk = rval[k];
+                if (kk < m) {  // always true unless a timed-out sort left a slot unwritten
+                    const float4 r0 = rec[2 * kk], r1 = rec[2 * kk + 1];
+                    const long long i = __float_as_uint(r1.z);
+                    const int r = __float_as_int(r1.w);
                     v = view_of_record(i, n, total);
                     g = (unsigned)(i - (long long)v * n);
-                    c = cnt[i];
-                    float2 p;
-                    if (c && record_rect(xy, radius, i, cb.c[v], p, x0, x1, y0, y1)) {
-                        e = cull_setup(p, conic_o[i], cull);
+                    c = cnt2[kk];
+                    const float2 p = make_float2(r0.x, r0.y);
+                    if (c && r > 0) {
+                        tile_rect(p.x, p.y, r, cb.c[v].gx, cb.c[v].gy, x0, x1, y0, y1);
+                        e = cull_setup(p, make_float4(r0.z, r0.w, r1.x, r1.y), cull);
                         cull_rows(e, y0, y1, ya, yb);
                         rows = (unsigned)(yb - ya);
                     }
@@ -700,6 +717,8 @@ BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity) {
     p.off_block_sums = o;   o = align_up(o + 8 * 3 * nb);
     p.off_rec = o;          o = align_up(o + 4 * 4 * nr);
     p.off_cnt = o;          o = align_up(o + 4 * nr);
+    p.off_cnt2 = o;         o = align_up(o + 4 * nr);
+    p.off_prec = o;         o = align_up(o + 32 * nr);
     p.off_lookback_rec = o; o = align_up(o + 4 * 256 * (size_t)kRecPasses * (size_t)(p.rec_tiles > 0 ? p.rec_tiles : 1));
     p.off_lookback = o;     o = align_up(o + 4 * 256 * (size_t)(p.n_passes > 0 ? p.n_passes : 1) *
                                          (size_t)(p.sort_tiles > 0 ? p.sort_tiles : 1));
@@ -717,7 +736,8 @@ static long long g_skip_publish_tile = -1;
 struct BinBufs {
     unsigned long long *sums, *d_m, *d_n;
     unsigned *hist_rec, *hist_tile, *base_rec, *base_tile, *counter, *flag, *lb_rec, *lb_tile;
-    unsigned *rkey[2], *rval[2], *talt, *valt, *cnt;
+    unsigned *rkey[2], *rval[2], *talt, *valt, *cnt, *cnt2;
+    float4* prec;
 };
 
 static BinBufs bufs(const BinPlan& plan, char* ws, ivrgs_bins* out) {
@@ -739,6 +759,8 @@ static BinBufs bufs(const BinPlan& plan, char* ws, ivrgs_bins* out) {
     b.talt = reinterpret_cast<unsigned*>(ws + plan.off_keys_alt);
     b.valt = reinterpret_cast<unsigned*>(ws + plan.off_vals_alt);
     b.cnt = reinterpret_cast<unsigned*>(ws + plan.off_cnt);
+    b.cnt2 = reinterpret_cast<unsigned*>(ws + plan.off_cnt2);
+    b.prec = reinterpret_cast<float4*>(ws + plan.off_prec);
     return b;
 }
 
@@ -811,8 +833,10 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     // covered records in record order, then by depth
     if (nb > 0) {
         IVRGS_PROF("k_compact", s);
-        k_compact<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt, reinterpret_cast<const float4*>(p->rgbd),
-                                                        plan.n_records, b.sums, b.rkey[0], b.rval[0], b.hist_rec);
+        k_compact<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt, xy, reinterpret_cast<const float4*>(p->conic_o),
+                                                        p->radius, reinterpret_cast<const float4*>(p->rgbd),
+                                                        plan.n_records, b.sums, b.rkey[0], b.rval[0], b.cnt2, b.prec,
+                                                        b.hist_rec);
     }
     {
         IVRGS_PROF("k_hist_scan", s);
@@ -825,7 +849,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     unsigned long long* sums2 = b.sums + 2 * (nb > 0 ? nb : 1);
     if (nb > 0) {
         IVRGS_PROF("k_count_sorted", s);
-        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt, plan.n_records, b.rval[0], b.d_m, sums2);
+        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt2, b.rval[0], b.d_m, sums2);
     }
     {
         IVRGS_PROF("k_scan_sums", s);
@@ -840,9 +864,8 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     }
     if (nb > 0) {
         IVRGS_PROF("k_emit", s);
-        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(xy, reinterpret_cast<const float4*>(p->conic_o), p->radius, p->n,
-                                                     cb, cull, b.rval[0], b.cnt, b.d_m, sums2, t0, v0, cap,
-                                                     plan.n_passes, b.hist_tile, b.flag);
+        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(b.prec, b.cnt2, p->n, cb, cull, b.rval[0], b.d_m, sums2, t0, v0,
+                                                     cap, plan.n_passes, b.hist_tile, b.flag);
     }
     if (plan.n_passes > 0) {
         IVRGS_PROF("k_hist_scan", s);

@@ -85,7 +85,7 @@ struct BinPlan {
     long long sort_tiles;  // radix tiles of the pair sort at full capacity
     // workspace layout (byte offsets); [0, clear_bytes) is zeroed by every call
     size_t off_flag, off_hist, off_base, off_counter, off_total, clear_bytes, off_block_sums, off_rec,
-        off_cnt, off_lookback_rec, off_lookback, off_keys_alt, off_vals_alt, total_bytes;
+        off_cnt, off_cnt2, off_prec, off_lookback_rec, off_lookback, off_keys_alt, off_vals_alt, total_bytes;
 };
 
 ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb);
@@ -118,6 +118,9 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
                           float* rgba, float* final_T, uint32_t* last, cudaStream_t s);
 cudaError_t launch_render_aux(const ivrgs_gaussians* g, const float* table, const ivrgs_projected* p,
                               const ivrgs_bins* b, const CamBatch& cb, float* aux, cudaStream_t s);
+size_t vq_workspace(int n_models, int K);
+cudaError_t launch_vq_build(const ivrgs_gaussians* g, int K, int iters, ivrgs_gaussians* out, char* ws,
+                            cudaStream_t s);
 size_t image_loss_workspace(const CamBatch& cb, long long n_pix);
 cudaError_t launch_image_loss(const float* rgba, const float* target, const CamBatch& cb, long long n_pix,
                               float lambda, char* ws, float* loss, float* dL, cudaStream_t s);

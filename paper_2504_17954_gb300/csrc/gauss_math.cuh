@@ -30,11 +30,36 @@ struct GaussLocal {
     bool visible;
 };
 
-// attribute loads: float32 storage, or the 16-bit IVRGS_MIXED storage decoded to float32
+// codebook value of attribute a (0 log_scale, 1 quat, 2 opacity_logit, 3 dcolor, 4..7 k_a..beta)
+// of model m for the uint8 index q (IVRGS_VQ storage)
+__device__ __forceinline__ float vq_value(const ivrgs_gaussians& g, int m, int a, unsigned q) {
+    return __ldg(g.codebook + ((long long)m * IVRGS_VQ_ATTRS + a) * g.vq_k + q);
+}
+
+// attribute loads: float32 storage, the 16-bit IVRGS_MIXED storage or the IVRGS_VQ codebook
+// indices, decoded to float32 (m = model of Gaussian i, used by IVRGS_VQ)
 template <int PREC>
-__device__ __forceinline__ void load_attrs(const ivrgs_gaussians& g, long long i, float mu[3], float4& q, float ls[3],
-                                           float& logit, float dc[3], float nrm[3], float4& kk) {
-    if constexpr (PREC == IVRGS_FP32) {
+__device__ __forceinline__ void load_attrs(const ivrgs_gaussians& g, long long i, int m, float mu[3], float4& q,
+                                           float ls[3], float& logit, float dc[3], float nrm[3], float4& kk) {
+    if constexpr (PREC == IVRGS_VQ) {
+        const float* mf = static_cast<const float*>(g.mean);
+        const float* nf = static_cast<const float*>(g.normal);
+        const unsigned char* si = static_cast<const unsigned char*>(g.log_scale);
+        const unsigned char* ci = static_cast<const unsigned char*>(g.dcolor);
+        const uchar4 qi = static_cast<const uchar4*>(g.quat)[i];
+        const uchar4 ki = static_cast<const uchar4*>(g.kads)[i];
+        for (int k = 0; k < 3; ++k) {
+            mu[k] = mf[3 * i + k];
+            nrm[k] = nf[3 * i + k];
+            ls[k] = vq_value(g, m, 0, si[3 * i + k]);
+            dc[k] = vq_value(g, m, 3, ci[3 * i + k]);
+        }
+        q = make_float4(vq_value(g, m, 1, qi.x), vq_value(g, m, 1, qi.y), vq_value(g, m, 1, qi.z),
+                        vq_value(g, m, 1, qi.w));
+        logit = vq_value(g, m, 2, static_cast<const unsigned char*>(g.opacity_logit)[i]);
+        kk = make_float4(vq_value(g, m, 4, ki.x), vq_value(g, m, 5, ki.y), vq_value(g, m, 6, ki.z),
+                         vq_value(g, m, 7, ki.w));
+    } else if constexpr (PREC == IVRGS_FP32) {
         const float* m = static_cast<const float*>(g.mean);
         const float* s = static_cast<const float*>(g.log_scale);
         const float* c = static_cast<const float*>(g.dcolor);
@@ -78,7 +103,7 @@ __device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float
     G.visible = __ldg(me + 4) != 0.0f;
     float ls[3], dcol[3], nrm[3], logit;
     float4 q, kk;
-    load_attrs<PREC>(g, i, G.mu, q, ls, logit, dcol, nrm, kk);
+    load_attrs<PREC>(g, i, G.model, G.mu, q, ls, logit, dcol, nrm, kk);
     G.qlen = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
     const float iq = 1.0f / G.qlen;
     const float w = q.x * iq, x = q.y * iq, y = q.z * iq, z = q.w * iq;

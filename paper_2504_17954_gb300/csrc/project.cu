@@ -128,7 +128,9 @@ cudaError_t launch_project(const ivrgs_gaussians* g, const float* table, const C
     if (g->n == 0) return cudaSuccess;
     {
         IVRGS_PROF("k_project", s);
-        if (g->precision == IVRGS_MIXED)
+        if (g->precision == IVRGS_VQ)
+            k_project<IVRGS_VQ><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, *out);
+        else if (g->precision == IVRGS_MIXED)
             k_project<IVRGS_MIXED><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, *out);
         else
             k_project<IVRGS_FP32><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, *out);

@@ -19,7 +19,18 @@ constexpr int kAuxBatch = 256;
 template <int PREC>
 __device__ __forceinline__ void load_aux_attrs(const ivrgs_gaussians& g, long long i, float nrm[3], float dc[3],
                                                float4& kk) {
-    if constexpr (PREC == IVRGS_FP32) {
+    if constexpr (PREC == IVRGS_VQ) {
+        const int m = g.model_id[i];
+        const float* n = static_cast<const float*>(g.normal);
+        const unsigned char* ci = static_cast<const unsigned char*>(g.dcolor);
+        for (int k = 0; k < 3; ++k) {
+            nrm[k] = n[3 * i + k];
+            dc[k] = vq_value(g, m, 3, ci[3 * i + k]);
+        }
+        const uchar4 ki = static_cast<const uchar4*>(g.kads)[i];
+        kk = make_float4(vq_value(g, m, 4, ki.x), vq_value(g, m, 5, ki.y), vq_value(g, m, 6, ki.z),
+                         vq_value(g, m, 7, ki.w));
+    } else if constexpr (PREC == IVRGS_FP32) {
         const float* n = static_cast<const float*>(g.normal);
         const float* c = static_cast<const float*>(g.dcolor);
         for (int k = 0; k < 3; ++k) {
@@ -151,7 +162,10 @@ cudaError_t launch_render_aux(const ivrgs_gaussians* g, const float* table, cons
     const float4* cd = reinterpret_cast<const float4*>(p->rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(b->ranges);
     float4* out = reinterpret_cast<float4*>(aux);
-    if (g->precision == IVRGS_MIXED)
+    if (g->precision == IVRGS_VQ)
+        k_render_aux<IVRGS_VQ><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, *g,
+                                                                        table, g->n_models, out);
+    else if (g->precision == IVRGS_MIXED)
         k_render_aux<IVRGS_MIXED><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, *g,
                                                                            table, g->n_models, out);
     else

@@ -36,8 +36,9 @@ def _check_cuda(t: torch.Tensor, name: str, dtype=torch.float32):
 class Gaussians:
     """Editable Gaussians on the device, structure of arrays (Sec. 4.3 attribute set).
 
-    precision 0 (float32) or 1 (16-bit storage, see ``pack_mixed``); ``anchor`` holds the
-    float32 position anchors of the 16-bit storage."""
+    precision 0 (float32), 1 (16-bit storage, see ``pack_mixed``) or 2 (vector-quantised, see
+    ``vq_compress``); ``anchor`` holds the float32 position anchors of the 16-bit storage,
+    ``codebook`` / ``vq_k`` the per-model codebooks of the quantised storage."""
     mean: torch.Tensor
     log_scale: torch.Tensor
     quat: torch.Tensor
@@ -49,6 +50,8 @@ class Gaussians:
     n_models: int
     precision: int = 0
     anchor: Optional[torch.Tensor] = None
+    codebook: Optional[torch.Tensor] = None
+    vq_k: int = 0
 
     @property
     def n(self) -> int:
@@ -64,6 +67,8 @@ class Gaussians:
             setattr(s, k, t.data_ptr())
         s.model_id = self.model_id.data_ptr() if self.model_id is not None else None
         s.anchor = self.anchor.data_ptr() if self.anchor is not None else None
+        s.codebook = self.codebook.data_ptr() if self.codebook is not None else None
+        s.vq_k = int(self.vq_k)
         return s
 
     @staticmethod
@@ -86,6 +91,26 @@ class Gaussians:
     def from_arrays(arrs: dict, n_models: int = 1, device="cuda") -> "Gaussians":
         t = lambda a: torch.as_tensor(a, dtype=torch.float32).to(device).contiguous()
         return Gaussians(*(t(arrs[k]) for k in ATTRS), model_id=None, n_models=n_models)
+
+
+def vq_compress(g: Gaussians, k: int = 256, iters: int = 16, stream=None) -> Gaussians:
+    """Vector-quantised storage of float32 Gaussians (Sec. 4.4; ivrgs_vq_build): per basic
+    model and attribute (all but mean and normal) a k-entry scalar codebook from ``iters``
+    Lloyd (k-means) iterations on the device, and one uint8 index per component. Mean, normal
+    and model ids are shared with ``g``."""
+    if g.precision != N.IVRGS_FP32 or g.model_id is None:
+        raise ValueError("vq_compress takes float32 Gaussians with model ids")
+    dev = g.mean.device
+    u8 = lambda w: torch.empty((g.n, w) if w > 1 else (g.n,), dtype=torch.uint8, device=dev)
+    out = Gaussians(mean=g.mean, log_scale=u8(3), quat=u8(4), opacity_logit=u8(1), dcolor=u8(3), normal=g.normal,
+                    kads=u8(4), model_id=g.model_id, n_models=g.n_models, precision=N.IVRGS_VQ,
+                    codebook=torch.empty((g.n_models, N.IVRGS_VQ_ATTRS, k), dtype=torch.float32, device=dev),
+                    vq_k=k)
+    gs, os_ = g.struct(), out.struct()
+    wsb = N.ivrgs_vq_build_workspace(g.n_models, k)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    N.ivrgs_vq_build(C.byref(gs), k, iters, C.byref(os_), _vp(ws), wsb, _stream(stream))
+    return out
 
 
 def pack_mixed(g: Gaussians, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), stream=None):
