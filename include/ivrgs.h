@@ -134,6 +134,14 @@ typedef struct {
     float* anchor;   /* IVRGS_MIXED: float32 [ceil(n / 256)][3]; unused otherwise */
     float* codebook; /* IVRGS_VQ: float32 [n_models][IVRGS_VQ_ATTRS][vq_k]; unused otherwise */
     int32_t vq_k;    /* IVRGS_VQ: codebook entries, 1..IVRGS_VQ_MAX_K */
+    /* Optional 3DGS colour (the view-dependent SH colour of Sec. 3 / Sec. 4.2, any storage):
+       float32 [n][(sh_degree + 1)^2][3] coefficients, sh_degree 0..3. If sh != NULL the colour
+       is max(0, sum_k sh_k Y_k(d) + 0.5) with d = (mean - campos) / |mean - campos| and the real
+       SH basis Y_k (orthonormal, Condon-Shortley sign) instead of the Blinn-Phong shading; dcolor,
+       normal, kads and the palette, lambda, b and light edits then do not enter; the opacity and
+       visibility edits do. In a gradient struct, sh (same layout) receives dL/dsh. */
+    float* sh;
+    int32_t sh_degree;
 } ivrgs_gaussians;
 
 /* Projected Gaussians, one record per (view v, Gaussian g) at index v * n + g.

@@ -83,6 +83,8 @@ class Composed:
     kads: np.ndarray
     model_id: np.ndarray
     n_models: int
+    sh: Optional[np.ndarray] = None  # [N, (deg+1)^2, 3]: 3DGS colour instead of Blinn-Phong
+    sh_degree: int = -1
 
     @property
     def n(self) -> int:
@@ -152,7 +154,7 @@ def project(comp: Composed, table: np.ndarray, cam, lowpass: float = LOWPASS, gu
                     radius_margin=np.zeros(n))
     oc = camera(cam)
     lib().orc_project(C.c_int64(n), *[_p(a) for a in comp.arrays()], _p(comp.model_id, C.c_int32),
-                      _p(table), C.c_int32(comp.n_models), C.byref(oc), C.c_double(lowpass), C.c_double(guard),
+                      *_sh_args(comp), _p(table), C.c_int32(comp.n_models), C.byref(oc), C.c_double(lowpass), C.c_double(guard),
                       _p(out.uv), _p(out.cov), _p(out.conic), _p(out.opacity), _p(out.rgb), _p(out.depth),
                       _p(out.radius, C.c_int32), _p(out.radius_margin))
     return out
@@ -247,7 +249,7 @@ def render_backward(r: Render, cams, dL_drgba: Sequence[np.ndarray], bg=(0.0, 0.
     comp, table = r.comp, r.table
     bg = np.ascontiguousarray(bg, np.float64)
     n = comp.n
-    params = {k: np.zeros_like(getattr(comp, k)) for k in PARAMS}
+    params = _grad_params(comp)
     dedit = np.zeros_like(table)
     dlight = np.zeros((len(cams), 3))
     per_view = []
@@ -264,12 +266,27 @@ def render_backward(r: Render, cams, dL_drgba: Sequence[np.ndarray], bg=(0.0, 0.
     return Grads(params, dedit, dlight, per_view)
 
 
+def _sh_args(comp):
+    if comp.sh is None:
+        return (None, C.c_int32(-1))
+    return (_p(np.ascontiguousarray(comp.sh, np.float64)), C.c_int32(comp.sh_degree))
+
+
+def _grad_params(comp):
+    params = {k: np.zeros_like(getattr(comp, k)) for k in PARAMS}
+    if comp.sh is not None:
+        params["sh"] = np.zeros_like(comp.sh, np.float64)
+    return params
+
+
 def _project_backward(comp, table, cam, lowpass, g, params, dedit, dlight_v):
     oc = camera(cam)
+    d_sh = params.get("sh")
     lib().orc_project_backward(C.c_int64(comp.n), *[_p(a) for a in comp.arrays()], _p(comp.model_id, C.c_int32),
-                               _p(table), C.c_int32(comp.n_models), C.byref(oc), C.c_double(lowpass),
-                               C.c_double(GUARD), _p(g["uv"]), _p(g["conic"]), _p(g["opacity"]), _p(g["rgb"]),
-                               *[_p(params[k]) for k in PARAMS], _p(dedit), _p(dlight_v))
+                               *_sh_args(comp), _p(table), C.c_int32(comp.n_models), C.byref(oc),
+                               C.c_double(lowpass), C.c_double(GUARD), _p(g["uv"]), _p(g["conic"]), _p(g["opacity"]),
+                               _p(g["rgb"]), *[_p(params[k]) for k in PARAMS], _p(d_sh) if d_sh is not None else None,
+                               _p(dedit), _p(dlight_v))
 
 
 # ----------------------------------------------------------------------------------------
@@ -320,7 +337,7 @@ def pixels_backward(comp, table, cams, projs, pix_per_view, dL_per_view, bg=(0.0
     """Gradients of a loss that touches only the sampled pixels (full-size gradient checks)."""
     n = comp.n
     bg = np.ascontiguousarray(bg, np.float64)
-    params = {k: np.zeros_like(getattr(comp, k)) for k in PARAMS}
+    params = _grad_params(comp)
     dedit = np.zeros_like(table)
     dlight = np.zeros((len(cams), 3))
     per_view = []

@@ -56,7 +56,56 @@ typedef struct {
     int64_t n;
     const double *mean, *log_scale, *quat, *opacity_logit, *dcolor, *normal, *kads;
     const int32_t* model_id;
+    const double* sh; /* NULL: Blinn-Phong colour; else [n][(deg+1)^2][3] SH coefficients */
+    int32_t sh_deg;
 } orc_gaussians;
+
+/* Real spherical harmonics up to degree 3 (the view-dependent colour of 3DGS that Sec. 3 and
+   Sec. 4.2 refer to), orthonormal on the unit sphere, with the Condon-Shortley sign: on a unit
+   direction (x, y, z), Y_0 = 1/(2 sqrt(pi)); degree 1: -a y, a z, -a x (a = sqrt(3/(4 pi)));
+   degree 2: b xy, -b yz, c (2z^2 - x^2 - y^2), -b xz, e (x^2 - y^2) (b = sqrt(15/(4 pi)),
+   c = sqrt(5/(16 pi)), e = sqrt(15/(16 pi))); degree 3: -f y(3x^2 - y^2), g xyz,
+   -h y(4z^2 - x^2 - y^2), k z(2z^2 - 3x^2 - 3y^2), -h x(4z^2 - x^2 - y^2), m z(x^2 - y^2),
+   -f x(x^2 - 3y^2) (f = sqrt(35/(32 pi)), g = sqrt(105/(4 pi)), h = sqrt(21/(32 pi)),
+   k = sqrt(7/(16 pi)), m = sqrt(105/(16 pi))). Y[k] and the gradient dY[k] w.r.t. (x, y, z)
+   (the polynomials differentiated as written). */
+static void sh_basis(const double d[3], int deg, double Y[16], double dY[16][3]) {
+    const double PI = 3.14159265358979323846;
+    const double x = d[0], y = d[1], z = d[2];
+    const double Y0 = 0.5 / sqrt(PI), a = sqrt(3.0 / (4 * PI)), b = sqrt(15.0 / (4 * PI)),
+                 c = sqrt(5.0 / (16 * PI)), e = sqrt(15.0 / (16 * PI)), f = sqrt(35.0 / (32 * PI)),
+                 g = sqrt(105.0 / (4 * PI)), h = sqrt(21.0 / (32 * PI)), k = sqrt(7.0 / (16 * PI)),
+                 m = sqrt(105.0 / (16 * PI));
+    memset(Y, 0, 16 * sizeof(double));
+    memset(dY, 0, 16 * 3 * sizeof(double));
+    Y[0] = Y0;
+    if (deg < 1) return;
+    Y[1] = -a * y; dY[1][1] = -a;
+    Y[2] = a * z;  dY[2][2] = a;
+    Y[3] = -a * x; dY[3][0] = -a;
+    if (deg < 2) return;
+    Y[4] = b * x * y;  dY[4][0] = b * y; dY[4][1] = b * x;
+    Y[5] = -b * y * z; dY[5][1] = -b * z; dY[5][2] = -b * y;
+    Y[6] = c * (2 * z * z - x * x - y * y); dY[6][0] = -2 * c * x; dY[6][1] = -2 * c * y; dY[6][2] = 4 * c * z;
+    Y[7] = -b * x * z; dY[7][0] = -b * z; dY[7][2] = -b * x;
+    Y[8] = e * (x * x - y * y); dY[8][0] = 2 * e * x; dY[8][1] = -2 * e * y;
+    if (deg < 3) return;
+    Y[9] = -f * y * (3 * x * x - y * y);  dY[9][0] = -6 * f * x * y; dY[9][1] = -f * (3 * x * x - 3 * y * y);
+    Y[10] = g * x * y * z; dY[10][0] = g * y * z; dY[10][1] = g * x * z; dY[10][2] = g * x * y;
+    Y[11] = -h * y * (4 * z * z - x * x - y * y);
+    dY[11][0] = 2 * h * x * y; dY[11][1] = -h * (4 * z * z - x * x - 3 * y * y); dY[11][2] = -8 * h * y * z;
+    Y[12] = k * z * (2 * z * z - 3 * x * x - 3 * y * y);
+    dY[12][0] = -6 * k * x * z; dY[12][1] = -6 * k * y * z; dY[12][2] = k * (6 * z * z - 3 * x * x - 3 * y * y);
+    Y[13] = -h * x * (4 * z * z - x * x - y * y);
+    dY[13][0] = -h * (4 * z * z - 3 * x * x - y * y); dY[13][1] = 2 * h * x * y; dY[13][2] = -8 * h * x * z;
+    Y[14] = m * z * (x * x - y * y); dY[14][0] = 2 * m * x * z; dY[14][1] = -2 * m * y * z; dY[14][2] = m * (x * x - y * y);
+    Y[15] = -f * x * (x * x - 3 * y * y); dY[15][0] = -f * (3 * x * x - 3 * y * y); dY[15][1] = 6 * f * x * y;
+}
+
+/* exported for the basis pins: Y[16] and dY[16][3] at direction d (unit) */
+void orc_sh_basis(const double* d, int32_t deg, double* Y, double* dY) {
+    sh_basis(d, deg, Y, (double(*)[3])dY);
+}
 
 /* edit table: per model m: [c_p(3), opacity scale, visible, 0, 0, 0]; then lambda(4), b(4),
    global light (l_x, l_y, l_z, on): with on != 0 every view with an orbital light uses
@@ -129,6 +178,10 @@ typedef struct {
     int gate;
     double spec_pow;
     double rgb[3];
+    int sh_on;               /* SH colour (3DGS) instead of Blinn-Phong */
+    double sdir[3], sdlen;   /* (mu - campos) / |.|, |mu - campos| */
+    double Ysh[16], dYsh[16][3];
+    int sh_clamp[3];         /* raw SH colour + 0.5 < 0: clamped to 0 */
 } orc_fwd;
 
 static void project_one(const orc_gaussians* G, int64_t g, const double* edit, int32_t n_models,
@@ -231,17 +284,32 @@ static void project_one(const orc_gaussians* G, int64_t g, const double* edit, i
     f->spec_pow = f->gate ? pow(f->nh, f->kp[3]) : 0.0;
     for (int c = 0; c < 3; ++c)
         f->rgb[c] = f->kp[0] * f->cv[c] + f->kp[1] * f->nl * f->cv[c] + (f->gate ? f->kp[2] * f->spec_pow : 0.0);
+    if (G->sh) { /* 3DGS colour: SH of the direction from the camera, + 0.5, clamped at 0 */
+        f->sh_on = 1;
+        f->sdlen = f->vlen;
+        for (int c = 0; c < 3; ++c) f->sdir[c] = -f->vdir[c];
+        sh_basis(f->sdir, G->sh_deg, f->Ysh, f->dYsh);
+        const int nb = (G->sh_deg + 1) * (G->sh_deg + 1);
+        const double* shg = G->sh + (int64_t)g * nb * 3;
+        for (int c = 0; c < 3; ++c) {
+            double v = 0.5;
+            for (int kk = 0; kk < nb; ++kk) v += shg[3 * kk + c] * f->Ysh[kk];
+            f->sh_clamp[c] = v < 0.0;
+            f->rgb[c] = v < 0.0 ? 0.0 : v;
+        }
+    }
     f->visible = 1;
 }
 
 /* Project all Gaussians for one view.  radius[g] == 0 marks a culled Gaussian. */
 void orc_project(int64_t n, const double* mean, const double* log_scale, const double* quat,
                  const double* opacity_logit, const double* dcolor, const double* normal,
-                 const double* kads, const int32_t* model_id, const double* edit, int32_t n_models,
+                 const double* kads, const int32_t* model_id, const double* sh, int32_t sh_deg,
+                 const double* edit, int32_t n_models,
                  const orc_camera* cam, double lowpass, double guard,
                  double* uv, double* cov, double* conic, double* opacity, double* rgb,
                  double* depth, int32_t* radius, double* radius_margin) {
-    orc_gaussians G = {n, mean, log_scale, quat, opacity_logit, dcolor, normal, kads, model_id};
+    orc_gaussians G = {n, mean, log_scale, quat, opacity_logit, dcolor, normal, kads, model_id, sh, sh_deg};
     orc_fwd f;
     for (int64_t g = 0; g < n; ++g) {
         project_one(&G, g, edit, n_models, cam, lowpass, guard, &f);
@@ -576,12 +644,14 @@ void orc_render_pixels_backward(const double* uv, const double* conic, const dou
  * --------------------------------------------------------------------------------------- */
 void orc_project_backward(int64_t n, const double* mean, const double* log_scale, const double* quat,
                           const double* opacity_logit, const double* dcolor, const double* normal,
-                          const double* kads, const int32_t* model_id, const double* edit, int32_t n_models,
+                          const double* kads, const int32_t* model_id, const double* sh, int32_t sh_deg,
+                          const double* edit, int32_t n_models,
                           const orc_camera* cam, double lowpass, double guard,
                           const double* g_uv, const double* g_conic, const double* g_opacity, const double* g_rgb,
                           double* d_mean, double* d_log_scale, double* d_quat, double* d_opacity_logit,
-                          double* d_dcolor, double* d_normal, double* d_kads, double* d_edit, double* d_light) {
-    orc_gaussians G = {n, mean, log_scale, quat, opacity_logit, dcolor, normal, kads, model_id};
+                          double* d_dcolor, double* d_normal, double* d_kads, double* d_sh, double* d_edit,
+                          double* d_light) {
+    orc_gaussians G = {n, mean, log_scale, quat, opacity_logit, dcolor, normal, kads, model_id, sh, sh_deg};
     const double* lam = edit + (int64_t)n_models * EDIT_STRIDE;
     double* d_lam = d_edit + (int64_t)n_models * EDIT_STRIDE;
     double* d_bias = d_lam + 4;
@@ -594,8 +664,26 @@ void orc_project_backward(int64_t n, const double* mean, const double* log_scale
         const double* me = edit + (int64_t)m * EDIT_STRIDE;
         double* dme = d_edit + (int64_t)m * EDIT_STRIDE;
         double dmu[3] = {0, 0, 0};
-        /* ---- shading ---- */
         const double* Gr = g_rgb + 3 * g;
+        if (f.sh_on) { /* ---- SH colour: coefficients and the view direction ---- */
+            const int nb = (sh_deg + 1) * (sh_deg + 1);
+            const double* shg = sh + (int64_t)g * nb * 3;
+            double* dshg = d_sh + (int64_t)g * nb * 3;
+            double dd[3] = {0, 0, 0};
+            for (int c = 0; c < 3; ++c) {
+                if (f.sh_clamp[c]) continue;
+                for (int kk = 0; kk < nb; ++kk) {
+                    dshg[3 * kk + c] += Gr[c] * f.Ysh[kk];
+                    for (int j = 0; j < 3; ++j) dd[j] += Gr[c] * shg[3 * kk + c] * f.dYsh[kk][j];
+                }
+            }
+            /* dir = (mu - campos) / |mu - campos| */
+            double pd = dot3(f.sdir, dd);
+            for (int c = 0; c < 3; ++c) dmu[c] += (dd[c] - f.sdir[c] * pd) / f.sdlen;
+            goto opacity;
+        }
+        {
+        /* ---- shading ---- */
         double Gc = Gr[0] * f.cv[0] + Gr[1] * f.cv[1] + Gr[2] * f.cv[2];
         double Gs = Gr[0] + Gr[1] + Gr[2];
         double dkp[4] = {Gc, f.nl * Gc, 0.0, 0.0};
@@ -651,6 +739,8 @@ void orc_project_backward(int64_t n, const double* mean, const double* log_scale
             double vd = dot3(f.vdir, dv);
             for (int c = 0; c < 3; ++c) dmu[c] -= (dv[c] - f.vdir[c] * vd) / f.vlen;
         }
+        }
+    opacity:
         /* ---- opacity ---- */
         d_opacity_logit[g] += g_opacity[g] * me[3] * f.sig_o * (1.0 - f.sig_o);
         dme[3] += g_opacity[g] * f.sig_o;

@@ -59,7 +59,8 @@ class ivrgs_gaussians(C.Structure):
     _fields_ = [("n", C.c_int64), ("precision", C.c_int32), ("n_models", C.c_int32), ("mean", C.c_void_p),
                 ("log_scale", C.c_void_p), ("quat", C.c_void_p), ("opacity_logit", C.c_void_p),
                 ("dcolor", C.c_void_p), ("normal", C.c_void_p), ("kads", C.c_void_p), ("model_id", C.c_void_p),
-                ("anchor", C.c_void_p), ("codebook", C.c_void_p), ("vq_k", C.c_int32)]
+                ("anchor", C.c_void_p), ("codebook", C.c_void_p), ("vq_k", C.c_int32), ("sh", C.c_void_p),
+                ("sh_degree", C.c_int32)]
 
 
 class ivrgs_projected(C.Structure):

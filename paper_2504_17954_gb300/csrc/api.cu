@@ -114,6 +114,10 @@ static ivrgs_status check_gaussians(const ivrgs_gaussians* g, const char* name, 
             return invalid(std::string(name) + ": misaligned attribute array");
     }
     if (need_model_id && !aligned(g->model_id, 2)) return invalid(std::string(name) + ": misaligned model_id");
+    if (g->sh) {
+        if (g->sh_degree < 0 || g->sh_degree > 3) return invalid(std::string(name) + ": sh_degree must be 0..3");
+        if (!aligned(g->sh, 4)) return invalid(std::string(name) + ": misaligned sh");
+    }
     return IVRGS_OK;
 }
 
@@ -393,6 +397,8 @@ static ivrgs_status render_backward_impl(int accumulate, const ivrgs_gaussians* 
     if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
     if ((st = check_gaussians(grad, "grad", false))) return st;
     if (grad->n != g->n) return invalid("grad->n must equal g->n");
+    if (g->sh && (!grad->sh || grad->sh_degree != g->sh_degree))
+        return invalid("g has SH colour: grad->sh must be set, with the same sh_degree");
     static thread_local CamBatch cb;
     if ((st = make_cam_batch(cams, n_views, &cb))) return st;
     if ((st = check_projected(p, g->n, n_views))) return st;

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
 }
 
 // ------------------------------------------------------------------------- a7
-template <int PREC>
+template <int PREC, bool SH>
 __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g, const float* __restrict__ table,
                                                      const __grid_constant__ CamBatch cb, float lowpass,
                                                      const float4* __restrict__ g0, const float4* __restrict__ g1,
@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
     GaussLocal G;
     if (active) load_gauss<PREC>(g, table, M, i, G);
     else G.visible = false;
+    if constexpr (!SH) G.sh = nullptr;  // the instantiation without SH colour carries none of its code
     const bool tl_on = __ldg(table + (long long)M * IVRGS_EDIT_STRIDE + 11) != 0.0f;  // uniform
     float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float dcv[3] = {0.f, 0.f, 0.f}, dkp[4] = {0.f, 0.f, 0.f, 0.f}, dnn[3] = {0.f, 0.f, 0.f}, dop = 0.f;
@@ -258,7 +259,36 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
                              (b.y != 0.f) | (b.z != 0.f) | (b.w != 0.f) | (bl != 0.f);
             ViewLocal V;
             if (any) project_view(G, c, lowpass, V);
+            if (SH && any && V.visible && G.sh) {  // ---- 3DGS colour: SH coefficients and the view direction
+                dop += b.y;
+                const float Gr[3] = {b.z, b.w, bl};
+                const float sx = -V.vd[0], sy = -V.vd[1], sz = -V.vd[2];
+                const int nb = (G.sh_deg + 1) * (G.sh_deg + 1);
+                float* gsh = grad.sh + i * 3ll * nb;
+                const float gr0 = V.shc[0] ? 0.f : Gr[0], gr1 = V.shc[1] ? 0.f : Gr[1], gr2 = V.shc[2] ? 0.f : Gr[2];
+                float dd[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    if (t >= nb) break;
+                    float gx, gy, gz;
+                    const float Yt = sh_term(t, sx, sy, sz, gx, gy, gz);
+                    gsh[3 * t + 0] += gr0 * Yt;
+                    gsh[3 * t + 1] += gr1 * Yt;
+                    gsh[3 * t + 2] += gr2 * Yt;
+                    const float w = gr0 * __ldg(G.sh + 3 * t) + gr1 * __ldg(G.sh + 3 * t + 1) + gr2 * __ldg(G.sh + 3 * t + 2);
+                    dd[0] += w * gx;
+                    dd[1] += w * gy;
+                    dd[2] += w * gz;
+                }
+                // d = (mu - campos) / |mu - campos|
+                const float pd = sx * dd[0] + sy * dd[1] + sz * dd[2];
+                const float iv = 1.0f / V.vlen;
+                dmu[0] += (dd[0] - sx * pd) * iv;
+                dmu[1] += (dd[1] - sy * pd) * iv;
+                dmu[2] += (dd[2] - sz * pd) * iv;
+            }
             if (any && V.visible) {
+                if (!G.sh) {
                 dop += b.y;
                 // ---- shading
                 const float Gr[3] = {b.z, b.w, bl};
@@ -304,6 +334,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
                     const float vd = V.vd[0] * dv[0] + V.vd[1] * dv[1] + V.vd[2] * dv[2];
                     const float iv = 1.0f / V.vlen;
                     for (int k = 0; k < 3; ++k) dmu[k] -= (dv[k] - V.vd[k] * vd) * iv;
+                }
                 }
                 // ---- conic -> Sigma'
                 const float A = V.A, B = V.B, C = V.C;
@@ -526,17 +557,24 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
             k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
                                                                          final_T, last, dl, g0, g1, g2);
     }
+    if (g->sh && !accumulate && g->n > 0) {  // SH gradients are added view by view
+        const size_t nb = (size_t)(g->sh_degree + 1) * (g->sh_degree + 1);
+        if ((e = cudaMemsetAsync(grad->sh, 0, sizeof(float) * 3 * nb * (size_t)g->n, s)) != cudaSuccess) return e;
+    }
     if (g->n > 0) {
         IVRGS_PROF("k_project_bwd", s);
-        if (g->precision == IVRGS_VQ)
-            k_project_bwd<IVRGS_VQ><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1, g2,
-                                                                                 *grad, edit_grad, accumulate);
-        else if (g->precision == IVRGS_MIXED)
-            k_project_bwd<IVRGS_MIXED><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1,
-                                                                                    g2, *grad, edit_grad, accumulate);
-        else
-            k_project_bwd<IVRGS_FP32><<<(unsigned)((g->n + 255) / 256), 256, 0, s>>>(*g, table, cb, lowpass, g0, g1,
-                                                                                   g2, *grad, edit_grad, accumulate);
+        const unsigned nb = (unsigned)((g->n + 255) / 256);
+#define IVRGS_PBWD(P, S) k_project_bwd<P, S><<<nb, 256, 0, s>>>(*g, table, cb, lowpass, g0, g1, g2, *grad, edit_grad, accumulate)
+        if (g->sh) {
+            if (g->precision == IVRGS_VQ) IVRGS_PBWD(IVRGS_VQ, true);
+            else if (g->precision == IVRGS_MIXED) IVRGS_PBWD(IVRGS_MIXED, true);
+            else IVRGS_PBWD(IVRGS_FP32, true);
+        } else {
+            if (g->precision == IVRGS_VQ) IVRGS_PBWD(IVRGS_VQ, false);
+            else if (g->precision == IVRGS_MIXED) IVRGS_PBWD(IVRGS_MIXED, false);
+            else IVRGS_PBWD(IVRGS_FP32, false);
+        }
+#undef IVRGS_PBWD
     }
     return cudaGetLastError();
 }

@@ -26,6 +26,8 @@ struct GaussLocal {
     float sm;               // opacity scale of the model
     float tl[3], tl_len;    // the edit table's global light, normalised, and its length
     bool tl_on;             // the global light replaces every orbital view's light_dir
+    const float* sh;        // this Gaussian's SH coefficients [nb][3] (3DGS colour) or nullptr
+    int sh_deg;
     int model;
     bool visible;
 };
@@ -128,6 +130,8 @@ __device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float
     G.k[0] = kk.x; G.k[1] = kk.y; G.k[2] = kk.z; G.k[3] = kk.w;
     const float* lam = table + (long long)n_models * IVRGS_EDIT_STRIDE;
     for (int c = 0; c < 4; ++c) G.kp[c] = __ldg(lam + c) * G.k[c] + __ldg(lam + 4 + c);
+    G.sh = g.sh ? g.sh + i * 3ll * (g.sh_degree + 1) * (g.sh_degree + 1) : nullptr;
+    G.sh_deg = g.sh_degree;
     G.tl_on = __ldg(lam + 11) != 0.0f;
     if (G.tl_on) {
         const float l0 = __ldg(lam + 8), l1 = __ldg(lam + 9), l2 = __ldg(lam + 10);
@@ -160,7 +164,45 @@ struct ViewLocal {
     float ndl, ndh, nl, nh, spow;
     bool gate;
     float rgb[3];
+    bool shc[3];  // SH colour clamped at 0 (per channel)
 };
+
+// Term t of the real SH basis below and its gradient, for unrolled loops (no arrays)
+__device__ __forceinline__ float sh_term(int t, float x, float y, float z, float& gx, float& gy, float& gz) {
+    const float PI = 3.14159265358979f;
+    const float a = sqrtf(3.f / (4.f * PI)), b = sqrtf(15.f / (4.f * PI)), c = sqrtf(5.f / (16.f * PI)),
+                e = sqrtf(15.f / (16.f * PI)), f = sqrtf(35.f / (32.f * PI)), g = sqrtf(105.f / (4.f * PI)),
+                h = sqrtf(21.f / (32.f * PI)), k = sqrtf(7.f / (16.f * PI)), m = sqrtf(105.f / (16.f * PI));
+    gx = gy = gz = 0.f;
+    switch (t) {
+        case 0: return 0.5f / sqrtf(PI);
+        case 1: gy = -a; return -a * y;
+        case 2: gz = a; return a * z;
+        case 3: gx = -a; return -a * x;
+        case 4: gx = b * y; gy = b * x; return b * x * y;
+        case 5: gy = -b * z; gz = -b * y; return -b * y * z;
+        case 6: gx = -2.f * c * x; gy = -2.f * c * y; gz = 4.f * c * z; return c * (2.f * z * z - x * x - y * y);
+        case 7: gx = -b * z; gz = -b * x; return -b * x * z;
+        case 8: gx = 2.f * e * x; gy = -2.f * e * y; return e * (x * x - y * y);
+        case 9: gx = -6.f * f * x * y; gy = -f * (3.f * x * x - 3.f * y * y); return -f * y * (3.f * x * x - y * y);
+        case 10: gx = g * y * z; gy = g * x * z; gz = g * x * y; return g * x * y * z;
+        case 11:
+            gx = 2.f * h * x * y; gy = -h * (4.f * z * z - x * x - 3.f * y * y); gz = -8.f * h * y * z;
+            return -h * y * (4.f * z * z - x * x - y * y);
+        case 12:
+            gx = -6.f * k * x * z; gy = -6.f * k * y * z; gz = k * (6.f * z * z - 3.f * x * x - 3.f * y * y);
+            return k * z * (2.f * z * z - 3.f * x * x - 3.f * y * y);
+        case 13:
+            gx = -h * (4.f * z * z - 3.f * x * x - y * y); gy = 2.f * h * x * y; gz = -8.f * h * x * z;
+            return -h * x * (4.f * z * z - x * x - y * y);
+        case 14: gx = 2.f * m * x * z; gy = -2.f * m * y * z; gz = m * (x * x - y * y); return m * z * (x * x - y * y);
+        default: gx = -f * (3.f * x * x - 3.f * y * y); gy = 6.f * f * x * y; return -f * x * (x * x - 3.f * y * y);
+    }
+}
+
+// sh_term: the real spherical harmonics up to degree 3 on a unit direction (x, y, z),
+// orthonormal on the sphere, Condon-Shortley sign, normalisations written as their closed forms
+// (sqrt(3/(4 pi)) etc.), term t and the gradient of its polynomial.
 
 __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& c, float lowpass, ViewLocal& V) {
     V.visible = false;
@@ -233,6 +275,21 @@ __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& 
     const float spec = V.gate ? G.kp[2] * V.spow : 0.0f;
     const float diff = G.kp[0] + G.kp[1] * V.nl;
     for (int k = 0; k < 3; ++k) V.rgb[k] = diff * G.cv[k] + spec;
+    if (G.sh) {  // 3DGS colour: SH of the direction from the camera (-vd), + 0.5, clamped at 0
+        const int nb = (G.sh_deg + 1) * (G.sh_deg + 1);
+        float v[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            if (t >= nb) break;
+            float gx, gy, gz;
+            const float Yt = sh_term(t, -V.vd[0], -V.vd[1], -V.vd[2], gx, gy, gz);
+            for (int ch = 0; ch < 3; ++ch) v[ch] = fmaf(__ldg(G.sh + 3 * t + ch), Yt, v[ch]);
+        }
+        for (int ch = 0; ch < 3; ++ch) {
+            V.shc[ch] = v[ch] < 0.0f;
+            V.rgb[ch] = fmaxf(v[ch], 0.0f);
+        }
+    }
     V.visible = true;
 }
 

@@ -52,6 +52,8 @@ class Gaussians:
     anchor: Optional[torch.Tensor] = None
     codebook: Optional[torch.Tensor] = None
     vq_k: int = 0
+    sh: Optional[torch.Tensor] = None  # [n, (sh_degree + 1)^2, 3] float32: 3DGS colour instead of Blinn-Phong
+    sh_degree: int = -1
 
     @property
     def n(self) -> int:
@@ -69,6 +71,8 @@ class Gaussians:
         s.anchor = self.anchor.data_ptr() if self.anchor is not None else None
         s.codebook = self.codebook.data_ptr() if self.codebook is not None else None
         s.vq_k = int(self.vq_k)
+        s.sh = self.sh.data_ptr() if self.sh is not None else None
+        s.sh_degree = int(self.sh_degree)
         return s
 
     @staticmethod
@@ -330,6 +334,9 @@ class Rasterizer:
         if grad is None:
             grad = Gaussians.empty(self.n, self.n_models, self.device)
             grad.model_id = None
+        if g.sh is not None and grad.sh is None:
+            grad.sh = torch.empty_like(g.sh)
+            grad.sh_degree = g.sh_degree
         gs = g.struct(tensors)
         gr = grad.struct()
         p, b = self.projected_struct(), self.bins_struct()
