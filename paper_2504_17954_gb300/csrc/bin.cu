@@ -246,23 +246,43 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const unsigned* __rest
     __syncthreads();
     const long long base = (long long)blockIdx.x * kScanBlock;
     unsigned long long off = vis_off[blockIdx.x];
+    // an item's loads are issued before the block scan that places it, and the next item's
+    // before this item's stores, so that the scans overlap the memory latency
+    struct Item {
+        unsigned c, key;
+        float2 p;
+        float4 co;
+        int r;
+    };
+    auto load = [&](long long i) {
+        Item it{};
+        if (i < total) {
+            it.c = cnt[i];
+            it.key = __float_as_uint(rgbd[i].w);
+            it.p = xy[i];
+            it.co = conic_o[i];
+            it.r = radius[i];
+        }
+        return it;
+    };
+    Item nxt = load(base + threadIdx.x);
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long i = base + (long long)j * kScanThreads + threadIdx.x;
-        const unsigned c = i < total ? cnt[i] : 0u;
+        const Item it = nxt;
+        if (j + 1 < kScanItems) nxt = load(i + kScanThreads);
+        const unsigned c = it.c;
         const unsigned f = c ? 1u : 0u;
         unsigned excl;
         const unsigned tot = block_excl_scan(f, excl, s_warp);
         if (f) {
             const unsigned long long k = off + excl;
-            const unsigned key = __float_as_uint(rgbd[i].w);
+            const unsigned key = it.key;
             rkey[k] = key;
             rval[k] = (unsigned)k;
             cnt2[k] = c;
-            const float2 p = xy[i];
-            const float4 co = conic_o[i];
-            rec[2 * k] = make_float4(p.x, p.y, co.x, co.y);
-            rec[2 * k + 1] = make_float4(co.z, co.w, __uint_as_float((unsigned)i), __int_as_float(radius[i]));
+            rec[2 * k] = make_float4(it.p.x, it.p.y, it.co.x, it.co.y);
+            rec[2 * k + 1] = make_float4(it.co.z, it.co.w, __uint_as_float((unsigned)i), __int_as_float(it.r));
 #pragma unroll
             for (int q = 0; q < kRecPasses; ++q) atomicAdd(&s_hist[q * 256 + ((key >> (8 * q)) & 255u)], 1u);
         }
