@@ -163,7 +163,7 @@ ivrgs_status ivrgs_set_option(const char* name, int64_t value) {
     if (!name) return invalid("name is NULL");
     const std::string k(name);
     if (k == "render_pixels_per_thread" || k == "render_bwd_pixels_per_thread") {
-        if (value != 1 && value != 2 && value != 4) return invalid(k + " must be 1, 2 or 4");
+        if (value != 1 && value != 2 && value != 4 && value != 8) return invalid(k + " must be 1, 2, 4 or 8");
         (k == "render_pixels_per_thread" ? options().render_ppt : options().render_bwd_ppt) = (int)value;
         return IVRGS_OK;
     }

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     const float fx = (float)px + 0.5f;
     const int q0 = py0 & 3;                               // offset of this thread's first row in its group
     const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
+    constexpr int NG = (P + 3) / 4;                       // 4-row exponent groups a thread spans
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
     const int lane = threadIdx.x & 31;
@@ -153,10 +154,12 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             float p2[P];
             bool ok0[P];
             bool any = false;
-            const RowGroup rgp = row_group(a, bb, fx, fyg);
+            RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
+#pragma unroll
+            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                p2[p] = row_p2(rgp, bb, q0 + p);
+                p2[p] = row_p2(rgp[(q0 + p) >> 2], bb, (q0 + p) & 3);
                 ok0[p] = ee < (int)my_last[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
                 any = any || ok0[p];
             }
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
                 const bool live = ok && raw < kAlphaMax;
                 const float dP = live ? dalpha * raw : 0.0f;
                 vv[5] += live ? dalpha * G : 0.0f;
-                const float dxp = rgp.dx, dyp = rgp.dy0 - (float)(q0 + p);
+                const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
                 const float px_ = dP * dxp, py_ = dP * dyp;
                 vv[0] += px_;
                 vv[1] += py_;
@@ -550,6 +553,9 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
         if (options().render_bwd_ppt == 1)
             k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, final_T,
                                                                      last, dl, g0, g1, g2);
+        else if (options().render_bwd_ppt == 8)
+            k_render_bwd<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
+                                                                         final_T, last, dl, g0, g1, g2);
         else if (options().render_bwd_ppt == 4)
             k_render_bwd<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
                                                                          final_T, last, dl, g0, g1, g2);

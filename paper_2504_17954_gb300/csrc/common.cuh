@@ -92,8 +92,8 @@ ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch*
 
 // tunable launch shapes (set through ivrgs_set_option; read by the launchers)
 struct Options {
-    int render_ppt = 4;      // pixels per thread of the forward blend (1, 2 or 4)
-    int render_bwd_ppt = 4;  // pixels per thread of the backward blend (1, 2 or 4)
+    int render_ppt = 4;      // pixels per thread of the forward blend (1, 2, 4 or 8)
+    int render_bwd_ppt = 4;  // pixels per thread of the backward blend (1, 2, 4 or 8)
     int sort_match = 0;      // radix ranking: 0 = warp ballots per digit bit, 1 = match.any
     int sort_scan = 0;       // radix offsets: 0 = decoupled look-back (onesweep), 1 = reduce-then-scan
 };

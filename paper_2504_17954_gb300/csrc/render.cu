@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     const float fx = (float)px + 0.5f;
     const int q0 = py0 & 3;                               // offset of this thread's first row in its group
     const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
+    constexpr int NG = (P + 3) / 4;                       // 4-row exponent groups a thread spans
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
 
@@ -88,10 +89,12 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
             float p2[P];
             bool ok[P];
             bool any = false;
-            const RowGroup rgp = row_group(a, bb, fx, fyg);
+            RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
+#pragma unroll
+            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                p2[p] = row_p2(rgp, bb, q0 + p);
+                p2[p] = row_p2(rgp[(q0 + p) >> 2], bb, (q0 + p) & 3);
                 ok[p] = !done[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
                 any = any || ok[p];
             }
@@ -146,6 +149,9 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
     if (options().render_ppt == 1)
         k_render<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out, final_T,
                                                              last);
+    else if (options().render_ppt == 8)
+        k_render<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
+                                                                 final_T, last);
     else if (options().render_ppt == 4)
         k_render<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
                                                                  final_T, last);
