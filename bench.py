@@ -284,7 +284,7 @@ def run_gpu(args, rank, world):
     for kv in args.opt:
         k, v = kv.split("=")
         N.ivrgs_set_option(k, int(v))
-    for k in ("render_pixels_per_thread", "render_bwd_pixels_per_thread", "sort_match", "sort_scan"):
+    for k in ("render_pixels_per_thread", "render_bwd_pixels_per_thread", "sort_match", "sort_scan", "sort_early"):
         opts[k] = N.ivrgs_get_option(k)
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)

@@ -187,7 +187,9 @@ int32_t ivrgs_version(void);
    of the forward / backward blend owns; "sort_match" (0 or 1): rank radix digits with warp
    ballots (0) or match.any (1); "sort_scan" (0 or 1): radix-pass offsets by decoupled
    look-back (0, one kernel per pass) or reduce-then-scan (1: a histogram kernel, a per-digit
-   scan and the scatter; no device-side waits). Results are identical for every setting.
+   scan and the scatter; no device-side waits); "sort_early" (0 or 1): in the tile-id passes, a
+   look-back radix tile publishes its digit counts after (0) or before (1) ranking its keys (the
+   depth passes always publish before). Results are identical for every setting.
    Returns IVRGS_ERR_INVALID_ARG for an unknown name or value. */
 ivrgs_status ivrgs_set_option(const char* name, int64_t value);
 ivrgs_status ivrgs_get_option(const char* name, int64_t* value);

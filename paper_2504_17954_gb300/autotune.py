@@ -21,6 +21,7 @@ SPACE = {
     "render_bwd_pixels_per_thread": (1, 2, 4, 8),
     "sort_match": (0, 1),
     "sort_scan": (0, 1),
+    "sort_early": (0, 1),
 }
 
 

@@ -167,9 +167,10 @@ ivrgs_status ivrgs_set_option(const char* name, int64_t value) {
         (k == "render_pixels_per_thread" ? options().render_ppt : options().render_bwd_ppt) = (int)value;
         return IVRGS_OK;
     }
-    if (k == "sort_match" || k == "sort_scan") {
+    if (k == "sort_match" || k == "sort_scan" || k == "sort_early") {
         if (value != 0 && value != 1) return invalid(k + " must be 0 or 1");
-        (k == "sort_match" ? options().sort_match : options().sort_scan) = (int)value;
+        (k == "sort_match" ? options().sort_match : k == "sort_scan" ? options().sort_scan : options().sort_early) =
+            (int)value;
         return IVRGS_OK;
     }
     return invalid("unknown option '" + k + "'");
@@ -183,6 +184,7 @@ ivrgs_status ivrgs_get_option(const char* name, int64_t* value) {
     else if (k == "render_bwd_pixels_per_thread") *value = options().render_bwd_ppt;
     else if (k == "sort_match") *value = options().sort_match;
     else if (k == "sort_scan") *value = options().sort_scan;
+    else if (k == "sort_early") *value = options().sort_early;
     else return invalid("unknown option '" + k + "'");
     return IVRGS_OK;
 }

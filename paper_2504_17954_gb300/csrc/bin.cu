@@ -474,7 +474,7 @@ __global__ void k_hist_scan(const unsigned* __restrict__ hist, unsigned* __restr
 // look-back). LOOKBACK = false: the scatter of a reduce-then-scan pass (tile = block index,
 // offsets read from `lookback`, which then holds the scanned digit table of k_upsweep and
 // k_digit_scan: entry [d][tile] = first output slot of digit d in this tile).
-template <bool LOOKBACK>
+template <bool LOOKBACK, bool EARLY>
 __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __restrict__ kin,
                                                            const unsigned* __restrict__ vin,
                                                            unsigned* __restrict__ kout, unsigned* __restrict__ vout,
@@ -515,6 +515,39 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
         key[j] = li < nvalid ? kin_t[li] : 0xffffffffu;
         s_vals[li] = li < nvalid ? vin_t[li] : 0u;
     }
+    const unsigned dg = (unsigned)tid;
+    unsigned cnt = 0;
+    if constexpr (EARLY) {
+        // counts first: the tile's digit counts are published before the ranking, so that a
+        // successor's look-back rarely finds this tile unpublished
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            // a bit-field extract of its own, so that the 16 digits are not kept live for the ranking
+            unsigned dj;
+            asm("bfe.u32 %0, %1, %2, 8;" : "=r"(dj) : "r"(key[j]), "r"(shift));
+            const unsigned d0 = __shfl_sync(0xffffffffu, dj, 0);
+            if (__all_sync(0xffffffffu, dj == d0)) {  // one digit across the warp: one update
+                if (lane == 0) atomicAdd(&s_whist[warp][d0], 32u);
+            } else {
+                atomicAdd(&s_whist[warp][dj], 1u);
+            }
+        }
+        __syncthreads();
+        // per digit: warp-exclusive offsets (the ranking below continues from them)
+#pragma unroll
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const unsigned c = s_whist[w][dg];
+            s_whist[w][dg] = cnt;
+            cnt += c;
+        }
+        if (LOOKBACK && tile != skip_publish_tile)
+            st_relaxed(lookback + tile * 256 + dg, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+        unsigned lexcl;
+        block_excl_scan(cnt, lexcl, s_warp);
+        s_local[dg] = lexcl;
+        s_global[dg] = cnt;  // parked until the look-back (not live across the ranking)
+        __syncthreads();
+    }
     // stable rank inside the warp, in (item, lane) order == index order
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
@@ -537,28 +570,27 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
         __syncwarp();
     }
     __syncthreads();
-    const unsigned dg = (unsigned)tid;
-    unsigned cnt = 0;
+    if constexpr (!EARLY) {
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-        const unsigned c = s_whist[w][dg];
-        s_whist[w][dg] = cnt;
-        cnt += c;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const unsigned c = s_whist[w][dg];
+            s_whist[w][dg] = cnt;
+            cnt += c;
+        }
+        if (LOOKBACK && tile != skip_publish_tile)
+            st_relaxed(lookback + tile * 256 + dg, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
+        unsigned lexcl;
+        block_excl_scan(cnt, lexcl, s_warp);
+        s_local[dg] = lexcl;
+        __syncthreads();
     }
-    unsigned* my_status = lookback + tile * 256 + dg;
-    const bool publish = tile != skip_publish_tile;
-    if (LOOKBACK && publish) st_relaxed(my_status, (tile == 0 ? kFlagPre : kFlagAgg) | cnt);
-    unsigned lexcl;
-    block_excl_scan(cnt, lexcl, s_warp);
-    s_local[dg] = lexcl;
-    __syncthreads();
     // local scatter into digit order first, so that keys and ranks are dead during the look-back
     {
         unsigned val[kSortItems];
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j) {
             const unsigned dj = (key[j] >> shift) & 255u;
-            pos[j] += s_local[dj] + s_whist[warp][dj];
+            pos[j] += s_local[dj] + (EARLY ? 0u : s_whist[warp][dj]);
             s_keys[pos[j]] = key[j];
             val[j] = s_vals[wofs + j * 32];
         }
@@ -603,7 +635,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
                     if (spins > 64) __nanosleep(64);
                 }
             }
-            if (publish) st_relaxed(my_status, kFlagPre | ((prefix + cnt) & kValMask));
+            if constexpr (EARLY) cnt = s_global[dg];
+            if (tile != skip_publish_tile) st_relaxed(lookback + tile * 256 + dg, kFlagPre | ((prefix + cnt) & kValMask));
         }
         s_global[dg] = base[dg] + prefix;
     }
@@ -808,7 +841,7 @@ cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const
 static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1,
                                    const unsigned long long* d_n, long long cap, const unsigned* base,
                                    unsigned* lookback, long long tiles, unsigned* counter, unsigned* flag,
-                                   const char* name, cudaStream_t s) {
+                                   bool early, const char* name, cudaStream_t s) {
     unsigned* kb[2] = {k0, k1};
     unsigned* vb[2] = {v0, v1};
     const bool rts = options().sort_scan != 0;
@@ -819,15 +852,18 @@ static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, uns
         if (rts) {
             k_upsweep<<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], d_n, cap, 8 * ps, lb);
             k_digit_scan<<<256, kDigitScanThreads, 0, s>>>(lb, base + 256 * ps, tiles);
-            k_onesweep<false><<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_n, cap,
-                                                                      8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                                                                      g_max_spin, g_skip_publish_tile,
-                                                                      options().sort_match);
+            k_onesweep<false, false><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+                kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
+                g_max_spin, g_skip_publish_tile, options().sort_match);
         } else {
-            k_onesweep<true><<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], vb[src], kb[dst], vb[dst], d_n, cap,
-                                                                     8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                                                                     g_max_spin, g_skip_publish_tile,
-                                                                     options().sort_match);
+            if (early)
+                k_onesweep<true, true><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+                    kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
+                    g_max_spin, g_skip_publish_tile, options().sort_match);
+            else
+                k_onesweep<true, false><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+                    kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
+                    g_max_spin, g_skip_publish_tile, options().sort_match);
         }
     }
     return cudaGetLastError();
@@ -863,7 +899,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         k_hist_scan<<<kRecPasses, 256, 0, s>>>(b.hist_rec, b.base_rec);
     }
     if ((e = onesweep_passes(kRecPasses, b.rkey[0], b.rval[0], b.rkey[1], b.rval[1], b.d_m, plan.n_records,
-                             b.base_rec, b.lb_rec, rec_tiles, b.counter, b.flag, "k_onesweep_rec", s)) != cudaSuccess)
+                             b.base_rec, b.lb_rec, rec_tiles, b.counter, b.flag, true, "k_onesweep_rec", s)) != cudaSuccess)
         return e;
     // pair offsets of the depth-ordered records
     unsigned long long* sums2 = b.sums + 2 * (nb > 0 ? nb : 1);
@@ -892,7 +928,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         k_hist_scan<<<plan.n_passes, 256, 0, s>>>(b.hist_tile, b.base_tile);
     }
     if ((e = onesweep_passes(plan.n_passes, t0, v0, t1, v1, b.d_n, cap, b.base_tile, b.lb_tile, pair_tiles,
-                             b.counter + kRecPasses, b.flag, "k_onesweep", s)) != cudaSuccess)
+                             b.counter + kRecPasses, b.flag, options().sort_early != 0, "k_onesweep", s)) != cudaSuccess)
         return e;
     if (n_work > 0) {
         IVRGS_PROF("k_ranges", s);

@@ -96,6 +96,7 @@ struct Options {
     int render_bwd_ppt = 4;  // pixels per thread of the backward blend (1, 2, 4 or 8)
     int sort_match = 0;      // radix ranking: 0 = warp ballots per digit bit, 1 = match.any
     int sort_scan = 0;       // radix offsets: 0 = decoupled look-back (onesweep), 1 = reduce-then-scan
+    int sort_early = 0;      // radix tile: 1 = publish its digit counts before ranking (look-back waits less)
 };
 Options& options();
 BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity);

@@ -34,14 +34,16 @@ def _records(sizes, n, seed):
     return rast, (xy, rad, depth)
 
 
-def test_lookback_timeout_is_reported_and_context_survives():
+@pytest.mark.parametrize("early", [0, 1])
+def test_lookback_timeout_is_reported_and_context_survives(early):
     sizes = [(256, 256)]
     rast, (xy, rad, depth) = _records(sizes, 20000, 8)
     rast.bin("exact")  # sizes the buffers
     torch.cuda.synchronize()
     L = N.lib()
-    old_scan = N.ivrgs_get_option("sort_scan")
+    old_scan, old_early = N.ivrgs_get_option("sort_scan"), N.ivrgs_get_option("sort_early")
     N.ivrgs_set_option("sort_scan", 0)  # the passes with device-side waits
+    N.ivrgs_set_option("sort_early", early)  # counts published after or before the ranking
     L.ivrgs_debug_bin_hooks(2000, 0)
     try:
         p, b = rast.projected_struct(), rast.bins_struct()
@@ -53,6 +55,7 @@ def test_lookback_timeout_is_reported_and_context_survives():
     finally:
         L.ivrgs_debug_bin_hooks(0, -1)
         N.ivrgs_set_option("sort_scan", old_scan)
+        N.ivrgs_set_option("sort_early", old_early)
     # the context is healthy: a normal call is exact again and the flag is cleared
     rast.bin("exact")
     torch.cuda.synchronize()

@@ -89,13 +89,15 @@ def _gpu_bin_from(sizes, xy, rad, depth, mode="exact", capacity=None):
     return rast
 
 
-@pytest.fixture(params=[0, 1], ids=["lookback", "rts"])
+@pytest.fixture(params=[(0, 0), (0, 1), (1, 0)], ids=["lookback", "lookback_early", "rts"])
 def sort_scan(request):
     from paper_2504_17954_gb300 import _native as N
-    old = N.ivrgs_get_option("sort_scan")
-    N.ivrgs_set_option("sort_scan", request.param)
+    old = (N.ivrgs_get_option("sort_scan"), N.ivrgs_get_option("sort_early"))
+    N.ivrgs_set_option("sort_scan", request.param[0])
+    N.ivrgs_set_option("sort_early", request.param[1])
     yield request.param
-    N.ivrgs_set_option("sort_scan", old)
+    N.ivrgs_set_option("sort_scan", old[0])
+    N.ivrgs_set_option("sort_early", old[1])
 
 
 @pytest.mark.parametrize("case", ["small", "ties", "ragged", "many", "single_tile", "empty"])
