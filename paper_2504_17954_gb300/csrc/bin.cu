@@ -483,7 +483,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
                                                            unsigned* __restrict__ lookback,
                                                            unsigned* __restrict__ counter, unsigned* __restrict__ flag,
                                                            long long max_spin, long long skip_publish_tile,
-                                                           int use_match) {
+                                                           int use_match, unsigned* __restrict__ ranges,
+                                                           long long n_tiles) {
     __shared__ unsigned s_tile;
     __shared__ unsigned s_whist[kSortThreads / 32][256];
     __shared__ unsigned s_local[256];
@@ -647,7 +648,42 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
         const unsigned o = s_global[dd] + ((unsigned)i - s_local[dd]);
         kout[o] = k;
         vout[o] = s_vals[i];
+        if (ranges != nullptr) {
+            // last pass: the tile is fully ordered by key, so equal keys form runs, and where a run
+            // begins the previous one ends. Inside a digit's stretch of this tile both boundaries are
+            // final (plain stores). At the first item of a digit an earlier tile may hold more of
+            // either key, so the start of this key and the end of the previous one are candidates:
+            // atomic maxima of ~start and of end against the zeroed table (k_ranges_fix decodes)
+            const unsigned kp = i > 0 ? s_keys[i - 1] : 0xffffffffu;
+            if (kp != k) {
+                const unsigned dp = (kp >> shift) & 255u;
+                const bool inner = i > 0 && dp == dd;
+                if ((long long)k < n_tiles) {
+                    if (inner) ranges[2ll * k] = ~o;
+                    else atomicMax(&ranges[2ll * k], ~o);
+                }
+                if (i > 0 && (long long)kp < n_tiles) {
+                    if (inner) ranges[2ll * kp + 1] = o;
+                    else atomicMax(&ranges[2ll * kp + 1], s_global[dp] + ((unsigned)i - s_local[dp]));
+                }
+            }
+            if (i == nvalid - 1 && (long long)k < n_tiles) atomicMax(&ranges[2ll * k + 1], o + 1u);
+        }
     }
+}
+
+// ranges written by the last radix pass: start stored complemented; an untouched tile is empty
+__global__ void __launch_bounds__(256) k_ranges_fix(unsigned* __restrict__ ranges, long long n_tiles) {
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (t >= n_tiles) return;
+    uint2 r = reinterpret_cast<uint2*>(ranges)[t];
+    if (r.y == 0u) {
+        r.x = 0u;
+    } else {
+        r.x = ~r.x;
+        if (r.x > r.y) r.x = r.y;  // only after a timed-out sort (reported); keeps the run empty
+    }
+    reinterpret_cast<uint2*>(ranges)[t] = r;
 }
 
 // ------------------------------------------------------------------------- reduce-then-scan
@@ -841,7 +877,8 @@ cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const
 static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1,
                                    const unsigned long long* d_n, long long cap, const unsigned* base,
                                    unsigned* lookback, long long tiles, unsigned* counter, unsigned* flag,
-                                   bool early, const char* name, cudaStream_t s) {
+                                   bool early, unsigned* ranges, long long n_tiles, const char* name,
+                                   cudaStream_t s) {
     unsigned* kb[2] = {k0, k1};
     unsigned* vb[2] = {v0, v1};
     const bool rts = options().sort_scan != 0;
@@ -854,16 +891,19 @@ static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, uns
             k_digit_scan<<<256, kDigitScanThreads, 0, s>>>(lb, base + 256 * ps, tiles);
             k_onesweep<false, false><<<(unsigned)tiles, kSortThreads, 0, s>>>(
                 kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                g_max_spin, g_skip_publish_tile, options().sort_match);
+                g_max_spin, g_skip_publish_tile, options().sort_match, ps == n_passes - 1 ? ranges : nullptr,
+                n_tiles);
         } else {
             if (early)
                 k_onesweep<true, true><<<(unsigned)tiles, kSortThreads, 0, s>>>(
                     kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                    g_max_spin, g_skip_publish_tile, options().sort_match);
+                    g_max_spin, g_skip_publish_tile, options().sort_match, ps == n_passes - 1 ? ranges : nullptr,
+                n_tiles);
             else
                 k_onesweep<true, false><<<(unsigned)tiles, kSortThreads, 0, s>>>(
                     kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                    g_max_spin, g_skip_publish_tile, options().sort_match);
+                    g_max_spin, g_skip_publish_tile, options().sort_match, ps == n_passes - 1 ? ranges : nullptr,
+                n_tiles);
         }
     }
     return cudaGetLastError();
@@ -899,7 +939,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         k_hist_scan<<<kRecPasses, 256, 0, s>>>(b.hist_rec, b.base_rec);
     }
     if ((e = onesweep_passes(kRecPasses, b.rkey[0], b.rval[0], b.rkey[1], b.rval[1], b.d_m, plan.n_records,
-                             b.base_rec, b.lb_rec, rec_tiles, b.counter, b.flag, true, "k_onesweep_rec", s)) != cudaSuccess)
+                             b.base_rec, b.lb_rec, rec_tiles, b.counter, b.flag, true, nullptr, 0, "k_onesweep_rec", s)) != cudaSuccess)
         return e;
     // pair offsets of the depth-ordered records
     unsigned long long* sums2 = b.sums + 2 * (nb > 0 ? nb : 1);
@@ -928,9 +968,13 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         k_hist_scan<<<plan.n_passes, 256, 0, s>>>(b.hist_tile, b.base_tile);
     }
     if ((e = onesweep_passes(plan.n_passes, t0, v0, t1, v1, b.d_n, cap, b.base_tile, b.lb_tile, pair_tiles,
-                             b.counter + kRecPasses, b.flag, options().sort_early != 0, "k_onesweep", s)) != cudaSuccess)
+                             b.counter + kRecPasses, b.flag, options().sort_early != 0, out->ranges, out->n_tiles,
+                             "k_onesweep", s)) != cudaSuccess)
         return e;
-    if (n_work > 0) {
+    if (plan.n_passes > 0 && pair_tiles > 0) {  // the last pass wrote the runs
+        IVRGS_PROF("k_ranges_fix", s);
+        k_ranges_fix<<<(unsigned)((out->n_tiles + 255) / 256), 256, 0, s>>>(out->ranges, out->n_tiles);
+    } else if (n_work > 0) {  // a single tile: no radix pass
         IVRGS_PROF("k_ranges", s);
         k_ranges<<<(unsigned)((n_work + 1023) / 1024), 256, 0, s>>>(out->tiles, b.d_n, cap, out->n_tiles,
                                                                    out->ranges);

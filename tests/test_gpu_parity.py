@@ -100,7 +100,7 @@ def sort_scan(request):
     N.ivrgs_set_option("sort_early", old[1])
 
 
-@pytest.mark.parametrize("case", ["small", "ties", "ragged", "many", "single_tile", "empty"])
+@pytest.mark.parametrize("case", ["small", "ties", "ragged", "many", "dense1", "dense2", "single_tile", "empty"])
 @pytest.mark.parametrize("mode", ["exact", "capacity"])
 def test_bin_bit_exact(case, mode, sort_scan):
     if case == "small":
@@ -111,6 +111,10 @@ def test_bin_bit_exact(case, mode, sort_scan):
         sizes, n, seed, kw = [(37, 53), (100, 7), (16, 16), (250, 130)], 2000, 3, {}
     elif case == "many":
         sizes, n, seed, kw = [(512, 512), (800, 800), (1024, 768)], 60000, 4, {"max_radius": 60}
+    elif case == "dense1":  # 12 tiles (one radix pass), each run spread over several radix tiles
+        sizes, n, seed, kw = [(64, 48)], 80000, 10, {"max_radius": 40}
+    elif case == "dense2":  # 289 tiles (two passes), runs of thousands of pairs
+        sizes, n, seed, kw = [(272, 272)], 40000, 11, {"max_radius": 150}
     elif case == "single_tile":
         sizes, n, seed, kw = [(16, 16)], 5000, 5, {}
     else:
@@ -128,6 +132,8 @@ def test_bin_bit_exact(case, mode, sort_scan):
     np.testing.assert_array_equal(r, ref.ranges)
     if case == "many":
         assert len(ref.keys) > 20 * 3072  # several radix tiles and all passes exercised
+    if case.startswith("dense"):
+        assert (r[:, 1] - r[:, 0]).max() > 2 * 4096  # a run covering three radix tiles or more
 
 
 def test_bin_capacity_reporting():
