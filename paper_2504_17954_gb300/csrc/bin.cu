@@ -294,17 +294,24 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const unsigned* __rest
 }
 
 // ------------------------------------------------------------------------- count of sorted records
+// pairs of the depth-ordered records, summed per block (sums[b], scanned afterwards) and per
+// warp range (wsums[8 b + w]): warp w of block b covers the records
+// [b kScanBlock + w kWarpRange, + kWarpRange), the unit the emission's warps work on
+constexpr int kWarpRange = 32 * kScanItems;
+constexpr int kScanWarps = kScanThreads / 32;
 __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* __restrict__ cnt2,
                                                                const unsigned* __restrict__ rval,
                                                                const unsigned long long* __restrict__ d_m,
-                                                               unsigned long long* __restrict__ sums) {
-    __shared__ unsigned s_red[kScanThreads / 32];
+                                                               unsigned long long* __restrict__ sums,
+                                                               unsigned* __restrict__ wsums) {
+    __shared__ unsigned s_red[kScanWarps];
     const long long m = (long long)*d_m;
-    const long long base = (long long)blockIdx.x * kScanBlock;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long base = (long long)blockIdx.x * kScanBlock + (long long)warp * kWarpRange;
     unsigned pairs = 0;
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
-        const long long k = base + (long long)j * kScanThreads + threadIdx.x;
+        const long long k = base + j * 32 + lane;
         if (k < m) {
             const long long kk = rval[k];
             if (kk < m) pairs += cnt2[kk];  // always true unless a timed-out sort left a slot unwritten
@@ -312,33 +319,38 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* _
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = pairs;
+    if (lane == 0) {
+        wsums[(long long)blockIdx.x * kScanWarps + warp] = pairs;
+        s_red[warp] = pairs;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long b = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) b += s_red[w];
+        for (int w = 0; w < kScanWarps; ++w) b += s_red[w];
         sums[blockIdx.x] = b;
     }
 }
 
 // ------------------------------------------------------------------------- emission
-// Each warp emits the pairs of its 32 records. Round 1: its lanes stride over the records' tile
-// rows (row runs), evaluating each row's kept columns [lo, hi) once. Round 2, for every 32 row
-// runs: its lanes stride over those runs' pairs, so consecutive lanes write consecutive slots.
-// The pairs a warp writes must equal the sum of its records' counts from k_count (the same
-// rounded arithmetic decides both); a mismatch sets bit 1 of the error flag.
+// Every warp emits the pairs of its own range of kWarpRange depth-ordered records, 32 at a
+// time, starting at the range's pair offset (no block-wide step, so a warp with large records
+// does not hold up the others). Round 1: its lanes stride over the 32 records' tile rows (row
+// runs), evaluating each row's kept columns [lo, hi) once. Round 2, for every 32 row runs: its
+// lanes stride over those runs' pairs, so consecutive lanes write consecutive slots.
+// The pairs a warp writes must equal the sum of its records' counts from the count pass (the
+// same rounded arithmetic decides both); a mismatch sets bit 1 of the error flag.
 __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict__ rec,
                                                        const unsigned* __restrict__ cnt2, long long n,
                                                        const __grid_constant__ CamBatch cb, int cull,
                                                        const unsigned* __restrict__ rval,
                                                        const unsigned long long* __restrict__ d_m,
                                                        const unsigned long long* __restrict__ pair_off,
+                                                       const unsigned* __restrict__ wsums,
                                                        unsigned* __restrict__ tiles, unsigned* __restrict__ vals,
                                                        long long cap, int n_passes, unsigned* __restrict__ hist,
                                                        unsigned* __restrict__ flag) {
     constexpr int kWarps = kScanThreads / 32;
     __shared__ unsigned s_hist[kMaxTilePasses * 256];
-    __shared__ unsigned s_warp[kWarps + 1];
     __shared__ unsigned s_rstart[kWarps][33];  // row-run prefix over the warp's records
     __shared__ unsigned s_pstart[kWarps][33];  // pair prefix over the current 32 row runs
     __shared__ unsigned s_rb[kWarps][32];      // tile id of each current run's first kept column
@@ -350,12 +362,14 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
     __syncthreads();
     const long long m = (long long)*d_m;
     const long long total = n * cb.n;
-    const long long base = (long long)blockIdx.x * kScanBlock;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long off = pair_off[blockIdx.x];
+    const long long base = (long long)blockIdx.x * kScanBlock + (long long)warp * kWarpRange;
+    unsigned long long wbase = pair_off[blockIdx.x];  // + the pairs of the block's earlier warp ranges
+    for (int w = 0; w < warp; ++w) wbase += wsums[(long long)blockIdx.x * kScanWarps + w];
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
-        const long long k = base + (long long)j * kScanThreads + threadIdx.x;
+        const long long k = base + j * 32 + lane;
+        if (__shfl_sync(0xffffffffu, k, 0) >= m) break;  // the rest of the range is past the end
         unsigned c = 0, rows = 0;
         {
             int x0 = 0, x1 = 0, y0 = 0, y1 = 0, ya = 0, yb = 0, v = 0;
@@ -387,16 +401,12 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
             s_t0[threadIdx.x] = (unsigned)cb.c[v].tile0;
             s_gx[threadIdx.x] = (unsigned)cb.c[v].gx;
         }
-        unsigned excl;
-        const unsigned tot = block_excl_scan(c, excl, s_warp);
         const unsigned rinc = warp_incl_scan(rows);
         s_rstart[warp][lane + 1] = rinc;
         if (lane == 0) s_rstart[warp][0] = 0;
         const unsigned cwarp = __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
         __syncwarp();
         const unsigned R = s_rstart[warp][32];
-        // absolute slot of the warp's first pair = block offset + exclusive offset of lane 0
-        const unsigned long long wbase = off + __shfl_sync(0xffffffffu, excl, 0);
         unsigned done = 0;
         for (unsigned r0 = 0; r0 < R; r0 += 32) {
             const unsigned rr = r0 + lane;
@@ -453,7 +463,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
             __syncwarp();
         }
         if (lane == 0 && done != cwarp) atomicOr(flag, 2u);
-        off += tot;
+        wbase += cwarp;
         __syncwarp();
     }
     __syncthreads();
@@ -803,7 +813,7 @@ BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity) {
     p.off_counter = o;      o = align_up(o + 4 * (kRecPasses + kMaxTilePasses));
     p.off_total = o;        o = align_up(o + 8 * 2);
     p.clear_bytes = o;
-    p.off_block_sums = o;   o = align_up(o + 8 * 3 * nb);
+    p.off_block_sums = o;   o = align_up(o + 8 * 3 * nb + 4 * (kScanThreads / 32) * nb);
     p.off_rec = o;          o = align_up(o + 4 * 4 * nr);
     p.off_cnt = o;          o = align_up(o + 4 * nr);
     p.off_cnt2 = o;         o = align_up(o + 4 * nr);
@@ -943,9 +953,10 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         return e;
     // pair offsets of the depth-ordered records
     unsigned long long* sums2 = b.sums + 2 * (nb > 0 ? nb : 1);
+    unsigned* wsums = reinterpret_cast<unsigned*>(sums2 + (nb > 0 ? nb : 1));
     if (nb > 0) {
         IVRGS_PROF("k_count_sorted", s);
-        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt2, b.rval[0], b.d_m, sums2);
+        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt2, b.rval[0], b.d_m, sums2, wsums);
     }
     {
         IVRGS_PROF("k_scan_sums", s);
@@ -960,8 +971,8 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     }
     if (nb > 0) {
         IVRGS_PROF("k_emit", s);
-        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(b.prec, b.cnt2, p->n, cb, cull, b.rval[0], b.d_m, sums2, t0, v0,
-                                                     cap, plan.n_passes, b.hist_tile, b.flag);
+        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(b.prec, b.cnt2, p->n, cb, cull, b.rval[0], b.d_m, sums2, wsums,
+                                                     t0, v0, cap, plan.n_passes, b.hist_tile, b.flag);
     }
     if (plan.n_passes > 0) {
         IVRGS_PROF("k_hist_scan", s);
