@@ -217,12 +217,14 @@ ivrgs_status ivrgs_compose_edit(const ivrgs_gaussians* models, int32_t n_models,
    the Blinn-Phong system; Sec. 4.3 c_v = c_p + dc; Sec. 4.5/4.6 edits). For every view
    v < n_views and Gaussian g: culls hidden models, z_c <= znear and det(Sigma') <= 0;
    Sigma = R(q) diag(exp 2 s) R(q)^T, Sigma' = J R Sigma R^T J^T + lowpass I; writes
-   out (n = g->n, n_views). The depth is the float64 sum ((R20 mx + R21 my) + R22 mz) + t2
-   rounded to float, so sort keys are exactly reproducible. */
+   out (n = g->n, n_views). The depth (sort key, near-plane test) is the float32 chain
+   fma(R22, mz, fma(R21, my, fma(R20, mx, t2))), each step one correctly rounded fused
+   multiply-add, so sort keys are exactly reproducible. */
 ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_camera* cams,
                            int32_t n_views, float lowpass, ivrgs_projected* out, void* stream);
 
-/* Workspace bytes ivrgs_bin needs for p->n * n_views records (below 2^32) and `capacity` pairs
+/* Workspace bytes ivrgs_bin needs for p->n * n_views records (below IVRGS_MAX_PAIRS, i.e. 2^30, as
+   for the pairs: the radix look-back carries 30-bit counts) and `capacity` pairs
    (about 57 bytes per record plus 9 per pair). */
 ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera* cams, int32_t tile_w,
                                  int32_t tile_h, int64_t capacity, size_t* bytes);

@@ -26,8 +26,10 @@
  * Integer decisions that the GPU takes in float32 (tile rectangle, sort key) are taken here
  * in float32 too, from the float64 values rounded once: the rectangle from (u, v) rounded
  * to float and the integer radius; the key from the float depth's bit pattern.  The depth
- * itself is the float64 sum ((R20 mx + R21 my) + R22 mz) + t2 of float32 inputs (each
- * product is exact in float64), rounded to float.
+ * that keys the sort and decides the near plane is the camera z as the float32 chain
+ * fma(R22, mz, fma(R21, my, fma(R20, mx, t2))) of the float32 inputs, every step one
+ * correctly rounded fused multiply-add (C fmaf), which the GPU evaluates identically; the
+ * rest of the projection uses the float64 camera-space position.
  *
  * Gradients (reverse mode of all of the above) are taken w.r.t. the stored parameters:
  * mean, log-scale, unnormalised quaternion and normal, opacity logit, colour offset,
@@ -197,7 +199,10 @@ static void project_one(const orc_gaussians* G, int64_t g, const double* edit, i
     /* viewing transform W: mu_c = R mu + t */
     for (int i = 0; i < 3; ++i) f->mc[i] = R[3 * i] * mu[0] + R[3 * i + 1] * mu[1] + R[3 * i + 2] * mu[2] + cam->t[i];
     double x = f->mc[0], y = f->mc[1], z = f->mc[2];
-    if (!(z > cam->znear)) return;
+    /* the float32 depth of the sort key (see the header); it also takes the near-plane decision */
+    const float z32 = fmaf((float)R[8], (float)mu[2],
+                           fmaf((float)R[7], (float)mu[1], fmaf((float)R[6], (float)mu[0], (float)cam->t[2])));
+    if (!(z32 > (float)cam->znear)) return;
     /* Sigma = R_q S S^T R_q^T */
     quat_rot(G->quat + 4 * g, f->qn, f->Rq);
     for (int k = 0; k < 3; ++k) f->S[k] = exp(G->log_scale[3 * g + k]);
@@ -252,7 +257,7 @@ static void project_one(const orc_gaussians* G, int64_t g, const double* edit, i
     if (f->radius <= 0) return;
     f->uv[0] = cam->fx * (x / z) + cam->cx;
     f->uv[1] = cam->fy * (y / z) + cam->cy;
-    f->depth = z;
+    f->depth = z32;
     /* editable opacity (Sec. 4.5): o' = s_m sigmoid(logit), not clamped */
     f->sig_o = sigmoid(G->opacity_logit[g]);
     f->opacity = me[3] * f->sig_o;

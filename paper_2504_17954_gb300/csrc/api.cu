@@ -271,7 +271,7 @@ ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera*
     static thread_local CamBatch cb;
     ivrgs_status st = make_cam_batch(cams, n_views, &cb);
     if (st) return st;
-    if (n * (long long)n_views >= (1ll << 32)) return invalid("n * n_views must be below 2^32");
+    if (n * (long long)n_views >= IVRGS_MAX_PAIRS) return invalid("n * n_views must be below 2^30 for binning");
     *bytes = plan_bin(n * (long long)n_views, cb.n_tiles, capacity).total_bytes;
     return IVRGS_OK;
 }
@@ -303,7 +303,8 @@ ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32
         return invalid("mode must be IVRGS_BIN_EXACT or IVRGS_BIN_CAPACITY, optionally | IVRGS_BIN_CULL");
     const int cull = (mode & IVRGS_BIN_CULL) ? 1 : 0;
     const bool capacity_mode = (mode & IVRGS_BIN_CAPACITY) != 0;
-    if (p->n * (long long)n_views >= (1ll << 32)) return invalid("n * n_views must be below 2^32");
+    // the radix look-back carries 30-bit counts, so the records of one call stay below 2^30
+    if (p->n * (long long)n_views >= IVRGS_MAX_PAIRS) return invalid("n * n_views must be below 2^30 for binning");
     const BinPlan plan = plan_bin(p->n * (long long)n_views, cb.n_tiles, out->capacity);
     if (!d_workspace || ws_bytes < plan.total_bytes) {
         set_error("workspace too small: need " + std::to_string(plan.total_bytes) + " bytes");

@@ -206,12 +206,12 @@ __device__ __forceinline__ float sh_term(int t, float x, float y, float z, float
 
 __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& c, float lowpass, ViewLocal& V) {
     V.visible = false;
-    // depth in float64: products of float32 values are exact, summation order fixed
-    const double zd = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)c.R[6], (double)G.mu[0]),
-                                                    __dmul_rn((double)c.R[7], (double)G.mu[1])),
-                                          __dmul_rn((double)c.R[8], (double)G.mu[2])),
-                                (double)c.t[2]);
-    if (!(zd > (double)c.znear)) return;
+    // camera depth as a fixed chain of three correctly rounded float32 FMAs,
+    // fma(R22, mz, fma(R21, my, fma(R20, mx, t2))): the sort key and the near-plane decision
+    // are reproducible bit for bit (float64 arithmetic runs at a small fraction of the float32
+    // rate on this GPU, and this is one of the projection's hottest expressions)
+    const float zd = fmaf(c.R[8], G.mu[2], fmaf(c.R[7], G.mu[1], fmaf(c.R[6], G.mu[0], c.t[2])));
+    if (!(zd > c.znear)) return;
     V.depth = (float)zd;
     V.z = V.depth;
     V.x = fmaf(c.R[0], G.mu[0], fmaf(c.R[1], G.mu[1], fmaf(c.R[2], G.mu[2], c.t[0])));

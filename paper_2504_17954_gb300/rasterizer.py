@@ -399,6 +399,8 @@ class WaveRasterizer:
                  bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20, cull: bool = True):
         self.cams = list(cams)
         self.waves: List[List[int]] = []
+        # records (n * views) of one binning call stay below the library's 2^30 limit
+        max_views = max(1, min(max_views, (N.IVRGS_MAX_PAIRS - 1) // max(n_gaussians, 1)))
         cur, pix = [], 0
         for v, c in enumerate(self.cams):
             if cur and (len(cur) >= max_views or pix + c.W * c.H > pixel_budget):

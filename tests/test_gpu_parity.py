@@ -65,7 +65,7 @@ def test_project_matches_oracle(which):
         assert (np.abs(co[v][vis, :3] - p.conic[vis]) / cmax).max() < 1e-4
         assert np.abs(co[v][vis, 3] - p.opacity[vis]).max() < 1e-6
         assert np.abs(cd[v][vis, :3] - p.rgb[vis]).max() < 1e-5
-        # depth: float64 sum rounded once -> exact float32 bits
+        # depth: the same float32 FMA chain on both sides -> exact float32 bits
         np.testing.assert_array_equal(cd[v][vis, 3].view(np.uint32), p.depth[vis].astype(np.float32).view(np.uint32))
 
 
@@ -92,12 +92,13 @@ def _gpu_bin_from(sizes, xy, rad, depth, mode="exact", capacity=None):
 @pytest.fixture(params=[(0, 0), (0, 1), (1, 0)], ids=["lookback", "lookback_early", "rts"])
 def sort_scan(request):
     from paper_2504_17954_gb300 import _native as N
-    old = (N.ivrgs_get_option("sort_scan"), N.ivrgs_get_option("sort_early"))
-    N.ivrgs_set_option("sort_scan", request.param[0])
-    N.ivrgs_set_option("sort_early", request.param[1])
+    names = ("sort_scan", "sort_early")
+    old = [N.ivrgs_get_option(k) for k in names]
+    for k, v in zip(names, request.param):
+        N.ivrgs_set_option(k, v)
     yield request.param
-    N.ivrgs_set_option("sort_scan", old[0])
-    N.ivrgs_set_option("sort_early", old[1])
+    for k, v in zip(names, old):
+        N.ivrgs_set_option(k, v)
 
 
 @pytest.mark.parametrize("case", ["small", "ties", "ragged", "many", "dense1", "dense2", "single_tile", "empty"])

@@ -43,6 +43,36 @@ def test_isotropic_on_axis(lowpass, sigma):
     assert p.depth[0] == pytest.approx(3.0)
 
 
+def test_depth_is_the_camera_z_within_the_fma_chain_bound():
+    """The depth that keys the sort is the camera-space z of the float32 inputs through three
+    correctly rounded fused multiply-adds: within 3.01 u (sum of the terms' magnitudes) of the
+    exact value (rational arithmetic, u = 2^-24), and it takes the near-plane decision."""
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    w = sg.tiny_scene(300, 32, 32, 3, n_models=1)
+    comp = oracle.compose(w.models)
+    table = oracle.edit_table(w.edits)
+    checked, culled = 0, 0
+    for dist in (3.0, 3.0, 0.6, 0.6):  # the close cameras put part of the scene behind the near plane
+        cam = sg.look_at(dist * sg.random_direction(rng), 32, 32)
+        p = oracle.project(comp, table, cam)
+        R = np.asarray(cam.R, np.float32).reshape(3, 3)
+        t2 = Fraction(float(np.float32(cam.t[2])))
+        for g in range(comp.n):
+            mu = comp.mean[g].astype(np.float32)
+            terms = [Fraction(float(R[2, j])) * Fraction(float(mu[j])) for j in range(3)] + [t2]
+            exact = sum(terms)
+            bound = 3.01 * 2.0 ** -24 * float(sum(abs(x) for x in terms))
+            if p.radius[g] > 0:
+                assert abs(float(Fraction(float(p.depth[g])) - exact)) <= bound, g
+                assert np.float32(p.depth[g]) == p.depth[g]  # a float32 value
+                checked += 1
+            if float(exact) <= float(np.float32(cam.znear)) - bound:
+                assert p.radius[g] == 0, g  # behind the near plane
+                culled += 1
+    assert checked > 500 and culled > 20, (checked, culled)
+
+
 def test_axis_aligned_and_quarter_turn():
     cam = axis_camera(W=64, H=64, z=4.0)
     ls = np.log(np.array([0.02, 0.005, 0.03])).astype(np.float32)
