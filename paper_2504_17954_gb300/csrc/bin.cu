@@ -351,10 +351,10 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                                                        unsigned* __restrict__ flag) {
     constexpr int kWarps = kScanThreads / 32;
     __shared__ unsigned s_hist[kMaxTilePasses * 256];
-    __shared__ unsigned s_rstart[kWarps][33];  // row-run prefix over the warp's records
-    __shared__ unsigned s_pstart[kWarps][33];  // pair prefix over the current 32 row runs
-    __shared__ unsigned s_rb[kWarps][32];      // tile id of each current run's first kept column
-    __shared__ unsigned s_rg[kWarps][32];      // Gaussian index of each current run
+    __shared__ unsigned s_rti[kWarps][32];     // lane of the k-th of the warp's records with rows
+    __shared__ unsigned s_rst[kWarps][32];     // its first row in the warp's row numbering
+    __shared__ unsigned s_rb[kWarps][32];      // k-th non-empty current run: tile id - pair number
+    __shared__ unsigned s_rg[kWarps][32];      // k-th non-empty current run: Gaussian index
     __shared__ CullEll s_e[kScanThreads];
     __shared__ int s_x0[kScanThreads], s_x1[kScanThreads], s_ya[kScanThreads];
     __shared__ unsigned s_g[kScanThreads], s_t0[kScanThreads], s_gx[kScanThreads];
@@ -401,24 +401,30 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
             s_t0[threadIdx.x] = (unsigned)cb.c[v].tile0;
             s_gx[threadIdx.x] = (unsigned)cb.c[v].gx;
         }
-        const unsigned rinc = warp_incl_scan(rows);
-        s_rstart[warp][lane + 1] = rinc;
-        if (lane == 0) s_rstart[warp][0] = 0;
+        // records with rows, compacted: row rr belongs to the k-th of them, k = number of their
+        // first rows at or before rr minus 1 (a 32-bit word of first rows per chunk of 32 rows)
+        const unsigned rinc = warp_incl_scan(rows), rexcl = rinc - rows;
+        const unsigned rnz = __ballot_sync(0xffffffffu, rows != 0u);
+        if (rows) {
+            const int k = __popc(rnz & ((1u << lane) - 1u));
+            s_rti[warp][k] = (unsigned)lane;
+            s_rst[warp][k] = rexcl;
+        }
         const unsigned cwarp = __shfl_sync(0xffffffffu, warp_incl_scan(c), 31);
         __syncwarp();
-        const unsigned R = s_rstart[warp][32];
-        unsigned done = 0;
+        const unsigned R = __shfl_sync(0xffffffffu, rinc, 31);
+        const unsigned upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;  // positions <= lane
+        unsigned done = 0, rcarry = 0;
         for (unsigned r0 = 0; r0 < R; r0 += 32) {
             const unsigned rr = r0 + lane;
+            const unsigned rword = __reduce_or_sync(
+                0xffffffffu, rows != 0u && rexcl >= r0 && rexcl - r0 < 32u ? 1u << (rexcl - r0) : 0u);
             int lo = 0, hi = 0;
             unsigned rowbase = 0, g = 0;
             if (rr < R) {
-                int r = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (s_rstart[warp][r + step] <= rr) r += step;
-                const int ti = warp * 32 + r;
-                const int ty = s_ya[ti] + (int)(rr - s_rstart[warp][r]);
+                const int k = (int)(rcarry + __popc(rword & upto)) - 1;
+                const int ti = warp * 32 + (int)s_rti[warp][k];
+                const int ty = s_ya[ti] + (int)(rr - s_rst[warp][k]);
                 cull_row(s_e[ti], ty, s_x0[ti], s_x1[ti], lo, hi);
                 rowbase = s_t0[ti] + (unsigned)ty * s_gx[ti];
                 g = s_g[ti];
@@ -438,26 +444,34 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                     }
                 }
             }
+            rcarry += __popc(rword);
+            // the non-empty runs of these rows, compacted the same way over their pairs
             const unsigned w = (unsigned)(hi - lo);
-            const unsigned pinc = warp_incl_scan(w);
-            s_pstart[warp][lane + 1] = pinc;
-            if (lane == 0) s_pstart[warp][0] = 0;
-            s_rb[warp][lane] = rowbase + (unsigned)lo;
-            s_rg[warp][lane] = g;
+            const unsigned pinc = warp_incl_scan(w), pexcl = pinc - w;
+            const unsigned pnz = __ballot_sync(0xffffffffu, w != 0u);
+            if (w) {
+                const int k = __popc(pnz & ((1u << lane) - 1u));
+                s_rb[warp][k] = rowbase + (unsigned)lo - pexcl;  // tile of pair q = s_rb[k] + q
+                s_rg[warp][k] = g;
+            }
             __syncwarp();
-            const unsigned W = s_pstart[warp][32];
-            for (unsigned q = lane; q < W; q += 32) {
-                int l = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (s_pstart[warp][l + step] <= q) l += step;
-                const unsigned tile = s_rb[warp][l] + (q - s_pstart[warp][l]);
-                const unsigned long long o = wbase + done + q;
-                if ((long long)o < cap) {
-                    tiles[o] = tile;
-                    vals[o] = s_rg[warp][l];
-                    atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
+            const unsigned W = __shfl_sync(0xffffffffu, pinc, 31);
+            unsigned pcarry = 0;
+            for (unsigned q0 = 0; q0 < W; q0 += 32) {
+                const unsigned q = q0 + lane;
+                const unsigned pword = __reduce_or_sync(
+                    0xffffffffu, w != 0u && pexcl >= q0 && pexcl - q0 < 32u ? 1u << (pexcl - q0) : 0u);
+                if (q < W) {
+                    const int k = (int)(pcarry + __popc(pword & upto)) - 1;
+                    const unsigned tile = s_rb[warp][k] + q;
+                    const unsigned long long o = wbase + done + q;
+                    if ((long long)o < cap) {
+                        tiles[o] = tile;
+                        vals[o] = s_rg[warp][k];
+                        atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
+                    }
                 }
+                pcarry += __popc(pword);
             }
             done += W;
             __syncwarp();
