@@ -353,11 +353,12 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
     __shared__ unsigned s_hist[kMaxTilePasses * 256];
     __shared__ unsigned s_rti[kWarps][32];     // lane of the k-th of the warp's records with rows
     __shared__ unsigned s_rst[kWarps][32];     // its first row in the warp's row numbering
-    __shared__ unsigned s_rb[kWarps][32];      // k-th non-empty current run: tile id - pair number
-    __shared__ unsigned s_rg[kWarps][32];      // k-th non-empty current run: Gaussian index
-    __shared__ CullEll s_e[kScanThreads];
-    __shared__ int s_x0[kScanThreads], s_x1[kScanThreads], s_ya[kScanThreads];
-    __shared__ unsigned s_g[kScanThreads], s_t0[kScanThreads], s_gx[kScanThreads];
+    __shared__ uint2 s_run[kWarps][32];        // k-th non-empty current run: (tile id - pair number, Gaussian)
+    // per record of the current group, four 16-byte words (one vector load each per row):
+    // (u, v, b/a, 1/a), (tau' a, det, Y, eyR), (mode, x0, x1, first row), (Gaussian, tile0, gx, -)
+    __shared__ float4 s_ell0[kScanThreads], s_ell1[kScanThreads];
+    __shared__ int4 s_rect[kScanThreads];
+    __shared__ uint4 s_map[kScanThreads];
     for (int k = threadIdx.x; k < n_passes * 256; k += kScanThreads) s_hist[k] = 0u;
     __syncthreads();
     const long long m = (long long)*d_m;
@@ -393,13 +394,10 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                     }
                 }
             }
-            s_e[threadIdx.x] = e;
-            s_x0[threadIdx.x] = x0;
-            s_x1[threadIdx.x] = x1;
-            s_ya[threadIdx.x] = ya;
-            s_g[threadIdx.x] = g;
-            s_t0[threadIdx.x] = (unsigned)cb.c[v].tile0;
-            s_gx[threadIdx.x] = (unsigned)cb.c[v].gx;
+            s_ell0[threadIdx.x] = make_float4(e.u, e.v, e.ba, e.inv_a);
+            s_ell1[threadIdx.x] = make_float4(e.ta, e.det, e.Y, e.eyR);
+            s_rect[threadIdx.x] = make_int4(e.mode, x0, x1, ya);
+            s_map[threadIdx.x] = make_uint4(g, (unsigned)cb.c[v].tile0, (unsigned)cb.c[v].gx, 0u);
         }
         // records with rows, compacted: row rr belongs to the k-th of them, k = number of their
         // first rows at or before rr minus 1 (a 32-bit word of first rows per chunk of 32 rows)
@@ -424,10 +422,14 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
             if (rr < R) {
                 const int k = (int)(rcarry + __popc(rword & upto)) - 1;
                 const int ti = warp * 32 + (int)s_rti[warp][k];
-                const int ty = s_ya[ti] + (int)(rr - s_rst[warp][k]);
-                cull_row(s_e[ti], ty, s_x0[ti], s_x1[ti], lo, hi);
-                rowbase = s_t0[ti] + (unsigned)ty * s_gx[ti];
-                g = s_g[ti];
+                const float4 q0 = s_ell0[ti], q1 = s_ell1[ti];
+                const int4 rc = s_rect[ti];
+                const uint4 mp = s_map[ti];
+                const CullEll e{q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, rc.x};
+                const int ty = rc.w + (int)(rr - s_rst[warp][k]);
+                cull_row(e, ty, rc.y, rc.z, lo, hi);
+                rowbase = mp.y + (unsigned)ty * mp.z;
+                g = mp.x;
                 if (hi > lo) {
                     // digits above the lowest byte: the run is contiguous in tile id (narrower
                     // than 256), so it adds to at most two digits per higher byte
@@ -451,8 +453,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
             const unsigned pnz = __ballot_sync(0xffffffffu, w != 0u);
             if (w) {
                 const int k = __popc(pnz & ((1u << lane) - 1u));
-                s_rb[warp][k] = rowbase + (unsigned)lo - pexcl;  // tile of pair q = s_rb[k] + q
-                s_rg[warp][k] = g;
+                s_run[warp][k] = make_uint2(rowbase + (unsigned)lo - pexcl, g);  // tile of pair q = .x + q
             }
             __syncwarp();
             const unsigned W = __shfl_sync(0xffffffffu, pinc, 31);
@@ -463,11 +464,12 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                     0xffffffffu, w != 0u && pexcl >= q0 && pexcl - q0 < 32u ? 1u << (pexcl - q0) : 0u);
                 if (q < W) {
                     const int k = (int)(pcarry + __popc(pword & upto)) - 1;
-                    const unsigned tile = s_rb[warp][k] + q;
+                    const uint2 run = s_run[warp][k];
+                    const unsigned tile = run.x + q;
                     const unsigned long long o = wbase + done + q;
                     if ((long long)o < cap) {
                         tiles[o] = tile;
-                        vals[o] = s_rg[warp][k];
+                        vals[o] = run.y;
                         atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
                     }
                 }
