@@ -8,7 +8,7 @@ include/ivrgs.h); this package marshals arguments to it.
 from . import _native
 from ._native import IvrgsError
 from .rasterizer import (Gaussians, Rasterizer, RenderFunction, camera_structs, compose_edit, pack_mixed, render,
-                         vq_compress)
+                         reorder_spatial, vq_compress)
 
 __all__ = ["_native", "IvrgsError", "Gaussians", "Rasterizer", "RenderFunction", "camera_structs", "compose_edit",
-           "pack_mixed", "render", "vq_compress"]
+           "pack_mixed", "render", "reorder_spatial", "vq_compress"]

@@ -294,16 +294,18 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const unsigned* __rest
 }
 
 // ------------------------------------------------------------------------- count of sorted records
-// pairs of the depth-ordered records, summed per block (sums[b], scanned afterwards) and per
-// warp range (wsums[8 b + w]): warp w of block b covers the records
-// [b kScanBlock + w kWarpRange, + kWarpRange), the unit the emission's warps work on
+// pairs of the depth-ordered records: cnts[k] = pairs of the k-th record in depth order (so that
+// the emission reads them in order), summed per block (sums[b], scanned afterwards) and per warp
+// range (wsums[8 b + w]): warp w of block b covers the records [b kScanBlock + w kWarpRange,
+// + kWarpRange), the unit the emission's warps work on
 constexpr int kWarpRange = 32 * kScanItems;
 constexpr int kScanWarps = kScanThreads / 32;
 __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* __restrict__ cnt2,
                                                                const unsigned* __restrict__ rval,
                                                                const unsigned long long* __restrict__ d_m,
                                                                unsigned long long* __restrict__ sums,
-                                                               unsigned* __restrict__ wsums) {
+                                                               unsigned* __restrict__ wsums,
+                                                               unsigned* __restrict__ cnts) {
     __shared__ unsigned s_red[kScanWarps];
     const long long m = (long long)*d_m;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -314,7 +316,9 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* _
         const long long k = base + j * 32 + lane;
         if (k < m) {
             const long long kk = rval[k];
-            if (kk < m) pairs += cnt2[kk];  // always true unless a timed-out sort left a slot unwritten
+            const unsigned c = kk < m ? cnt2[kk] : 0u;  // kk < m unless a timed-out sort left a slot unwritten
+            cnts[k] = c;
+            pairs += c;
         }
     }
 #pragma unroll
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* _
 // The pairs a warp writes must equal the sum of its records' counts from the count pass (the
 // same rounded arithmetic decides both); a mismatch sets bit 1 of the error flag.
 __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict__ rec,
-                                                       const unsigned* __restrict__ cnt2, long long n,
+                                                       const unsigned* __restrict__ cnts, long long n,
                                                        const __grid_constant__ CamBatch cb, int cull,
                                                        const unsigned* __restrict__ rval,
                                                        const unsigned long long* __restrict__ d_m,
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                     const int r = __float_as_int(r1.w);
                     v = view_of_record(i, n, total);
                     g = (unsigned)(i - (long long)v * n);
-                    c = cnt2[kk];
+                    c = cnts[k];
                     const float2 p = make_float2(r0.x, r0.y);
                     if (c && r > 0) {
                         tile_rect(p.x, p.y, r, cb.c[v].gx, cb.c[v].gy, x0, x1, y0, y1);
@@ -972,7 +976,8 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     unsigned* wsums = reinterpret_cast<unsigned*>(sums2 + (nb > 0 ? nb : 1));
     if (nb > 0) {
         IVRGS_PROF("k_count_sorted", s);
-        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt2, b.rval[0], b.d_m, sums2, wsums);
+        // (the record-order counts are dead after the compaction: their buffer takes the sorted ones)
+        k_count_sorted<<<(unsigned)nb, kScanThreads, 0, s>>>(b.cnt2, b.rval[0], b.d_m, sums2, wsums, b.cnt);
     }
     {
         IVRGS_PROF("k_scan_sums", s);
@@ -987,7 +992,7 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     }
     if (nb > 0) {
         IVRGS_PROF("k_emit", s);
-        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(b.prec, b.cnt2, p->n, cb, cull, b.rval[0], b.d_m, sums2, wsums,
+        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(b.prec, b.cnt, p->n, cb, cull, b.rval[0], b.d_m, sums2, wsums,
                                                      t0, v0, cap, plan.n_passes, b.hist_tile, b.flag);
     }
     if (plan.n_passes > 0) {
