@@ -14,6 +14,7 @@
 // dL/dc_v, dL/dk', dL/dn and dL/do' are accumulated over views in registers and pushed
 // through the view-independent parts (quaternion, scale, edits) once.
 #include "blend_alpha.cuh"
+#include "f32x2.cuh"
 #include "gauss_math.cuh"
 
 namespace ivrgs {
@@ -75,7 +76,9 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
     const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
     const float fx = (float)px + 0.5f;
-    const int q0 = py0 & 3;                               // offset of this thread's first row in its group
+    // offset of this thread's first row in its 4-row group (0 whenever P is a multiple of 4,
+    // since py0 is then one too: known at compile time, so the groups are indexed statically)
+    const int q0 = (P % 4 == 0) ? 0 : (py0 & 3);
     const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
     constexpr int NG = (P + 3) / 4;                       // 4-row exponent groups a thread spans
     const uint2 rg = ranges[tile];
@@ -87,6 +90,8 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
     float T[P], DS[P];
     float4 d[P];
     unsigned my_last[P];
+    F2 T2[P / 2 > 0 ? P / 2 : 1], DS2[P / 2 > 0 ? P / 2 : 1];  // even P: the same, as pixel pairs
+    F2 DX2[P / 2 > 0 ? P / 2 : 1], DY2[P / 2 > 0 ? P / 2 : 1], DZ2[P / 2 > 0 ? P / 2 : 1];
     unsigned mx = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -103,6 +108,16 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
         T[p] = Tf;
         DS[p] = Tf * (d[p].x * bg.x + d[p].y * bg.y + d[p].z * bg.z - d[p].w);
         mx = max(mx, my_last[p]);
+    }
+    if constexpr (P % 2 == 0) {
+#pragma unroll
+        for (int h = 0; h < P / 2; ++h) {
+            T2[h] = f2(T[2 * h], T[2 * h + 1]);
+            DS2[h] = f2(DS[2 * h], DS[2 * h + 1]);
+            DX2[h] = f2(d[2 * h].x, d[2 * h + 1].x);
+            DY2[h] = f2(d[2 * h].y, d[2 * h + 1].y);
+            DZ2[h] = f2(d[2 * h].z, d[2 * h + 1].z);
+        }
     }
     if (threadIdx.x == 0) s_max = 0u;
     __syncthreads();
@@ -165,37 +180,104 @@ __global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
             }
             if (!__any_sync(0xffffffffu, any)) continue;
             bool contrib = false;
-            // the P pixels update independently (predicated, no branches) so they interleave
+            if constexpr (P % 2 == 0) {
+                // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
+                // the order in which a thread adds its pixels' moments differs)
+                const F2 zero = f2(0.f, 0.f), one = f2(1.f, 1.f);
+                const F2 O2 = f2(bb.y, bb.y), BZ = f2(bb.z, bb.z), BW = f2(bb.w, bb.w), BL = f2(blue, blue);
+                F2 V0 = zero, V1 = zero, V2 = zero, V3 = zero, V4 = zero, V5 = zero, V6 = zero, V7 = zero, VB = zero;
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float G = fast_ex2(p2[p]);
-                const float raw = bb.y * G;
-                const float alpha = fminf(kAlphaMax, raw);
-                const bool ok = ok0[p] && alpha >= kAlphaMin;
-                contrib = contrib || ok;
-                const float r = fast_rcp(1.0f - alpha);
-                const float Ti = T[p] * r;
-                const float w = ok ? Ti * alpha : 0.0f;
-                const float4 dd = d[p];
-                vv[6] = fmaf(w, dd.x, vv[6]);
-                vv[7] = fmaf(w, dd.y, vv[7]);
-                vb = fmaf(w, dd.z, vb);
-                const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
-                const float dalpha = Ti * dc - DS[p] * r;
-                DS[p] = fmaf(w, dc, DS[p]);
-                T[p] = ok ? Ti : T[p];
-                // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
-                // selected rather than multiplied so that an infinite G never reaches the sums)
-                const bool live = ok && raw < kAlphaMax;
-                const float dP = live ? dalpha * raw : 0.0f;
-                vv[5] += live ? dalpha * G : 0.0f;
-                const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
-                const float px_ = dP * dxp, py_ = dP * dyp;
-                vv[0] += px_;
-                vv[1] += py_;
-                vv[2] = fmaf(px_, dxp, vv[2]);
-                vv[3] = fmaf(px_, dyp, vv[3]);
-                vv[4] = fmaf(py_, dyp, vv[4]);
+                for (int h = 0; h < P / 2; ++h) {
+                    const int pa = 2 * h, pb = 2 * h + 1;
+                    const F2 G = f2(fast_ex2(p2[pa]), fast_ex2(p2[pb]));
+                    const F2 RAW = mul2(O2, G);
+                    float raw_a, raw_b;
+                    split(RAW, raw_a, raw_b);
+                    const float al_a = fminf(kAlphaMax, raw_a), al_b = fminf(kAlphaMax, raw_b);
+                    const bool ok_a = ok0[pa] && al_a >= kAlphaMin, ok_b = ok0[pb] && al_b >= kAlphaMin;
+                    contrib = contrib || ok_a || ok_b;
+                    const F2 A = f2(al_a, al_b);
+                    float om_a, om_b;
+                    split(sub2(one, A), om_a, om_b);
+                    const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
+                    const F2 TI = mul2(T2[h], R);
+                    float wt_a, wt_b;
+                    split(mul2(TI, A), wt_a, wt_b);
+                    const F2 W = f2(ok_a ? wt_a : 0.0f, ok_b ? wt_b : 0.0f);
+                    V6 = fma2(W, DX2[h], V6);
+                    V7 = fma2(W, DY2[h], V7);
+                    VB = fma2(W, DZ2[h], VB);
+                    const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
+                    const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
+                    DS2[h] = fma2(W, DC, DS2[h]);
+                    {
+                        float ti_a, ti_b, t_a, t_b;
+                        split(TI, ti_a, ti_b);
+                        split(T2[h], t_a, t_b);
+                        T2[h] = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
+                    }
+                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
+                    // (selected after the product, so that an infinite G never reaches the sums)
+                    const bool live_a = ok_a && raw_a < kAlphaMax, live_b = ok_b && raw_b < kAlphaMax;
+                    float dp_a, dp_b, dg_a, dg_b;
+                    split(mul2(DA, RAW), dp_a, dp_b);
+                    split(mul2(DA, G), dg_a, dg_b);
+                    const F2 DP = f2(live_a ? dp_a : 0.0f, live_b ? dp_b : 0.0f);
+                    V5 = add2(V5, f2(live_a ? dg_a : 0.0f, live_b ? dg_b : 0.0f));
+                    const RowGroup& ga = rgp[(q0 + pa) >> 2];
+                    const RowGroup& gb = rgp[(q0 + pb) >> 2];
+                    const F2 DXP = f2(ga.dx, gb.dx);
+                    const F2 DYP = f2(ga.dy0 - (float)((q0 + pa) & 3), gb.dy0 - (float)((q0 + pb) & 3));
+                    const F2 PX = mul2(DP, DXP), PY = mul2(DP, DYP);
+                    V0 = add2(V0, PX);
+                    V1 = add2(V1, PY);
+                    V2 = fma2(PX, DXP, V2);
+                    V3 = fma2(PX, DYP, V3);
+                    V4 = fma2(PY, DYP, V4);
+                }
+                const F2 Vs[8] = {V0, V1, V2, V3, V4, V5, V6, V7};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    float lo, hi;
+                    split(Vs[k], lo, hi);
+                    vv[k] = lo + hi;
+                }
+                float lo, hi;
+                split(VB, lo, hi);
+                vb = lo + hi;
+            } else {
+                // the P pixels update independently (predicated, no branches) so they interleave
+    #pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float G = fast_ex2(p2[p]);
+                    const float raw = bb.y * G;
+                    const float alpha = fminf(kAlphaMax, raw);
+                    const bool ok = ok0[p] && alpha >= kAlphaMin;
+                    contrib = contrib || ok;
+                    const float r = fast_rcp(1.0f - alpha);
+                    const float Ti = T[p] * r;
+                    const float w = ok ? Ti * alpha : 0.0f;
+                    const float4 dd = d[p];
+                    vv[6] = fmaf(w, dd.x, vv[6]);
+                    vv[7] = fmaf(w, dd.y, vv[7]);
+                    vb = fmaf(w, dd.z, vb);
+                    const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
+                    const float dalpha = Ti * dc - DS[p] * r;
+                    DS[p] = fmaf(w, dc, DS[p]);
+                    T[p] = ok ? Ti : T[p];
+                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
+                    // selected rather than multiplied so that an infinite G never reaches the sums)
+                    const bool live = ok && raw < kAlphaMax;
+                    const float dP = live ? dalpha * raw : 0.0f;
+                    vv[5] += live ? dalpha * G : 0.0f;
+                    const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
+                    const float px_ = dP * dxp, py_ = dP * dyp;
+                    vv[0] += px_;
+                    vv[1] += py_;
+                    vv[2] = fmaf(px_, dxp, vv[2]);
+                    vv[3] = fmaf(px_, dyp, vv[3]);
+                    vv[4] = fmaf(py_, dyp, vv[4]);
+                }
             }
             const unsigned m = __ballot_sync(0xffffffffu, contrib);
             if (m == 0u) continue;
