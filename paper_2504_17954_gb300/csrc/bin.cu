@@ -51,17 +51,6 @@ __device__ __forceinline__ int view_of_record(long long i, long long n, long lon
     return total <= 0xffffffffll ? (int)((unsigned)i / (unsigned)n) : (int)(i / n);
 }
 
-// rectangle of record i; false if the record covers no tile
-__device__ __forceinline__ bool record_rect(const float2* __restrict__ xy, const int* __restrict__ radius, long long i,
-                                            const CamDev& c, float2& p, int& x0, int& x1, int& y0, int& y1) {
-    const int r = radius[i];
-    x0 = x1 = y0 = y1 = 0;
-    if (r <= 0) return false;
-    p = xy[i];
-    tile_rect(p.x, p.y, r, c.gx, c.gy, x0, x1, y0, y1);
-    return x1 > x0 && y1 > y0;
-}
-
 // tile rows [ya, yb) of the rectangle whose band of pixel-centre rows [16 ty + 0.5, 16 ty + 15.5]
 // meets the ellipse's height [v - Y, v + Y] (the rows in it are still tested one by one)
 __device__ __forceinline__ void cull_rows(const CullEll& e, int y0, int y1, int& ya, int& yb) {
@@ -80,14 +69,13 @@ __device__ __forceinline__ void cull_rows(const CullEll& e, int y0, int y1, int&
 }
 
 // number of pairs of record i: every tile of its rectangle, or with culling the kept tiles
-__device__ __forceinline__ unsigned record_pairs(const float2* __restrict__ xy, const float4* __restrict__ conic_o,
-                                                 const int* __restrict__ radius, long long i, const CamDev& c,
-                                                 int cull) {
-    float2 p;
+__device__ __forceinline__ unsigned record_pairs(float2 p, float4 co, int r, const CamDev& c, int cull) {
+    if (r <= 0) return 0u;
     int x0, x1, y0, y1;
-    if (!record_rect(xy, radius, i, c, p, x0, x1, y0, y1)) return 0u;
+    tile_rect(p.x, p.y, r, c.gx, c.gy, x0, x1, y0, y1);
+    if (!(x1 > x0 && y1 > y0)) return 0u;
     if (!cull) return (unsigned)((x1 - x0) * (y1 - y0));
-    const CullEll e = cull_setup(p, conic_o[i], 1);
+    const CullEll e = cull_setup(p, co, 1);
     int ya, yb;
     cull_rows(e, y0, y1, ya, yb);
     unsigned tot = 0;
@@ -157,11 +145,29 @@ __global__ void __launch_bounds__(kScanThreads) k_count(const float2* __restrict
     const long long total = n * cb.n;
     const long long base = (long long)blockIdx.x * kScanBlock;
     unsigned vis = 0, pairs = 0;
+    // the next record's loads are issued before this record's arithmetic (latency overlap)
+    struct Rec {
+        float2 p;
+        float4 co;
+        int r;
+    };
+    auto load = [&](long long i) {
+        Rec q{};
+        if (i < total) {
+            q.r = radius[i];
+            q.p = xy[i];
+            q.co = conic_o[i];
+        }
+        return q;
+    };
+    Rec nxt = load(base + threadIdx.x);
 #pragma unroll 1
     for (int j = 0; j < kScanItems; ++j) {
         const long long i = base + (long long)j * kScanThreads + threadIdx.x;
+        const Rec q = nxt;
+        if (j + 1 < kScanItems) nxt = load(i + kScanThreads);
         if (i < total) {
-            const unsigned c = record_pairs(xy, conic_o, radius, i, cb.c[view_of_record(i, n, total)], cull);
+            const unsigned c = record_pairs(q.p, q.co, q.r, cb.c[view_of_record(i, n, total)], cull);
             cnt[i] = c;
             vis += c ? 1u : 0u;
             pairs += c;
