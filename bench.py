@@ -126,22 +126,23 @@ OPS_BWD = 40.0  # backward blend: recompute alpha + transmittance recovery + nin
 
 
 def kernel_work(name, w, stats):
-    """Algorithmic work of one launch of `name`: (bound, amount, unit, per-unit note)."""
+    """Algorithmic work of one launch of `name`: (bound, amount, unit). Bytes count each array
+    once (what the kernel must read and write), operations the FP32 lane ops per evaluated entry."""
     n, V, pairs, evals = stats["n"], stats["V"], stats["pairs"], stats["evals"]
     if name == "k_render":
         return "alu", OPS_FWD * evals, "op"
     if name == "k_render_bwd":
         return "alu", OPS_BWD * evals, "op"
-    if name == "k_onesweep":
-        return "hbm", 24.0 * pairs, "B"
-    if name == "k_project":
-        return "hbm", 88.0 * n + 44.0 * n * V, "B"
-    if name == "k_project_bwd":
-        return "hbm", 88.0 * n + 36.0 * n * V + 88.0 * n, "B"
-    if name == "k_emit":
-        return "hbm", 16.0 * n * V + 12.0 * pairs, "B"
-    if name == "k_count":
-        return "hbm", 12.0 * n * V, "B"
+    if name == "k_onesweep":  # one tile-id pass: u32 key + u32 value, read and written
+        return "hbm", 16.0 * pairs, "B"
+    if name == "k_project":  # 86 B of attributes per Gaussian in, a 44 B record per (view, Gaussian) out
+        return "hbm", 86.0 * n + 44.0 * n * V, "B"
+    if name == "k_project_bwd":  # attributes in, 36 B of record gradients per (view, Gaussian) in, 84 B out
+        return "hbm", 86.0 * n + 36.0 * n * V + 84.0 * n, "B"
+    if name == "k_emit":  # 8 B per pair written (the depth-ordered record reads are counted per pair: 0)
+        return "hbm", 8.0 * pairs, "B"
+    if name == "k_count":  # position, conic + opacity and radius in, the pair count out, per record
+        return "hbm", 32.0 * n * V, "B"
     return None
 
 
@@ -393,6 +394,20 @@ def run_gpu(args, rank, world):
                 "frac": ach / peak, "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x {pk['sm_max_mhz']:.0f} MHz",
                 "traffic": traffic}
     roof["work_per_launch"] = wk[1] if wk else None
+    # every kernel with an algorithmic work figure, against the same peaks
+    stages = {}
+    for name, (c_, t_) in kernels.items():
+        kw = kernel_work(name, w, stats)
+        if kw is None:
+            continue
+        sec = t_ / c_ / 1e3
+        if kw[0] == "hbm":
+            a_ = kw[1] / sec / 1e9
+            stages[name] = {"bound": "hbm", "achieved": a_, "unit": "GB/s", "frac": a_ / pk["hbm_gbs"]}
+        else:
+            pk_alu = N_SM * FP32_LANES * pk["sm_max_mhz"] * 1e6 / 1e12
+            a_ = kw[1] / sec / 1e12
+            stages[name] = {"bound": "alu", "achieved": a_, "unit": "Top/s", "frac": a_ / pk_alu}
     roof["timing"] = "per-kernel CUDA events (library, launching stream) over K eager steps"
     roof["evaluated_entries_per_launch"] = evals
 
@@ -408,7 +423,7 @@ def run_gpu(args, rank, world):
            "fwd_mpix_s": fwd_value, "fwd_ms_per_step": ms_fwd_total / K,
            "launch": "eager" if args.eager else "cuda-graph replay",
            "eager_mpix_s": h.mpix(ms_eager, K),
-           "roofline": roof, "kernels": kern_table, "clocks": clocks,
+           "roofline": roof, "stage_roofline": stages, "kernels": kern_table, "clocks": clocks,
            "batched_mixed": mixed, "batched_vq": vqd, "plain_single_view": single, "inverse_exploration": inverse,
            "source_hash": source_hash(),
            "gpu_launches": int(round(launches_per_step * K))}
