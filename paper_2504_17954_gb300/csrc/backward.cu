@@ -55,8 +55,10 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
 }
 
 // Per tile, P vertically adjacent pixels per thread; each warp covers a compact band of rows.
+// With 4 pixels per thread the register budget is set for 18 CTAs per SM (56 registers, no
+// spills), two more than the compiler's own choice.
 template <int P>
-__global__ void __launch_bounds__(kTilePix / P) k_render_bwd(
+__global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
     const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
     const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
     float3 bg, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
