@@ -13,7 +13,8 @@ from tests import _gpu
 pytestmark = pytest.mark.gpu
 
 
-def test_pipeline_matches_sequential_steps():
+@pytest.mark.parametrize("graphs", [True, False], ids=["graphs", "eager"])
+def test_pipeline_matches_sequential_steps(graphs):
     base = sg.tiny_scene(3000, 64, 48, 81, log_scale_mu=-3.3, n_models=2)
     rng = np.random.default_rng(81)
     cams = [sg.look_at(3.0 * sg.random_direction(rng), 64, 48), sg.look_at(3.0 * sg.random_direction(rng), 48, 40)]
@@ -32,8 +33,8 @@ def test_pipeline_matches_sequential_steps():
         host_in.append(blk)
     host_img = [torch.empty((rast.n_pix, 4), dtype=torch.float32).pin_memory() for _ in range(K)]
     host_grad = [torch.empty_like(b).pin_memory() for b in host_in]
-    pipe = HostPipeline(rast, comp.model_id, comp.n_models)
-    pipe.run(host_in, table, dl, host_img, host_grad)
+    pipe = HostPipeline(rast, comp.model_id, comp.n_models, table, dl, graphs=graphs)
+    pipe.run(host_in, host_img, host_grad)
     torch.cuda.synchronize()
     for k in range(K):
         views = block_views(host_in[k].cuda(), comp.n)
