@@ -349,6 +349,7 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* _
 // lanes stride over those runs' pairs, so consecutive lanes write consecutive slots.
 // The pairs a warp writes must equal the sum of its records' counts from the count pass (the
 // same rounded arithmetic decides both); a mismatch sets bit 1 of the error flag.
+template <typename KT>
 __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict__ rec,
                                                        const unsigned* __restrict__ cnts, long long n,
                                                        const __grid_constant__ CamBatch cb, int cull,
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                                                        const unsigned long long* __restrict__ d_m,
                                                        const unsigned long long* __restrict__ pair_off,
                                                        const unsigned* __restrict__ wsums,
-                                                       unsigned* __restrict__ tiles, unsigned* __restrict__ vals,
+                                                       KT* __restrict__ tiles, unsigned* __restrict__ vals,
                                                        long long cap, int n_passes, unsigned* __restrict__ hist,
                                                        unsigned* __restrict__ flag) {
     constexpr int kWarps = kScanThreads / 32;
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                     const unsigned tile = run.x + q;
                     const unsigned long long o = wbase + done + q;
                     if ((long long)o < cap) {
-                        tiles[o] = tile;
+                        tiles[o] = (KT)tile;
                         vals[o] = run.y;
                         atomicAdd(&s_hist[tile & 255u], 1u);  // low byte: consecutive slots differ
                     }
@@ -505,15 +506,17 @@ __global__ void k_hist_scan(const unsigned* __restrict__ hist, unsigned* __restr
     base[blockIdx.x * 256 + threadIdx.x] = excl;
 }
 
-// ------------------------------------------------------------------------- onesweep pass (u32 keys)
+// ------------------------------------------------------------------------- onesweep pass
 // LOOKBACK = true: onesweep (tiles taken in launch order from `counter`, offsets by decoupled
 // look-back). LOOKBACK = false: the scatter of a reduce-then-scan pass (tile = block index,
 // offsets read from `lookback`, which then holds the scanned digit table of k_upsweep and
 // k_digit_scan: entry [d][tile] = first output slot of digit d in this tile).
-template <bool LOOKBACK, bool EARLY>
-__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __restrict__ kin,
+// Keys are read as KIn and written as KOut (u32, or u16 for tile ids below 2^16 between the
+// emission and the last pass, which writes u32); values are u32.
+template <bool LOOKBACK, bool EARLY, typename KIn = unsigned, typename KOut = unsigned>
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const KIn* __restrict__ kin,
                                                            const unsigned* __restrict__ vin,
-                                                           unsigned* __restrict__ kout, unsigned* __restrict__ vout,
+                                                           KOut* __restrict__ kout, unsigned* __restrict__ vout,
                                                            const unsigned long long* __restrict__ d_n, long long cap,
                                                            int shift, const unsigned* __restrict__ base,
                                                            unsigned* __restrict__ lookback,
@@ -543,13 +546,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
     // digit (255) ranks them after every real key of the tile (they are never written out)
     const int nvalid = (int)((n - start) < kSortTile ? (n - start) : kSortTile);
     const int wofs = warp * 32 * kSortItems + lane;
-    const unsigned* kin_t = kin + start;
+    const KIn* kin_t = kin + start;
     const unsigned* vin_t = vin + start;
     // values wait in shared memory, in input order, until their destinations are known
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const int li = wofs + j * 32;
-        key[j] = li < nvalid ? kin_t[li] : 0xffffffffu;
+        key[j] = li < nvalid ? (unsigned)kin_t[li] : 0xffffffffu;
         s_vals[li] = li < nvalid ? vin_t[li] : 0u;
     }
     const unsigned dg = (unsigned)tid;
@@ -682,7 +685,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(const unsigned* __
         const unsigned k = s_keys[i];
         const unsigned dd = (k >> shift) & 255u;
         const unsigned o = s_global[dd] + ((unsigned)i - s_local[dd]);
-        kout[o] = k;
+        kout[o] = (KOut)k;
         vout[o] = s_vals[i];
         if (ranges != nullptr) {
             // last pass: the tile is fully ordered by key, so equal keys form runs, and where a run
@@ -910,36 +913,46 @@ cudaError_t launch_bin_count(const ivrgs_projected* p, const CamBatch& cb, const
     return cudaGetLastError();
 }
 
-static cudaError_t onesweep_passes(int n_passes, unsigned* k0, unsigned* v0, unsigned* k1, unsigned* v1,
+// key16: the keys between passes are u16 (the first pass reads u16, the last writes u32)
+static cudaError_t onesweep_passes(int n_passes, void* k0, unsigned* v0, void* k1, unsigned* v1,
                                    const unsigned long long* d_n, long long cap, const unsigned* base,
                                    unsigned* lookback, long long tiles, unsigned* counter, unsigned* flag,
-                                   bool early, unsigned* ranges, long long n_tiles, const char* name,
+                                   bool early, bool key16, unsigned* ranges, long long n_tiles, const char* name,
                                    cudaStream_t s) {
-    unsigned* kb[2] = {k0, k1};
+    void* kb[2] = {k0, k1};
     unsigned* vb[2] = {v0, v1};
     const bool rts = options().sort_scan != 0;
+    using u16 = unsigned short;
     for (int ps = 0; ps < n_passes && tiles > 0; ++ps) {
         const int src = ps & 1, dst = src ^ 1;
         unsigned* lb = lookback + (size_t)256 * ps * tiles;
+        unsigned* rg = ps == n_passes - 1 ? ranges : nullptr;
+        const unsigned* bs = base + 256 * ps;
+        const long long ms = g_max_spin, skip = g_skip_publish_tile;
+        const int mt = options().sort_match;
         IVRGS_PROF(name, s);
         if (rts) {
-            k_upsweep<<<(unsigned)tiles, kSortThreads, 0, s>>>(kb[src], d_n, cap, 8 * ps, lb);
-            k_digit_scan<<<256, kDigitScanThreads, 0, s>>>(lb, base + 256 * ps, tiles);
+            k_upsweep<<<(unsigned)tiles, kSortThreads, 0, s>>>(static_cast<const unsigned*>(kb[src]), d_n, cap, 8 * ps, lb);
+            k_digit_scan<<<256, kDigitScanThreads, 0, s>>>(lb, bs, tiles);
             k_onesweep<false, false><<<(unsigned)tiles, kSortThreads, 0, s>>>(
-                kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                g_max_spin, g_skip_publish_tile, options().sort_match, ps == n_passes - 1 ? ranges : nullptr,
-                n_tiles);
+                static_cast<const unsigned*>(kb[src]), vb[src], static_cast<unsigned*>(kb[dst]), vb[dst], d_n, cap,
+                8 * ps, bs, lb, counter + ps, flag, ms, skip, mt, rg, n_tiles);
+        } else if (early) {
+            k_onesweep<true, true><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+                static_cast<const unsigned*>(kb[src]), vb[src], static_cast<unsigned*>(kb[dst]), vb[dst], d_n, cap,
+                8 * ps, bs, lb, counter + ps, flag, ms, skip, mt, rg, n_tiles);
+        } else if (key16 && ps < n_passes - 1) {
+            k_onesweep<true, false, u16, u16><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+                static_cast<const u16*>(kb[src]), vb[src], static_cast<u16*>(kb[dst]), vb[dst], d_n, cap, 8 * ps, bs,
+                lb, counter + ps, flag, ms, skip, mt, rg, n_tiles);
+        } else if (key16) {
+            k_onesweep<true, false, u16, unsigned><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+                static_cast<const u16*>(kb[src]), vb[src], static_cast<unsigned*>(kb[dst]), vb[dst], d_n, cap, 8 * ps,
+                bs, lb, counter + ps, flag, ms, skip, mt, rg, n_tiles);
         } else {
-            if (early)
-                k_onesweep<true, true><<<(unsigned)tiles, kSortThreads, 0, s>>>(
-                    kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                    g_max_spin, g_skip_publish_tile, options().sort_match, ps == n_passes - 1 ? ranges : nullptr,
-                n_tiles);
-            else
-                k_onesweep<true, false><<<(unsigned)tiles, kSortThreads, 0, s>>>(
-                    kb[src], vb[src], kb[dst], vb[dst], d_n, cap, 8 * ps, base + 256 * ps, lb, counter + ps, flag,
-                    g_max_spin, g_skip_publish_tile, options().sort_match, ps == n_passes - 1 ? ranges : nullptr,
-                n_tiles);
+            k_onesweep<true, false><<<(unsigned)tiles, kSortThreads, 0, s>>>(
+                static_cast<const unsigned*>(kb[src]), vb[src], static_cast<unsigned*>(kb[dst]), vb[dst], d_n, cap,
+                8 * ps, bs, lb, counter + ps, flag, ms, skip, mt, rg, n_tiles);
         }
     }
     return cudaGetLastError();
@@ -975,7 +988,8 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         k_hist_scan<<<kRecPasses, 256, 0, s>>>(b.hist_rec, b.base_rec);
     }
     if ((e = onesweep_passes(kRecPasses, b.rkey[0], b.rval[0], b.rkey[1], b.rval[1], b.d_m, plan.n_records,
-                             b.base_rec, b.lb_rec, rec_tiles, b.counter, b.flag, true, nullptr, 0, "k_onesweep_rec", s)) != cudaSuccess)
+                             b.base_rec, b.lb_rec, rec_tiles, b.counter, b.flag, true, false, nullptr, 0, "k_onesweep_rec",
+                             s)) != cudaSuccess)
         return e;
     // pair offsets of the depth-ordered records
     unsigned long long* sums2 = b.sums + 2 * (nb > 0 ? nb : 1);
@@ -990,6 +1004,10 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
         k_scan_sums<<<1, 1024, 0, s>>>(sums2, nb, b.d_n, b.d_n);
     }
     // pairs in depth order, then stable by tile; the last pass lands in the caller's arrays
+    // tile ids below 2^16 travel as u16 between the emission and the last pass (6 bytes per pair
+    // instead of 8 through every pass but the last), in the default pass form
+    const bool key16 = plan.n_passes >= 1 && plan.key_bits <= 16 && options().sort_scan == 0 &&
+                       options().sort_early == 0;
     unsigned *t0, *v0, *t1, *v1;
     if (plan.n_passes % 2 == 0) {
         t0 = out->tiles; v0 = out->values; t1 = b.talt; v1 = b.valt;
@@ -998,16 +1016,22 @@ cudaError_t launch_bin_sort(const ivrgs_projected* p, const CamBatch& cb, const 
     }
     if (nb > 0) {
         IVRGS_PROF("k_emit", s);
-        k_emit<<<(unsigned)nb, kScanThreads, 0, s>>>(b.prec, b.cnt, p->n, cb, cull, b.rval[0], b.d_m, sums2, wsums,
-                                                     t0, v0, cap, plan.n_passes, b.hist_tile, b.flag);
+        if (key16)
+            k_emit<unsigned short><<<(unsigned)nb, kScanThreads, 0, s>>>(
+                b.prec, b.cnt, p->n, cb, cull, b.rval[0], b.d_m, sums2, wsums, reinterpret_cast<unsigned short*>(t0),
+                v0, cap, plan.n_passes, b.hist_tile, b.flag);
+        else
+            k_emit<unsigned><<<(unsigned)nb, kScanThreads, 0, s>>>(b.prec, b.cnt, p->n, cb, cull, b.rval[0], b.d_m,
+                                                                  sums2, wsums, t0, v0, cap, plan.n_passes,
+                                                                  b.hist_tile, b.flag);
     }
     if (plan.n_passes > 0) {
         IVRGS_PROF("k_hist_scan", s);
         k_hist_scan<<<plan.n_passes, 256, 0, s>>>(b.hist_tile, b.base_tile);
     }
     if ((e = onesweep_passes(plan.n_passes, t0, v0, t1, v1, b.d_n, cap, b.base_tile, b.lb_tile, pair_tiles,
-                             b.counter + kRecPasses, b.flag, options().sort_early != 0, out->ranges, out->n_tiles,
-                             "k_onesweep", s)) != cudaSuccess)
+                             b.counter + kRecPasses, b.flag, options().sort_early != 0, key16, out->ranges,
+                             out->n_tiles, "k_onesweep", s)) != cudaSuccess)
         return e;
     if (plan.n_passes > 0 && pair_tiles > 0) {  // the last pass wrote the runs
         IVRGS_PROF("k_ranges_fix", s);
