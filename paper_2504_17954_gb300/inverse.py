@@ -10,8 +10,7 @@ whole iteration can be captured into one CUDA graph. This module only marshals a
 """
 from __future__ import annotations
 
-import ctypes as C
-from typing import List, Optional
+from typing import List
 
 import torch
 

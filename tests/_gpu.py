@@ -17,7 +17,6 @@ import math
 from typing import List
 
 import numpy as np
-import torch
 
 import oracle
 import scenegen as sg

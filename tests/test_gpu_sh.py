@@ -7,7 +7,6 @@ import torch
 
 import oracle
 import scenegen as sg
-from paper_2504_17954_gb300 import Gaussians, Rasterizer, compose_edit
 from tests import _gpu
 
 pytestmark = pytest.mark.gpu

@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import scenegen as sg
-from paper_2504_17954_gb300 import Gaussians, compose_edit, pack_mixed
+from paper_2504_17954_gb300 import Gaussians, compose_edit
 from paper_2504_17954_gb300.rasterizer import Rasterizer, WaveRasterizer
 from tests import _gpu
 

@@ -19,7 +19,7 @@ from scipy.spatial.transform import Rotation
 import oracle
 import scenegen as sg
 from oracle import brute
-from tests._util import axis_camera, cat_models, logit, single_model
+from tests._util import axis_camera, cat_models, single_model
 
 
 def _proj1(model, cam, lowpass=oracle.LOWPASS, edits=None):
