@@ -11,13 +11,15 @@
 //   compact:  the covered records, in record order, as (depth bits, compacted index), with
 //             their pair counts and a packed 32-byte copy of what the emission needs;
 //   sort 1:   stable LSD radix sort of the covered records by depth bits (4 onesweep passes);
-//   count 2:  pair counts of the depth-ordered records, block sums, scan;
+//   count 2:  pair counts of the depth-ordered records (in that order), block and warp-range
+//             sums, scan;
 //   emit:     warp-cooperative emission of one (tile id, Gaussian) pair per covered tile, in
-//             depth order, with the digit histograms of the tile ids: the lanes of a warp
-//             first stride over the row runs of its 32 records (one culling evaluation per
-//             run), then over the pairs of 32 runs at a time, so stores stay coalesced;
+//             depth order, with the digit histograms of the tile ids: every warp takes its
+//             own 256 records, 32 at a time; its lanes first stride over the row runs of the
+//             32 records (one culling evaluation per run), then over the pairs of 32 runs at
+//             a time, so stores stay coalesced (tile ids as u16 when they fit);
 //   sort 2:   stable LSD radix sort of the pairs by tile id (one pass per 8 tile bits);
-//   ranges:   [start, end) of every tile's run.
+//   ranges:   [start, end) of every tile's run, written by the last pass of sort 2.
 //
 // Because sort 2 is stable and its input is in (depth, view, Gaussian) order, the output
 // is ordered by (tile, depth, Gaussian) -- the same order as one stable sort by
@@ -787,6 +789,7 @@ __global__ void __launch_bounds__(kDigitScanThreads) k_digit_scan(unsigned* __re
 }
 
 // ------------------------------------------------------------------------- ranges
+// from the sorted tile ids (the single-tile case, which has no radix pass to write them)
 __global__ void __launch_bounds__(256) k_ranges(const unsigned* __restrict__ tiles,
                                                 const unsigned long long* __restrict__ d_n, long long cap,
                                                 long long n_tiles, unsigned* __restrict__ ranges) {
