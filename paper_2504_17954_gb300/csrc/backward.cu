@@ -335,13 +335,26 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
     const bool tl_on = __ldg(table + (long long)M * IVRGS_EDIT_STRIDE + 11) != 0.0f;  // uniform
     float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float dcv[3] = {0.f, 0.f, 0.f}, dkp[4] = {0.f, 0.f, 0.f, 0.f}, dnn[3] = {0.f, 0.f, 0.f}, dop = 0.f;
+    // the next view's record gradients are loaded before this view's arithmetic (latency overlap)
+    float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nbq = na;
+    float nbl = 0.f;
+    if (G.visible && cb.n > 0) {
+        na = g0[i];
+        nbq = g1[i];
+        nbl = g2[i];
+    }
     for (int v = 0; v < cb.n; ++v) {
         const CamDev& c = cb.c[v];
         float dlv[3] = {0.f, 0.f, 0.f};
+        const float4 a = na, b = nbq;
+        const float bl = nbl;
+        if (G.visible && v + 1 < cb.n) {
+            const long long o1 = (long long)(v + 1) * n + i;
+            na = g0[o1];
+            nbq = g1[o1];
+            nbl = g2[o1];
+        }
         if (G.visible) {
-            const long long o = (long long)v * n + i;
-            const float4 a = g0[o], b = g1[o];
-            const float bl = g2[o];
             const bool any = (a.x != 0.f) | (a.y != 0.f) | (a.z != 0.f) | (a.w != 0.f) | (b.x != 0.f) |
                              (b.y != 0.f) | (b.z != 0.f) | (b.w != 0.f) | (bl != 0.f);
             ViewLocal V;
