@@ -17,8 +17,8 @@ import torch
 from . import _native as N
 
 SPACE = {
-    "render_pixels_per_thread": (1, 2, 4, 8),
-    "render_bwd_pixels_per_thread": (1, 2, 4, 8),
+    "render_pixels_per_thread": (0, 1, 2, 4, 8),
+    "render_bwd_pixels_per_thread": (0, 1, 2, 4, 8),
     "sort_match": (0, 1),
     "sort_scan": (0, 1),
     "sort_early": (0, 1),

@@ -163,7 +163,8 @@ ivrgs_status ivrgs_set_option(const char* name, int64_t value) {
     if (!name) return invalid("name is NULL");
     const std::string k(name);
     if (k == "render_pixels_per_thread" || k == "render_bwd_pixels_per_thread") {
-        if (value != 1 && value != 2 && value != 4 && value != 8) return invalid(k + " must be 1, 2, 4 or 8");
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+            return invalid(k + " must be 0 (by tile count), 1, 2, 4 or 8");
         (k == "render_pixels_per_thread" ? options().render_ppt : options().render_bwd_ppt) = (int)value;
         return IVRGS_OK;
     }

@@ -647,13 +647,14 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
         const uint2* rg = reinterpret_cast<const uint2*>(b->ranges);
         const float3 bgc = make_float3(bg[0], bg[1], bg[2]);
         const float4* dl = reinterpret_cast<const float4*>(dL);
-        if (options().render_bwd_ppt == 1)
+        const int ppt = blend_ppt(options().render_bwd_ppt, cb.n_tiles, true);
+        if (ppt == 1)
             k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, final_T,
                                                                      last, dl, g0, g1, g2);
-        else if (options().render_bwd_ppt == 8)
+        else if (ppt == 8)
             k_render_bwd<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
                                                                          final_T, last, dl, g0, g1, g2);
-        else if (options().render_bwd_ppt == 4)
+        else if (ppt == 4)
             k_render_bwd<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
                                                                          final_T, last, dl, g0, g1, g2);
         else

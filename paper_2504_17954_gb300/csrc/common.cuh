@@ -92,13 +92,24 @@ ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch*
 
 // tunable launch shapes (set through ivrgs_set_option; read by the launchers)
 struct Options {
-    int render_ppt = 4;      // pixels per thread of the forward blend (1, 2, 4 or 8)
-    int render_bwd_ppt = 4;  // pixels per thread of the backward blend (1, 2, 4 or 8)
+    int render_ppt = 0;      // pixels per thread of the forward blend (1, 2, 4 or 8; 0 = by tile count)
+    int render_bwd_ppt = 0;  // pixels per thread of the backward blend (1, 2, 4 or 8; 0 = by tile count)
     int sort_match = 0;      // radix ranking: 0 = warp ballots per digit bit, 1 = match.any
     int sort_scan = 0;       // radix offsets: 0 = decoupled look-back (onesweep), 1 = reduce-then-scan
     int sort_early = 0;      // radix tile: 1 = publish its digit counts before ranking (look-back waits less)
 };
 Options& options();
+// Pixels per thread of a blend launch over n_tiles tiles: the option, or with 0 (the default) a
+// choice by occupancy. Four pixels per thread (64-thread CTAs, 18 per SM: ~2,700 at a time on
+// 152 SMs) issue the fewest instructions per pixel and win once the tiles fill the GPU more than
+// once (measured on GB300: 4,096 and 26,000 tiles); below that each CTA's walk is latency-bound
+// and more warps per tile (fewer pixels per thread) finish sooner (64 and 2,500 tiles).
+constexpr long long kAutoPptTiles = 3072;
+inline int blend_ppt(int option, long long n_tiles, bool backward) {
+    if (option != 0) return option;
+    if (n_tiles >= kAutoPptTiles) return 4;
+    return backward ? 1 : 2;
+}
 BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity);
 
 // launchers (each returns cudaGetLastError() of its launches)

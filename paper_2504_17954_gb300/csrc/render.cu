@@ -146,13 +146,14 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
     const uint2* rg = reinterpret_cast<const uint2*>(b->ranges);
     const float3 bgc = make_float3(bg[0], bg[1], bg[2]);
     float4* out = reinterpret_cast<float4*>(rgba);
-    if (options().render_ppt == 1)
+    const int ppt = blend_ppt(options().render_ppt, cb.n_tiles, false);
+    if (ppt == 1)
         k_render<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out, final_T,
                                                              last);
-    else if (options().render_ppt == 8)
+    else if (ppt == 8)
         k_render<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
                                                                  final_T, last);
-    else if (options().render_ppt == 4)
+    else if (ppt == 4)
         k_render<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
                                                                  final_T, last);
     else

@@ -210,7 +210,7 @@ def test_render_only_matches_oracle_on_shared_records(which):
 
 
 # ------------------------------------------------------------------ end to end forward
-@pytest.fixture(params=[1, 2, 4, 8], ids=["ppt1", "ppt2", "ppt4", "ppt8"])
+@pytest.fixture(params=[0, 1, 2, 4, 8], ids=["ppt_auto", "ppt1", "ppt2", "ppt4", "ppt8"])
 def pixels_per_thread(request):
     from paper_2504_17954_gb300 import _native as N
     old = (N.ivrgs_get_option("render_pixels_per_thread"), N.ivrgs_get_option("render_bwd_pixels_per_thread"))
