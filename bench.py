@@ -133,14 +133,15 @@ def kernel_work(name, w, stats):
         return "alu", OPS_FWD * evals, "op"
     if name == "k_render_bwd":
         return "alu", OPS_BWD * evals, "op"
-    if name == "k_onesweep":  # one tile-id pass: u32 key + u32 value, read and written
-        return "hbm", 16.0 * pairs, "B"
+    if name == "k_onesweep":  # one tile-id pass: key + u32 value, read and written (u16 keys but the
+        # last pass's output below 2^16 tiles: 12 B and 14 B, averaged over the two passes)
+        return "hbm", (13.0 if stats.get("tiles", 1 << 16) < (1 << 16) else 16.0) * pairs, "B"
     if name == "k_project":  # 86 B of attributes per Gaussian in, a 44 B record per (view, Gaussian) out
         return "hbm", 86.0 * n + 44.0 * n * V, "B"
     if name == "k_project_bwd":  # attributes in, 36 B of record gradients per (view, Gaussian) in, 84 B out
         return "hbm", 86.0 * n + 36.0 * n * V + 84.0 * n, "B"
-    if name == "k_emit":  # 8 B per pair written (the depth-ordered record reads are counted per pair: 0)
-        return "hbm", 8.0 * pairs, "B"
+    if name == "k_emit":  # the pairs written: u16 or u32 tile id + u32 value (record reads not counted)
+        return "hbm", (6.0 if stats.get("tiles", 1 << 16) < (1 << 16) else 8.0) * pairs, "B"
     if name == "k_count":  # position, conic + opacity and radius in, the pair count out, per record
         return "hbm", 32.0 * n * V, "B"
     return None
@@ -371,7 +372,7 @@ def run_gpu(args, rank, world):
 
     # roofline of the dominant kernel (largest share of device time in the eager timed steps)
     pk = peaks()
-    stats = {"n": comp.n, "V": len(w.cameras), "pairs": n_pairs, "evals": evals}
+    stats = {"n": comp.n, "V": len(w.cameras), "pairs": n_pairs, "evals": evals, "tiles": rast.n_tiles}
     kern_table = {}
     for name, (cnt, tot) in kernels.items():
         kern_table[name] = {"launches": cnt, "ms_per_launch": tot / cnt, "share": tot / sum(x[1] for x in kernels.values())}
