@@ -299,15 +299,13 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
                     atomicAdd(&g2[gi], vb);
                 }
             } else {
-                float x = warp_sum8_transposed(vv, lane);  // lane holds the total of index lane >> 2
+                // every lane turns its moments into (du, dv, da, db, dc) first (linear, so the sum
+                // is the same): no lane-dependent branches after the reduction
+                const float tv[8] = {(2.0f * a.z * vv[0] + a.w * vv[1]) * il, (a.w * vv[0] + 2.0f * bb.x * vv[1]) * il,
+                                     -0.5f * vv[2], -vv[3], -0.5f * vv[4], vv[5], vv[6], vv[7]};
+                const float x = warp_sum8_transposed(tv, lane);  // lane holds the total of index lane >> 2
                 vb = warp_sum(vb);
                 const int idx = lane >> 2;
-                const float other = __shfl_xor_sync(0xffffffffu, x, 4);  // m1 <-> m2 between idx 0 and 1
-                if (idx == 0) x = (2.0f * a.z * x + a.w * other) * il;
-                else if (idx == 1) x = (a.w * other + 2.0f * bb.x * x) * il;
-                else if (idx == 2) x = -0.5f * x;
-                else if (idx == 3) x = -x;
-                else if (idx == 4) x = -0.5f * x;
                 if ((lane & 3) == 0) atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
                 if (lane == 0) atomicAdd(&g2[gi], vb);
             }
