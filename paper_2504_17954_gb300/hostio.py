@@ -38,9 +38,12 @@ def block_views(block: torch.Tensor, n: int) -> List[torch.Tensor]:
 
 
 def pack_host(g: Gaussians) -> torch.Tensor:
-    """A pinned host block holding the float32 attributes of g (the input of one step)."""
+    """A pinned host block holding the float32 attributes of g (the input of one step). The
+    pipeline carries the Blinn-Phong attribute set; SH colour is not part of the block."""
     if g.precision != N.IVRGS_FP32:
         raise ValueError("the host pipeline carries float32 attributes")
+    if g.sh is not None:
+        raise ValueError("the host pipeline carries the Blinn-Phong attributes, not SH colour")
     n = g.n
     blk = torch.empty(FLOATS_PER_GAUSSIAN * n, dtype=torch.float32).pin_memory()
     for t, k in zip(block_views(blk, n), ATTRS):
