@@ -93,9 +93,29 @@ def workload_from(inp: dict) -> sg.Workload:
     return sg.Workload("golden", models, cams, ed, bg=f32(inp["bg"]))
 
 
+# a float32 evaluation may decide differently from the FP64 oracle only near a tie: a radius
+# 3 sqrt(lambda_max) within 1e-5 (relative) of an integer, a rectangle edge within 1e-3 px of a
+# tile boundary (the record refuses such scenes), or a pixel whose alpha cut-off, termination
+# or P > 0 decision is within 1e-3 (relative) of its threshold (flagged per sampled pixel)
+RADIUS_TIE, EDGE_TIE_PX, PIXEL_TIE = 1e-5, 1e-3, 1e-3
+
+
+def check_no_record_ties(p) -> None:
+    live = p.radius > 0
+    r = p.radius.astype(np.float64)
+    near = live & (p.radius_margin < RADIUS_TIE)
+    for e in (p.uv[:, 0] - r, p.uv[:, 0] + r, p.uv[:, 1] - r, p.uv[:, 1] + r):
+        q = e / 16.0
+        near |= live & (np.abs(q - np.round(q)) * 16.0 < EDGE_TIE_PX)
+    if near.any():
+        raise ValueError(f"records {np.flatnonzero(near).tolist()} sit at a float32 decision tie")
+
+
 def outputs(w: sg.Workload) -> dict:
     """What the oracle computes for the scene: the fixture's expected values."""
     ref = oracle.render(w.models, w.edits, w.cameras, bg=w.bg)
+    for p in ref.projs:
+        check_no_record_ties(p)
     dls = [dl_drgba(c.W, c.H, v) for v, c in enumerate(w.cameras)]
     g = oracle.render_backward(ref, w.cameras, dls, bg=w.bg)
     views = []
@@ -109,6 +129,7 @@ def outputs(w: sg.Workload) -> dict:
             "pixels": _plain(pix),
             "rgba": _plain(img.reshape(-1, 4)[pix]),
             "last": _plain(ref.last[v].reshape(-1)[pix]),
+            "near_tie": _plain((ref.margins[v].reshape(-1, oracle.N_MARGINS)[pix, :3] < PIXEL_TIE).any(1)),
             "rgba_sum": _plain(img.reshape(-1, 4).sum(0)),
         })
     return {

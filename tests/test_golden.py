@@ -98,7 +98,7 @@ def test_oracle_reproduces_the_record(rec):
     for k in ("tile_offset", "ranges", "values"):
         assert got[k] == want[k], k
     for v, (gv, wv) in enumerate(zip(got["views"], want["views"])):
-        for k in ("radius", "pixels", "last"):
+        for k in ("radius", "pixels", "last", "near_tie"):
             assert gv[k] == wv[k], (v, k)
         assert gv["depth32"] == wv["depth32"] and gv["uv32"] == wv["uv32"], v
         _close(gv["rgba"], wv["rgba"], f"view {v} rgba")
