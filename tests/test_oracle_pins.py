@@ -439,3 +439,38 @@ def test_aux_maps_reduce_to_alpha_and_colour():
     live = p.radius > 0
     assert np.all(maps[..., 0] <= p.depth[live].max() * maps[..., 11] + 1e-12)
     assert np.all(maps[..., 0] >= p.depth[live].min() * maps[..., 11] - 1e-12)
+
+
+def test_aux_maps_of_constant_attributes():
+    """With every Gaussian sharing one offset colour dc, one k = (k_a, k_d, k_s, beta) and one
+    camera depth z0 (all means on the plane z_c = z0), the maps are those constants times the
+    coverage 1 - T: dc (1 - T), (lambda k + b)(1 - T) with the light-magnitude edit of Sec. 4.6
+    applied componentwise, and z0 (1 - T). A dropped or misplaced edit term, a wrong channel
+    order or a depth other than the camera z fails one of them."""
+    w = sg.tiny_scene(400, 40, 32, 72, log_scale_mu=-3.0, n_models=2)
+    cam = w.cameras[0]
+    R = np.asarray(cam.R, np.float64).reshape(3, 3)
+    t = np.asarray(cam.t, np.float64)
+    z0 = 3.0
+    rng = np.random.default_rng(5)
+    dc = np.array([0.12, -0.07, 0.2], np.float32)
+    k = np.array([0.3, 0.6, 0.25, 12.0], np.float32)
+    for m in w.models:
+        xy = rng.uniform(-0.45, 0.45, (m.n, 2)) * z0 / 3.0
+        xc = np.c_[xy, np.full(m.n, z0)]          # camera coordinates on the plane z_c = z0
+        m.mean[:] = ((xc - t) @ R).astype(np.float32)  # world = R^T (x_c - t)
+        m.dcolor[:] = dc
+        m.kads[:] = k
+    ed = w.edits
+    ed.lam = np.array([1.3, 0.7, 1.1, 0.9], np.float32)
+    ed.bias = np.array([0.05, -0.02, 0.1, 2.0], np.float32)
+    r = oracle.render(w.models, ed, w.cameras)
+    maps = oracle.render_aux(r, w.cameras)[0]
+    cov = maps[..., 11]
+    assert cov.max() > 0.3
+    np.testing.assert_allclose(cov, r.images[0][..., 3], rtol=0, atol=1e-15)
+    kp = ed.lam.astype(np.float64) * k.astype(np.float64) + ed.bias.astype(np.float64)
+    np.testing.assert_allclose(maps[..., 4:7], cov[..., None] * dc.astype(np.float64), rtol=0, atol=1e-13)
+    np.testing.assert_allclose(maps[..., 7:11], cov[..., None] * kp, rtol=0, atol=1e-12)
+    # float32 storage of the means moves each camera depth by a few ulps of z0
+    np.testing.assert_allclose(maps[..., 0], z0 * cov, rtol=0, atol=1e-5 * z0)
