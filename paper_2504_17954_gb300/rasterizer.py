@@ -411,6 +411,25 @@ class Rasterizer:
 
 
 # ----------------------------------------------------------------------------------------
+def plan_waves(cams, n_gaussians: int, max_views: int = 32, pixel_budget: int = 24 << 20) -> List[List[int]]:
+    """Consecutive groups of view indices, in view order, each rendered by one set of calls:
+    at most ``max_views`` views, and fewer than the library's 2^30 records (n_gaussians * views)
+    per binning call; a wave closes before a view that would take its pixels over
+    ``pixel_budget`` (a single view larger than the budget forms a wave of its own)."""
+    max_views = max(1, min(max_views, (N.IVRGS_MAX_PAIRS - 1) // max(n_gaussians, 1)))
+    waves: List[List[int]] = []
+    cur, pix = [], 0
+    for v, c in enumerate(cams):
+        if cur and (len(cur) >= max_views or pix + c.W * c.H > pixel_budget):
+            waves.append(cur)
+            cur, pix = [], 0
+        cur.append(v)
+        pix += c.W * c.H
+    if cur:
+        waves.append(cur)
+    return waves
+
+
 class WaveRasterizer:
     """Many views rendered in waves of at most ``max_views`` views and ``pixel_budget`` pixels
     (so that no binning call exceeds the library's per-call pair limit); the backward sums the
@@ -419,18 +438,7 @@ class WaveRasterizer:
     def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", lowpass: float = 0.3,
                  bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20, cull: bool = True):
         self.cams = list(cams)
-        self.waves: List[List[int]] = []
-        # records (n * views) of one binning call stay below the library's 2^30 limit
-        max_views = max(1, min(max_views, (N.IVRGS_MAX_PAIRS - 1) // max(n_gaussians, 1)))
-        cur, pix = [], 0
-        for v, c in enumerate(self.cams):
-            if cur and (len(cur) >= max_views or pix + c.W * c.H > pixel_budget):
-                self.waves.append(cur)
-                cur, pix = [], 0
-            cur.append(v)
-            pix += c.W * c.H
-        if cur:
-            self.waves.append(cur)
+        self.waves: List[List[int]] = plan_waves(self.cams, n_gaussians, max_views, pixel_budget)
         self.rasts = [Rasterizer([self.cams[v] for v in wv], n_gaussians, n_models, device=device, lowpass=lowpass,
                                  bg=bg, cull=cull) for wv in self.waves]
         self.n_models = n_models
