@@ -70,3 +70,25 @@ def test_header_constants_match_binding():
             assert getattr(N, name) == int(val), name
             checked += 1
     assert checked >= 8 and N.IVRGS_BIN_CULL == 2
+
+
+def test_option_table_matches_the_autotuner_space(lib):
+    """Every launch-shape option the autotuner searches is accepted by the library with every
+    value in its range (set, read back, restored); out-of-range values and unknown names are
+    refused with IVRGS_ERR_INVALID_ARG and leave the option unchanged. Host state only."""
+    from paper_2504_17954_gb300.autotune import SPACE
+    for name, values in SPACE.items():
+        old = N.ivrgs_get_option(name)
+        try:
+            for v in values:
+                N.ivrgs_set_option(name, v)
+                assert N.ivrgs_get_option(name) == v, (name, v)
+            for bad in (-1, max(values) + 1, 3 if 3 not in values else 16):
+                st = lib.ivrgs_set_option(name.encode(), C.c_int64(bad))
+                assert st == N.IVRGS_ERR_INVALID_ARG, (name, bad)
+                assert N.ivrgs_get_option(name) == values[-1], (name, bad)
+        finally:
+            N.ivrgs_set_option(name, old)
+    assert lib.ivrgs_set_option(b"no_such_option", C.c_int64(1)) == N.IVRGS_ERR_INVALID_ARG
+    v = C.c_int64(0)
+    assert lib.ivrgs_get_option(b"no_such_option", C.byref(v)) == N.IVRGS_ERR_INVALID_ARG
