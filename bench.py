@@ -264,7 +264,7 @@ def source_hash():
 
 
 def recorded_traffic(kernel, workload):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if it matches this build."""
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it matches these CUDA sources."""
     path = os.path.join(ROOT, "profiles", f"traffic_{workload}.md")
     if not os.path.exists(path):
         return None

@@ -51,7 +51,7 @@ enum {
     IVRGS_ERR_CAPACITY = 2,    /* output/workspace too small; the required size is reported */
     IVRGS_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
     IVRGS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (see ivrgs_bin) */
-    IVRGS_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+    IVRGS_ERR_UNSUPPORTED = 5  /* valid request this library version does not implement */
 };
 
 #define IVRGS_MAX_VIEWS 128    /* views per call (cameras travel as kernel parameters) */
@@ -166,7 +166,7 @@ typedef struct {
    of each tile's run ((0, 0) for an empty tile). d_n_pairs: device uint64 scalar receiving the
    number of pairs (in CAPACITY mode a value > capacity means the outputs are incomplete). */
 typedef struct {
-    int32_t tile_w, tile_h; /* 16 x 16 in this build */
+    int32_t tile_w, tile_h; /* 16 x 16 in this library version */
     int64_t n_tiles;
     int64_t capacity;
     uint32_t* tiles;
