@@ -573,7 +573,9 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "gaussians": comp.n, "sample": sample},
+            "config": {"workload": w.name, "gaussians": comp.n, "models": len(w.models), "views": len(w.cameras),
+                       "pixels_per_replica": sum(q.W * q.H for q in w.cameras), "sample": sample,
+                       "parallelism": "rank 0 only, host cores"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
