@@ -56,6 +56,9 @@ def workload(name):
 
 
 # ------------------------------------------------------------------------------------ clocks
+CLOCK_LOAD_S = 0.8
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -80,6 +83,16 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout: float = 3.0):
+        """Wait (bounded) until the sampler has printed its first line."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self):
+        """Samples before this point (an idle GPU) are left out of the report."""
+        self.first = len(self.lines)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -91,7 +104,8 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[getattr(self, "first", 0):] or self.lines
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -318,12 +332,23 @@ def run_gpu(args, rank, world):
     for _ in range(2):
         h.run_step(True)
     K = args.steps
+    # nvidia-smi samples every 200 ms, longer than the timed steps take: the sampler starts
+    # before CLOCK_LOAD_S of the same step replayed back to back (untimed), and runs on through
+    # the timed regions, so its samples see the clocks of this load
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
+    sampler.wait_first()
+    sampler.mark()
+    n_load, t_load = 0, time.perf_counter()
+    while time.perf_counter() - t_load < CLOCK_LOAD_S:
+        h.run_step(True)
+        torch.cuda.synchronize()
+        n_load += 1
     ms_total, _ = h.timed(K, True)
     ms_fwd_total, _ = h.timed(K, False)
     ms_eager, kernels = h.timed(K, True, prof=True)
     clocks = sampler.stop()
+    clocks["window"] = f"{n_load} untimed steps ({CLOCK_LOAD_S} s) back to back, then the timed steps"
     value, fwd_value = h.mpix(ms_total, K), h.mpix(ms_fwd_total, K)
 
     # the batched form with 16-bit attribute storage, same workload
