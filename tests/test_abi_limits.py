@@ -38,3 +38,18 @@ def test_view_limit():
     assert st == N.IVRGS_ERR_INVALID_ARG and "n_views" in msg
     st, _, _ = _ws(10, [sg.look_at([3, 0, 0], 16, 16)] * N.IVRGS_MAX_VIEWS, 64)
     assert st == N.IVRGS_OK
+
+
+def test_empty_and_negative_sizes():
+    """Zero Gaussians and zero pair capacity are valid (an empty scene sizes a small
+    workspace); negative sizes are refused before any device work."""
+    cams = [sg.look_at([3, 0, 0], 64, 64)]
+    st, nbytes, _ = _ws(0, cams, 0)
+    assert st == N.IVRGS_OK and nbytes > 0
+    st, _, msg = _ws(-1, cams, 0)
+    assert st == N.IVRGS_ERR_INVALID_ARG and "bad n" in msg
+    st, _, msg = _ws(10, cams, -5)
+    assert st == N.IVRGS_ERR_INVALID_ARG and "capacity" in msg
+    b = C.c_size_t(0)
+    assert N.lib().ivrgs_render_backward_workspace(C.c_int64(0), C.c_int32(1), C.byref(b)) == N.IVRGS_OK
+    assert N.lib().ivrgs_render_backward_workspace(C.c_int64(-1), C.c_int32(1), C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
