@@ -310,6 +310,48 @@ def test_sampled_pixels_backward_matches_full_backward():
     assert np.abs(g_full.light[1]).max() > 0
 
 
+@pytest.mark.parametrize("headlight", [True, False])
+def test_rigid_motion_of_scene_and_camera_leaves_the_image_unchanged(headlight):
+    """Moving the whole scene and the camera by one rigid motion x -> Q x + d (means, normals
+    and an orbital light direction rotated, each quaternion composed as r q with r the
+    rotation's quaternion, camera R' = R Q^T, t' = t - R Q^T d) leaves the image unchanged up to
+    the float32 rounding of the moved inputs. Sec. 3's projection and shading depend only on
+    relative geometry; a transposed rotation from a quaternion, a wrong composition order or a
+    world-space quantity used where a camera-space one is meant breaks this."""
+    import copy
+
+    from scipy.spatial.transform import Rotation
+    w = sg.tiny_scene(400, 48, 40, 21, log_scale_mu=-2.8, headlight=headlight, n_models=2)
+    rot = Rotation.from_rotvec([0.3, -0.7, 0.4])
+    Q = rot.as_matrix()
+    x, y, z, qw = rot.as_quat()  # scalar last
+    d = np.array([0.21, -0.13, 0.08])
+
+    def compose_r(q):  # Hamilton product r q, quaternions (w, x, y, z)
+        w2, x2, y2, z2 = q.T
+        return np.stack([qw * w2 - x * x2 - y * y2 - z * z2, qw * x2 + x * w2 + y * z2 - z * y2,
+                         qw * y2 - x * z2 + y * w2 + z * x2, qw * z2 + x * y2 - y * x2 + z * w2], 1)
+
+    moved = []
+    for m in w.models:
+        c = m.copy()
+        c.mean = (m.mean.astype(np.float64) @ Q.T + d).astype(np.float32)
+        c.quat = compose_r(m.quat.astype(np.float64)).astype(np.float32)
+        c.normal = (m.normal.astype(np.float64) @ Q.T).astype(np.float32)
+        moved.append(c)
+    cam = w.cameras[0]
+    cam2 = copy.deepcopy(cam)
+    R2 = cam.R.reshape(3, 3).astype(np.float64) @ Q.T
+    cam2.R = R2.astype(np.float32).reshape(9)
+    cam2.t = (cam.t.astype(np.float64) - R2 @ d).astype(np.float32)
+    cam2.campos = (Q @ cam.campos.astype(np.float64) + d).astype(np.float32)
+    cam2.light_dir = (Q @ cam.light_dir.astype(np.float64)).astype(np.float32)
+    a = oracle.render(w.models, w.edits, [cam]).images[0]
+    b = oracle.render(moved, w.edits, [cam2]).images[0]
+    assert a[..., 3].max() > 0.5
+    assert np.abs(a - b).max() < 1e-5
+
+
 # ------------------------------------------------------------------ invariants (Sec. 4.5)
 def test_spatially_disjoint_models_compose_to_union():
     a = sg.tiny_scene(30, 64, 32, 7, log_scale_mu=-3.2).models[0]
