@@ -352,6 +352,30 @@ def test_rigid_motion_of_scene_and_camera_leaves_the_image_unchanged(headlight):
     assert np.abs(a - b).max() < 1e-5
 
 
+@pytest.mark.parametrize("headlight", [True, False])
+def test_uniform_scaling_of_scene_and_camera_leaves_the_image_unchanged(headlight):
+    """Scaling positions by 2 and the Gaussians' sizes by 2 (log-scale + ln 2), with the camera
+    at twice its distance (t' = 2 t), leaves every pixel unchanged: the pinhole Jacobian J
+    scales as 1/z and Sigma as s^2, so J W Sigma W^T J^T, the dilation, the radii, the depth
+    order and the shading are unchanged. A Jacobian with a wrong power of z breaks this."""
+    import copy
+    w = sg.tiny_scene(400, 48, 40, 23, log_scale_mu=-2.8, headlight=headlight, n_models=2)
+    scaled = []
+    for m in w.models:
+        c = m.copy()
+        c.mean = (2.0 * m.mean).astype(np.float32)  # exact
+        c.log_scale = (m.log_scale.astype(np.float64) + np.log(2.0)).astype(np.float32)
+        scaled.append(c)
+    cam = w.cameras[0]
+    cam2 = copy.deepcopy(cam)
+    cam2.t = (2.0 * cam.t).astype(np.float32)
+    cam2.campos = (2.0 * cam.campos).astype(np.float32)
+    a = oracle.render(w.models, w.edits, [cam]).images[0]
+    b = oracle.render(scaled, w.edits, [cam2]).images[0]
+    assert a[..., 3].max() > 0.5
+    assert np.abs(a - b).max() < 1e-5
+
+
 # ------------------------------------------------------------------ invariants (Sec. 4.5)
 def test_spatially_disjoint_models_compose_to_union():
     a = sg.tiny_scene(30, 64, 32, 7, log_scale_mu=-3.2).models[0]
