@@ -145,18 +145,21 @@ class Projected:
     depth: np.ndarray    # [N]
     radius: np.ndarray   # [N] int32, 0 = culled
     radius_margin: np.ndarray
+    # distance of the float64 depth to the nearest float32 rounding midpoint, relative to
+    # |t_z| + sum_k |R_zk mu_k| (how far the float32 sort key is from a rounding tie)
+    depth_margin: Optional[np.ndarray] = None
 
 
 def project(comp: Composed, table: np.ndarray, cam, lowpass: float = LOWPASS, guard: float = GUARD) -> Projected:
     n = comp.n
     out = Projected(uv=np.zeros((n, 2)), cov=np.zeros((n, 3)), conic=np.zeros((n, 3)), opacity=np.zeros(n),
                     rgb=np.zeros((n, 3)), depth=np.zeros(n), radius=np.zeros(n, np.int32),
-                    radius_margin=np.zeros(n))
+                    radius_margin=np.zeros(n), depth_margin=np.zeros(n))
     oc = camera(cam)
     lib().orc_project(C.c_int64(n), *[_p(a) for a in comp.arrays()], _p(comp.model_id, C.c_int32),
                       *_sh_args(comp), _p(table), C.c_int32(comp.n_models), C.byref(oc), C.c_double(lowpass), C.c_double(guard),
                       _p(out.uv), _p(out.cov), _p(out.conic), _p(out.opacity), _p(out.rgb), _p(out.depth),
-                      _p(out.radius, C.c_int32), _p(out.radius_margin))
+                      _p(out.radius, C.c_int32), _p(out.radius_margin), _p(out.depth_margin))
     return out
 
 

@@ -25,11 +25,9 @@
  *
  * Integer decisions that the GPU takes in float32 (tile rectangle, sort key) are taken here
  * in float32 too, from the float64 values rounded once: the rectangle from (u, v) rounded
- * to float and the integer radius; the key from the float depth's bit pattern.  The depth
- * that keys the sort and decides the near plane is the camera z as the float32 chain
- * fma(R22, mz, fma(R21, my, fma(R20, mx, t2))) of the float32 inputs, every step one
- * correctly rounded fused multiply-add (C fmaf), which the GPU evaluates identically; the
- * rest of the projection uses the float64 camera-space position.
+ * to float and the integer radius; the key from the bit pattern of the float64 camera depth
+ * z = (R mu + t)_z rounded once to float32.  The near-plane decision compares the float64 z
+ * with z_near.
  *
  * Gradients (reverse mode of all of the above) are taken w.r.t. the stored parameters:
  * mean, log-scale, unnormalised quaternion and normal, opacity logit, colour offset,
@@ -169,6 +167,7 @@ typedef struct {
     double radius_margin;
     double uv[2];
     double depth;
+    double depth_margin;  /* distance of z to the nearest float32 rounding midpoint / (|t2| + sum |R2k mk|) */
     /* shading */
     double sig_o, opacity;
     double cv[3], kp[4];
@@ -199,10 +198,16 @@ static void project_one(const orc_gaussians* G, int64_t g, const double* edit, i
     /* viewing transform W: mu_c = R mu + t */
     for (int i = 0; i < 3; ++i) f->mc[i] = R[3 * i] * mu[0] + R[3 * i + 1] * mu[1] + R[3 * i + 2] * mu[2] + cam->t[i];
     double x = f->mc[0], y = f->mc[1], z = f->mc[2];
-    /* the float32 depth of the sort key (see the header); it also takes the near-plane decision */
-    const float z32 = fmaf((float)R[8], (float)mu[2],
-                           fmaf((float)R[7], (float)mu[1], fmaf((float)R[6], (float)mu[0], (float)cam->t[2])));
-    if (!(z32 > (float)cam->znear)) return;
+    f->depth = z;
+    {   /* how close z lies to a point where its rounding to float32 changes (for certification) */
+        double mag = fabs(cam->t[2]) + fabs(R[6] * mu[0]) + fabs(R[7] * mu[1]) + fabs(R[8] * mu[2]);
+        float z32 = (float)z;
+        double lo = 0.5 * ((double)z32 + (double)nextafterf(z32, -INFINITY));
+        double hi = 0.5 * ((double)z32 + (double)nextafterf(z32, INFINITY));
+        double d = fabs(z - lo) < fabs(z - hi) ? fabs(z - lo) : fabs(z - hi);
+        f->depth_margin = mag > 0.0 ? d / mag : d;
+    }
+    if (!(z > cam->znear)) return; /* behind the near plane */
     /* Sigma = R_q S S^T R_q^T */
     quat_rot(G->quat + 4 * g, f->qn, f->Rq);
     for (int k = 0; k < 3; ++k) f->S[k] = exp(G->log_scale[3 * g + k]);
@@ -257,7 +262,6 @@ static void project_one(const orc_gaussians* G, int64_t g, const double* edit, i
     if (f->radius <= 0) return;
     f->uv[0] = cam->fx * (x / z) + cam->cx;
     f->uv[1] = cam->fy * (y / z) + cam->cy;
-    f->depth = z32;
     /* editable opacity (Sec. 4.5): o' = s_m sigmoid(logit), not clamped */
     f->sig_o = sigmoid(G->opacity_logit[g]);
     f->opacity = me[3] * f->sig_o;
@@ -313,7 +317,7 @@ void orc_project(int64_t n, const double* mean, const double* log_scale, const d
                  const double* edit, int32_t n_models,
                  const orc_camera* cam, double lowpass, double guard,
                  double* uv, double* cov, double* conic, double* opacity, double* rgb,
-                 double* depth, int32_t* radius, double* radius_margin) {
+                 double* depth, int32_t* radius, double* radius_margin, double* depth_margin) {
     orc_gaussians G = {n, mean, log_scale, quat, opacity_logit, dcolor, normal, kads, model_id, sh, sh_deg};
     orc_fwd f;
     for (int64_t g = 0; g < n; ++g) {
@@ -328,6 +332,7 @@ void orc_project(int64_t n, const double* mean, const double* log_scale, const d
         }
         opacity[g] = f.opacity;
         depth[g] = f.depth;
+        depth_margin[g] = f.depth_margin;
     }
 }
 
@@ -471,25 +476,37 @@ static void blend_pixel(const orc_view_proj* P, const uint32_t* list, int64_t le
     if (rec_n) *rec_n = nrec;
 }
 
-/* Render one view from its projected records and its slice of the bins.
-   ranges/values are global (all views); tile0 is this view's first global tile. */
+/* Render the tiles [t_begin, t_end) (row-major within the view) of one view from its projected
+   records and its slice of the bins. ranges/values are global (all views); tile0 is this view's
+   first global tile.  Tiles are independent, so disjoint tile ranges may run concurrently. */
+void orc_render_view_tiles(const double* uv, const double* conic, const double* opacity, const double* rgb,
+                           const uint32_t* values, const uint32_t* ranges, int64_t tile0,
+                           int32_t W, int32_t H, int32_t tw, int32_t th, const double* bg,
+                           double* rgba, double* final_T, uint32_t* last, double* margins,
+                           int64_t t_begin, int64_t t_end) {
+    orc_view_proj P = {uv, conic, opacity, rgb};
+    int32_t gx = (W + tw - 1) / tw;
+    for (int64_t tl = t_begin; tl < t_end; ++tl) {
+        int32_t ty = (int32_t)(tl / gx), tx = (int32_t)(tl % gx);
+        int64_t t = tile0 + tl;
+        uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+        for (int32_t j = ty * th; j < (ty + 1) * th && j < H; ++j)
+            for (int32_t i = tx * tw; i < (tx + 1) * tw && i < W; ++i) {
+                int64_t p = (int64_t)j * W + i;
+                blend_pixel(&P, values + s, (int64_t)e - s, i + 0.5, j + 0.5, bg, rgba + 4 * p,
+                            final_T + p, last + p, margins ? margins + N_MARGINS * p : NULL, NULL, NULL, NULL);
+            }
+    }
+}
+
+/* Render one view (all of its tiles). */
 void orc_render_view(const double* uv, const double* conic, const double* opacity, const double* rgb,
                      const uint32_t* values, const uint32_t* ranges, int64_t tile0,
                      int32_t W, int32_t H, int32_t tw, int32_t th, const double* bg,
                      double* rgba, double* final_T, uint32_t* last, double* margins) {
-    orc_view_proj P = {uv, conic, opacity, rgb};
-    int32_t gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
-    for (int32_t ty = 0; ty < gy; ++ty)
-        for (int32_t tx = 0; tx < gx; ++tx) {
-            int64_t t = tile0 + (int64_t)ty * gx + tx;
-            uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
-            for (int32_t j = ty * th; j < (ty + 1) * th && j < H; ++j)
-                for (int32_t i = tx * tw; i < (tx + 1) * tw && i < W; ++i) {
-                    int64_t p = (int64_t)j * W + i;
-                    blend_pixel(&P, values + s, (int64_t)e - s, i + 0.5, j + 0.5, bg, rgba + 4 * p,
-                                final_T + p, last + p, margins ? margins + N_MARGINS * p : NULL, NULL, NULL, NULL);
-                }
-        }
+    int64_t nt = (int64_t)((W + tw - 1) / tw) * ((H + th - 1) / th);
+    orc_render_view_tiles(uv, conic, opacity, rgb, values, ranges, tile0, W, H, tw, th, bg, rgba, final_T, last,
+                          margins, 0, nt);
 }
 
 /* Auxiliary maps (Sec. 4.2 first equation: D, N = sum_i T_i alpha_i {d_i, n_i}; Sec. 4.3: the
@@ -594,34 +611,46 @@ static void blend_pixel_backward(const orc_view_proj* P, const uint32_t* list, i
     }
 }
 
-void orc_render_view_backward(const double* uv, const double* conic, const double* opacity, const double* rgb,
-                              const uint32_t* values, const uint32_t* ranges, int64_t tile0, int32_t W,
-                              int32_t H, int32_t tw, int32_t th, const double* bg, const double* dL_drgba,
-                              double* g_uv, double* g_conic, double* g_opacity, double* g_rgb) {
+/* Backward of the tiles [t_begin, t_end) of one view, accumulating (+=) into the per-Gaussian
+   record gradients; concurrent tile ranges need gradient buffers of their own. */
+void orc_render_view_backward_tiles(const double* uv, const double* conic, const double* opacity,
+                                    const double* rgb, const uint32_t* values, const uint32_t* ranges,
+                                    int64_t tile0, int32_t W, int32_t H, int32_t tw, int32_t th, const double* bg,
+                                    const double* dL_drgba, double* g_uv, double* g_conic, double* g_opacity,
+                                    double* g_rgb, int64_t t_begin, int64_t t_end) {
     orc_view_proj P = {uv, conic, opacity, rgb};
-    int32_t gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int32_t gx = (W + tw - 1) / tw;
     int64_t maxlen = 1;
-    for (int64_t t = 0; t < (int64_t)gx * gy; ++t) {
+    for (int64_t t = t_begin; t < t_end; ++t) {
         int64_t l = (int64_t)ranges[2 * (tile0 + t) + 1] - ranges[2 * (tile0 + t)];
         if (l > maxlen) maxlen = l;
     }
     int64_t* rk = (int64_t*)malloc(sizeof(int64_t) * (size_t)maxlen);
     double* rT = (double*)malloc(sizeof(double) * (size_t)maxlen);
-    for (int32_t ty = 0; ty < gy; ++ty)
-        for (int32_t tx = 0; tx < gx; ++tx) {
-            int64_t t = tile0 + (int64_t)ty * gx + tx;
-            uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
-            for (int32_t j = ty * th; j < (ty + 1) * th && j < H; ++j)
-                for (int32_t i = tx * tw; i < (tx + 1) * tw && i < W; ++i) {
-                    int64_t p = (int64_t)j * W + i;
-                    const double* d = dL_drgba + 4 * p;
-                    if (d[0] == 0.0 && d[1] == 0.0 && d[2] == 0.0 && d[3] == 0.0) continue;
-                    blend_pixel_backward(&P, values + s, (int64_t)e - s, i + 0.5, j + 0.5, bg, d, rk, rT, g_uv,
-                                         g_conic, g_opacity, g_rgb);
-                }
-        }
+    for (int64_t tl = t_begin; tl < t_end; ++tl) {
+        int32_t ty = (int32_t)(tl / gx), tx = (int32_t)(tl % gx);
+        int64_t t = tile0 + tl;
+        uint32_t s = ranges[2 * t], e = ranges[2 * t + 1];
+        for (int32_t j = ty * th; j < (ty + 1) * th && j < H; ++j)
+            for (int32_t i = tx * tw; i < (tx + 1) * tw && i < W; ++i) {
+                int64_t p = (int64_t)j * W + i;
+                const double* d = dL_drgba + 4 * p;
+                if (d[0] == 0.0 && d[1] == 0.0 && d[2] == 0.0 && d[3] == 0.0) continue;
+                blend_pixel_backward(&P, values + s, (int64_t)e - s, i + 0.5, j + 0.5, bg, d, rk, rT, g_uv,
+                                     g_conic, g_opacity, g_rgb);
+            }
+    }
     free(rk);
     free(rT);
+}
+
+void orc_render_view_backward(const double* uv, const double* conic, const double* opacity, const double* rgb,
+                              const uint32_t* values, const uint32_t* ranges, int64_t tile0, int32_t W,
+                              int32_t H, int32_t tw, int32_t th, const double* bg, const double* dL_drgba,
+                              double* g_uv, double* g_conic, double* g_opacity, double* g_rgb) {
+    int64_t nt = (int64_t)((W + tw - 1) / tw) * ((H + th - 1) / th);
+    orc_render_view_backward_tiles(uv, conic, opacity, rgb, values, ranges, tile0, W, H, tw, th, bg, dL_drgba, g_uv,
+                                   g_conic, g_opacity, g_rgb, 0, nt);
 }
 
 /* Backward for an explicit pixel set with explicit lists (sampled full-size checks). */

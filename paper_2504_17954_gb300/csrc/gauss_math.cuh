@@ -204,15 +204,36 @@ __device__ __forceinline__ float sh_term(int t, float x, float y, float z, float
 // orthonormal on the sphere, Condon-Shortley sign, normalisations written as their closed forms
 // (sqrt(3/(4 pi)) etc.), term t and the gradient of its polynomial.
 
+// Camera depth z = R20 mx + R21 my + R22 mz + t2 of float32 inputs, rounded once to float32.
+// Compensated dot product (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26(6), 2005, algorithm Dot2): every product is split exactly into p + e with one
+// fused multiply-add, every running sum into s + e with Knuth's TwoSum, and the error terms are
+// summed apart. s + c then lies within ~10 u^2 (|t2| + sum |R2k mk|) of the exact z (u = 2^-24),
+// and the final addition, one correctly rounded float32 operation, returns the float32 nearest to
+// z unless z lies that close to a midpoint between two floats. The sort key is thereby the exact
+// depth rounded once, with no float64 arithmetic (which runs at a small fraction of the float32
+// rate on this GPU). The _rn intrinsics keep the compiler from contracting or reordering.
+__device__ __forceinline__ float camera_depth(const float R2[3], float t2, const float mu[3]) {
+    float s = t2, c = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float p = __fmul_rn(R2[k], mu[k]);
+        const float pe = __fmaf_rn(R2[k], mu[k], -p);  // R2k mk - p, exact
+        const float s1 = __fadd_rn(s, p);
+        const float bv = __fsub_rn(s1, s);
+        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bv)), __fsub_rn(p, bv));  // s + p - s1, exact
+        s = s1;
+        c = __fadd_rn(c, __fadd_rn(se, pe));
+    }
+    return __fadd_rn(s, c);
+}
+
 __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& c, float lowpass, ViewLocal& V) {
     V.visible = false;
-    // camera depth as a fixed chain of three correctly rounded float32 FMAs,
-    // fma(R22, mz, fma(R21, my, fma(R20, mx, t2))): the sort key and the near-plane decision
-    // are reproducible bit for bit (float64 arithmetic runs at a small fraction of the float32
-    // rate on this GPU, and this is one of the projection's hottest expressions)
-    const float zd = fmaf(c.R[8], G.mu[2], fmaf(c.R[7], G.mu[1], fmaf(c.R[6], G.mu[0], c.t[2])));
+    // the sort key and the near-plane decision: the exact camera z rounded once to float32
+    const float zd = camera_depth(c.R + 6, c.t[2], G.mu);
     if (!(zd > c.znear)) return;
-    V.depth = (float)zd;
+    V.depth = zd;
     V.z = V.depth;
     V.x = fmaf(c.R[0], G.mu[0], fmaf(c.R[1], G.mu[1], fmaf(c.R[2], G.mu[2], c.t[0])));
     V.y = fmaf(c.R[3], G.mu[0], fmaf(c.R[4], G.mu[1], fmaf(c.R[5], G.mu[2], c.t[1])));

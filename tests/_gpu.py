@@ -5,7 +5,11 @@ FP64 oracle under the certification rules for float32-vs-float64 near-ties:
 
 * a Gaussian-view record is *uncertain* when its float64 radius 3 sqrt(lambda_max) lies within
   1e-5 (relative) of an integer, or an edge (u +- r) of its tile rectangle lies within 1e-3 px
-  of a tile boundary; its tile membership may legitimately differ;
+  of a tile boundary (its tile membership may legitimately differ), when its float64 camera
+  depth lies within 2^-40 (relative to |t_z| + sum |R_zk mu_k|) of a float32 rounding midpoint
+  (the kernel's depth, the exact depth rounded once from a compensated float32 evaluation, may
+  round the other way, so its place in the depth order may differ), or within 1e-6 of the near
+  plane (the kernel decides on the float32 depth and near plane);
 * a pixel is *excused* from the 2e-4 image tolerance only if the oracle's own decision record
   for it shows a near-tie (|ln(255 alpha)|, |ln(T'/1e-4)| or the relative |P| below 1e-3) or it
   lies in a tile touched (one tile of slack) by an uncertain record.
@@ -26,6 +30,8 @@ IMG_TOL = 2e-4
 MARGIN = 1e-3
 RADIUS_MARGIN = 1e-5
 RECT_MARGIN_PX = 1e-3
+DEPTH_MARGIN = 2.0 ** -40
+NEAR_MARGIN = 1e-6
 
 
 def device_models(models) -> List[Gaussians]:
@@ -69,9 +75,21 @@ def oracle_last_gaussian(offs: np.ndarray, lists: np.ndarray, last: np.ndarray) 
     return out
 
 
+def depth_uncertain(p: oracle.Projected) -> np.ndarray:
+    """Live records whose float32 sort key may legitimately differ from the oracle's."""
+    return (p.radius > 0) & (p.depth_margin < DEPTH_MARGIN)
+
+
+def near_plane_uncertain(p: oracle.Projected, znear: float = sg.ZNEAR) -> np.ndarray:
+    """Records that either side may cull at the near plane (the oracle's float64 z is within
+    NEAR_MARGIN of it); their footprint is unknown where the oracle culled them."""
+    return np.abs(p.depth - znear) < NEAR_MARGIN
+
+
 def uncertain_records(p: oracle.Projected, tile: int = 16) -> np.ndarray:
     live = p.radius > 0
     unc = live & (p.radius_margin < RADIUS_MARGIN)
+    unc |= depth_uncertain(p) | near_plane_uncertain(p)
     r = p.radius.astype(np.float64)
     for e in (p.uv[:, 0] - r, p.uv[:, 0] + r, p.uv[:, 1] - r, p.uv[:, 1] + r):
         q = e / tile
@@ -83,6 +101,8 @@ def uncertain_records(p: oracle.Projected, tile: int = 16) -> np.ndarray:
 def uncertain_tile_mask(p: oracle.Projected, unc: np.ndarray, W: int, H: int, tile: int = 16) -> np.ndarray:
     gx, gy = (W + tile - 1) // tile, (H + tile - 1) // tile
     mask = np.zeros((gy, gx), bool)
+    if (unc & near_plane_uncertain(p)).any():  # a record at the near plane may cover any pixel
+        mask[:] = True
     for g in np.nonzero(unc)[0]:
         u, v = p.uv[g]
         r = p.radius[g] + 1
@@ -132,3 +152,26 @@ def gpu_keys(rast: Rasterizer):
 def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
     den = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / den) if den > 0 else float(np.linalg.norm(a))
+
+
+GRAD_TOL = 1e-3
+
+
+def grad_errors(got, want):
+    """(relative L2 error ||g - g*|| / ||g*||, largest element error max |g - g*| / max |g*|)."""
+    want = np.asarray(want, np.float64)
+    got = np.asarray(got, np.float64).reshape(want.shape)
+    den = np.linalg.norm(want)
+    l2 = float(np.linalg.norm(got - want) / den) if den > 0 else float(np.linalg.norm(got))
+    mx = float(np.abs(want).max(initial=0.0))
+    d = float(np.abs(got - want).max(initial=0.0))
+    el = d / mx if mx > 0 else d
+    return l2, el
+
+
+def assert_grad(got, want, what, tol=GRAD_TOL):
+    """The gradient bar: relative L2 error per tensor and every element's error, relative to the
+    tensor's largest entry, both within tol."""
+    l2, el = grad_errors(got, want)
+    assert l2 <= tol and el <= tol, f"{what}: relative L2 {l2:.2e}, element-wise {el:.2e} of max |g*| (bar {tol:.0e})"
+    return l2, el

@@ -95,15 +95,18 @@ def workload_from(inp: dict) -> sg.Workload:
 
 # a float32 evaluation may decide differently from the FP64 oracle only near a tie: a radius
 # 3 sqrt(lambda_max) within 1e-5 (relative) of an integer, a rectangle edge within 1e-3 px of a
-# tile boundary (the record refuses such scenes), or a pixel whose alpha cut-off, termination
-# or P > 0 decision is within 1e-3 (relative) of its threshold (flagged per sampled pixel)
-RADIUS_TIE, EDGE_TIE_PX, PIXEL_TIE = 1e-5, 1e-3, 1e-3
+# tile boundary, a camera depth within 2^-40 (relative) of a float32 rounding midpoint or within
+# 1e-6 of the near plane (the record refuses such scenes), or a pixel whose alpha cut-off,
+# termination or P > 0 decision is within 1e-3 (relative) of its threshold (flagged per pixel)
+RADIUS_TIE, EDGE_TIE_PX, DEPTH_TIE, NEAR_TIE, PIXEL_TIE = 1e-5, 1e-3, 2.0 ** -40, 1e-6, 1e-3
 
 
 def check_no_record_ties(p) -> None:
     live = p.radius > 0
     r = p.radius.astype(np.float64)
     near = live & (p.radius_margin < RADIUS_TIE)
+    near |= live & (p.depth_margin < DEPTH_TIE)
+    near |= np.abs(p.depth - sg.ZNEAR) < NEAR_TIE
     for e in (p.uv[:, 0] - r, p.uv[:, 0] + r, p.uv[:, 1] - r, p.uv[:, 1] + r):
         q = e / 16.0
         near |= live & (np.abs(q - np.round(q)) * 16.0 < EDGE_TIE_PX)

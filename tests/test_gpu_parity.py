@@ -3,7 +3,8 @@
 Rows: a1 compose/edit, a2 projection + shading, a3/a4 binning + radix sort (bit-exact on
 shared inputs), a5 compositing (render-only on shared inputs, and end to end), a6/a7 backward.
 Tolerances: images 2e-4 per channel outside oracle-certified near-ties; gradients 1e-3
-relative L2 per tensor; keys, values, ranges, radii and depth bits exact.
+relative L2 per tensor and 1e-3 of the tensor's largest entry element by element; keys,
+values, ranges, radii and depth bits exact outside certified near-ties.
 """
 import numpy as np
 import pytest
@@ -65,8 +66,12 @@ def test_project_matches_oracle(which):
         assert (np.abs(co[v][vis, :3] - p.conic[vis]) / cmax).max() < 1e-4
         assert np.abs(co[v][vis, 3] - p.opacity[vis]).max() < 1e-6
         assert np.abs(cd[v][vis, :3] - p.rgb[vis]).max() < 1e-5
-        # depth: the same float32 FMA chain on both sides -> exact float32 bits
-        np.testing.assert_array_equal(cd[v][vis, 3].view(np.uint32), p.depth[vis].astype(np.float32).view(np.uint32))
+        # depth: the float64 camera z rounded once to float32, the same bits on both sides
+        # except where z lies within 2^-40 (relative) of a rounding midpoint (certified, counted)
+        dok = vis & ~_gpu.depth_uncertain(p)
+        np.testing.assert_array_equal(cd[v][dok, 3].view(np.uint32), p.depth[dok].astype(np.float32).view(np.uint32))
+        print(f"{which} view {v}: {int(vis.sum())} depth keys compared, "
+              f"{int((vis & _gpu.depth_uncertain(p)).sum())} certified near a float32 rounding midpoint")
 
 
 # ------------------------------------------------------------------ a3 + a4 (shared inputs, bit-exact)
@@ -270,22 +275,20 @@ def test_backward_matches_oracle(which, pixels_per_thread):
     ref = oracle.render(w.models, w.edits, w.cameras, bg=w.bg)
     gref = oracle.render_backward(ref, w.cameras, dls, bg=w.bg)
     for k in oracle.PARAMS:
-        g = getattr(grad, k).cpu().numpy().astype(np.float64).reshape(gref.params[k].shape)
-        e = _gpu.rel_l2(g, gref.params[k])
-        assert e < 1e-3, (k, e)
+        _gpu.assert_grad(getattr(grad, k).cpu().numpy(), gref.params[k], k)
     ne = len(gref.edit)
     eg = egrad.cpu().numpy().astype(np.float64)
     M = len(w.models)
     for m in range(M):
         sl = slice(8 * m, 8 * m + 4)
-        assert _gpu.rel_l2(eg[sl], gref.edit[sl]) < 1e-3, (m, eg[sl], gref.edit[sl])
-    assert _gpu.rel_l2(eg[8 * M:ne], gref.edit[8 * M:]) < 1e-3
+        _gpu.assert_grad(eg[sl], gref.edit[sl], f"edit of model {m}")
+    _gpu.assert_grad(eg[8 * M:ne], gref.edit[8 * M:], "lambda, b and the global light")
     if which == "fd_table_light":  # the global light's gradient on its own
-        assert _gpu.rel_l2(eg[8 * M + 8:8 * M + 11], gref.edit[8 * M + 8:8 * M + 11]) < 1e-3
+        _gpu.assert_grad(eg[8 * M + 8:8 * M + 11], gref.edit[8 * M + 8:8 * M + 11], "global light")
         assert np.abs(gref.edit[8 * M + 8:8 * M + 11]).max() > 0
     light = eg[ne:].reshape(len(w.cameras), 4)[:, :3]
     for v, c in enumerate(w.cameras):
         if c.headlight:
             assert np.all(light[v] == 0)
         else:
-            assert _gpu.rel_l2(light[v], gref.light[v]) < 1e-3, (v, light[v], gref.light[v])
+            _gpu.assert_grad(light[v], gref.light[v], f"light of view {v}")

@@ -43,34 +43,70 @@ def test_isotropic_on_axis(lowpass, sigma):
     assert p.depth[0] == pytest.approx(3.0)
 
 
-def test_depth_is_the_camera_z_within_the_fma_chain_bound():
-    """The depth that keys the sort is the camera-space z of the float32 inputs through three
-    correctly rounded fused multiply-adds: within 3.01 u (sum of the terms' magnitudes) of the
-    exact value (rational arithmetic, u = 2^-24), and it takes the near-plane decision."""
+def _rn32(q):
+    """The float32 nearest to the rational q (ties to even), decided in exact arithmetic."""
+    from fractions import Fraction
+    f = np.float32(float(q))
+    cands = [np.nextafter(f, np.float32(-np.inf)), f, np.nextafter(f, np.float32(np.inf))]
+    return min(cands, key=lambda c: (abs(Fraction(float(c)) - q), int(np.float32(c).view(np.uint32)) & 1))
+
+
+def test_depth_key_is_the_exact_camera_z_rounded_once():
+    """The depth that keys the sort is the camera-space z of the (float32) mean, R_z . mu + t_z,
+    in float64 (within 4 ulp of float64 of the exact rational value), and its float32 key is the
+    exact value rounded once to the nearest float32 wherever the oracle does not certify it as
+    near a rounding midpoint (depth_margin); the near-plane decision follows the exact z; and
+    along every tile list of a scene with many close depths the exact rational depths never
+    decrease (the order the sort produces is the order of the true depths)."""
     from fractions import Fraction
     rng = np.random.default_rng(12)
     w = sg.tiny_scene(300, 32, 32, 3, n_models=1)
     comp = oracle.compose(w.models)
     table = oracle.edit_table(w.edits)
-    checked, culled = 0, 0
+    checked, culled, certified = 0, 0, 0
     for dist in (3.0, 3.0, 0.6, 0.6):  # the close cameras put part of the scene behind the near plane
         cam = sg.look_at(dist * sg.random_direction(rng), 32, 32)
         p = oracle.project(comp, table, cam)
         R = np.asarray(cam.R, np.float32).reshape(3, 3)
         t2 = Fraction(float(np.float32(cam.t[2])))
+        exact_z = []
         for g in range(comp.n):
             mu = comp.mean[g].astype(np.float32)
             terms = [Fraction(float(R[2, j])) * Fraction(float(mu[j])) for j in range(3)] + [t2]
             exact = sum(terms)
-            bound = 3.01 * 2.0 ** -24 * float(sum(abs(x) for x in terms))
+            exact_z.append(exact)
+            mag = float(sum(abs(x) for x in terms))
+            assert abs(float(Fraction(float(p.depth[g])) - exact)) <= 4 * 2.0 ** -53 * mag, g
             if p.radius[g] > 0:
-                assert abs(float(Fraction(float(p.depth[g])) - exact)) <= bound, g
-                assert np.float32(p.depth[g]) == p.depth[g]  # a float32 value
+                if p.depth_margin[g] < 2.0 ** -40:
+                    certified += 1
+                else:
+                    assert np.float32(p.depth[g]) == _rn32(exact), g
                 checked += 1
-            if float(exact) <= float(np.float32(cam.znear)) - bound:
+            if exact <= Fraction(cam.znear):
                 assert p.radius[g] == 0, g  # behind the near plane
                 culled += 1
-    assert checked > 500 and culled > 20, (checked, culled)
+        # order along the tile lists of this view (float32 keys from the float64 depth)
+        b = oracle.bin_pairs(*oracle.decision_inputs([p]), [(cam.W, cam.H)])
+        for a, e in b.ranges:
+            zs = [exact_z[int(v)] for v in b.values[a:e]]
+            assert all(z0 <= z1 for z0, z1 in zip(zs, zs[1:]))
+    assert checked > 500 and culled > 20 and certified == 0, (checked, culled, certified)
+
+
+def test_depth_margin_flags_values_near_a_rounding_midpoint():
+    """A Gaussian whose camera z is a float32 midpoint gets a depth margin of 0; one whose z is a
+    float32 value gets the largest, half an ulp (relative to |t_z| + sum |R_zk mu_k| = z)."""
+    z32 = np.float32(3.0)
+    mid = (float(z32) + float(np.nextafter(z32, np.float32(np.inf)))) / 2.0
+    m = single_model([0.0, 0.0, 0.0], log_scale=[-3.0] * 3)
+    for z, want in ((mid, 0.0), (float(z32), 0.5 * float(np.spacing(z32)) / float(z32))):
+        c = axis_camera(W=32, H=32, z=3.0)
+        c.t = np.array([0.0, 0.0, z])  # float64: the oracle takes the camera as given
+        p = _proj1(m, c, 0.3)
+        assert p.radius[0] > 0 and p.depth[0] == z
+        assert p.depth_margin[0] == pytest.approx(want, rel=1e-9, abs=1e-18)
+
 
 
 def test_axis_aligned_and_quarter_turn():
