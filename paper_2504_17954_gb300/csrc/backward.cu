@@ -10,9 +10,11 @@
 // per-Gaussian sums are reduced across the warp (all lanes walk the same entry) and added
 // with one vector atomic per warp.
 //
-// a7, per Gaussian: the projection and shading are recomputed per view; dL/dSigma,
-// dL/dc_v, dL/dk', dL/dn and dL/do' are accumulated over views in registers and pushed
-// through the view-independent parts (quaternion, scale, edits) once.
+// a7, per Gaussian: the projection and shading are recomputed per view; dL/dSigma (in the
+// Gaussian's own frame), dL/dc_v, dL/dk', dL/dn and dL/do' are accumulated over views in
+// registers and pushed through the view-independent parts (quaternion, scale, edits) once.
+// The conic's gradient reaches Sigma' through the eigenbasis of Sigma', which keeps long, thin
+// Gaussians' scale and rotation gradients free of cancellation in float32.
 #include "blend_alpha.cuh"
 #include "f32x2.cuh"
 #include "gauss_math.cuh"
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
     else G.visible = false;
     if constexpr (!SH) G.sh = nullptr;  // the instantiation without SH colour carries none of its code
     const bool tl_on = __ldg(table + (long long)M * IVRGS_EDIT_STRIDE + 11) != 0.0f;  // uniform
-    float dmu[3] = {0.f, 0.f, 0.f}, dSig[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float dmu[3] = {0.f, 0.f, 0.f}, dSl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dSl: dL/dSigma in the Gaussian's frame
     float dcv[3] = {0.f, 0.f, 0.f}, dkp[4] = {0.f, 0.f, 0.f, 0.f}, dnn[3] = {0.f, 0.f, 0.f}, dop = 0.f;
     // the next view's record gradients are loaded before this view's arithmetic (latency overlap)
     float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nbq = na;
@@ -434,34 +436,72 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
                     for (int k = 0; k < 3; ++k) dmu[k] -= (dv[k] - V.vd[k] * vd) * iv;
                 }
                 }
-                // ---- conic -> Sigma'
+                // ---- conic -> Sigma' -> (Sigma, T), in the eigenbasis of Sigma'
+                // dL/dSigma' = -K Gk K, K = Sigma'^-1 (the conic), Gk = dL/dK as a symmetric
+                // matrix. With Sigma' = E diag(l1, l2) E^T this is E D E^T, D_ij = -(E^T Gk E)_ij
+                // k_i k_j, where k1 = 1/l1 and k2 = l1/det are the conic's eigenvalues. Written out
+                // in the pixel basis (the adjugate over det^2), the long-axis entry of a long, thin
+                // Gaussian is a difference of terms larger by (l1/l2)^2; here each entry of D is
+                // one product. dSigma is kept in the Gaussian's own frame, Rq^T dSigma Rq = P^T D P
+                // with P = E^T T Rq, where the long axis's row of P is nearly orthogonal to the
+                // short one's, so the scale gradients need no cancellation either.
                 const float A = V.A, B = V.B, C = V.C;
-                const float id2 = 1.0f / (V.det * V.det);
-                const float dA = (a.z * (-C * C) + a.w * (B * C) + b.x * (-B * B)) * id2;
-                const float dB = (a.z * (2.f * B * C) + a.w * (-(A * C + B * B)) + b.x * (2.f * A * B)) * id2;
-                const float dC = (a.z * (-B * B) + a.w * (A * B) + b.x * (-A * A)) * id2;
-                const float G00 = dA, G01 = 0.5f * dB, G11 = dC;
-                const float* T = V.T;
-                // dSigma += T^T G2 T (symmetric; store xx, xy, xz, yy, yz, zz)
-                float GT[6];  // G2 T (2x3)
-                for (int j = 0; j < 3; ++j) {
-                    GT[j] = G00 * T[j] + G01 * T[3 + j];
-                    GT[3 + j] = G01 * T[j] + G11 * T[3 + j];
+                const float hd = 0.5f * (A - C);
+                const float rr = sqrtf(hd * hd + B * B);
+                const float l1 = 0.5f * (A + C) + rr;
+                // e1 from the row of (Sigma' - l1 I) whose entries do not cancel; e2 = (-ey, ex)
+                float ex = hd >= 0.f ? hd + rr : B, ey = hd >= 0.f ? B : rr - hd;
+                const float en = ex * ex + ey * ey;
+                if (en > 0.f) {
+                    const float sn = rsqrtf(en);
+                    ex *= sn;
+                    ey *= sn;
+                } else {
+                    ex = 1.f;
+                    ey = 0.f;
                 }
-                dSig[0] += T[0] * GT[0] + T[3] * GT[3];
-                dSig[1] += T[0] * GT[1] + T[3] * GT[4];
-                dSig[2] += T[0] * GT[2] + T[3] * GT[5];
-                dSig[3] += T[1] * GT[1] + T[4] * GT[4];
-                dSig[4] += T[1] * GT[2] + T[4] * GT[5];
-                dSig[5] += T[2] * GT[2] + T[5] * GT[5];
-                // dT = 2 G2 T Sigma
-                const float* S = G.Sig;
+                const float ga = a.z, gb = a.w, gc = b.x;  // dL/d(a, b, c) of the conic
+                const float H11 = ga * ex * ex + gb * ex * ey + gc * ey * ey;
+                const float H22 = ga * ey * ey - gb * ex * ey + gc * ex * ex;
+                const float H12 = (gc - ga) * ex * ey + 0.5f * gb * (ex * ex - ey * ey);
+                const float k1 = 1.0f / l1, k2 = l1 / V.det;
+                const float D11 = -H11 * k1 * k1, D12 = -H12 * (k1 * k2), D22 = -H22 * k2 * k2;
+                const float* T = V.T;
+                float p1[3], p2[3];  // rows of P = E^T T Rq
+                {
+                    float q1[3], q2[3];
+                    for (int j = 0; j < 3; ++j) {
+                        q1[j] = ex * T[j] + ey * T[3 + j];
+                        q2[j] = ex * T[3 + j] - ey * T[j];
+                    }
+                    for (int k = 0; k < 3; ++k) {
+                        p1[k] = q1[0] * G.Rq[k] + q1[1] * G.Rq[3 + k] + q1[2] * G.Rq[6 + k];
+                        p2[k] = q2[0] * G.Rq[k] + q2[1] * G.Rq[3 + k] + q2[2] * G.Rq[6 + k];
+                    }
+                }
+                // dSigma in the Gaussian's frame += P^T D P (xx, xy, xz, yy, yz, zz)
+                {
+                    int o = 0;
+                    for (int r = 0; r < 3; ++r)
+                        for (int k = r; k < 3; ++k, ++o)
+                            dSl[o] += D11 * p1[r] * p1[k] + D12 * (p1[r] * p2[k] + p2[r] * p1[k]) + D22 * p2[r] * p2[k];
+                }
+                // dT = 2 dSigma' T Sigma = 2 E D (P diag(s^2)) Rq^T
                 float dT[6];
-                for (int r = 0; r < 2; ++r) {
-                    const float* q = GT + 3 * r;
-                    dT[3 * r + 0] = 2.f * (q[0] * S[0] + q[1] * S[1] + q[2] * S[2]);
-                    dT[3 * r + 1] = 2.f * (q[0] * S[1] + q[1] * S[3] + q[2] * S[4]);
-                    dT[3 * r + 2] = 2.f * (q[0] * S[2] + q[1] * S[4] + q[2] * S[5]);
+                {
+                    float w1[3], w2[3];
+                    for (int k = 0; k < 3; ++k) {
+                        const float s2 = G.sc[k] * G.sc[k];
+                        const float a1 = p1[k] * s2, a2 = p2[k] * s2;
+                        w1[k] = D11 * a1 + D12 * a2;
+                        w2[k] = D12 * a1 + D22 * a2;
+                    }
+                    for (int j = 0; j < 3; ++j) {
+                        const float u1 = w1[0] * G.Rq[3 * j] + w1[1] * G.Rq[3 * j + 1] + w1[2] * G.Rq[3 * j + 2];
+                        const float u2 = w2[0] * G.Rq[3 * j] + w2[1] * G.Rq[3 * j + 1] + w2[2] * G.Rq[3 * j + 2];
+                        dT[j] = 2.f * (ex * u1 - ey * u2);
+                        dT[3 + j] = 2.f * (ey * u1 + ex * u2);
+                    }
                 }
                 // dJ = dT W^T; only J00, J02, J11, J12 are non-zero
                 const float dJ00 = dT[0] * c.R[0] + dT[1] * c.R[1] + dT[2] * c.R[2];
@@ -513,22 +553,15 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const ivrgs_gaussians g,
         float glogit = 0.f, gdc[3] = {0.f, 0.f, 0.f}, gk[4] = {0.f, 0.f, 0.f, 0.f};
         if (G.visible) {
             for (int k = 0; k < 3; ++k) gm[k] = dmu[k];
-            // Sigma = M M^T, M = Rq diag(sc): dM = 2 dSigma M
-            float M_[9], dS[9];
-            for (int r = 0; r < 3; ++r)
-                for (int k = 0; k < 3; ++k) M_[3 * r + k] = G.Rq[3 * r + k] * G.sc[k];
-            dS[0] = dSig[0]; dS[1] = dSig[1]; dS[2] = dSig[2];
-            dS[3] = dSig[1]; dS[4] = dSig[3]; dS[5] = dSig[4];
-            dS[6] = dSig[2]; dS[7] = dSig[4]; dS[8] = dSig[5];
+            // Sigma = Rq diag(s^2) Rq^T with dSigma given in the Gaussian's frame (dSl = Rq^T dSigma Rq):
+            // d log s_k = 2 s_k^2 dSl_kk, dL/dRq = 2 Rq dSl diag(s^2)
+            const float dS[9] = {dSl[0], dSl[1], dSl[2], dSl[1], dSl[3], dSl[4], dSl[2], dSl[4], dSl[5]};
             float dR[9];
             for (int k = 0; k < 3; ++k) {
-                float ds = 0.f;
-                for (int r = 0; r < 3; ++r) {
-                    const float dM = 2.f * (dS[3 * r] * M_[k] + dS[3 * r + 1] * M_[3 + k] + dS[3 * r + 2] * M_[6 + k]);
-                    ds += G.Rq[3 * r + k] * dM;
-                    dR[3 * r + k] = dM * G.sc[k];
-                }
-                gls[k] = ds * G.sc[k];
+                const float s2 = G.sc[k] * G.sc[k];
+                gls[k] = 2.f * s2 * dS[4 * k];
+                for (int r = 0; r < 3; ++r)
+                    dR[3 * r + k] = 2.f * s2 * (G.Rq[3 * r] * dS[k] + G.Rq[3 * r + 1] * dS[3 + k] + G.Rq[3 * r + 2] * dS[6 + k]);
             }
             const float w = G.qn[0], x = G.qn[1], y = G.qn[2], z = G.qn[3];
             float dq[4];

@@ -58,8 +58,7 @@ def test_single_gaussian():
         assert bad == 0, err
     gref = oracle.render_backward(ref, w.cameras, dls, bg=w.bg)
     for k in oracle.PARAMS:
-        g = getattr(grad, k).cpu().numpy().astype(np.float64).reshape(gref.params[k].shape)
-        assert _gpu.rel_l2(g, gref.params[k]) < 1e-3, k
+        _gpu.assert_grad(getattr(grad, k).cpu().numpy(), gref.params[k], k)
 
 
 def test_everything_behind_the_camera():

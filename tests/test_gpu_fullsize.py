@@ -7,7 +7,8 @@ default launch shapes): sampled pixels and sampled-loss gradients against the FP
 * 500k Gaussians / one 800^2 view: sampled pixels and gradients.
 * 1.5M Gaussians / 6 models with colour, opacity and visibility edits, 16 views at 1024^2
   with an orbital light sweep: sampled pixels on 4 of the views.
-Images within 2e-4 outside oracle-certified near-ties; gradients within 1e-3 relative L2.
+Images within 2e-4 outside oracle-certified near-ties; gradients within 1e-3 relative L2 and
+element by element within 1e-3 of each tensor's largest entry.
 """
 import numpy as np
 import pytest
@@ -82,13 +83,11 @@ def _check_grads(rast, comp_dev, table_dev, w, sampled, comp, table, per_view, s
     ref = oracle.pixels_backward(comp, table, cams, [projs[v] for v in views], [pix_v[v] for v in views],
                                  [dl_v[v] for v in views], bg=w.bg)
     for k in oracle.PARAMS:
-        g = getattr(grad, k).cpu().numpy().astype(np.float64).reshape(ref.params[k].shape)
         assert np.linalg.norm(ref.params[k]) > 0, k
-        e = _gpu.rel_l2(g, ref.params[k])
-        assert e < 1e-3, (k, e)
-    M = len(w.models)
+        l2, el = _gpu.assert_grad(getattr(grad, k).cpu().numpy(), ref.params[k], k)
+        print(f"{k}: relative L2 {l2:.2e}, element-wise {el:.2e} of max |g*|")
     eg = egrad.cpu().numpy().astype(np.float64)
-    assert _gpu.rel_l2(eg[:len(ref.edit)], ref.edit) < 1e-3
+    _gpu.assert_grad(eg[:len(ref.edit)], ref.edit, "edit table")
 
 
 def test_fullsize_1m_8_views_pixels_and_gradients():

@@ -51,9 +51,8 @@ def test_static_scratch_backward_matches_workspace_backward_twice():
         grad, egrad = _backward_static(rast, comp, table, dl)
         torch.cuda.synchronize()
         for k in ATTRS:
-            e = _gpu.rel_l2(getattr(grad, k).cpu().numpy().astype(np.float64), ref[k])
-            assert e <= GRAD_TOL, (k, e)
-        assert _gpu.rel_l2(egrad.cpu().numpy().astype(np.float64), eref) <= GRAD_TOL
+            _gpu.assert_grad(getattr(grad, k).cpu().numpy(), ref[k], k, GRAD_TOL)
+        _gpu.assert_grad(egrad.cpu().numpy(), eref, "edit table", GRAD_TOL)
 
 
 def test_static_scratch_refuses_oversized_problems():
