@@ -235,6 +235,10 @@ class Rasterizer:
     with mode="exact" the buffer grows to the exact pair count when needed. ``cull`` drops the
     pairs of tiles that the Gaussian's opacity cut-off ellipse misses (IVRGS_BIN_CULL): the same
     images and gradients from shorter tile lists; ``cull=False`` gives the full rectangle lists.
+
+    ``generation`` counts the eager calls that rewrite the per-render state (projection,
+    binning, compositing); ``RenderFunction`` uses it to refuse a backward whose forward state
+    has since been overwritten. Replays of a captured graph do not advance it.
     """
 
     def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", capacity: Optional[int] = None,
@@ -268,6 +272,7 @@ class Rasterizer:
         self.ws_bwd = None
         self.edit_grad = torch.empty(N.lib().ivrgs_edit_table_floats(self.n_models) + 4 * self.V,
                                      dtype=torch.float32, device=dev)
+        self.generation = 0
 
     # -- buffers
     def _ensure_capacity(self, cap: int):
@@ -299,11 +304,13 @@ class Rasterizer:
 
     # -- steps
     def project(self, g: Gaussians, edit_table: torch.Tensor, stream=None, tensors=None):
+        self.generation += 1
         gs = g.struct(tensors)
         p = self.projected_struct()
         N.ivrgs_project(C.byref(gs), _vp(edit_table), self.cam_arr, self.V, self.lowpass, C.byref(p), _stream(stream))
 
     def bin(self, mode: str = "exact", stream=None) -> int:
+        self.generation += 1
         p = self.projected_struct()
         if mode == "exact":
             while True:
@@ -324,6 +331,7 @@ class Rasterizer:
         return -1
 
     def render(self, stream=None):
+        self.generation += 1
         p, b = self.projected_struct(), self.bins_struct()
         N.ivrgs_render(C.byref(p), C.byref(b), self.cam_arr, self.V, self.bg, _vp(self.rgba), _vp(self.final_T),
                        _vp(self.last), _stream(stream))
@@ -474,13 +482,18 @@ class RenderFunction(torch.autograd.Function):
 
     The forward keeps only the projected records, the bins, the final transmittance and the
     last-contributor index per pixel (inside the Rasterizer); the per-pixel transmittance
-    of every contributor is recomputed in the backward, not stored.
+    of every contributor is recomputed in the backward, not stored. Because that state lives in
+    the Rasterizer, a render's backward must run before the same Rasterizer renders again: a
+    later forward on it makes the earlier render's backward raise (one Rasterizer per render
+    that takes part in a loss). The per-view light-direction gradients of the last backward
+    are left in ``rast.light_grad`` ([V, 3]).
     """
 
     @staticmethod
     def forward(ctx, rast: Rasterizer, g: Gaussians, edit_table, *attrs):
         rast.forward(g, edit_table.detach(), tensors=[a.detach() for a in attrs])
         ctx.rast, ctx.g = rast, g
+        ctx.generation = rast.generation
         ctx.save_for_backward(edit_table, *attrs)
         return rast.rgba.clone()
 
@@ -488,6 +501,10 @@ class RenderFunction(torch.autograd.Function):
     def backward(ctx, d_rgba):
         edit_table, *attrs = ctx.saved_tensors
         rast: Rasterizer = ctx.rast
+        if rast.generation != ctx.generation:
+            raise RuntimeError("render(): the Rasterizer has rendered again since this forward, so the "
+                               "records, tile lists and per-pixel state its backward needs are gone; "
+                               "use one Rasterizer per render that takes part in a loss")
         grad, egrad = rast.backward(ctx.g, edit_table.detach(), d_rgba.contiguous(),
                                     tensors=[a.detach() for a in attrs])
         ne = edit_table.numel()
