@@ -417,6 +417,50 @@ int64_t orc_bin(int32_t n_views, int64_t n, const float* uv, const int32_t* radi
     return total;
 }
 
+/* The pairs of ONE view whose tile row lies in [row_begin, row_end), ordered as orc_bin orders
+   them (by tile, then depth bits, then emission order, i.e. Gaussian index), with global tile
+   ids (tile0 = the view's first global tile).  Returns the pair count; writes keys and values
+   only if it is <= capacity.  Disjoint row bands concatenated in row order give orc_bin's
+   ordering of that view, so bands may be binned concurrently. */
+int64_t orc_bin_view_rows(int64_t n, const float* uv, const int32_t* radius, const float* depth, int32_t W,
+                          int32_t H, int32_t tw, int32_t th, int64_t tile0, int32_t row_begin, int32_t row_end,
+                          uint64_t* keys, uint32_t* values, int64_t capacity) {
+    int32_t gx = (W + tw - 1) / tw, gy = (H + th - 1) / th;
+    int32_t rc[4];
+    int64_t total = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        if (radius[g] <= 0) continue;
+        rect32(uv[2 * g], uv[2 * g + 1], radius[g], gx, gy, tw, th, rc);
+        int32_t y0 = rc[2] > row_begin ? rc[2] : row_begin, y1 = rc[3] < row_end ? rc[3] : row_end;
+        if (y1 > y0) total += (int64_t)(rc[1] - rc[0]) * (y1 - y0);
+    }
+    if (total > capacity) return total;
+    orc_pair* P = (orc_pair*)malloc(sizeof(orc_pair) * (size_t)(total > 0 ? total : 1));
+    int64_t k = 0;
+    for (int64_t g = 0; g < n; ++g) {
+        if (radius[g] <= 0) continue;
+        rect32(uv[2 * g], uv[2 * g + 1], radius[g], gx, gy, tw, th, rc);
+        int32_t y0 = rc[2] > row_begin ? rc[2] : row_begin, y1 = rc[3] < row_end ? rc[3] : row_end;
+        uint32_t bits;
+        memcpy(&bits, &depth[g], 4);
+        for (int ty = y0; ty < y1; ++ty)
+            for (int tx = rc[0]; tx < rc[1]; ++tx) {
+                uint64_t tile = (uint64_t)(tile0 + (int64_t)ty * gx + tx);
+                P[k].key = (tile << 32) | bits;
+                P[k].seq = k;
+                P[k].value = (uint32_t)g;
+                ++k;
+            }
+    }
+    qsort(P, (size_t)total, sizeof(orc_pair), pair_cmp);
+    for (int64_t i = 0; i < total; ++i) {
+        keys[i] = P[i].key;
+        values[i] = P[i].value;
+    }
+    free(P);
+    return total;
+}
+
 /* ---------------------------------------------------------------------------------------
  * Front-to-back compositing of one pixel over an ordered list (Sec. 3, second equation).
  * margins[0]: smallest |ln(alpha*255)| over evaluated entries (1/255 cut-off);

@@ -7,7 +7,8 @@ over ranges of tiles (tiles are independent, Sec. 3's compositing is per pixel).
 accumulate do so into buffers of their own, summed at the end, so gradient sums are taken in a
 different order than the single-threaded oracle's (the last bits of float64 may differ).
 ctypes releases the GIL for the duration of each C call, so Python threads run the C code
-concurrently. The binning (one sort per view) stays on one thread.
+concurrently. The binning of a view is split into bands of tile rows, each sorted on its own
+thread; the bands concatenated in row order are the view's sorted pairs.
 """
 from __future__ import annotations
 
@@ -17,8 +18,8 @@ from typing import List
 
 import numpy as np
 
-from . import (C, LOWPASS, N_MARGINS, Composed, Projected, _grad_params, _p, _project_backward,
-               bin_pairs, decision_inputs, lib, project)
+from . import (C, LOWPASS, N_MARGINS, Bins, Composed, Projected, _grad_params, _p, _project_backward,
+               decision_inputs, lib, project)
 
 
 def default_threads() -> int:
@@ -44,13 +45,40 @@ def project_parallel(pool, comp: Composed, table, cam, threads: int, lowpass: fl
                      depth_margin=cat("depth_margin"))
 
 
+def bin_view_parallel(pool, p: Projected, cam, threads: int, tile=(16, 16)) -> Bins:
+    """The binning of one view (what bin_pairs gives for it) from bands of tile rows, each
+    sorted on its own thread (orc_bin_view_rows), concatenated in row order."""
+    uv32, rad, d32 = (np.ascontiguousarray(a[0]) for a in decision_inputs([p]))
+    gx, gy = (cam.W + tile[0] - 1) // tile[0], (cam.H + tile[1] - 1) // tile[1]
+
+    def band(rows):
+        args = (C.c_int64(len(rad)), _p(uv32, C.c_float), _p(rad, C.c_int32), _p(d32, C.c_float), C.c_int32(cam.W),
+                C.c_int32(cam.H), C.c_int32(tile[0]), C.c_int32(tile[1]), C.c_int64(0), C.c_int32(rows[0]),
+                C.c_int32(rows[1]))
+        dk, dv = np.zeros(1, np.uint64), np.zeros(1, np.uint32)
+        cnt = lib().orc_bin_view_rows(*args, _p(dk, C.c_uint64), _p(dv, C.c_uint32), C.c_int64(0))
+        keys, vals = np.zeros(max(cnt, 1), np.uint64), np.zeros(max(cnt, 1), np.uint32)
+        lib().orc_bin_view_rows(*args, _p(keys, C.c_uint64), _p(vals, C.c_uint32), C.c_int64(cnt))
+        return keys[:cnt], vals[:cnt]
+    parts = list(pool.map(band, _chunks(gy, 4 * threads)))
+    keys = np.concatenate([k for k, _ in parts]) if parts else np.zeros(0, np.uint64)
+    vals = np.concatenate([v for _, v in parts]) if parts else np.zeros(0, np.uint32)
+    t = (keys >> np.uint64(32)).astype(np.int64)
+    nt = gx * gy
+    ranges = np.zeros((nt, 2), np.uint32)
+    ranges[:, 0] = np.searchsorted(t, np.arange(nt), side="left")
+    ranges[:, 1] = np.searchsorted(t, np.arange(nt), side="right")
+    ranges[ranges[:, 0] == ranges[:, 1]] = 0  # empty tiles: [0, 0), as orc_bin leaves them
+    return Bins(keys=keys, values=vals, ranges=ranges, tile_offset=np.array([0, nt], np.int64))
+
+
 def render_view_parallel(comp: Composed, table, cam, bg, threads: int = 0, tile=(16, 16), lowpass: float = LOWPASS):
     """Forward of one view on all cores: (rgba [H, W, 4], final T, last, margins, projection, bins)."""
     threads = threads or default_threads()
     bg = np.ascontiguousarray(bg, np.float64)
     with ThreadPoolExecutor(threads) as pool:
         p = project_parallel(pool, comp, table, cam, threads, lowpass)
-        bins = bin_pairs(*decision_inputs([p]), [(cam.W, cam.H)], tile)
+        bins = bin_view_parallel(pool, p, cam, threads, tile)
         rgba = np.zeros((cam.H, cam.W, 4)); T = np.zeros((cam.H, cam.W))
         last = np.zeros((cam.H, cam.W), np.uint32); mg = np.zeros((cam.H, cam.W, N_MARGINS))
         nt = ((cam.W + tile[0] - 1) // tile[0]) * ((cam.H + tile[1] - 1) // tile[1])
@@ -98,4 +126,5 @@ def render_backward_view_parallel(comp: Composed, table, cam, p: Projected, bins
     return params, np.sum([o[0] for o in outs], axis=0), np.sum([o[1] for o in outs], axis=0)
 
 
-__all__ = ["default_threads", "project_parallel", "render_view_parallel", "render_backward_view_parallel"]
+__all__ = ["default_threads", "project_parallel", "bin_view_parallel", "render_view_parallel",
+           "render_backward_view_parallel"]

@@ -204,6 +204,34 @@ __global__ void __launch_bounds__(kLossThreads) k_ssim_v2(const float4* __restri
     dL[c.pix0 + q] = make_float4(g[0], g[1], g[2], 0.f);
 }
 
+// lambda = 0 (the plain L1 loss): dL/dx = sign(x - y) / N per colour channel and the block
+// sums of |x - y|, without the SSIM passes (the SSIM block sums are written as 0)
+__global__ void __launch_bounds__(kLossThreads) k_l1_loss(const float4* __restrict__ x, const float4* __restrict__ y,
+                                                          const __grid_constant__ CamBatch cb, float gL1,
+                                                          float4* __restrict__ dL, double* __restrict__ part) {
+    __shared__ float s_red[kLossThreads / 32];
+    const CamDev& c = cb.c[blockIdx.y];
+    const long long q = (long long)blockIdx.x * kLossThreads + threadIdx.x;
+    float l1 = 0.f;
+    if (q < (long long)c.W * c.H) {
+        const float4 a = x[c.pix0 + q], b = y[c.pix0 + q];
+        const float d[3] = {a.x - b.x, a.y - b.y, a.z - b.z};
+        float g[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            g[ch] = d[ch] > 0.f ? gL1 : (d[ch] < 0.f ? -gL1 : 0.f);
+            l1 += fabsf(d[ch]);
+        }
+        dL[c.pix0 + q] = make_float4(g[0], g[1], g[2], 0.f);
+    }
+    const long long pb = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    const float tl = block_sum(l1, s_red);
+    if (threadIdx.x == 0) {
+        part[2 * pb] = 0.0;
+        part[2 * pb + 1] = tl;
+    }
+}
+
 __global__ void k_loss_final(const double* __restrict__ part, long long n_part, double n_elems, float lambda,
                              float* __restrict__ loss) {
     __shared__ double s_s[256], s_l[256];
@@ -258,7 +286,11 @@ cudaError_t launch_image_loss(const float* rgba, const float* target, const CamB
     const float4* x = reinterpret_cast<const float4*>(rgba);
     const float4* y = reinterpret_cast<const float4*>(target);
     const float gS = -lambda / (float)n_elems, gL1 = (1.0f - lambda) / (float)n_elems;
-    {
+    if (lambda == 0.0f) {
+        IVRGS_PROF("k_l1_loss", s);
+        k_l1_loss<<<grid, kLossThreads, 0, s>>>(x, y, cb, gL1, reinterpret_cast<float4*>(dL), part);
+        k_loss_final<<<1, 256, 0, s>>>(part, bx * cb.n, (double)n_elems, lambda, loss);
+    } else {
         IVRGS_PROF("k_image_loss", s);
         k_ssim_h1<<<grid, kLossThreads, 0, s>>>(x, y, cb, win, h1);
         k_ssim_v1<<<grid, kLossThreads, 0, s>>>(x, y, h1, cb, win, gS, d1, part);

@@ -378,10 +378,12 @@ class Rasterizer:
 
     # -- CUDA graphs
     def capture(self, g: Gaussians, edit_table: torch.Tensor, dL_drgba: Optional[torch.Tensor] = None,
-                grad: Optional[Gaussians] = None, warmup: int = 2) -> "torch.cuda.CUDAGraph":
+                grad: Optional[Gaussians] = None, warmup: int = 2, loss=None) -> "torch.cuda.CUDAGraph":
         """Capture one step (projection, CAPACITY-mode binning, compositing and, if dL_drgba is
         given, the backward into ``grad``) as a CUDA graph; ``graph.replay()`` reruns it on the
-        current contents of the Gaussian, edit-table and dL buffers.
+        current contents of the Gaussian, edit-table and dL buffers. ``loss``, if given, is called
+        (and captured) between the compositing and the backward, e.g. an image loss that writes
+        dL_drgba from ``self.rgba``.
 
         The pair buffer must already hold the step's pairs (run ``forward(mode="exact")`` once);
         after a replay, ``d_n_pairs > capacity`` means the step overflowed and must be rerun
@@ -397,17 +399,20 @@ class Rasterizer:
         N.prof_enable(False)
         side = torch.cuda.Stream(device=self.device)
         side.wait_stream(torch.cuda.current_stream(self.device))
+        def step():
+            self.forward(g, edit_table, mode="capacity")
+            if loss is not None:
+                loss()
+            if dL_drgba is not None:
+                self.backward(g, edit_table, dL_drgba, grad=grad)
+
         with torch.cuda.stream(side):  # warm-up outside capture (lazy module loading etc.)
             for _ in range(warmup):
-                self.forward(g, edit_table, mode="capacity")
-                if dL_drgba is not None:
-                    self.backward(g, edit_table, dL_drgba, grad=grad)
+                step()
         torch.cuda.current_stream(self.device).wait_stream(side)
         graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph):
-            self.forward(g, edit_table, mode="capacity")
-            if dL_drgba is not None:
-                self.backward(g, edit_table, dL_drgba, grad=grad)
+            step()
         return graph
 
     # -- views of the packed image
@@ -474,6 +479,57 @@ class WaveRasterizer:
             if v in wv:
                 return r.view_image(wv.index(v))
         raise IndexError(v)
+
+    def size_buffers(self, g: Gaussians, edit_table: torch.Tensor, slack: float = 1.1):
+        """One EXACT-mode forward per wave, then pair buffers with ``slack`` times the counts:
+        what CAPACITY-mode binning (and so ``capture``) needs."""
+        for r in self.rasts:
+            r.forward(g, edit_table, mode="exact")
+        torch.cuda.synchronize()
+        for r in self.rasts:
+            r._ensure_capacity(int(r.n_pairs * slack) + 4096)
+
+    def overflowed(self) -> bool:
+        """True if a wave's last CAPACITY-mode binning had more pairs than its buffer holds."""
+        return any(int(r.d_n_pairs.item()) > r.capacity for r in self.rasts)
+
+    def capture(self, g: Gaussians, edit_table: torch.Tensor, dL_per_wave: Optional[Sequence[torch.Tensor]] = None,
+                grad: Optional[Gaussians] = None, warmup: int = 2) -> "torch.cuda.CUDAGraph":
+        """Every wave's projection, CAPACITY-mode binning and compositing and, with
+        ``dL_per_wave``, the backward summed over the waves (into ``grad``, ``self.edit_grad`` and
+        ``self.light_grad``) as ONE CUDA graph; ``graph.replay()`` reruns the whole step on the
+        current contents of the Gaussian, edit-table and dL buffers. Run ``size_buffers`` first;
+        after a replay, ``overflowed()`` tells whether a wave must be re-sized and captured again."""
+        dev = self.rasts[0].device
+        ne = edit_table.numel()
+        if dL_per_wave is not None and grad is None:
+            grad = Gaussians.empty(self.rasts[0].n, self.n_models, dev)
+            grad.model_id = None
+        self.graph_grad = grad
+        self.edit_grad = torch.zeros(ne + 4 * max(len(wv) for wv in self.waves), dtype=torch.float32, device=dev)
+        self.light_grad = torch.zeros((self.V, 3), dtype=torch.float32, device=dev)
+        # a graph writes through the raw addresses of these buffers: keep every captured graph's alive
+        self._graph_buffers = getattr(self, "_graph_buffers", []) + [(grad, self.edit_grad, self.light_grad)]
+        N.prof_enable(False)
+
+        def step():
+            for r in self.rasts:
+                r.forward(g, edit_table, mode="capacity")
+            if dL_per_wave is not None:
+                for k, (r, wv) in enumerate(zip(self.rasts, self.waves)):
+                    r.backward(g, edit_table, dL_per_wave[k], grad=grad, accumulate=k > 0, edit_grad=self.edit_grad)
+                    self.light_grad[wv[0]:wv[-1] + 1] = self.edit_grad[ne:ne + 4 * len(wv)].view(len(wv), 4)[:, :3]
+
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                step()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        return graph
 
 
 # ----------------------------------------------------------------------------------------

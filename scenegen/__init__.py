@@ -461,6 +461,18 @@ def bf16_bits_to_f32(bits) -> np.ndarray:
     return (np.asarray(bits, np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32)
 
 
+def morton_order(mean, model_id, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """The memory layout of a composed set: indices sorted (stably) by (model id, 30-bit Morton
+    code of the float32 mean quantised to 1024 steps per axis inside the box [lo, hi])."""
+    mean = np.ascontiguousarray(mean, np.float32)
+    lo32, hi32 = np.asarray(lo, np.float32), np.asarray(hi, np.float32)
+    inv = (np.float32(1.0) / (hi32 - lo32)).astype(np.float32)
+    q = np.clip((mean - lo32) * inv * np.float32(1024.0), np.float32(0.0), np.float32(1023.0)).astype(np.uint32)
+    code = (_spread10(q[:, 0]) << np.uint32(2)) | (_spread10(q[:, 1]) << np.uint32(1)) | _spread10(q[:, 2])
+    key = (np.asarray(model_id).astype(np.uint64) << np.uint64(30)) | code.astype(np.uint64)
+    return np.argsort(key, kind="stable")
+
+
 def pack_mixed_arrays(mean, log_scale, quat, opacity_logit, dcolor, normal, kads, model_id,
                       lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0)):
     """The 16-bit storage of concatenated float32 attributes: reorder by (model id, Morton code
@@ -470,12 +482,7 @@ def pack_mixed_arrays(mean, log_scale, quat, opacity_logit, dcolor, normal, kads
     f = lambda a: np.ascontiguousarray(a, np.float32)
     mean, log_scale, quat, dcolor, normal, kads = map(f, (mean, log_scale, quat, dcolor, normal, kads))
     opacity_logit = f(opacity_logit)
-    lo32, hi32 = np.asarray(lo, np.float32), np.asarray(hi, np.float32)
-    inv = (np.float32(1.0) / (hi32 - lo32)).astype(np.float32)
-    q = np.clip((mean - lo32) * inv * np.float32(1024.0), np.float32(0.0), np.float32(1023.0)).astype(np.uint32)
-    code = (_spread10(q[:, 0]) << np.uint32(2)) | (_spread10(q[:, 1]) << np.uint32(1)) | _spread10(q[:, 2])
-    key = (np.asarray(model_id).astype(np.uint64) << np.uint64(30)) | code.astype(np.uint64)
-    order = np.argsort(key, kind="stable")
+    order = morton_order(mean, model_id, lo, hi)
     n = len(order)
     m = mean[order]
     n_chunks = (n + ANCHOR_CHUNK - 1) // ANCHOR_CHUNK

@@ -1,37 +1,25 @@
 """GPU-side harness shared by the `-m gpu` tests (and the smoke check).
 
 Runs the CUDA path through the C ABI (``paper_2504_17954_gb300``) and compares it with the
-FP64 oracle under the certification rules for float32-vs-float64 near-ties:
-
-* a Gaussian-view record is *uncertain* when its float64 radius 3 sqrt(lambda_max) lies within
-  1e-5 (relative) of an integer, or an edge (u +- r) of its tile rectangle lies within 1e-3 px
-  of a tile boundary (its tile membership may legitimately differ), when its float64 camera
-  depth lies within 2^-40 (relative to |t_z| + sum |R_zk mu_k|) of a float32 rounding midpoint
-  (the kernel's depth, the exact depth rounded once from a compensated float32 evaluation, may
-  round the other way, so its place in the depth order may differ), or within 1e-6 of the near
-  plane (the kernel decides on the float32 depth and near plane);
-* a pixel is *excused* from the 2e-4 image tolerance only if the oracle's own decision record
-  for it shows a near-tie (|ln(255 alpha)|, |ln(T'/1e-4)| or the relative |P| below 1e-3) or it
-  lies in a tile touched (one tile of slack) by an uncertain record.
-The number of excused pixels is returned so tests can bound it.
+FP64 oracle under the certification rules for float32-vs-float64 near-ties of
+``oracle/certify.py`` (re-exported here): uncertain records (radius, rectangle edge, depth
+rounding, near plane) and excused pixels (the oracle's own near-tie record, or a tile touched by
+an uncertain record). The number of excused pixels is returned so tests can bound it.
 """
 from __future__ import annotations
 
-import math
 from typing import List
 
 import numpy as np
 
 import oracle
 import scenegen as sg
+from oracle.certify import (DEPTH_MARGIN, MARGIN, NEAR_MARGIN, RADIUS_MARGIN, RECT_MARGIN_PX,  # noqa: F401
+                            compare_image, depth_uncertain, near_plane_uncertain, near_tie,
+                            uncertain_records, uncertain_tile_mask)
 from paper_2504_17954_gb300 import Gaussians, Rasterizer, compose_edit
 
 IMG_TOL = 2e-4
-MARGIN = 1e-3
-RADIUS_MARGIN = 1e-5
-RECT_MARGIN_PX = 1e-3
-DEPTH_MARGIN = 2.0 ** -40
-NEAR_MARGIN = 1e-6
 
 
 def device_models(models) -> List[Gaussians]:
@@ -73,63 +61,6 @@ def oracle_last_gaussian(offs: np.ndarray, lists: np.ndarray, last: np.ndarray) 
     has = last > 0
     out[has] = lists[offs[:-1][has] + last[has].astype(np.int64) - 1]
     return out
-
-
-def depth_uncertain(p: oracle.Projected) -> np.ndarray:
-    """Live records whose float32 sort key may legitimately differ from the oracle's."""
-    return (p.radius > 0) & (p.depth_margin < DEPTH_MARGIN)
-
-
-def near_plane_uncertain(p: oracle.Projected, znear: float = sg.ZNEAR) -> np.ndarray:
-    """Records that either side may cull at the near plane (the oracle's float64 z is within
-    NEAR_MARGIN of it); their footprint is unknown where the oracle culled them."""
-    return np.abs(p.depth - znear) < NEAR_MARGIN
-
-
-def uncertain_records(p: oracle.Projected, tile: int = 16) -> np.ndarray:
-    live = p.radius > 0
-    unc = live & (p.radius_margin < RADIUS_MARGIN)
-    unc |= depth_uncertain(p) | near_plane_uncertain(p)
-    r = p.radius.astype(np.float64)
-    for e in (p.uv[:, 0] - r, p.uv[:, 0] + r, p.uv[:, 1] - r, p.uv[:, 1] + r):
-        q = e / tile
-        d = np.abs(q - np.round(q)) * tile
-        unc |= live & (d < RECT_MARGIN_PX)
-    return unc
-
-
-def uncertain_tile_mask(p: oracle.Projected, unc: np.ndarray, W: int, H: int, tile: int = 16) -> np.ndarray:
-    gx, gy = (W + tile - 1) // tile, (H + tile - 1) // tile
-    mask = np.zeros((gy, gx), bool)
-    if (unc & near_plane_uncertain(p)).any():  # a record at the near plane may cover any pixel
-        mask[:] = True
-    for g in np.nonzero(unc)[0]:
-        u, v = p.uv[g]
-        r = p.radius[g] + 1
-        x0 = max(int(math.floor((u - r) / tile)) - 1, 0)
-        x1 = min(int(math.floor((u + r) / tile)) + 2, gx)
-        y0 = max(int(math.floor((v - r) / tile)) - 1, 0)
-        y1 = min(int(math.floor((v + r) / tile)) + 2, gy)
-        if x0 < x1 and y0 < y1:
-            mask[y0:y1, x0:x1] = True
-    return np.kron(mask, np.ones((tile, tile), bool))[:H, :W]
-
-
-def near_tie(margins: np.ndarray) -> np.ndarray:
-    return (margins[..., 0] < MARGIN) | (margins[..., 1] < MARGIN) | (margins[..., 2] < MARGIN)
-
-
-def compare_image(gpu: np.ndarray, ref: np.ndarray, margins: np.ndarray, extra_excuse=None, tol=IMG_TOL):
-    """Returns (max error over non-excused pixels, number excused, number of pixels over tol)."""
-    err = np.abs(gpu.astype(np.float64) - ref).max(-1)
-    over = err > tol
-    ok_excuse = near_tie(margins)
-    if extra_excuse is not None:
-        ok_excuse |= extra_excuse
-    bad = over & ~ok_excuse
-    excused = over & ok_excuse
-    strict = np.where(excused, 0.0, err)
-    return float(strict.max()) if strict.size else 0.0, int(excused.sum()), int(bad.sum())
 
 
 def gpu_keys(rast: Rasterizer):

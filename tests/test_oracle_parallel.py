@@ -1,6 +1,6 @@
 """The all-core oracle driver (oracle/parallel.py) against the single-threaded oracle: the same
-C routines over ranges of Gaussians and tiles, so the image, final T, last contributors and
-decision margins are bit for bit the same, and the gradients (per-thread sums added at the
+C routines over ranges of Gaussians, tile-row bands and tiles, so the sorted pairs, the image,
+final T, last contributors and decision margins are bit for bit the same, and the gradients (per-thread sums added at the
 end) agree to float64 rounding."""
 import numpy as np
 
@@ -22,7 +22,9 @@ def test_parallel_oracle_equals_the_serial_one():
     np.testing.assert_array_equal(T, ref.final_T[0])
     np.testing.assert_array_equal(last, ref.last[0])
     np.testing.assert_array_equal(mg, ref.margins[0])
+    np.testing.assert_array_equal(bins.keys, ref.bins.keys)
     np.testing.assert_array_equal(bins.values, ref.bins.values)
+    np.testing.assert_array_equal(bins.ranges, ref.bins.ranges)
     dl = np.random.default_rng(93).normal(0, 1, (cam.H, cam.W, 4))
     gref = oracle.render_backward(ref, [cam], [dl], bg=bg)
     params, dedit, dlight = parallel.render_backward_view_parallel(comp, table, cam, p, bins, dl, bg, threads=5)
