@@ -145,8 +145,11 @@ typedef struct {
 } ivrgs_gaussians;
 
 /* Projected Gaussians, one record per (view v, Gaussian g) at index v * n + g.
-   xy [.][2] = (u, v) pixel-space mean; conic_o [.][4] = (a, b, c, o') with (a, b; b, c) the
-   inverse of Sigma' and o' the edited opacity; rgbd [.][4] = (r, g, b, depth) shaded colour
+   xy [.][2] = (u, v) pixel-space mean; conic_o [.][4] = (g, b, c, o') with K = (a, b; b, c) the
+   inverse of Sigma', g = a - b^2 / c = 1 / Sigma'_xx (K in completed-square form: the exponent
+   -(a e_x^2 + 2 b e_x e_y + c e_y^2) / 2 is evaluated as -(c (e_y + (b/c) e_x)^2 + g e_x^2) / 2,
+   which keeps its float32 rounding small for long, thin Gaussians) and o' the edited opacity;
+   rgbd [.][4] = (r, g, b, depth) shaded colour
    and camera-space depth; radius [.] = ceil(3 sqrt(lambda_max)) in pixels, 0 if culled
    (the other fields of a culled record are unspecified). */
 typedef struct {
@@ -190,7 +193,18 @@ int32_t ivrgs_version(void);
    look-back (0, one kernel per pass) or reduce-then-scan (1: a histogram kernel, a per-digit
    scan and the scatter; no device-side waits); "sort_early" (0 or 1): in the tile-id passes, a
    look-back radix tile publishes its digit counts after (0) or before (1) ranking its keys (the
-   depth passes always publish before). Results are identical for every setting.
+   depth passes always publish before); "render_split" (0 to 4): both blends walk every tile's
+   run with one CTA (2, the default), or cut runs longer than "render_split_min" entries (32,
+   64, 128, 256, 384 (default), 512, 768, 1024, 2048 or 4096) into up to 8 chunks walked by
+   the 8 CTAs of a thread-block cluster whose partial results merge through distributed shared
+   memory (1), or do so when the call has fewer than 3072 tiles (0), or do so in the backward
+   only, when the call has fewer than 3072 tiles (3), or walk the runs longer than
+   render_split_min unsplit in a launch of their own, started first, when the call has fewer
+   than 3072 tiles (4). The kernel of the long runs runs on a library-owned stream beside the
+   kernel of the other tiles (forked from and joined back to the caller's stream, capturable).
+   Results are identical for
+   every setting, except that the split walk regroups the float32 transmittance products (last
+   bits; a termination decision only at a float32 near-tie).
    Returns IVRGS_ERR_INVALID_ARG for an unknown name or value. */
 ivrgs_status ivrgs_set_option(const char* name, int64_t value);
 ivrgs_status ivrgs_get_option(const char* name, int64_t* value);
@@ -248,7 +262,7 @@ ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera*
    composited value unchanged): a pair is emitted only if its tile meets the Gaussian's
    opacity cut-off ellipse, q(e) = a e_x^2 + 2 b e_x e_y + c e_y^2 <= 2 ln(255 o') + 0.25 for
    some point e of the box spanned by the tile's pixel centres (conic (a, b, c) and o' from
-   p->conic_o). Outside that
+   p->conic_o, a = g + b^2 / c). Outside that
    ellipse alpha < 1/255, so the compositing skips the Gaussian at every pixel of a dropped
    tile. The lists are the rectangle lists above with those pairs removed, in the same order.
    Conics with a c > 4096 (a c - b^2) keep their whole rectangle.
@@ -350,7 +364,9 @@ ivrgs_status ivrgs_render_backward_accumulate(const ivrgs_gaussians* g, const fl
    view-Gaussian record plus 256) must fit, i.e. n * n_views <= 932,060; a larger request
    returns IVRGS_ERR_CAPACITY before anything is launched.
    The first call on a device looks up the array's device address with that device current
-   and caches it, so make that first call before any stream capture. Every call uses the
+   and caches it with the current CUDA context, so make that first call before any stream
+   capture; a call under a different context (after cudaDeviceReset, say) looks the address
+   up again, and that call too belongs before any capture. Every call uses the
    same array and leaves its contents behind (each call clears what must start at zero);
    calls that overlap on the GPU -- concurrent streams, host threads or processes sharing
    the context -- race on the array, so the caller must serialise them. */
@@ -382,8 +398,9 @@ ivrgs_status ivrgs_image_loss_workspace(const ivrgs_camera* cams, int32_t n_view
    similarity with an 11 x 11 Gaussian window (sigma 1.5, normalised), C1 = 0.01^2, C2 = 0.03^2,
    zero padding at each view's border. d_rgba, d_target: packed images [.][4] (alpha ignored),
    16-byte aligned. Writes d_loss[0..2] = (loss, L1, SSIM) and d_dL_drgba [.][4] = dloss/d(r, g,
-   b) with 0 for alpha, for the views' pixels only. Workspace: ivrgs_image_loss_workspace bytes,
-   256-byte aligned. */
+   b) with 0 for alpha, for the views' pixels only. With lambda_ssim = 0 (the plain L1 loss) the
+   SSIM passes are skipped and d_loss[2] is written as 0. Workspace: ivrgs_image_loss_workspace
+   bytes, 256-byte aligned. */
 ivrgs_status ivrgs_image_loss(const float* d_rgba, const float* d_target, const ivrgs_camera* cams, int32_t n_views,
                               float lambda_ssim, void* d_workspace, size_t ws_bytes, float* d_loss,
                               float* d_dL_drgba, void* stream);

@@ -1,13 +1,15 @@
 """Autotuner for the library's launch shapes.
 
-Times every combination of the options ``ivrgs_set_option`` accepts (pixels per thread of the
-forward and backward blend, radix ranking) on the caller's own workload with CUDA events, keeps
-the fastest, and caches the choice in a JSON file keyed by GPU name and a workload signature.
-Every option gives the same results, so tuning changes speed only.
+Searches the options ``ivrgs_set_option`` accepts (pixels per thread of the forward and backward
+blend, the split walk of long runs over CTA clusters and its chunk length, radix ranking and
+offsets) on the caller's own workload with CUDA events: coordinate descent from the current
+setting, one option at a time over all its values, repeated until a sweep changes nothing (at
+most ``sweeps`` times). The choice is cached in a JSON file keyed by GPU name and a workload
+signature. Every option gives the same results (up to float32 rounding in the split walk), so
+tuning changes speed only.
 """
 from __future__ import annotations
 
-import itertools
 import json
 import os
 from typing import Callable, Dict, Optional
@@ -19,6 +21,8 @@ from . import _native as N
 SPACE = {
     "render_pixels_per_thread": (0, 1, 2, 4, 8),
     "render_bwd_pixels_per_thread": (0, 1, 2, 4, 8),
+    "render_split": (0, 1, 2, 3, 4),
+    "render_split_min": (128, 256, 384, 768, 1024),
     "sort_match": (0, 1),
     "sort_scan": (0, 1),
     "sort_early": (0, 1),
@@ -56,7 +60,7 @@ def time_ms(step: Callable[[], None], reps: int = 5) -> float:
 
 
 def tune(step: Callable[[], None], signature: str, reps: int = 5, use_cache: bool = True,
-         space: Optional[Dict[str, tuple]] = None) -> Dict[str, int]:
+         space: Optional[Dict[str, tuple]] = None, sweeps: int = 2) -> Dict[str, int]:
     """Pick the fastest option combination for ``step`` and apply it.
 
     ``signature`` names the workload (sizes, views); the result is cached per GPU name."""
@@ -74,19 +78,32 @@ def tune(step: Callable[[], None], signature: str, reps: int = 5, use_cache: boo
         choice = cache[key]["choice"]
         apply(choice)
         return choice
-    before = current()
-    results = []
     names = list(space)
-    for combo in itertools.product(*(space[k] for k in names)):
-        choice = dict(zip(names, combo))
-        apply(choice)
-        results.append((time_ms(step, reps), choice))
-    results.sort(key=lambda r: r[0])
-    best = results[0][1]
+    start = current()
+    best = {k: start[k] if start.get(k) in space[k] else space[k][0] for k in names}
+    apply(best)
+    seen = {}
+
+    def measure(choice):
+        sig = tuple(choice[k] for k in names)
+        if sig not in seen:
+            apply(choice)
+            seen[sig] = time_ms(step, reps)
+        return seen[sig]
+    best_ms = default_ms = measure(best)
+    for _ in range(sweeps):
+        changed = False
+        for k in names:
+            for val in space[k]:
+                trial = dict(best, **{k: val})
+                t = measure(trial)
+                if t < best_ms:
+                    best, best_ms, changed = trial, t, True
+        if not changed:
+            break
     apply(best)
     if use_cache:
-        cache[key] = {"choice": best, "ms": results[0][0], "default_ms": next(t for t, c in results if c == before)
-                      if any(c == before for _, c in results) else None}
+        cache[key] = {"choice": best, "ms": best_ms, "default_ms": default_ms, "evaluated": len(seen)}
         try:
             os.makedirs(os.path.dirname(path), exist_ok=True)
             with open(path, "w") as f:

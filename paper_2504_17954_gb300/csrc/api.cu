@@ -3,6 +3,7 @@
 
 #include <cstdio>
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -17,6 +18,51 @@ Options& options() {
 }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+struct SideStream {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+constexpr int kMaxSideDevices = 64;
+SideStream g_side[kMaxSideDevices];
+std::mutex g_side_mu;       // guards creation
+std::mutex g_side_pair_mu;  // held from split_fork to split_join
+int g_side_dev = -1;
+}  // namespace
+
+cudaError_t split_fork(cudaStream_t s, cudaStream_t* side) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxSideDevices) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lk(g_side_mu);
+        SideStream& ss = g_side[dev];
+        if (!ss.side) {
+            if ((e = cudaStreamCreateWithFlags(&ss.side, cudaStreamNonBlocking)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+            if ((e = cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+        }
+    }
+    g_side_pair_mu.lock();
+    g_side_dev = dev;
+    SideStream& ss = g_side[dev];
+    if ((e = cudaEventRecord(ss.fork, s)) != cudaSuccess || (e = cudaStreamWaitEvent(ss.side, ss.fork, 0)) != cudaSuccess) {
+        g_side_pair_mu.unlock();
+        return e;
+    }
+    *side = ss.side;
+    return cudaSuccess;
+}
+
+cudaError_t split_join(cudaStream_t s) {
+    SideStream& ss = g_side[g_side_dev];
+    cudaError_t e = cudaEventRecord(ss.join, ss.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ss.join, 0);
+    g_side_pair_mu.unlock();
+    return e;
+}
 
 ivrgs_status cuda_status(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return IVRGS_OK;
@@ -168,6 +214,20 @@ ivrgs_status ivrgs_set_option(const char* name, int64_t value) {
         (k == "render_pixels_per_thread" ? options().render_ppt : options().render_bwd_ppt) = (int)value;
         return IVRGS_OK;
     }
+    if (k == "render_split") {
+        if (value < 0 || value > 4)
+            return invalid(k + " must be 0 (by tile count), 1 (always), 2 (never), 3 (backward only) or 4 (long "
+                               "runs first, unsplit)");
+        options().render_split = (int)value;
+        return IVRGS_OK;
+    }
+    if (k == "render_split_min") {
+        bool ok = false;
+        for (int c : {32, 64, 128, 256, 384, 512, 768, 1024, 2048, 4096}) ok = ok || value == c;
+        if (!ok) return invalid(k + " must be one of 32, 64, 128, 256, 384, 512, 768, 1024, 2048, 4096");
+        options().render_split_min = (int)value;
+        return IVRGS_OK;
+    }
     if (k == "sort_match" || k == "sort_scan" || k == "sort_early") {
         if (value != 0 && value != 1) return invalid(k + " must be 0 or 1");
         (k == "sort_match" ? options().sort_match : k == "sort_scan" ? options().sort_scan : options().sort_early) =
@@ -186,6 +246,8 @@ ivrgs_status ivrgs_get_option(const char* name, int64_t* value) {
     else if (k == "sort_match") *value = options().sort_match;
     else if (k == "sort_scan") *value = options().sort_scan;
     else if (k == "sort_early") *value = options().sort_early;
+    else if (k == "render_split") *value = options().render_split;
+    else if (k == "render_split_min") *value = options().render_split_min;
     else return invalid("unknown option '" + k + "'");
     return IVRGS_OK;
 }

@@ -15,9 +15,14 @@
 // registers and pushed through the view-independent parts (quaternion, scale, edits) once.
 // The conic's gradient reaches Sigma' through the eigenbasis of Sigma', which keeps long, thin
 // Gaussians' scale and rotation gradients free of cancellation in float32.
+#include <climits>
+#include <cooperative_groups.h>
+
 #include "blend_alpha.cuh"
 #include "f32x2.cuh"
 #include "gauss_math.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ivrgs {
 
@@ -56,62 +61,70 @@ __device__ __forceinline__ float warp_sum8_transposed(const float v[8], int lane
     return x;
 }
 
-// Per tile, P vertically adjacent pixels per thread; each warp covers a compact band of rows.
-// With 4 pixels per thread the register budget is set for 18 CTAs per SM (56 registers, no
-// spills), two more than the compiler's own choice.
+// Per-thread state of the backward walk of P pixels: T just behind the entries still to walk
+// (recovered by division while walking back), DS = dL/dC . S - dL/dA T_final with S the colour
+// accumulated behind (sum over the contributors behind of T_j alpha_j c_j, plus T_final bg), the
+// pixel's dL/dRGBA and its last contributor (1 + position in the run).
 template <int P>
-__global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
-    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
-    const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
-    float3 bg, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
-    const float4* __restrict__ dL, float4* __restrict__ g0, float4* __restrict__ g1, float* __restrict__ g2) {
-    constexpr int NT = kTilePix / P;
-    constexpr int kBatch = 256;
-    __shared__ float4 s_a[kBatch];
-    __shared__ float4 s_b[kBatch];
-    __shared__ float2 s_c[kBatch];
-    __shared__ long long s_gi[kBatch];
-    __shared__ unsigned s_max;
-    const long long tile = blockIdx.x;
-    const int v = view_of_tile(cb, tile);
-    const CamDev& cam = cb.c[v];
-    const int local = (int)(tile - cam.tile0);
-    const int tx = local % cam.gx, ty = local / cam.gx;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
-    const float fx = (float)px + 0.5f;
-    // offset of this thread's first row in its 4-row group (0 whenever P is a multiple of 4,
-    // since py0 is then one too: known at compile time, so the groups are indexed statically)
-    const int q0 = (P % 4 == 0) ? 0 : (py0 & 3);
-    const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
-    constexpr int NG = (P + 3) / 4;                       // 4-row exponent groups a thread spans
-    const uint2 rg = ranges[tile];
-    const long long vbase = (long long)v * n;
-    const int lane = threadIdx.x & 31;
-
-    // per pixel: T (recovered walking back) and DS = dL/dC . S - dL/dA T_final with
-    // S = sum over the contributors behind the current one of T_j alpha_j c_j + T_final bg
+struct BwdPix {
     float T[P], DS[P];
     float4 d[P];
     unsigned my_last[P];
-    F2 T2[P / 2 > 0 ? P / 2 : 1], DS2[P / 2 > 0 ? P / 2 : 1];  // even P: the same, as pixel pairs
-    F2 DX2[P / 2 > 0 ? P / 2 : 1], DY2[P / 2 > 0 ? P / 2 : 1], DZ2[P / 2 > 0 ? P / 2 : 1];
+};
+
+// Back-to-front walk of the entries [e_lo, e_top) of a tile's run for this thread's P pixels
+// from their state, adding the per-Gaussian record gradients; e_top is at most the CTA's largest
+// last contributor and w_top the warp's (entries at or beyond it are skipped by the whole warp).
+// e_lo and e_top are the same for every thread of the CTA.
+constexpr int kBwdBatch = 256;
+
+// The backward state of this thread's P pixels from the forward's final T and last contributor
+// and dL/dRGBA (DS = T_final (dL/dC . bg - dL/dA)); returns the largest last contributor.
+template <int P>
+__device__ __forceinline__ unsigned bwd_init(const CamDev& cam, int px, int py0, float3 bg,
+                                             const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
+                                             const float4* __restrict__ dL, BwdPix<P>& st) {
     unsigned mx = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const int py = py0 + p;
         float Tf = 1.0f;
-        my_last[p] = 0;
-        d[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        st.my_last[p] = 0;
+        st.d[p] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (px < cam.W && py < cam.H) {
             const long long pix = cam.pix0 + (long long)py * cam.W + px;
             Tf = final_T[pix];
-            my_last[p] = last_in[pix];
-            d[p] = dL[pix];
+            st.my_last[p] = last_in[pix];
+            st.d[p] = dL[pix];
         }
-        T[p] = Tf;
-        DS[p] = Tf * (d[p].x * bg.x + d[p].y * bg.y + d[p].z * bg.z - d[p].w);
-        mx = max(mx, my_last[p]);
+        st.T[p] = Tf;
+        st.DS[p] = Tf * (st.d[p].x * bg.x + st.d[p].y * bg.y + st.d[p].z * bg.z - st.d[p].w);
+        mx = max(mx, st.my_last[p]);
+    }
+    return mx;
+}
+
+template <int P>
+__device__ __forceinline__ void bwd_walk(int e_lo, int e_top, int w_top, const float2* __restrict__ xy,
+                                         const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+                                         long long n, const unsigned* __restrict__ values, unsigned run0,
+                                         long long vbase, float fx, float fyg, int q0, BwdPix<P>& st, float4* s_a,
+                                         float4* s_b, float2* s_c, long long* s_gi, float4* __restrict__ g0,
+                                         float4* __restrict__ g1, float* __restrict__ g2) {
+    constexpr int NT = kTilePix / P;
+    constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
+    const int lane = threadIdx.x & 31;
+    float T[P], DS[P];
+    float4 d[P];
+    unsigned my_last[P];
+    F2 T2[P / 2 > 0 ? P / 2 : 1], DS2[P / 2 > 0 ? P / 2 : 1];  // even P: the same, as pixel pairs
+    F2 DX2[P / 2 > 0 ? P / 2 : 1], DY2[P / 2 > 0 ? P / 2 : 1], DZ2[P / 2 > 0 ? P / 2 : 1];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        T[p] = st.T[p];
+        DS[p] = st.DS[p];
+        d[p] = st.d[p];
+        my_last[p] = st.my_last[p];
     }
     if constexpr (P % 2 == 0) {
 #pragma unroll
@@ -123,22 +136,15 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
             DZ2[h] = f2(d[2 * h].z, d[2 * h + 1].z);
         }
     }
-    if (threadIdx.x == 0) s_max = 0u;
-    __syncthreads();
-    atomicMax(&s_max, mx);
-    __syncthreads();
-    const int max_last = (int)s_max;
-    const int warp_last = (int)__reduce_max_sync(0xffffffffu, mx);
-
-    for (int b_end = max_last; b_end > 0; b_end -= kBatch) {
-        const int b_start = max(0, b_end - kBatch);
+    for (int b_end = e_top; b_end > e_lo; b_end -= kBwdBatch) {
+        const int b_start = max(e_lo, b_end - kBwdBatch);
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kBatch / NT; ++q) {
+        for (int q = 0; q < kBwdBatch / NT; ++q) {
             const int slot = threadIdx.x + q * NT;
             const int e = b_end - 1 - slot;
             if (e >= b_start) {
-                const unsigned g = values[rg.x + e];
+                const unsigned g = values[run0 + e];
                 long long gi = vbase + g;
                 float4 sa, sb;
                 float2 sc;
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
         }
         __syncthreads();
         // entries at or beyond every lane's last contributor are skipped by the whole warp
-        const int j0 = max(0, b_end - warp_last);
+        const int j0 = max(0, b_end - w_top);
         const int cnt = b_end - b_start;
         for (int j = j0; j < cnt; ++j) {
             const int ee = b_end - 1 - j;
@@ -178,7 +184,7 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
             for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                p2[p] = row_p2(rgp[(q0 + p) >> 2], bb, (q0 + p) & 3);
+                p2[p] = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
                 ok0[p] = ee < (int)my_last[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
                 any = any || ok0[p];
             }
@@ -288,14 +294,16 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
             const long long gi = s_gi[j];
             float* t0 = reinterpret_cast<float*>(g0 + gi);
             float* t1 = reinterpret_cast<float*>(g1 + gi);
-            // moments -> (du, dv, da, db, dc): P = p2 / log2(e), p2 = A' dx^2 + B' dx dy + C' dy^2
-            //   du = (2 A' m1 + B' m2)/log2e, dv = (B' m1 + 2 C' m2)/log2e,
+            // moments -> (du, dv, da, db, dc): P = p2 / log2(e), p2 = C' (dy + beta dx)^2 + G' dx^2
+            //   (staged C' = a.z, beta = a.w, G' = bb.x), so with t = beta m1 + m2
+            //   du = 2 (G' m1 + C' beta t)/log2e, dv = 2 C' t/log2e,
             //   da = -m3/2, db = -m4, dc = -m5/2
-            const float il = 1.0f / kLog2e;
+            const float il = 2.0f / kLog2e;
+            const float tm = fmaf(a.w, vv[0], vv[1]);
             if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction
                 if (contrib) {
-                    const float du = (2.0f * a.z * vv[0] + a.w * vv[1]) * il;
-                    const float dv = (a.w * vv[0] + 2.0f * bb.x * vv[1]) * il;
+                    const float du = fmaf(bb.x, vv[0], a.z * a.w * tm) * il;
+                    const float dv = a.z * tm * il;
                     atomicAdd(reinterpret_cast<float4*>(t0), make_float4(du, dv, -0.5f * vv[2], -vv[3]));
                     atomicAdd(reinterpret_cast<float4*>(t1), make_float4(-0.5f * vv[4], vv[5], vv[6], vv[7]));
                     atomicAdd(&g2[gi], vb);
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
             } else {
                 // every lane turns its moments into (du, dv, da, db, dc) first (linear, so the sum
                 // is the same): no lane-dependent branches after the reduction
-                const float tv[8] = {(2.0f * a.z * vv[0] + a.w * vv[1]) * il, (a.w * vv[0] + 2.0f * bb.x * vv[1]) * il,
+                const float tv[8] = {fmaf(bb.x, vv[0], a.z * a.w * tm) * il, a.z * tm * il,
                                      -0.5f * vv[2], -vv[3], -0.5f * vv[4], vv[5], vv[6], vv[7]};
                 const float x = warp_sum8_transposed(tv, lane);  // lane holds the total of index lane >> 2
                 vb = warp_sum(vb);
@@ -312,6 +320,209 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
                 if (lane == 0) atomicAdd(&g2[gi], vb);
             }
         }
+    }
+}
+
+// Per tile, P vertically adjacent pixels per thread; each warp covers a compact band of rows.
+// With 4 pixels per thread the register budget is set for 18 CTAs per SM (56 registers, no
+// spills), two more than the compiler's own choice.
+template <int P>
+__global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
+    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
+    const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
+    float3 bg, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
+    const float4* __restrict__ dL, float4* __restrict__ g0, float4* __restrict__ g1, float* __restrict__ g2,
+    int split_min) {
+    __shared__ float4 s_a[kBwdBatch];
+    __shared__ float4 s_b[kBwdBatch];
+    __shared__ float2 s_c[kBwdBatch];
+    __shared__ long long s_gi[kBwdBatch];
+    __shared__ unsigned s_max;
+    const long long tile = blockIdx.x;
+    const int v = view_of_tile(cb, tile);
+    const CamDev& cam = cb.c[v];
+    const int local = (int)(tile - cam.tile0);
+    const int tx = local % cam.gx, ty = local / cam.gx;
+    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
+    const float fx = (float)px + 0.5f;
+    // offset of this thread's first row in its 4-row group (0 whenever P is a multiple of 4,
+    // since py0 is then one too: known at compile time, so the groups are indexed statically)
+    const int q0 = (P % 4 == 0) ? 0 : (py0 & 3);
+    const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
+    const uint2 rg = ranges[tile];
+    BwdPix<P> st;
+    const unsigned mx = bwd_init<P>(cam, px, py0, bg, final_T, last_in, dL, st);
+    if (threadIdx.x == 0) s_max = 0u;
+    __syncthreads();
+    atomicMax(&s_max, mx);
+    __syncthreads();
+    const int top = (int)s_max;
+    // tile selection as in k_render: split_min >= 0 keeps the walks of at most split_min entries,
+    // split_min < 0 the walks longer than -split_min - 1
+    const int len = min((int)(rg.y - rg.x), top);
+    if (split_min >= 0 ? len > split_min : len <= -split_min - 1) return;
+    bwd_walk<P>(0, top, (int)__reduce_max_sync(0xffffffffu, mx), xy, conic_o, rgbd, n, values, rg.x,
+                (long long)v * n, fx, fyg, q0, st, s_a, s_b, s_c, s_gi, g0, g1, g2);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Split backward for tiles with long runs: a cluster of kSplit CTAs per tile, CTA k walking the
+// chunk [lo_k, hi_k) of the run back to front (the chunks as in the split forward). Each chunk
+// needs the transmittance just behind its part of the walk and DS, the colour accumulated
+// behind it dotted with dL/dC. Both follow from per-chunk forward partials over the pixel's
+// contributors (entries before its last contributor): T_k = prod (1 - alpha) and
+// D_k = dL/dC . sum T_local alpha c (from T_local = 1). With T_pre_k = prod_{j<k} T_j, the chunk
+// walks back from T_pre_k T_k (from T_final in the chunk holding the last contributor) and
+// DS = T_final (dL/dC . bg - dL/dA) + sum_{j>k} T_pre_j D_j. The partials travel through
+// distributed shared memory. Only walks longer than split_min entries are split; k_render_bwd,
+// launched after, takes every other tile.
+// ---------------------------------------------------------------------------------------------
+// Forward partials of the entries [lo, hi) over each pixel's contributors (entries before its
+// last contributor with alpha >= 1/255): T_k and D_k as above. lo, hi uniform per CTA.
+template <int P>
+__device__ __forceinline__ void bwd_chunk_partial(int lo, int hi, const float2* __restrict__ xy,
+                                                  const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+                                                  long long n, const unsigned* __restrict__ values, unsigned run0,
+                                                  long long vbase, float fx, float fyg, int q0, const BwdPix<P>& st,
+                                                  float (&Tk)[P], float (&Dk)[P], float4* s_a, float4* s_b,
+                                                  float2* s_c) {
+    constexpr int NT = kTilePix / P;
+    constexpr int NG = (P + 3) / 4;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        Tk[p] = 1.0f;
+        Dk[p] = 0.0f;
+    }
+    for (int b0 = lo; b0 < hi; b0 += kBwdBatch) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kBwdBatch / NT; ++q) {
+            const int slot = threadIdx.x + q * NT;
+            const int e = b0 + slot;
+            if (e < hi) {
+                const unsigned g = values[run0 + e];
+                float4 sa, sb;
+                float2 sc;
+                if (g < (unsigned long long)n) {
+                    const long long gi = vbase + g;
+                    stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
+                } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
+                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                                   sa, sb, sc);
+                }
+                s_a[slot] = sa;
+                s_b[slot] = sb;
+                s_c[slot] = sc;
+            }
+        }
+        __syncthreads();
+        const int cnt = min(kBwdBatch, hi - b0);
+        for (int j = 0; j < cnt; ++j) {
+            const int e = b0 + j;
+            const float4 a = s_a[j];
+            const float4 bb = s_b[j];
+            const float2 cc = s_c[j];
+            RowGroup rgp[NG];
+#pragma unroll
+            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float p2 = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
+                const bool ok = e < (int)st.my_last[p] && p2 <= 0.0f && p2 >= cc.y;
+                const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
+                const bool add = ok && alpha >= kAlphaMin;
+                const float w = add ? alpha * Tk[p] : 0.0f;
+                const float4 dd = st.d[p];
+                Dk[p] = fmaf(w, dd.x * bb.z + dd.y * bb.w + dd.z * cc.x, Dk[p]);
+                Tk[p] = add ? Tk[p] * (1.0f - alpha) : Tk[p];
+            }
+        }
+    }
+}
+
+template <int P>
+__global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k_render_bwd_split(
+    const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
+    const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
+    float3 bg, int split_min, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
+    const float4* __restrict__ dL, float4* __restrict__ g0, float4* __restrict__ g1, float* __restrict__ g2) {
+    __shared__ float4 s_a[kBwdBatch];
+    __shared__ float4 s_b[kBwdBatch];
+    __shared__ float2 s_c[kBwdBatch];
+    __shared__ long long s_gi[kBwdBatch];
+    __shared__ float s_T[kTilePix], s_D[kTilePix];
+    __shared__ unsigned s_max;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const long long tile = blockIdx.x / kSplit;
+    const int v = view_of_tile(cb, tile);
+    const CamDev& cam = cb.c[v];
+    const int local = (int)(tile - cam.tile0);
+    const int tx = local % cam.gx, ty = local / cam.gx;
+    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
+    const float fx = (float)px + 0.5f;
+    const int q0 = (P % 4 == 0) ? 0 : (py0 & 3);
+    const float fyg = (float)(py0 - q0) + 0.5f;
+    const uint2 rg = ranges[tile];
+    const long long vbase = (long long)v * n;
+    BwdPix<P> st;
+    const unsigned mx = bwd_init<P>(cam, px, py0, bg, final_T, last_in, dL, st);
+    if (threadIdx.x == 0) s_max = 0u;
+    __syncthreads();
+    atomicMax(&s_max, mx);
+    __syncthreads();
+    const int cta_last = (int)s_max, warp_last = (int)__reduce_max_sync(0xffffffffu, mx);
+    int nc, lo, hi;
+    split_chunk(min((int)(rg.y - rg.x), cta_last), split_min, rank, nc, lo, hi);
+    if (nc == 1) return;  // a short walk: k_render_bwd takes it (the whole cluster leaves, before any cluster barrier)
+    int pl[P];  // pixel index within the tile
+#pragma unroll
+    for (int p = 0; p < P; ++p) pl[p] = (threadIdx.x / kTile) * P * kTile + p * kTile + (threadIdx.x & (kTile - 1));
+    // 1. per-chunk forward partials (one chunk: not needed)
+    float Tk[P], Dk[P];
+    if (nc > 1 && rank < nc) {
+        bwd_chunk_partial<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, st, Tk, Dk, s_a, s_b, s_c);
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            Tk[p] = 1.0f;
+            Dk[p] = 0.0f;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        s_T[pl[p]] = Tk[p];
+        s_D[pl[p]] = Dk[p];
+    }
+    cl.sync();
+    // 2. the state just behind this chunk's part of the walk
+    if (nc > 1 && rank < nc) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            float t = 1.0f, behind = 0.0f, tpre = 1.0f;
+            for (int j = 0; j < nc; ++j) {
+                const float Tj = *cl.map_shared_rank(&s_T[pl[p]], j);
+                if (j == rank) tpre = t;
+                if (j > rank) behind = fmaf(t, *cl.map_shared_rank(&s_D[pl[p]], j), behind);
+                t *= Tj;
+            }
+            const int last = (int)st.my_last[p];
+            if (last > lo && last <= hi) {  // the chunk holding the last contributor: behind it, T_final
+                // (st.T, st.DS as initialised)
+            } else if (last > hi) {
+                st.T[p] = tpre * Tk[p];
+                st.DS[p] += behind;
+            }
+        }
+    }
+    cl.sync();  // every CTA has read the partials it needs
+    // 3. walk back over the chunk
+    if (rank < nc) {
+        const int top = min(hi, cta_last);
+        bwd_walk<P>(lo, top, min(hi, warp_last), xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, st, s_a, s_b,
+                    s_c, s_gi, g0, g1, g2);
     }
 }
 
@@ -679,18 +890,59 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
         const float3 bgc = make_float3(bg[0], bg[1], bg[2]);
         const float4* dl = reinterpret_cast<const float4*>(dL);
         const int ppt = blend_ppt(options().render_bwd_ppt, cb.n_tiles, true);
+        // with the split walk, walks longer than split_min go to the cluster kernel, on a side
+        // stream beside k_render_bwd, which takes the rest; without it, k_render_bwd takes every tile
+        const bool split = use_split(options().render_split, cb.n_tiles);
+        const int sm = split ? options().render_split_min : INT_MAX;
+        cudaStream_t side = s;
+        if (split && (e = split_fork(s, &side)) != cudaSuccess) return e;
+        if (split && options().render_split == 4) {  // the long walks first, on the side stream, unsplit
+            const int hs = -sm - 1;
+            if (ppt == 1)
+                k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
+                                                                            final_T, last, dl, g0, g1, g2, hs);
+            else if (ppt == 8)
+                k_render_bwd<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb,
+                                                                                bgc, final_T, last, dl, g0, g1, g2, hs);
+            else if (ppt == 4)
+                k_render_bwd<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb,
+                                                                                bgc, final_T, last, dl, g0, g1, g2, hs);
+            else
+                k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb,
+                                                                                bgc, final_T, last, dl, g0, g1, g2, hs);
+        } else if (split) {
+            const unsigned grid = (unsigned)(cb.n_tiles * kSplit);
+            if (ppt == 1)
+                k_render_bwd_split<1><<<grid, kTilePix, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
+                                                                   final_T, last, dl, g0, g1, g2);
+            else if (ppt == 8)
+                k_render_bwd_split<8><<<grid, kTilePix / 8, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
+                                                                       final_T, last, dl, g0, g1, g2);
+            else if (ppt == 4)
+                k_render_bwd_split<4><<<grid, kTilePix / 4, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
+                                                                       final_T, last, dl, g0, g1, g2);
+            else
+                k_render_bwd_split<2><<<grid, kTilePix / 2, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
+                                                                       final_T, last, dl, g0, g1, g2);
+        }
         if (ppt == 1)
             k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, final_T,
-                                                                     last, dl, g0, g1, g2);
+                                                                     last, dl, g0, g1, g2, sm);
         else if (ppt == 8)
             k_render_bwd<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
-                                                                         final_T, last, dl, g0, g1, g2);
+                                                                         final_T, last, dl, g0, g1, g2, sm);
         else if (ppt == 4)
             k_render_bwd<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
-                                                                         final_T, last, dl, g0, g1, g2);
+                                                                         final_T, last, dl, g0, g1, g2, sm);
         else
             k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
-                                                                         final_T, last, dl, g0, g1, g2);
+                                                                         final_T, last, dl, g0, g1, g2, sm);
+        if (split) {
+            const cudaError_t el = cudaGetLastError();
+            const cudaError_t ej = split_join(s);
+            if (el != cudaSuccess) return el;
+            if (ej != cudaSuccess) return ej;
+        }
     }
     if (g->sh && !accumulate && g->n > 0) {  // SH gradients are added view by view
         const size_t nb = (size_t)(g->sh_degree + 1) * (g->sh_degree + 1);

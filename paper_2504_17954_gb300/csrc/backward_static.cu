@@ -4,7 +4,9 @@
 // file-scope device array below, which every GPU that loads the library keeps until the
 // process exits. The host never dereferences the array's name: on the first call on each
 // device the device address is looked up with cudaGetSymbolAddress (with that device
-// current) and cached; that address is handed to the regular backward entry point.
+// current) and cached together with the CUDA context it belongs to; a call under another
+// context (after cudaDeviceReset, or a context the caller created) looks it up again. That
+// address is handed to the regular backward entry point.
 #include <mutex>
 #include <string>
 
@@ -19,6 +21,25 @@ static __device__ __align__(256) unsigned char g_bwd_scratch[kStaticScratchBytes
 
 static std::mutex g_scratch_mu;
 static void* g_scratch_ptr[kMaxDevices] = {};
+static void* g_scratch_ctx[kMaxDevices] = {};
+
+// The calling thread's current CUDA context (the driver's cuCtxGetCurrent, reached through the
+// runtime's entry-point query so that the library needs no link-time driver dependency); NULL
+// when none is current or the query is unavailable.
+static void* current_context() {
+    typedef int (*CtxGetCurrent)(void**);
+    static CtxGetCurrent fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<CtxGetCurrent>(f);
+    }();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 static ivrgs_status scratch_address(void** out) {
     int dev = -1;
@@ -29,11 +50,13 @@ static ivrgs_status scratch_address(void** out) {
         return IVRGS_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    void* ctx = current_context();
+    if (!g_scratch_ptr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_bwd_scratch);
+        e = cudaGetSymbolAddress(&p, g_bwd_scratch);  // also makes the device's context current
         if (e != cudaSuccess) return cuda_status(e, "ivrgs_render_backward_static: cudaGetSymbolAddress");
         g_scratch_ptr[dev] = p;
+        g_scratch_ctx[dev] = ctx ? ctx : current_context();
     }
     *out = g_scratch_ptr[dev];
     return IVRGS_OK;

@@ -6,39 +6,81 @@
 
 namespace ivrgs {
 
-// staged Gaussian: sa = (u, v, A', B'), sb = (C', o', r, g), sc = (b, p2_skip) with
-// A' = -a log2e / 2, B' = -b log2e, C' = -c log2e / 2 (so that p2 = log2(e) * P is one FMA
-// chain) and p2_skip = log2(1 / (255 o')) - 1e-3: below it o' 2^p2 < 1/255 for certain (the
-// margin covers the rounding of log2 and of ex2.approx by orders of magnitude), so the entry
-// can be skipped before the exponential without changing any decision.
+// The exponent P = -(a dx^2 + 2 b dx dy + c dy^2) / 2 of the conic K = (a, b; b, c) is evaluated
+// in its completed-square form P = -(c y^2 + g dx^2) / 2 with y = dy + (b / c) dx and
+// g = a - b^2 / c (the record holds (g, b, c, o')): two non-negative terms, so for long, thin
+// Gaussians the small values of P along the long axis are not differences of large terms (in
+// float32 the expanded form loses ~1e-3 of P at an axis ratio of 80, this one ~3e-5).
+//
+// staged Gaussian: sa = (u, v, C', beta), sb = (G', o', r, g), sc = (b, p2_skip) with
+// C' = -c log2e / 2, beta = b / c, G' = -g log2e / 2 (so that p2 = log2(e) * P = C' y^2 + G' dx^2)
+// and p2_skip = log2(1 / (255 o')) - 1e-3: below it o' 2^p2 < 1/255 for certain (the margin
+// covers the rounding of log2 and of ex2.approx by orders of magnitude), so the entry can be
+// skipped before the exponential without changing any decision.
 __device__ __forceinline__ void stage_gaussian(const float2 m, const float4 co, const float4 cd, float4& sa,
                                                float4& sb, float2& sc) {
-    sa = make_float4(m.x, m.y, (-0.5f * kLog2e) * co.x, (-kLog2e) * co.y);
-    sb = make_float4((-0.5f * kLog2e) * co.z, co.w, cd.x, cd.y);
+    sa = make_float4(m.x, m.y, (-0.5f * kLog2e) * co.z, co.y / co.z);
+    sb = make_float4((-0.5f * kLog2e) * co.x, co.w, cd.x, cd.y);
     const float thr = co.w > 0.0f ? -log2f(255.0f * co.w) - 1e-3f : -INFINITY;
     sc = make_float2(cd.z, co.w > 0.0f ? thr : INFINITY);
 }
 
 // p2 = log2(e) * P over an aligned group of 4 pixel rows of one column. With dx = u - px and
-// dy0 = v - py0 at the group's first row, row py0 + p has dy = dy0 - p and
-//   p2(p) = base - p k1 + p^2 C',  base = A' dx^2 + B' dx dy0 + C' dy0^2,  k1 = B' dx + 2 C' dy0.
-// Forward and backward evaluate exactly these fused operations for every pixel, whatever the
-// number of pixels per thread, so their float32 decisions agree bit for bit.
+// dy0 = v - py0 at the group's first row, row py0 + p has dy = dy0 - p, y = y0 - p with
+// y0 = dy0 + beta dx, and
+//   p2(p) = C' (y0 - p)^2 + G' dx^2 = base - p k1 + p^2 C',  base = C' y0^2 + G' dx^2,  k1 = 2 C' y0.
+// base is a sum of two non-negative terms, and with p <= 3 the expansion over the group's rows
+// adds only rounding of the order of C' itself. Forward and backward evaluate exactly these
+// explicitly rounded operations (no contraction or reordering can make them differ) for every
+// pixel, whatever the number of pixels per thread, so their float32 decisions agree bit for bit.
 struct RowGroup {
     float dx, dy0, base, k1;
 };
 
 __device__ __forceinline__ RowGroup row_group(const float4& sa, const float4& sb, float fx, float fy0) {
     RowGroup q;
-    q.dx = sa.x - fx;
-    q.dy0 = sa.y - fy0;
-    q.base = fmaf(sa.z * q.dx, q.dx, fmaf(sa.w * q.dx, q.dy0, sb.x * q.dy0 * q.dy0));
-    q.k1 = fmaf(2.0f * sb.x, q.dy0, sa.w * q.dx);
+    q.dx = __fsub_rn(sa.x, fx);
+    q.dy0 = __fsub_rn(sa.y, fy0);
+    const float y0 = __fmaf_rn(sa.w, q.dx, q.dy0);
+    const float cy = __fmul_rn(sa.z, y0);
+    q.base = __fmaf_rn(cy, y0, __fmul_rn(__fmul_rn(sb.x, q.dx), q.dx));
+    q.k1 = __fmul_rn(2.0f, cy);
     return q;
 }
 
-__device__ __forceinline__ float row_p2(const RowGroup& q, const float4& sb, int p) {
-    return fmaf(sb.x, (float)(p * p), fmaf(-(float)p, q.k1, q.base));
+__device__ __forceinline__ float row_p2(const RowGroup& q, const float4& sa, int p) {
+    return __fmaf_rn(sa.z, (float)(p * p), __fmaf_rn(-(float)p, q.k1, q.base));
+}
+
+// Position of a thread's pixels in its tile.
+struct TilePos {
+    int px, py0, q0;
+    float fx, fyg;
+};
+
+template <int P>
+__device__ __forceinline__ TilePos tile_pos(const CamDev& cam, long long tile) {
+    TilePos t;
+    const int local = (int)(tile - cam.tile0);
+    const int tx = local % cam.gx, ty = local / cam.gx;
+    t.px = tx * kTile + (threadIdx.x & (kTile - 1));
+    t.py0 = ty * kTile + (threadIdx.x / kTile) * P;
+    t.fx = (float)t.px + 0.5f;
+    t.q0 = t.py0 & 3;                              // offset of this thread's first row in its group
+    t.fyg = (float)(t.py0 - t.q0) + 0.5f;          // centre of the group's first row
+    return t;
+}
+
+// Split walk of a long run over a cluster of kSplit CTAs: a run of len entries is cut into nc
+// chunks of equal length (nc = 1 up to split_min entries, else ceil(len / split_min), at most
+// kSplit); CTA `rank` takes [lo, hi).
+constexpr int kSplit = 8;
+
+__device__ __forceinline__ void split_chunk(int len, int split_min, int rank, int& nc, int& lo, int& hi) {
+    nc = len <= split_min ? 1 : min(kSplit, (len + split_min - 1) / split_min);
+    const int ch = (len + nc - 1) / nc;
+    lo = min(len, rank * ch);
+    hi = min(len, lo + ch);
 }
 
 __device__ __forceinline__ float fast_rcp(float x) {

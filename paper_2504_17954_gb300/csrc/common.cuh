@@ -97,6 +97,11 @@ struct Options {
     int sort_match = 0;      // radix ranking: 0 = warp ballots per digit bit, 1 = match.any
     int sort_scan = 0;       // radix offsets: 0 = decoupled look-back (onesweep), 1 = reduce-then-scan
     int sort_early = 0;      // radix tile: 1 = publish its digit counts before ranking (look-back waits less)
+    int render_split = 2;    // blends: 2 = one CTA per tile (the default: measured fastest); 0 = split
+                             // long runs over a CTA cluster when the tiles do not fill the GPU, 1 =
+                             // always, 3 = the backward only (by tile count), 4 = no split, but the
+                             // long runs in a launch of their own, first (by tile count)
+    int render_split_min = 384;  // entries per chunk at least (a run this long or shorter is one chunk)
 };
 Options& options();
 // Pixels per thread of a blend launch over n_tiles tiles: the option, or with 0 (the default) a
@@ -110,7 +115,24 @@ inline int blend_ppt(int option, long long n_tiles, bool backward) {
     if (n_tiles >= kAutoPptTiles) return 4;
     return backward ? 1 : 2;
 }
+// Split walk (a cluster of CTAs per tile, each compositing a chunk of the run) for a blend launch
+// over n_tiles tiles: the option, or by default when the tiles do not fill the GPU (where the
+// heaviest tiles' serial walks set the launch time).
+inline bool use_split(int option, long long n_tiles) {
+    if (option == 1) return true;
+    if (option == 2) return false;
+    return n_tiles < kAutoPptTiles;  // 0, and 3 (the forward checks for 3 itself)
+}
 BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity);
+
+// Fork/join of the split walk: the cluster kernel of the long runs runs on a library stream
+// beside the caller's stream's kernel of the other tiles. fork() makes the side stream wait for
+// the caller's stream and returns it; join() makes the caller's stream wait for the side
+// stream. One side stream and two events per device, created on first use and kept for the
+// process; fork() holds a lock until join() so that host threads cannot interleave the pair.
+// Both steps are capturable (the side stream joins an ongoing capture of the caller's stream).
+cudaError_t split_fork(cudaStream_t s, cudaStream_t* side);
+cudaError_t split_join(cudaStream_t s);
 
 // launchers (each returns cudaGetLastError() of its launches)
 cudaError_t launch_compose(const ivrgs_gaussians* models, int32_t n_models, ivrgs_gaussians* composed,

@@ -18,7 +18,6 @@ struct GaussLocal {
     float qn[4], qlen;       // normalised quaternion, |q|
     float Rq[9];            // rotation of qn
     float sc[3];            // exp(log s)
-    float Sig[6];           // Sigma: xx, xy, xz, yy, yz, zz
     float nn[3], nlen;      // normalised normal, |n|
     float cv[3];            // c_p + dc
     float k[4], kp[4];      // stored k and edited k' = lambda k + b
@@ -114,15 +113,6 @@ __device__ __forceinline__ void load_gauss(const ivrgs_gaussians& g, const float
     G.Rq[3] = 2.f * (x * y + w * z); G.Rq[4] = 1.f - 2.f * (x * x + z * z); G.Rq[5] = 2.f * (y * z - w * x);
     G.Rq[6] = 2.f * (x * z - w * y); G.Rq[7] = 2.f * (y * z + w * x); G.Rq[8] = 1.f - 2.f * (x * x + y * y);
     for (int k = 0; k < 3; ++k) G.sc[k] = expf(ls[k]);
-    float M[9];
-    for (int r = 0; r < 3; ++r)
-        for (int k = 0; k < 3; ++k) M[3 * r + k] = G.Rq[3 * r + k] * G.sc[k];
-    G.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-    G.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-    G.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-    G.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-    G.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-    G.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
     G.nlen = sqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
     const float inl = 1.0f / G.nlen;
     G.nn[0] = nrm[0] * inl; G.nn[1] = nrm[1] * inl; G.nn[2] = nrm[2] * inl;
@@ -155,7 +145,8 @@ struct ViewLocal {
     bool clx, cly;
     float T[6];           // J W (2x3)
     float A, B, C, det;   // Sigma' (dilated) and its determinant
-    float conic[3];
+    float conic[3];       // K = Sigma'^-1 = (a, b; b, c)
+    float gam;            // a - b^2 / c = 1 / A: K's completed-square form (the record's first entry)
     int radius;
     float u, v;
     float depth;
@@ -228,6 +219,15 @@ __device__ __forceinline__ float camera_depth(const float R2[3], float t2, const
     return __fadd_rn(s, c);
 }
 
+// a d - b c with one rounding error (Kahan's algorithm for 2x2 determinants: the product b c is
+// split exactly by an FMA, and its rounding error added back)
+__device__ __forceinline__ float diff_of_products(float a, float d, float b, float c) {
+    const float w = __fmul_rn(b, c);
+    const float e = __fmaf_rn(-b, c, w);
+    const float f = __fmaf_rn(a, d, -w);
+    return __fadd_rn(f, e);
+}
+
 __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& c, float lowpass, ViewLocal& V) {
     V.visible = false;
     // the sort key and the near-plane decision: the exact camera z rounded once to float32
@@ -249,26 +249,34 @@ __device__ __forceinline__ void project_view(const GaussLocal& G, const CamDev& 
         V.T[j] = J00 * c.R[j] + J02 * c.R[6 + j];
         V.T[3 + j] = J11 * c.R[3 + j] + J12 * c.R[6 + j];
     }
-    const float* S = G.Sig;
-    // U = T Sigma (2x3)
-    float U[6];
-    for (int a = 0; a < 2; ++a) {
-        const float* t = V.T + 3 * a;
-        U[3 * a + 0] = t[0] * S[0] + t[1] * S[1] + t[2] * S[2];
-        U[3 * a + 1] = t[0] * S[1] + t[1] * S[3] + t[2] * S[4];
-        U[3 * a + 2] = t[0] * S[2] + t[1] * S[4] + t[2] * S[5];
+    // Sigma' = W W^T + lowpass I with W = T Rq diag(s) (2x3): A and C are sums of squares, B one
+    // dot product, and det(W W^T) the sum of the squared 2x2 minors of W (Cauchy-Binet), so the
+    // determinant is a sum of non-negative terms; for long, thin Gaussians the short axis of
+    // Sigma' is then not lost to cancellation between A C and B^2
+    float W0[3], W1[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        W0[k] = (V.T[0] * G.Rq[k] + V.T[1] * G.Rq[3 + k] + V.T[2] * G.Rq[6 + k]) * G.sc[k];
+        W1[k] = (V.T[3] * G.Rq[k] + V.T[4] * G.Rq[3 + k] + V.T[5] * G.Rq[6 + k]) * G.sc[k];
     }
-    V.A = U[0] * V.T[0] + U[1] * V.T[1] + U[2] * V.T[2] + lowpass;
-    V.B = U[0] * V.T[3] + U[1] * V.T[4] + U[2] * V.T[5];
-    V.C = U[3] * V.T[3] + U[4] * V.T[4] + U[5] * V.T[5] + lowpass;
-    V.det = V.A * V.C - V.B * V.B;
+    const float A0 = W0[0] * W0[0] + W0[1] * W0[1] + W0[2] * W0[2];
+    const float C0 = W1[0] * W1[0] + W1[1] * W1[1] + W1[2] * W1[2];
+    const float m01 = diff_of_products(W0[0], W1[1], W0[1], W1[0]);
+    const float m02 = diff_of_products(W0[0], W1[2], W0[2], W1[0]);
+    const float m12 = diff_of_products(W0[1], W1[2], W0[2], W1[1]);
+    V.A = A0 + lowpass;
+    V.B = W0[0] * W1[0] + W0[1] * W1[1] + W0[2] * W1[2];
+    V.C = C0 + lowpass;
+    V.det = fmaf(lowpass, A0 + C0 + lowpass, m01 * m01 + m02 * m02 + m12 * m12);
     if (!(V.det > 0.0f)) return;
     const float idet = 1.0f / V.det;
     V.conic[0] = V.C * idet;
     V.conic[1] = -V.B * idet;
     V.conic[2] = V.A * idet;
-    const float mid = 0.5f * (V.A + V.C);
-    const float lmax = mid + sqrtf(fmaxf(mid * mid - V.det, 0.0f));
+    V.gam = 1.0f / V.A;
+    // lambda_max = (A + C)/2 + sqrt(((A - C)/2)^2 + B^2): the larger eigenvalue without cancellation
+    const float mid = 0.5f * (V.A + V.C), hd = 0.5f * (V.A - V.C);
+    const float lmax = mid + sqrtf(hd * hd + V.B * V.B);
     V.radius = (int)ceilf(3.0f * sqrtf(lmax));
     if (V.radius <= 0) return;
     V.u = c.fx * tx + c.cx;

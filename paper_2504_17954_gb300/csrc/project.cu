@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256) k_project(const ivrgs_gaussians g, const 
             continue;
         }
         reinterpret_cast<float2*>(out.xy)[o] = make_float2(V.u, V.v);
-        reinterpret_cast<float4*>(out.conic_o)[o] = make_float4(V.conic[0], V.conic[1], V.conic[2], G.o);
+        reinterpret_cast<float4*>(out.conic_o)[o] = make_float4(V.gam, V.conic[1], V.conic[2], G.o);
         reinterpret_cast<float4*>(out.rgbd)[o] = make_float4(V.rgb[0], V.rgb[1], V.rgb[2], V.depth);
         out.radius[o] = V.radius;
     }

@@ -7,63 +7,48 @@
 // Gaussians: the CTA stages each batch (mean, conic pre-scaled by -log2(e)/2 so that the
 // exponent is one FMA chain, opacity, colour), then every pixel walks it. The CTA leaves as
 // soon as every pixel has reached T < 1e-4 (barrier count).
+#include <climits>
+#include <cooperative_groups.h>
+
 #include "blend_alpha.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ivrgs {
 
 constexpr int kBatch = 256;
 
+// Per-thread state of P vertically adjacent pixels of one column of a tile.
 template <int P>
-__global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restrict__ xy,
-                                                         const float4* __restrict__ conic_o,
-                                                         const float4* __restrict__ rgbd, long long n,
-                                                         const unsigned* __restrict__ values,
-                                                         const uint2* __restrict__ ranges,
-                                                         const __grid_constant__ CamBatch cb, float3 bg,
-                                                         float4* __restrict__ rgba, float* __restrict__ final_T,
-                                                         unsigned* __restrict__ last_out) {
-    constexpr int NT = kTilePix / P;
-    __shared__ float4 s_a[kBatch];
-    __shared__ float4 s_b[kBatch];
-    __shared__ float2 s_c[kBatch];
-    const long long tile = blockIdx.x;
-    const int v = view_of_tile(cb, tile);
-    const CamDev& cam = cb.c[v];
-    const int local = (int)(tile - cam.tile0);
-    const int tx = local % cam.gx, ty = local / cam.gx;
-    const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
-    const float fx = (float)px + 0.5f;
-    const int q0 = py0 & 3;                               // offset of this thread's first row in its group
-    const float fyg = (float)(py0 - q0) + 0.5f;            // centre of the group's first row
-    constexpr int NG = (P + 3) / 4;                       // 4-row exponent groups a thread spans
-    const uint2 rg = ranges[tile];
-    const long long vbase = (long long)v * n;
-
+struct FwdPix {
     float C0[P], C1[P], C2[P], T[P];
     unsigned last[P];
-    bool done[P], inside[P];
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const int py = py0 + p;
-        inside[p] = px < cam.W && py < cam.H;
-        C0[p] = C1[p] = C2[p] = 0.f;
-        T[p] = 1.f;
-        last[p] = 0;
-        done[p] = !inside[p];
-    }
-    const int len = (int)(rg.y - rg.x);
-    for (int b0 = 0; b0 < len; b0 += kBatch) {
+    bool done[P];
+};
+
+// Front-to-back walk of the entries [e0, e1) of a tile's run for this thread's P pixels, from
+// their current state. The CTA stages batches of kBatch Gaussians in shared memory and leaves
+// as soon as every pixel is done (barrier count), so e0, e1 must be the same for every thread
+// of the CTA. `last` records 1 + the position of the last added entry in the run.
+template <int P>
+__device__ __forceinline__ void fwd_walk(int e0, int e1, const float2* __restrict__ xy,
+                                         const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+                                         long long n, const unsigned* __restrict__ values, unsigned run0,
+                                         long long vbase, const TilePos& tp, FwdPix<P>& s, float4* s_a, float4* s_b,
+                                         float2* s_c) {
+    constexpr int NT = kTilePix / P;
+    constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
+    for (int b0 = e0; b0 < e1; b0 += kBatch) {
         bool all = true;
 #pragma unroll
-        for (int p = 0; p < P; ++p) all = all && done[p];
+        for (int p = 0; p < P; ++p) all = all && s.done[p];
         if (__syncthreads_count(all) == NT) break;
 #pragma unroll
         for (int q = 0; q < kBatch / NT; ++q) {
             const int slot = threadIdx.x + q * NT;
             const int e = b0 + slot;
-            if (e < len) {
-                const unsigned g = values[rg.x + e];
+            if (e < e1) {
+                const unsigned g = values[run0 + e];
                 float4 sa, sb;
                 float2 sc;
                 if (g < (unsigned long long)n) {
@@ -81,7 +66,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
         __syncthreads();
         // the walk below holds warp-wide votes: a warp skips or leaves it only as a whole
         if (__all_sync(0xffffffffu, all)) continue;
-        const int cnt = min(kBatch, len - b0);
+        const int cnt = min(kBatch, e1 - b0);
         for (int j = 0; j < cnt; ++j) {
             const float4 a = s_a[j];
             const float4 bb = s_b[j];
@@ -91,11 +76,11 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
             bool any = false;
             RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
 #pragma unroll
-            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
+            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, tp.fx, tp.fyg + 4.0f * (float)gq);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                p2[p] = row_p2(rgp[(q0 + p) >> 2], bb, (q0 + p) & 3);
-                ok[p] = !done[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
+                p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
+                ok[p] = !s.done[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
                 any = any || ok[p];
             }
             if (__any_sync(0xffffffffu, any)) {
@@ -105,35 +90,232 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
                 for (int p = 0; p < P; ++p) {
                     const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2[p]));
                     const bool okp = ok[p] && alpha >= kAlphaMin;
-                    const float Tn = T[p] * (1.0f - alpha);
+                    const float Tn = s.T[p] * (1.0f - alpha);
                     const bool stop = okp && Tn < kTMin;
                     const bool add = okp && !stop;
-                    const float w = add ? alpha * T[p] : 0.0f;
-                    C0[p] = fmaf(w, bb.z, C0[p]);
-                    C1[p] = fmaf(w, bb.w, C1[p]);
-                    C2[p] = fmaf(w, cc.x, C2[p]);
-                    T[p] = add ? Tn : T[p];
-                    last[p] = add ? idx : last[p];
-                    done[p] = done[p] || stop;
+                    const float w = add ? alpha * s.T[p] : 0.0f;
+                    s.C0[p] = fmaf(w, bb.z, s.C0[p]);
+                    s.C1[p] = fmaf(w, bb.w, s.C1[p]);
+                    s.C2[p] = fmaf(w, cc.x, s.C2[p]);
+                    s.T[p] = add ? Tn : s.T[p];
+                    s.last[p] = add ? idx : s.last[p];
+                    s.done[p] = s.done[p] || stop;
                 }
             }
             if ((j & 7) == 7) {
                 bool mine = true;
 #pragma unroll
-                for (int p = 0; p < P; ++p) mine = mine && done[p];
+                for (int p = 0; p < P; ++p) mine = mine && s.done[p];
                 if (__all_sync(0xffffffffu, mine)) break;
             }
         }
     }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restrict__ xy,
+                                                         const float4* __restrict__ conic_o,
+                                                         const float4* __restrict__ rgbd, long long n,
+                                                         const unsigned* __restrict__ values,
+                                                         const uint2* __restrict__ ranges,
+                                                         const __grid_constant__ CamBatch cb, float3 bg,
+                                                         float4* __restrict__ rgba, float* __restrict__ final_T,
+                                                         unsigned* __restrict__ last_out, int split_min) {
+    __shared__ float4 s_a[kBatch];
+    __shared__ float4 s_b[kBatch];
+    __shared__ float2 s_c[kBatch];
+    const long long tile = blockIdx.x;
+    const uint2 rg = ranges[tile];
+    // tile selection: split_min >= 0 keeps the runs of at most split_min entries (the others go
+    // to k_render_split, or to a launch of their own), split_min < 0 the runs longer than
+    // -split_min - 1
+    const int len = (int)(rg.y - rg.x);
+    if (split_min >= 0 ? len > split_min : len <= -split_min - 1) return;
+    const int v = view_of_tile(cb, tile);
+    const CamDev& cam = cb.c[v];
+    const TilePos tp = tile_pos<P>(cam, tile);
+    FwdPix<P> s;
+    bool inside[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        inside[p] = tp.px < cam.W && tp.py0 + p < cam.H;
+        s.C0[p] = s.C1[p] = s.C2[p] = 0.f;
+        s.T[p] = 1.f;
+        s.last[p] = 0;
+        s.done[p] = !inside[p];
+    }
+    fwd_walk<P>(0, (int)(rg.y - rg.x), xy, conic_o, rgbd, n, values, rg.x, (long long)v * n, tp, s, s_a, s_b, s_c);
 #pragma unroll
     for (int p = 0; p < P; ++p)
         if (inside[p]) {
-            const int py = py0 + p;
-            const long long pix = cam.pix0 + (long long)py * cam.W + px;
-            rgba[pix] = make_float4(C0[p] + T[p] * bg.x, C1[p] + T[p] * bg.y, C2[p] + T[p] * bg.z, 1.0f - T[p]);
-            final_T[pix] = T[p];
-            last_out[pix] = last[p];
+            const long long pix = cam.pix0 + (long long)(tp.py0 + p) * cam.W + tp.px;
+            rgba[pix] = make_float4(s.C0[p] + s.T[p] * bg.x, s.C1[p] + s.T[p] * bg.y, s.C2[p] + s.T[p] * bg.z,
+                                    1.0f - s.T[p]);
+            final_T[pix] = s.T[p];
+            last_out[pix] = s.last[p];
         }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Split walk for tiles with long runs (the run of a tile is one serial chain per pixel; on a
+// view whose few hundred heavy tiles carry most of the entries, the heaviest tile's chain sets the
+// launch time). A thread-block cluster of kSplit CTAs takes one tile; CTA k composites the
+// chunk [k ch, (k + 1) ch) of the run from T = 1, so the chunks run on kSplit SMs at once.
+// Front-to-back "over" is associative: with per-chunk colour C_k and transmittance T_k, the
+// pixel is sum_k T_pre_k C_k, T_pre_k = prod_{j<k} T_j. The one coupling is the termination at
+// T < 1e-4, which depends on the transmittance in front of the chunk: a chunk whose pixel walk
+// stopped on its own (T_k fell below 1e-4 from 1) or whose T_pre_k T_k is below 1e-4 holds the
+// pixel's termination; that chunk is walked again from T_pre_k with the sequential rule (exact
+// termination entry and last contributor), and the chunks behind it are dropped. The partial
+// results travel through distributed shared memory. Only runs longer than split_min entries
+// are split: their clusters are the only ones that stay, and k_render, launched after, walks
+// every other tile (a cluster per light tile would hold 8 CTA slots for one CTA's work).
+// Products regroup, so T can differ from the sequential walk in the last bits (a termination
+// decision only at a float32 near-tie).
+// ---------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
+    k_render_split(const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+                   long long n, const unsigned* __restrict__ values, const uint2* __restrict__ ranges,
+                   const __grid_constant__ CamBatch cb, float3 bg, int split_min, float4* __restrict__ rgba,
+                   float* __restrict__ final_T, unsigned* __restrict__ last_out) {
+    __shared__ float4 s_a[kBatch];
+    __shared__ float4 s_b[kBatch];
+    __shared__ float2 s_c[kBatch];
+    __shared__ float s_T[kTilePix], s_C0[kTilePix], s_C1[kTilePix], s_C2[kTilePix];
+    __shared__ unsigned s_last[kTilePix];
+    __shared__ int s_state[kTilePix];  // after the walk: 1 stopped in the chunk; after the merge: 0 dropped,
+                                       // 1 passed, 2 holds the termination
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const long long tile = blockIdx.x / kSplit;
+    const int v = view_of_tile(cb, tile);
+    const CamDev& cam = cb.c[v];
+    const TilePos tp = tile_pos<P>(cam, tile);
+    const uint2 rg = ranges[tile];
+    const long long vbase = (long long)v * n;
+    int nc, lo, hi;
+    split_chunk((int)(rg.y - rg.x), split_min, rank, nc, lo, hi);
+    if (nc == 1) return;  // a short run: k_render walks it (the whole cluster leaves, before any cluster barrier)
+    const bool active = rank < nc;
+    FwdPix<P> s;
+    bool inside[P];
+    int pl[P];  // pixel index within the tile
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        inside[p] = tp.px < cam.W && tp.py0 + p < cam.H;
+        pl[p] = (threadIdx.x / kTile) * P * kTile + p * kTile + (threadIdx.x & (kTile - 1));
+        s.C0[p] = s.C1[p] = s.C2[p] = 0.f;
+        s.T[p] = 1.f;
+        s.last[p] = 0;
+        s.done[p] = !inside[p];
+    }
+    // 1. every active CTA walks its chunk from T = 1 (CTA 0's walk is the sequential one)
+    if (active) fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, s, s_a, s_b, s_c);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        s_T[pl[p]] = s.T[p];
+        s_state[pl[p]] = (inside[p] && s.done[p]) ? 1 : 0;
+    }
+    cl.sync();
+    // 2. transmittance in front of this chunk and whether an earlier chunk holds the termination
+    float Tpre[P];
+    int state[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        float t = 1.0f;
+        bool ended = false;
+        for (int j = 0; j < rank && j < nc; ++j) {
+            const float Tj = *cl.map_shared_rank(&s_T[pl[p]], j);
+            const int stop_j = *cl.map_shared_rank(&s_state[pl[p]], j);
+            if (!ended) {
+                if (stop_j || t * Tj < kTMin) ended = true;
+                else t *= Tj;
+            }
+        }
+        Tpre[p] = t;
+        if (!active || ended || !inside[p]) state[p] = 0;
+        else if (rank > 0 && (s.done[p] || t * s.T[p] < kTMin)) state[p] = 2;
+        else state[p] = 1;
+    }
+    cl.sync();  // every CTA has read the chunk results it needs
+    // 3. the chunk holding a pixel's termination is walked again from T_pre (sequential rule)
+    bool rewalk = false;
+#pragma unroll
+    for (int p = 0; p < P; ++p) rewalk = rewalk || state[p] == 2;
+    if (__syncthreads_or(rewalk)) {
+        FwdPix<P> r;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            r.C0[p] = r.C1[p] = r.C2[p] = 0.f;
+            r.T[p] = Tpre[p];
+            r.last[p] = 0;
+            r.done[p] = state[p] != 2;
+        }
+        fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, r, s_a, s_b, s_c);
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+            if (state[p] == 2) {
+                s.C0[p] = r.C0[p];
+                s.C1[p] = r.C1[p];
+                s.C2[p] = r.C2[p];
+                s.T[p] = r.T[p];
+                s.last[p] = r.last[p];
+            }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const bool scale = state[p] == 1 && rank > 0;  // a passed chunk's colour seen through T_pre
+        s_C0[pl[p]] = state[p] == 0 ? 0.f : (scale ? Tpre[p] * s.C0[p] : s.C0[p]);
+        s_C1[pl[p]] = state[p] == 0 ? 0.f : (scale ? Tpre[p] * s.C1[p] : s.C1[p]);
+        s_C2[pl[p]] = state[p] == 0 ? 0.f : (scale ? Tpre[p] * s.C2[p] : s.C2[p]);
+        s_T[pl[p]] = scale ? Tpre[p] * s.T[p] : s.T[p];
+        s_last[pl[p]] = state[p] == 0 ? 0u : s.last[p];
+        s_state[pl[p]] = state[p];
+    }
+    cl.sync();
+    // 4. CTA 0 adds the chunks in order and writes the pixels
+    if (rank == 0) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            if (!inside[p]) continue;
+            float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+            unsigned last = 0;
+            for (int j = 0; j < nc; ++j) {
+                if (*cl.map_shared_rank(&s_state[pl[p]], j) == 0) continue;
+                C0 += *cl.map_shared_rank(&s_C0[pl[p]], j);
+                C1 += *cl.map_shared_rank(&s_C1[pl[p]], j);
+                C2 += *cl.map_shared_rank(&s_C2[pl[p]], j);
+                T = *cl.map_shared_rank(&s_T[pl[p]], j);
+                const unsigned lj = *cl.map_shared_rank(&s_last[pl[p]], j);
+                last = lj > 0 ? lj : last;
+            }
+            const long long pix = cam.pix0 + (long long)(tp.py0 + p) * cam.W + tp.px;
+            rgba[pix] = make_float4(C0 + T * bg.x, C1 + T * bg.y, C2 + T * bg.z, 1.0f - T);
+            final_T[pix] = T;
+            last_out[pix] = last;
+        }
+    }
+    cl.sync();  // the other CTAs' shared memory stays alive until CTA 0 has read it
+}
+
+// k_render over every tile whose run has at most split_min entries
+static cudaError_t launch_render_tiles(const float2* xy, const float4* co, const float4* cd, long long n,
+                                       const ivrgs_bins* b, const uint2* rg, const CamBatch& cb, float3 bgc,
+                                       float4* out, float* final_T, uint32_t* last, int ppt, int sm, cudaStream_t s) {
+    if (ppt == 1)
+        k_render<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
+                                                             last, sm);
+    else if (ppt == 8)
+        k_render<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
+                                                                 last, sm);
+    else if (ppt == 4)
+        k_render<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
+                                                                 last, sm);
+    else
+        k_render<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
+                                                                 last, sm);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const CamBatch& cb, const float* bg,
@@ -147,19 +329,45 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
     const float3 bgc = make_float3(bg[0], bg[1], bg[2]);
     float4* out = reinterpret_cast<float4*>(rgba);
     const int ppt = blend_ppt(options().render_ppt, cb.n_tiles, false);
-    if (ppt == 1)
-        k_render<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out, final_T,
-                                                             last);
-    else if (ppt == 8)
-        k_render<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
-                                                                 final_T, last);
-    else if (ppt == 4)
-        k_render<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
-                                                                 final_T, last);
-    else
-        k_render<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, out,
-                                                                 final_T, last);
-    return cudaGetLastError();
+    // with the split walk, runs longer than split_min go to the cluster kernel, on a side stream
+    // beside k_render, which takes the rest; without it, k_render takes every tile
+    const bool split = use_split(options().render_split, cb.n_tiles) && options().render_split != 3;
+    const int sm = split ? options().render_split_min : INT_MAX;
+    if (split && options().render_split == 4) {  // the long runs first, on the side stream, unsplit
+        cudaStream_t side;
+        cudaError_t e = split_fork(s, &side);
+        if (e != cudaSuccess) return e;
+        e = launch_render_tiles(xy, co, cd, p->n, b, rg, cb, bgc, out, final_T, last, ppt, -sm - 1, side);
+        cudaError_t e2 = cudaSuccess;
+        if (e == cudaSuccess) e2 = launch_render_tiles(xy, co, cd, p->n, b, rg, cb, bgc, out, final_T, last, ppt, sm, s);
+        const cudaError_t e3 = split_join(s);
+        return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+    }
+    if (split) {
+        cudaStream_t side;
+        cudaError_t e = split_fork(s, &side);
+        if (e != cudaSuccess) return e;
+        const unsigned grid = (unsigned)(cb.n_tiles * kSplit);
+        if (ppt == 1)
+            k_render_split<1><<<grid, kTilePix, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out, final_T,
+                                                            last);
+        else if (ppt == 8)
+            k_render_split<8><<<grid, kTilePix / 8, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out,
+                                                               final_T, last);
+        else if (ppt == 4)
+            k_render_split<4><<<grid, kTilePix / 4, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out,
+                                                               final_T, last);
+        else
+            k_render_split<2><<<grid, kTilePix / 2, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out,
+                                                               final_T, last);
+        e = cudaGetLastError();
+        cudaError_t e2 = cudaSuccess;
+        if (e == cudaSuccess) e2 = launch_render_tiles(xy, co, cd, p->n, b, rg, cb, bgc, out, final_T, last, ppt, sm, s);
+        const cudaError_t e3 = split_join(s);
+        return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+    }
+    return launch_render_tiles(xy, co, cd, p->n, b, rg, cb, bgc, out, final_T, last, ppt, sm, s);
 }
+
 
 }  // namespace ivrgs

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restric
             const float4 bb = s_b[j];
             const float2 cc = s_c[j];
             const RowGroup rgp = row_group(a, bb, fx, fyg);
-            const float p2 = row_p2(rgp, bb, q0);
+            const float p2 = row_p2(rgp, a, q0);
             const bool ok = !done && p2 <= 0.0f && p2 >= cc.y;
             if (__any_sync(0xffffffffu, ok)) {
                 const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));

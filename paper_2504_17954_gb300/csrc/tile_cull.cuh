@@ -1,7 +1,8 @@
 // Tile culling by the opacity cut-off ellipse (IVRGS_BIN_CULL).
 //
 // The compositing skips a Gaussian wherever alpha = min(0.99, o' G) < 1/255 (Sec. 3 blend, with
-// the 1/255 threshold of 3DGS). With conic (a, b, c), e = pixel - centre and
+// the 1/255 threshold of 3DGS). With conic (a, b, c) (the record holds (g, b, c, o'), g = a -
+// b^2 / c, so a = g + b^2 / c and det = a c - b^2 = g c without cancellation), e = pixel - centre and
 // q(e) = a e_x^2 + 2 b e_x e_y + c e_y^2 we have G = exp(-q/2), so the Gaussian changes no pixel
 // where q > tau = 2 ln(255 o'). A tile of its square rectangle in which every pixel centre has
 // q > tau can therefore be dropped from the tile lists without changing any composited value,
@@ -53,8 +54,8 @@ __device__ __forceinline__ CullEll cull_setup(float2 uv, float4 co, int enabled)
     e.ba = e.inv_a = e.ta = e.det = e.Y = e.eyR = 0.0f;
     e.mode = 2;
     if (!enabled) return e;
-    const float a = co.x, b = co.y, c = co.z, o = co.w;
-    if (!(isfinite(a) && isfinite(b) && isfinite(c) && isfinite(o) && isfinite(uv.x) && isfinite(uv.y))) return e;
+    const float g = co.x, b = co.y, c = co.z, o = co.w;
+    if (!(isfinite(g) && isfinite(b) && isfinite(c) && isfinite(o) && isfinite(uv.x) && isfinite(uv.y))) return e;
     const float s = __fmul_rn(255.0f, o);
     if (!(s > 0.0f)) {  // o' <= 0: alpha = 0 everywhere
         e.mode = 0;
@@ -65,8 +66,10 @@ __device__ __forceinline__ CullEll cull_setup(float2 uv, float4 co, int enabled)
         e.mode = 0;
         return e;
     }
-    const float det = __fmaf_rn(a, c, -__fmul_rn(b, b));
-    if (!(a > 0.0f) || !(c > 0.0f) || !(det > 0.0f) || __fmul_rn(a, c) > __fmul_rn(kCullCond, det)) return e;
+    if (!(c > 0.0f)) return e;
+    const float a = __fmaf_rn(b, __fdiv_rn(b, c), g);
+    const float det = __fmul_rn(g, c);
+    if (!(a > 0.0f) || !(det > 0.0f) || !isfinite(a) || __fmul_rn(a, c) > __fmul_rn(kCullCond, det)) return e;
     e.inv_a = cull_div(1.0f, a);
     e.ba = __fmul_rn(b, e.inv_a);
     e.ta = __fmul_rn(tau, a);

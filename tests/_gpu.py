@@ -8,6 +8,7 @@ an uncertain record). The number of excused pixels is returned so tests can boun
 """
 from __future__ import annotations
 
+import contextlib
 from typing import List
 
 import numpy as np
@@ -106,3 +107,17 @@ def assert_grad(got, want, what, tol=GRAD_TOL):
     l2, el = grad_errors(got, want)
     assert l2 <= tol and el <= tol, f"{what}: relative L2 {l2:.2e}, element-wise {el:.2e} of max |g*| (bar {tol:.0e})"
     return l2, el
+
+
+@contextlib.contextmanager
+def sequential_walk():
+    """Both blends with one CTA per tile (ivrgs option render_split = 2): the split walk regroups
+    the float32 transmittance products by chunk, so bit-identity checks between two renders (or
+    against the auxiliary maps' sequential walk) hold only for the sequential walk."""
+    from paper_2504_17954_gb300 import _native as N
+    old = N.ivrgs_get_option("render_split")
+    N.ivrgs_set_option("render_split", 2)
+    try:
+        yield
+    finally:
+        N.ivrgs_set_option("render_split", old)

@@ -36,7 +36,8 @@ def _compare(gpu_aux, ref_aux, margins, extra=None):
 def test_aux_maps_match_oracle(which):
     w = sg.config1() if which == "cfg1" else _multi_view_scene(seed=81)
     rast, comp, table = _gpu.setup(w)
-    rast.forward(comp, table)
+    with _gpu.sequential_walk():  # the aux walk is the sequential one: compare bit for bit with it
+        rast.forward(comp, table)
     aux = rast.render_aux(comp, table)
     torch.cuda.synchronize()
     assert torch.equal(aux[:, 11], rast.rgba[:, 3])
@@ -63,7 +64,8 @@ def test_aux_maps_mixed_storage():
     from paper_2504_17954_gb300 import Rasterizer, compose_edit
     _, table = compose_edit(None, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias)
     rast = Rasterizer(w.cameras, g.n, M, bg=w.bg)
-    rast.forward(g, table)
+    with _gpu.sequential_walk():
+        rast.forward(g, table)
     aux = rast.render_aux(g, table)
     torch.cuda.synchronize()
     assert torch.equal(aux[:, 11], rast.rgba[:, 3])

@@ -8,10 +8,11 @@ every pixel of that tile, so:
 * each removed pair is skipped by the FP64 oracle at all pixel centres of its tile:
   min(0.99, o' exp(-q/2)) < 1/255 with the oracle's own conic and opacity;
 * images, final transmittances and last contributors are bit-identical with and without
-  culling; the gradients differ only by the order of their float32 atomic sums: with and
-  without culling they meet the gradient bar against the FP64 oracle (1e-3 relative L2 and
-  1e-3 of the largest entry element by element), the thin-Gaussian scene included, and lie
-  within 1e-4 of each other except in that scene (where order noise of its sums shows more).
+  culling, and the images are within 2e-4 of the FP64 oracle; the gradients differ only by the
+  order of their float32 atomic sums: with and without culling they meet the gradient bar
+  against the FP64 oracle (1e-3 relative L2 and 1e-3 of the largest entry element by element),
+  the thin-Gaussian scene included, and lie within 1e-4 of each other except in that scene
+  (where order noise of its sums shows more).
 
 Scenes: the 10k-Gaussian 128^2 case, a three-view scene with colour/opacity/light edits and an
 orbital light, a scene whose opacity edits put many o' around 1/255, and a scene with strongly
@@ -85,8 +86,16 @@ def _max_alpha_over_tile(p, cam, g, tx, ty):
     return out
 
 
+@pytest.fixture
+def sequential_walk():
+    """The blends' one-CTA-per-tile walk: the split walk's chunks follow the list lengths, which
+    culling changes, so only the sequential walk gives bit-identical results on both list kinds."""
+    with _gpu.sequential_walk():
+        yield
+
+
 @pytest.mark.parametrize("which", ["cfg1", "multi", "low_opacity", "elongated"])
-def test_culled_lists_keep_results(which):
+def test_culled_lists_keep_results(which, sequential_walk):
     w = _scene(which)
     rng = np.random.default_rng(35)
     n_pix = sum(c.W * c.H for c in w.cameras)
@@ -105,22 +114,22 @@ def test_culled_lists_keep_results(which):
     # per-(tile, warp) gradient contributions are the same; only the order of the float atomics
     # that sum them differs: both meet the gradient bar against the FP64 oracle.
     ref = oracle.render(w.models, w.edits, w.cameras, bg=w.bg)
+    excused = 0
+    for v, c in enumerate(w.cameras):
+        unc = _gpu.uncertain_records(ref.projs[v])
+        extra = _gpu.uncertain_tile_mask(ref.projs[v], unc, c.W, c.H)
+        err, exc, bad = _gpu.compare_image(r1.view_image(v).cpu().numpy(), ref.images[v], ref.margins[v], extra)
+        assert bad == 0, (which, v, err)
+        excused += exc
+    assert excused <= max(3, 0.001 * r1.n_pix)
     dls = []
     for c in w.cameras:
         off = r0.cam_arr[len(dls)].pix_offset
         dls.append(dl[off:off + c.W * c.H].cpu().numpy().astype(np.float64).reshape(c.H, c.W, 4))
     gref = oracle.render_backward(ref, w.cameras, dls, bg=w.bg)
     for k in oracle.PARAMS:
-        if which == "elongated":
-            # the relative-L2 bar holds; element by element the float32 evaluation of the
-            # quadratic form in pixel coordinates (cancellation ~ the axis ratio squared) limits
-            # the worst Gaussian of this scene to a few 1e-3 of the largest entry
-            e0 = _gpu.grad_errors(g0[k].cpu().numpy(), gref.params[k])
-            e1 = _gpu.grad_errors(g1[k].cpu().numpy(), gref.params[k])
-            assert max(e0[0], e1[0]) <= _gpu.GRAD_TOL and max(e0[1], e1[1]) <= 1e-2, (k, e0, e1)
-        else:
-            e0 = _gpu.assert_grad(g0[k].cpu().numpy(), gref.params[k], f"{k}, rectangle lists")
-            e1 = _gpu.assert_grad(g1[k].cpu().numpy(), gref.params[k], f"{k}, culled lists")
+        e0 = _gpu.assert_grad(g0[k].cpu().numpy(), gref.params[k], f"{k}, rectangle lists")
+        e1 = _gpu.assert_grad(g1[k].cpu().numpy(), gref.params[k], f"{k}, culled lists")
         d01 = _gpu.rel_l2(g1[k].cpu().numpy().astype(np.float64), g0[k].cpu().numpy().astype(np.float64))
         print(f"{which} {k}: vs oracle (L2, element-wise) rect {e0[0]:.2e} {e0[1]:.2e} "
               f"culled {e1[0]:.2e} {e1[1]:.2e}; culled vs rect {d01:.2e}")

@@ -62,8 +62,10 @@ def test_project_matches_oracle(which):
         vis = (rad[v] > 0) & (p.radius > 0)
         assert vis.sum() > 0.5 * (p.radius > 0).sum()
         assert np.abs(xy[v][vis] - p.uv[vis]).max() < 2e-3
+        # the record holds the conic in completed-square form (g, b, c), g = a - b^2/c = 1/Sigma'_xx
+        want = np.c_[1.0 / p.cov[vis, 0], p.conic[vis, 1:]]
         cmax = np.abs(p.conic[vis]).max(1, keepdims=True)
-        assert (np.abs(co[v][vis, :3] - p.conic[vis]) / cmax).max() < 1e-4
+        assert (np.abs(co[v][vis, :3] - want) / cmax).max() < 1e-4
         assert np.abs(co[v][vis, 3] - p.opacity[vis]).max() < 1e-6
         assert np.abs(cd[v][vis, :3] - p.rgb[vis]).max() < 1e-5
         # depth: the float64 camera z rounded once to float32, the same bits on both sides
@@ -158,14 +160,21 @@ def test_bin_capacity_reporting():
 
 # ------------------------------------------------------------------ a5 render-only on shared inputs
 def _shared_records(w):
-    """Oracle float64 projection rounded to float32: the same inputs for both blends."""
+    """Oracle float64 projection rounded to float32: the same inputs for both blends. The
+    conic travels as the record's (g, b, c) (g = 1/Sigma'_xx) rounded to float32 (held in the
+    returned records' `cov` field); the oracle blends the conic those values define,
+    a = g + b^2/c."""
     comp = oracle.compose(w.models)
     tab = oracle.edit_table(w.edits)
     projs = [oracle.project(comp, tab, c) for c in w.cameras]
     f32 = []
     for p in projs:
+        live = p.radius > 0
+        g32 = np.where(live, 1.0 / np.where(live, p.cov[:, 0], 1.0), 1.0).astype(np.float32).astype(np.float64)
+        b32, c32 = (p.conic[:, k].astype(np.float32).astype(np.float64) for k in (1, 2))
+        c32 = np.where(live, c32, 1.0)
         q = oracle.Projected(uv=p.uv.astype(np.float32).astype(np.float64),
-                             cov=p.cov, conic=p.conic.astype(np.float32).astype(np.float64),
+                             cov=np.c_[g32, b32, c32], conic=np.c_[g32 + b32 * b32 / c32, b32, c32],
                              opacity=p.opacity.astype(np.float32).astype(np.float64),
                              rgb=p.rgb.astype(np.float32).astype(np.float64),
                              depth=p.depth.astype(np.float32).astype(np.float64), radius=p.radius,
@@ -182,8 +191,8 @@ def test_render_only_matches_oracle_on_shared_records(which):
     n = projs[0].radius.shape[0]
     rast = Rasterizer(w.cameras, n, len(w.models), bg=w.bg, cull=False)  # lists compared with the oracle's
     rast.xy.copy_(torch.as_tensor(np.concatenate([p.uv for p in projs]).astype(np.float32)))
-    rast.conic_o.copy_(torch.as_tensor(np.concatenate(
-        [np.c_[p.conic, p.opacity] for p in projs]).astype(np.float32)))
+    rast.conic_o.copy_(torch.as_tensor(np.concatenate(  # the record form (g, b, c, o')
+        [np.c_[p.cov, p.opacity] for p in projs]).astype(np.float32)))
     rast.rgbd.copy_(torch.as_tensor(np.concatenate([np.c_[p.rgb, p.depth] for p in projs]).astype(np.float32)))
     rast.radius.copy_(torch.as_tensor(np.concatenate([p.radius for p in projs]).astype(np.int32)))
     rast.bin("exact")
@@ -215,15 +224,25 @@ def test_render_only_matches_oracle_on_shared_records(which):
 
 
 # ------------------------------------------------------------------ end to end forward
-@pytest.fixture(params=[0, 1, 2, 4, 8], ids=["ppt_auto", "ppt1", "ppt2", "ppt4", "ppt8"])
+# blend launch shapes: (pixels per thread, render_split (2 = one CTA per tile, the default; 0 =
+# split by tile count; 1 = split always; 4 = long runs first), entries per chunk). "split32" cuts
+# every run longer than 32 entries into up to 8 chunks over a CTA cluster, "split_auto" splits
+# the small scenes here (few tiles) at the default 384, "longfirst32" walks the runs longer than
+# 32 entries in a launch of their own, first.
+@pytest.fixture(params=[(0, 2, 384), (1, 2, 384), (2, 2, 384), (4, 2, 384), (8, 2, 384), (0, 0, 384), (0, 1, 32),
+                        (4, 1, 32), (1, 1, 32), (0, 4, 32)],
+                ids=["ppt_auto", "ppt1", "ppt2", "ppt4", "ppt8", "split_auto", "split32", "split32_ppt4", "split32_ppt1",
+                     "longfirst32"])
 def pixels_per_thread(request):
     from paper_2504_17954_gb300 import _native as N
-    old = (N.ivrgs_get_option("render_pixels_per_thread"), N.ivrgs_get_option("render_bwd_pixels_per_thread"))
-    N.ivrgs_set_option("render_pixels_per_thread", request.param)
-    N.ivrgs_set_option("render_bwd_pixels_per_thread", request.param)
+    names = ("render_pixels_per_thread", "render_bwd_pixels_per_thread", "render_split", "render_split_min")
+    old = [N.ivrgs_get_option(k) for k in names]
+    ppt, split, smin = request.param
+    for k, val in zip(names, (ppt, ppt, split, smin)):
+        N.ivrgs_set_option(k, val)
     yield request.param
-    N.ivrgs_set_option("render_pixels_per_thread", old[0])
-    N.ivrgs_set_option("render_bwd_pixels_per_thread", old[1])
+    for k, val in zip(names, old):
+        N.ivrgs_set_option(k, val)
 
 
 @pytest.mark.parametrize("which", ["cfg1", "multi"])
