@@ -185,7 +185,7 @@ __device__ __forceinline__ void bwd_walk(int e_lo, int e_top, int w_top, const f
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 p2[p] = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
-                ok0[p] = ee < (int)my_last[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
+                ok0[p] = ee < (int)my_last[p] && in_reach(p2[p], cc.y);
                 any = any || ok0[p];
             }
             if (!__any_sync(0xffffffffu, any)) continue;
@@ -429,13 +429,13 @@ __device__ __forceinline__ void bwd_chunk_partial(int lo, int hi, const float2* 
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const float p2 = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
-                const bool ok = e < (int)st.my_last[p] && p2 <= 0.0f && p2 >= cc.y;
+                const bool ok = e < (int)st.my_last[p] && in_reach(p2, cc.y);
                 const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
                 const bool add = ok && alpha >= kAlphaMin;
                 const float w = add ? alpha * Tk[p] : 0.0f;
                 const float4 dd = st.d[p];
                 Dk[p] = fmaf(w, dd.x * bb.z + dd.y * bb.w + dd.z * cc.x, Dk[p]);
-                Tk[p] = add ? Tk[p] * (1.0f - alpha) : Tk[p];
+                Tk[p] = add ? Tk[p] * (1.0f - alpha) : Tk[p];  // the forward's T (1 - alpha)
             }
         }
     }

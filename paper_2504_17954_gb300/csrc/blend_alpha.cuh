@@ -12,18 +12,25 @@ namespace ivrgs {
 // Gaussians the small values of P along the long axis are not differences of large terms (in
 // float32 the expanded form loses ~1e-3 of P at an axis ratio of 80, this one ~3e-5).
 //
-// staged Gaussian: sa = (u, v, C', beta), sb = (G', o', r, g), sc = (b, p2_skip) with
+// staged Gaussian: sa = (u, v, C', beta), sb = (G', o', r, g), sc = (b, mid) with
 // C' = -c log2e / 2, beta = b / c, G' = -g log2e / 2 (so that p2 = log2(e) * P = C' y^2 + G' dx^2)
-// and p2_skip = log2(1 / (255 o')) - 1e-3: below it o' 2^p2 < 1/255 for certain (the margin
-// covers the rounding of log2 and of ex2.approx by orders of magnitude), so the entry can be
-// skipped before the exponential without changing any decision.
+// and mid = thr / 2, thr = log2(1 / (255 o')) - 1e-3: below thr, o' 2^p2 < 1/255 for certain
+// (the margin covers the rounding of log2 and of ex2.approx by orders of magnitude), so an
+// entry outside [thr, 0] can be skipped before the exponential without changing any decision.
+// The range test is one compare, |p2 - mid| <= -mid (in_reach); mid is NaN for o' <= 0, so
+// that nothing is in reach.
 __device__ __forceinline__ void stage_gaussian(const float2 m, const float4 co, const float4 cd, float4& sa,
                                                float4& sb, float2& sc) {
     sa = make_float4(m.x, m.y, (-0.5f * kLog2e) * co.z, co.y / co.z);
     sb = make_float4((-0.5f * kLog2e) * co.x, co.w, cd.x, cd.y);
-    const float thr = co.w > 0.0f ? -log2f(255.0f * co.w) - 1e-3f : -INFINITY;
-    sc = make_float2(cd.z, co.w > 0.0f ? thr : INFINITY);
+    const float thr = co.w > 0.0f ? -log2f(255.0f * co.w) - 1e-3f : 0.0f;
+    sc = make_float2(cd.z, co.w > 0.0f ? 0.5f * thr : __int_as_float(0x7fc00000));
 }
+
+// p2 in [2 mid, 0] (up to the rounding of p2 - mid, which can only admit p2 within an ulp of
+// an end: values that the alpha cut-off after the exponential decides exactly, or P ~ 0 at the
+// centre, a float32 near-tie of the P > 0 guard)
+__device__ __forceinline__ bool in_reach(float p2, float mid) { return fabsf(__fsub_rn(p2, mid)) <= -mid; }
 
 // p2 = log2(e) * P over an aligned group of 4 pixel rows of one column. With dx = u - px and
 // dy0 = v - py0 at the group's first row, row py0 + p has dy = dy0 - p, y = y0 - p with

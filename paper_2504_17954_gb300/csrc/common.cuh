@@ -97,10 +97,10 @@ struct Options {
     int sort_match = 0;      // radix ranking: 0 = warp ballots per digit bit, 1 = match.any
     int sort_scan = 0;       // radix offsets: 0 = decoupled look-back (onesweep), 1 = reduce-then-scan
     int sort_early = 0;      // radix tile: 1 = publish its digit counts before ranking (look-back waits less)
-    int render_split = 2;    // blends: 2 = one CTA per tile (the default: measured fastest); 0 = split
-                             // long runs over a CTA cluster when the tiles do not fill the GPU, 1 =
-                             // always, 3 = the backward only (by tile count), 4 = no split, but the
-                             // long runs in a launch of their own, first (by tile count)
+    int render_split = 0;    // blends: 0 = split long runs over a CTA cluster when the call has fewer
+                             // than kSplitTiles tiles (the default), 1 = always, 2 = never, 3 = the
+                             // backward only (by tile count), 4 = no split, but the long runs in a
+                             // launch of their own, first (by tile count)
     int render_split_min = 384;  // entries per chunk at least (a run this long or shorter is one chunk)
 };
 Options& options();
@@ -116,12 +116,14 @@ inline int blend_ppt(int option, long long n_tiles, bool backward) {
     return backward ? 1 : 2;
 }
 // Split walk (a cluster of CTAs per tile, each compositing a chunk of the run) for a blend launch
-// over n_tiles tiles: the option, or by default when the tiles do not fill the GPU (where the
-// heaviest tiles' serial walks set the launch time).
+// over n_tiles tiles: the option, or by default below two tiles per SM, where the heaviest tiles'
+// serial walks are the launch (measured on GB300: the 10k-Gaussian 128^2 view, 64 tiles, 2.5x
+// faster fwd+bwd; the 800^2 view, 2500 tiles, 0.7x: there the split's extra work outweighs it).
+constexpr long long kSplitTiles = 304;
 inline bool use_split(int option, long long n_tiles) {
     if (option == 1) return true;
     if (option == 2) return false;
-    return n_tiles < kAutoPptTiles;  // 0, and 3 (the forward checks for 3 itself)
+    return n_tiles < kSplitTiles;  // 0, 3 and 4 (the forward checks for 3 itself)
 }
 BinPlan plan_bin(long long n_records, long long n_tiles, long long capacity);
 

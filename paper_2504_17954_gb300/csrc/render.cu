@@ -80,7 +80,7 @@ __device__ __forceinline__ void fwd_walk(int e0, int e1, const float2* __restric
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
-                ok[p] = !s.done[p] && p2[p] <= 0.0f && p2[p] >= cc.y;
+                ok[p] = !s.done[p] && in_reach(p2[p], cc.y);
                 any = any || ok[p];
             }
             if (__any_sync(0xffffffffu, any)) {

@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restric
             const float2 cc = s_c[j];
             const RowGroup rgp = row_group(a, bb, fx, fyg);
             const float p2 = row_p2(rgp, a, q0);
-            const bool ok = !done && p2 <= 0.0f && p2 >= cc.y;
+            const bool ok = !done && in_reach(p2, cc.y);
             if (__any_sync(0xffffffffu, ok)) {
+                // the forward blend's update (k_render), so that 1 - T equals its alpha bit for bit
                 const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
                 const bool okp = ok && alpha >= kAlphaMin;
                 const float Tn = T * (1.0f - alpha);
