@@ -69,6 +69,32 @@ def uncertain_tile_mask(p: Projected, unc: np.ndarray, W: int, H: int, tile: int
     return np.kron(mask, np.ones((tile, tile), bool))[:H, :W]
 
 
+def uncertain_pixels(p: Projected, unc: np.ndarray, pix: np.ndarray, margin: float = 1e-2) -> np.ndarray:
+    """The pixels pix[k] = (i, j) that an uncertain record reaches: its float64 alpha o' exp(P)
+    at the pixel centre is at least (1/255) e^-margin. A record changes a pixel's compositing only
+    through its alpha there (below the cut-off both sides skip it, wherever it is listed), so a
+    float32 decision about an uncertain record (its tile membership, radius or depth order) can
+    only show at these pixels; a record uncertain at the near plane may cover any pixel. Finer
+    than uncertain_tile_mask, which excuses every pixel of every tile the record touches."""
+    pix = np.asarray(pix, np.int64).reshape(-1, 2)
+    out = np.zeros(len(pix), bool)
+    if len(pix) == 0:
+        return out
+    if (unc & near_plane_uncertain(p)).any():
+        out[:] = True
+        return out
+    cx = pix[:, 0].astype(np.float64) + 0.5
+    cy = pix[:, 1].astype(np.float64) + 0.5
+    cut = math.log(1.0 / 255.0) - margin
+    for g in np.nonzero(unc & (p.opacity > 0))[0]:
+        a, b, c = p.conic[g]
+        dx = p.uv[g, 0] - cx
+        dy = p.uv[g, 1] - cy
+        P = -0.5 * (a * dx * dx + 2.0 * b * dx * dy + c * dy * dy)
+        out |= P + math.log(p.opacity[g]) >= cut
+    return out
+
+
 def near_tie(margins: np.ndarray) -> np.ndarray:
     return (margins[..., 0] < MARGIN) | (margins[..., 1] < MARGIN) | (margins[..., 2] < MARGIN)
 

@@ -72,11 +72,7 @@ struct BwdPix {
     unsigned my_last[P];
 };
 
-// Back-to-front walk of the entries [e_lo, e_top) of a tile's run for this thread's P pixels
-// from their state, adding the per-Gaussian record gradients; e_top is at most the CTA's largest
-// last contributor and w_top the warp's (entries at or beyond it are skipped by the whole warp).
-// e_lo and e_top are the same for every thread of the CTA.
-constexpr int kBwdBatch = 256;
+constexpr int kBwdBatch = 256;  // entries staged per batch
 
 // The backward state of this thread's P pixels from the forward's final T and last contributor
 // and dL/dRGBA (DS = T_final (dL/dC . bg - dL/dA)); returns the largest last contributor.
@@ -104,16 +100,218 @@ __device__ __forceinline__ unsigned bwd_init(const CamDev& cam, int px, int py0,
     return mx;
 }
 
+// Back-to-front walk of nl staged slots of a batch (slot j holds entry b_end - 1 - j of the tile's
+// run): list[0..nl) (in slot order, from band_list) with band_cull, else j0 .. j0 + nl - 1, for
+// this thread's P pixels, adding the per-Gaussian record gradients. The live state comes by
+// reference: T, DS per pixel (for even P as pixel pairs T2, DS2 instead) and the pixels'
+// dL/dRGBA (d; for even P also as pairs DX2, DY2, DZ2). Every lane of a warp calls it with the
+// same slots (the walk holds warp-wide votes).
+template <int P, int H = (P / 2 > 0 ? P / 2 : 1)>
+__device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int nl, int b_end, float fx,
+                                          float fyg, int q0, float (&T)[P], float (&DS)[P], const float4 (&d)[P],
+                                          const unsigned (&my_last)[P], F2 (&T2)[H], F2 (&DS2)[H],
+                                          const F2 (&DX2)[H], const F2 (&DY2)[H], const F2 (&DZ2)[H],
+                                          const float4* s_a, const float4* s_b, const float2* s_c,
+                                          const long long* s_gi, float4* __restrict__ g0, float4* __restrict__ g1,
+                                          float* __restrict__ g2) {
+    constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < nl; ++i) {
+        const int j = band_cull<P>() ? (int)list[i] : j0 + i;
+        const int ee = b_end - 1 - j;
+        const float4 a = s_a[j];
+        const float4 bb = s_b[j];
+        const float2 cc = s_c[j];
+        const float blue = cc.x;
+        // per-thread sums over its pixels: vv = (m1, m2, m3, m4, m5, d o', d r, d g) with the
+        // moments m1 = sum dP dx, m2 = sum dP dy, m3 = sum dP dx^2, m4 = sum dP dx dy,
+        // m5 = sum dP dy^2 (the conic and mean gradients are linear in them); vb = d blue
+        float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float vb = 0.f;
+        float p2[P];
+        bool ok0[P];
+        bool any = false;
+        RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            p2[p] = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
+            ok0[p] = ee < (int)my_last[p] && in_reach(p2[p], cc.y);
+            any = any || ok0[p];
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        bool contrib = false;
+        if constexpr (P % 2 == 0) {
+            // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
+            // the order in which a thread adds its pixels' moments differs)
+            const F2 zero = f2(0.f, 0.f), one = f2(1.f, 1.f);
+            const F2 O2 = f2(bb.y, bb.y), BZ = f2(bb.z, bb.z), BW = f2(bb.w, bb.w), BL = f2(blue, blue);
+            F2 V0 = zero, V1 = zero, V2 = zero, V3 = zero, V4 = zero, V5 = zero, V6 = zero, V7 = zero, VB = zero;
+#pragma unroll
+            for (int h = 0; h < P / 2; ++h) {
+                const int pa = 2 * h, pb = 2 * h + 1;
+                const F2 G = f2(fast_ex2(p2[pa]), fast_ex2(p2[pb]));
+                const F2 RAW = mul2(O2, G);
+                float raw_a, raw_b;
+                split(RAW, raw_a, raw_b);
+                const float al_a = fminf(kAlphaMax, raw_a), al_b = fminf(kAlphaMax, raw_b);
+                const bool ok_a = ok0[pa] && al_a >= kAlphaMin, ok_b = ok0[pb] && al_b >= kAlphaMin;
+                contrib = contrib || ok_a || ok_b;
+                const F2 A = f2(al_a, al_b);
+                float om_a, om_b;
+                split(sub2(one, A), om_a, om_b);
+                const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
+                const F2 TI = mul2(T2[h], R);
+                float wt_a, wt_b;
+                split(mul2(TI, A), wt_a, wt_b);
+                const F2 W = f2(ok_a ? wt_a : 0.0f, ok_b ? wt_b : 0.0f);
+                V6 = fma2(W, DX2[h], V6);
+                V7 = fma2(W, DY2[h], V7);
+                VB = fma2(W, DZ2[h], VB);
+                const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
+                const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
+                DS2[h] = fma2(W, DC, DS2[h]);
+                {
+                    float ti_a, ti_b, t_a, t_b;
+                    split(TI, ti_a, ti_b);
+                    split(T2[h], t_a, t_b);
+                    T2[h] = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
+                }
+                // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
+                // (selected after the product, so that an infinite G never reaches the sums)
+                const bool live_a = ok_a && raw_a < kAlphaMax, live_b = ok_b && raw_b < kAlphaMax;
+                float dp_a, dp_b, dg_a, dg_b;
+                split(mul2(DA, RAW), dp_a, dp_b);
+                split(mul2(DA, G), dg_a, dg_b);
+                const F2 DP = f2(live_a ? dp_a : 0.0f, live_b ? dp_b : 0.0f);
+                V5 = add2(V5, f2(live_a ? dg_a : 0.0f, live_b ? dg_b : 0.0f));
+                const RowGroup& ga = rgp[(q0 + pa) >> 2];
+                const RowGroup& gb = rgp[(q0 + pb) >> 2];
+                const F2 DXP = f2(ga.dx, gb.dx);
+                const F2 DYP = f2(ga.dy0 - (float)((q0 + pa) & 3), gb.dy0 - (float)((q0 + pb) & 3));
+                const F2 PX = mul2(DP, DXP), PY = mul2(DP, DYP);
+                V0 = add2(V0, PX);
+                V1 = add2(V1, PY);
+                V2 = fma2(PX, DXP, V2);
+                V3 = fma2(PX, DYP, V3);
+                V4 = fma2(PY, DYP, V4);
+            }
+            const F2 Vs[8] = {V0, V1, V2, V3, V4, V5, V6, V7};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                float lo, hi;
+                split(Vs[k], lo, hi);
+                vv[k] = lo + hi;
+            }
+            float lo, hi;
+            split(VB, lo, hi);
+            vb = lo + hi;
+        } else {
+            // the P pixels update independently (predicated, no branches) so they interleave
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float G = fast_ex2(p2[p]);
+                const float raw = bb.y * G;
+                const float alpha = fminf(kAlphaMax, raw);
+                const bool ok = ok0[p] && alpha >= kAlphaMin;
+                contrib = contrib || ok;
+                const float r = fast_rcp(1.0f - alpha);
+                const float Ti = T[p] * r;
+                const float w = ok ? Ti * alpha : 0.0f;
+                const float4 dd = d[p];
+                vv[6] = fmaf(w, dd.x, vv[6]);
+                vv[7] = fmaf(w, dd.y, vv[7]);
+                vb = fmaf(w, dd.z, vb);
+                const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
+                const float dalpha = Ti * dc - DS[p] * r;
+                DS[p] = fmaf(w, dc, DS[p]);
+                T[p] = ok ? Ti : T[p];
+                // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
+                // selected rather than multiplied so that an infinite G never reaches the sums)
+                const bool live = ok && raw < kAlphaMax;
+                const float dP = live ? dalpha * raw : 0.0f;
+                vv[5] += live ? dalpha * G : 0.0f;
+                const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
+                const float px_ = dP * dxp, py_ = dP * dyp;
+                vv[0] += px_;
+                vv[1] += py_;
+                vv[2] = fmaf(px_, dxp, vv[2]);
+                vv[3] = fmaf(px_, dyp, vv[3]);
+                vv[4] = fmaf(py_, dyp, vv[4]);
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, contrib);
+        if (m == 0u) continue;
+        const long long gi = s_gi[j];
+        float* t0 = reinterpret_cast<float*>(g0 + gi);
+        float* t1 = reinterpret_cast<float*>(g1 + gi);
+        // moments -> (du, dv, da, db, dc): P = p2 / log2(e), p2 = C' (dy + beta dx)^2 + G' dx^2
+        //   (staged C' = a.z, beta = a.w, G' = bb.x), so with t = beta m1 + m2
+        //   du = 2 (G' m1 + C' beta t)/log2e, dv = 2 C' t/log2e,
+        //   da = -m3/2, db = -m4, dc = -m5/2
+        const float il = 2.0f / kLog2e;
+        const float tm = fmaf(a.w, vv[0], vv[1]);
+        if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction
+            if (contrib) {
+                const float du = fmaf(bb.x, vv[0], a.z * a.w * tm) * il;
+                const float dv = a.z * tm * il;
+                atomicAdd(reinterpret_cast<float4*>(t0), make_float4(du, dv, -0.5f * vv[2], -vv[3]));
+                atomicAdd(reinterpret_cast<float4*>(t1), make_float4(-0.5f * vv[4], vv[5], vv[6], vv[7]));
+                atomicAdd(&g2[gi], vb);
+            }
+        } else {
+            // every lane turns its moments into (du, dv, da, db, dc) first (linear, so the sum
+            // is the same): no lane-dependent branches after the reduction
+            const float tv[8] = {fmaf(bb.x, vv[0], a.z * a.w * tm) * il, a.z * tm * il,
+                                 -0.5f * vv[2], -vv[3], -0.5f * vv[4], vv[5], vv[6], vv[7]};
+            const float x = warp_sum8_transposed(tv, lane);  // lane holds the total of index lane >> 2
+            vb = warp_sum(vb);
+            const int idx = lane >> 2;
+            if ((lane & 3) == 0) atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
+            if (lane == 0) atomicAdd(&g2[gi], vb);
+        }
+    }
+}
+
+// Stages entry e of the tile's run (record values[run0 + e] of view base vbase) in slot `slot`,
+// with its record index for the gradient atomics.
+__device__ __forceinline__ void stage_entry_bwd(int slot, int e, const float2* __restrict__ xy,
+                                                const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+                                                long long n, const unsigned* __restrict__ values, unsigned run0,
+                                                long long vbase, float4* s_a, float4* s_b, float2* s_c,
+                                                long long* s_gi, float2* s_rows) {
+    const unsigned g = values[run0 + e];
+    long long gi = vbase + g;
+    float4 sa, sb;
+    float2 sc;
+    if (g < (unsigned long long)n) {
+        stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
+    } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
+        gi = vbase;
+        stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), sa,
+                       sb, sc);
+    }
+    s_a[slot] = sa;
+    s_b[slot] = sb;
+    s_c[slot] = sc;
+    s_gi[slot] = gi;
+    if (s_rows != nullptr) s_rows[slot] = reach_rows(sa, sb, sc);
+}
+
+// Back-to-front walk of the entries [e_lo, e_top) of a tile's run for this thread's P pixels
+// from their state, adding the per-Gaussian record gradients; e_top is at most the CTA's largest
+// last contributor and w_top the warp's (entries at or beyond it are skipped by the whole warp).
+// e_lo and e_top are the same for every thread of the CTA.
 template <int P>
 __device__ __forceinline__ void bwd_walk(int e_lo, int e_top, int w_top, const float2* __restrict__ xy,
                                          const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
                                          long long n, const unsigned* __restrict__ values, unsigned run0,
-                                         long long vbase, float fx, float fyg, int q0, BwdPix<P>& st, float4* s_a,
-                                         float4* s_b, float2* s_c, long long* s_gi, float4* __restrict__ g0,
-                                         float4* __restrict__ g1, float* __restrict__ g2) {
+                                         long long vbase, float fx, float fyg, int q0, float ylo, BwdPix<P>& st,
+                                         float4* s_a, float4* s_b, float2* s_c, long long* s_gi, float2* s_rows,
+                                         unsigned char* list, float4* __restrict__ g0, float4* __restrict__ g1,
+                                         float* __restrict__ g2) {
     constexpr int NT = kTilePix / P;
-    constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
-    const int lane = threadIdx.x & 31;
     float T[P], DS[P];
     float4 d[P];
     unsigned my_last[P];
@@ -143,183 +341,18 @@ __device__ __forceinline__ void bwd_walk(int e_lo, int e_top, int w_top, const f
         for (int q = 0; q < kBwdBatch / NT; ++q) {
             const int slot = threadIdx.x + q * NT;
             const int e = b_end - 1 - slot;
-            if (e >= b_start) {
-                const unsigned g = values[run0 + e];
-                long long gi = vbase + g;
-                float4 sa, sb;
-                float2 sc;
-                if (g < (unsigned long long)n) {
-                    stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
-                } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
-                    gi = vbase;
-                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                                   sa, sb, sc);
-                }
-                s_a[slot] = sa;
-                s_b[slot] = sb;
-                s_c[slot] = sc;
-                s_gi[slot] = gi;
-            }
+            if (e >= b_start)
+                stage_entry_bwd(slot, e, xy, conic_o, rgbd, n, values, run0, vbase, s_a, s_b, s_c, s_gi,
+                                band_cull<P>() ? s_rows : nullptr);
         }
         __syncthreads();
-        // entries at or beyond every lane's last contributor are skipped by the whole warp
+        // entries at or beyond every lane's last contributor are skipped by the whole warp, and with
+        // band_cull so are those out of reach of the warp's rows
         const int j0 = max(0, b_end - w_top);
-        const int cnt = b_end - b_start;
-        for (int j = j0; j < cnt; ++j) {
-            const int ee = b_end - 1 - j;
-            const float4 a = s_a[j];
-            const float4 bb = s_b[j];
-            const float2 cc = s_c[j];
-            const float blue = cc.x;
-            // per-thread sums over its pixels: vv = (m1, m2, m3, m4, m5, d o', d r, d g) with the
-            // moments m1 = sum dP dx, m2 = sum dP dy, m3 = sum dP dx^2, m4 = sum dP dx dy,
-            // m5 = sum dP dy^2 (the conic and mean gradients are linear in them); vb = d blue
-            float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float vb = 0.f;
-            float p2[P];
-            bool ok0[P];
-            bool any = false;
-            RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
-#pragma unroll
-            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                p2[p] = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
-                ok0[p] = ee < (int)my_last[p] && in_reach(p2[p], cc.y);
-                any = any || ok0[p];
-            }
-            if (!__any_sync(0xffffffffu, any)) continue;
-            bool contrib = false;
-            if constexpr (P % 2 == 0) {
-                // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
-                // the order in which a thread adds its pixels' moments differs)
-                const F2 zero = f2(0.f, 0.f), one = f2(1.f, 1.f);
-                const F2 O2 = f2(bb.y, bb.y), BZ = f2(bb.z, bb.z), BW = f2(bb.w, bb.w), BL = f2(blue, blue);
-                F2 V0 = zero, V1 = zero, V2 = zero, V3 = zero, V4 = zero, V5 = zero, V6 = zero, V7 = zero, VB = zero;
-#pragma unroll
-                for (int h = 0; h < P / 2; ++h) {
-                    const int pa = 2 * h, pb = 2 * h + 1;
-                    const F2 G = f2(fast_ex2(p2[pa]), fast_ex2(p2[pb]));
-                    const F2 RAW = mul2(O2, G);
-                    float raw_a, raw_b;
-                    split(RAW, raw_a, raw_b);
-                    const float al_a = fminf(kAlphaMax, raw_a), al_b = fminf(kAlphaMax, raw_b);
-                    const bool ok_a = ok0[pa] && al_a >= kAlphaMin, ok_b = ok0[pb] && al_b >= kAlphaMin;
-                    contrib = contrib || ok_a || ok_b;
-                    const F2 A = f2(al_a, al_b);
-                    float om_a, om_b;
-                    split(sub2(one, A), om_a, om_b);
-                    const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
-                    const F2 TI = mul2(T2[h], R);
-                    float wt_a, wt_b;
-                    split(mul2(TI, A), wt_a, wt_b);
-                    const F2 W = f2(ok_a ? wt_a : 0.0f, ok_b ? wt_b : 0.0f);
-                    V6 = fma2(W, DX2[h], V6);
-                    V7 = fma2(W, DY2[h], V7);
-                    VB = fma2(W, DZ2[h], VB);
-                    const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
-                    const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
-                    DS2[h] = fma2(W, DC, DS2[h]);
-                    {
-                        float ti_a, ti_b, t_a, t_b;
-                        split(TI, ti_a, ti_b);
-                        split(T2[h], t_a, t_b);
-                        T2[h] = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
-                    }
-                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
-                    // (selected after the product, so that an infinite G never reaches the sums)
-                    const bool live_a = ok_a && raw_a < kAlphaMax, live_b = ok_b && raw_b < kAlphaMax;
-                    float dp_a, dp_b, dg_a, dg_b;
-                    split(mul2(DA, RAW), dp_a, dp_b);
-                    split(mul2(DA, G), dg_a, dg_b);
-                    const F2 DP = f2(live_a ? dp_a : 0.0f, live_b ? dp_b : 0.0f);
-                    V5 = add2(V5, f2(live_a ? dg_a : 0.0f, live_b ? dg_b : 0.0f));
-                    const RowGroup& ga = rgp[(q0 + pa) >> 2];
-                    const RowGroup& gb = rgp[(q0 + pb) >> 2];
-                    const F2 DXP = f2(ga.dx, gb.dx);
-                    const F2 DYP = f2(ga.dy0 - (float)((q0 + pa) & 3), gb.dy0 - (float)((q0 + pb) & 3));
-                    const F2 PX = mul2(DP, DXP), PY = mul2(DP, DYP);
-                    V0 = add2(V0, PX);
-                    V1 = add2(V1, PY);
-                    V2 = fma2(PX, DXP, V2);
-                    V3 = fma2(PX, DYP, V3);
-                    V4 = fma2(PY, DYP, V4);
-                }
-                const F2 Vs[8] = {V0, V1, V2, V3, V4, V5, V6, V7};
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    float lo, hi;
-                    split(Vs[k], lo, hi);
-                    vv[k] = lo + hi;
-                }
-                float lo, hi;
-                split(VB, lo, hi);
-                vb = lo + hi;
-            } else {
-                // the P pixels update independently (predicated, no branches) so they interleave
-    #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float G = fast_ex2(p2[p]);
-                    const float raw = bb.y * G;
-                    const float alpha = fminf(kAlphaMax, raw);
-                    const bool ok = ok0[p] && alpha >= kAlphaMin;
-                    contrib = contrib || ok;
-                    const float r = fast_rcp(1.0f - alpha);
-                    const float Ti = T[p] * r;
-                    const float w = ok ? Ti * alpha : 0.0f;
-                    const float4 dd = d[p];
-                    vv[6] = fmaf(w, dd.x, vv[6]);
-                    vv[7] = fmaf(w, dd.y, vv[7]);
-                    vb = fmaf(w, dd.z, vb);
-                    const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
-                    const float dalpha = Ti * dc - DS[p] * r;
-                    DS[p] = fmaf(w, dc, DS[p]);
-                    T[p] = ok ? Ti : T[p];
-                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
-                    // selected rather than multiplied so that an infinite G never reaches the sums)
-                    const bool live = ok && raw < kAlphaMax;
-                    const float dP = live ? dalpha * raw : 0.0f;
-                    vv[5] += live ? dalpha * G : 0.0f;
-                    const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
-                    const float px_ = dP * dxp, py_ = dP * dyp;
-                    vv[0] += px_;
-                    vv[1] += py_;
-                    vv[2] = fmaf(px_, dxp, vv[2]);
-                    vv[3] = fmaf(px_, dyp, vv[3]);
-                    vv[4] = fmaf(py_, dyp, vv[4]);
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, contrib);
-            if (m == 0u) continue;
-            const long long gi = s_gi[j];
-            float* t0 = reinterpret_cast<float*>(g0 + gi);
-            float* t1 = reinterpret_cast<float*>(g1 + gi);
-            // moments -> (du, dv, da, db, dc): P = p2 / log2(e), p2 = C' (dy + beta dx)^2 + G' dx^2
-            //   (staged C' = a.z, beta = a.w, G' = bb.x), so with t = beta m1 + m2
-            //   du = 2 (G' m1 + C' beta t)/log2e, dv = 2 C' t/log2e,
-            //   da = -m3/2, db = -m4, dc = -m5/2
-            const float il = 2.0f / kLog2e;
-            const float tm = fmaf(a.w, vv[0], vv[1]);
-            if ((m & (m - 1u)) == 0u) {  // one contributing lane: no reduction
-                if (contrib) {
-                    const float du = fmaf(bb.x, vv[0], a.z * a.w * tm) * il;
-                    const float dv = a.z * tm * il;
-                    atomicAdd(reinterpret_cast<float4*>(t0), make_float4(du, dv, -0.5f * vv[2], -vv[3]));
-                    atomicAdd(reinterpret_cast<float4*>(t1), make_float4(-0.5f * vv[4], vv[5], vv[6], vv[7]));
-                    atomicAdd(&g2[gi], vb);
-                }
-            } else {
-                // every lane turns its moments into (du, dv, da, db, dc) first (linear, so the sum
-                // is the same): no lane-dependent branches after the reduction
-                const float tv[8] = {fmaf(bb.x, vv[0], a.z * a.w * tm) * il, a.z * tm * il,
-                                     -0.5f * vv[2], -vv[3], -0.5f * vv[4], vv[5], vv[6], vv[7]};
-                const float x = warp_sum8_transposed(tv, lane);  // lane holds the total of index lane >> 2
-                vb = warp_sum(vb);
-                const int idx = lane >> 2;
-                if ((lane & 3) == 0) atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
-                if (lane == 0) atomicAdd(&g2[gi], vb);
-            }
-        }
+        int nl = b_end - b_start - j0;
+        if constexpr (band_cull<P>()) nl = band_list(j0, b_end - b_start, ylo, ylo + (float)(2 * P - 1), s_rows, list);
+        bwd_batch<P>(list, j0, nl, b_end, fx, fyg, q0, T, DS, d, my_last, T2, DS2, DX2, DY2, DZ2, s_a, s_b, s_c, s_gi,
+                     g0, g1, g2);
     }
 }
 
@@ -337,6 +370,8 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
     __shared__ float4 s_b[kBwdBatch];
     __shared__ float2 s_c[kBwdBatch];
     __shared__ long long s_gi[kBwdBatch];
+    __shared__ float2 s_rows[band_cull<P>() ? kBwdBatch : 1];
+    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBwdBatch : 1];
     __shared__ unsigned s_max;
     const long long tile = blockIdx.x;
     const int v = view_of_tile(cb, tile);
@@ -362,8 +397,10 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
     // split_min < 0 the walks longer than -split_min - 1
     const int len = min((int)(rg.y - rg.x), top);
     if (split_min >= 0 ? len > split_min : len <= -split_min - 1) return;
+    const float ylo = (float)(py0 - ((int)(threadIdx.x & 16u) >> 4) * P) + 0.5f;  // this warp's first pixel row
     bwd_walk<P>(0, top, (int)__reduce_max_sync(0xffffffffu, mx), xy, conic_o, rgbd, n, values, rg.x,
-                (long long)v * n, fx, fyg, q0, st, s_a, s_b, s_c, s_gi, g0, g1, g2);
+                (long long)v * n, fx, fyg, q0, ylo, st, s_a, s_b, s_c, s_gi, s_rows,
+                s_list + (band_cull<P>() ? (threadIdx.x >> 5) * kBwdBatch : 0), g0, g1, g2);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -451,6 +488,8 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k
     __shared__ float4 s_b[kBwdBatch];
     __shared__ float2 s_c[kBwdBatch];
     __shared__ long long s_gi[kBwdBatch];
+    __shared__ float2 s_rows[band_cull<P>() ? kBwdBatch : 1];
+    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBwdBatch : 1];
     __shared__ float s_T[kTilePix], s_D[kTilePix];
     __shared__ unsigned s_max;
     cg::cluster_group cl = cg::this_cluster();
@@ -521,8 +560,10 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k
     // 3. walk back over the chunk
     if (rank < nc) {
         const int top = min(hi, cta_last);
-        bwd_walk<P>(lo, top, min(hi, warp_last), xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, st, s_a, s_b,
-                    s_c, s_gi, g0, g1, g2);
+        const float ylo = (float)(py0 - ((int)(threadIdx.x & 16u) >> 4) * P) + 0.5f;
+        bwd_walk<P>(lo, top, min(hi, warp_last), xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, ylo, st, s_a,
+                    s_b, s_c, s_gi, s_rows, s_list + (band_cull<P>() ? (threadIdx.x >> 5) * kBwdBatch : 0), g0,
+                    g1, g2);
     }
 }
 

@@ -27,6 +27,50 @@ __device__ __forceinline__ void stage_gaussian(const float2 m, const float4 co, 
     sc = make_float2(cd.z, co.w > 0.0f ? 0.5f * thr : __int_as_float(0x7fc00000));
 }
 
+// Rows a staged Gaussian can reach: the cut-off ellipse p2 >= thr is, in (dx, y) with
+// y = dy + beta dx, the axis-aligned |C'| y^2 + |G'| dx^2 <= |thr|, whose extent in dy is
+// +-H, H = sqrt(|thr| (1 / |C'| + beta^2 / |G'|)) (the support of that ellipse in the direction
+// (-beta, 1)). Returned as (v - H', v + H') with H' = H (1 + 2^-8) + 2^-6 px, a margin far above
+// the float32 rounding of H and of p2, so that no pixel row outside it can pass in_reach. NaN
+// (no row) when nothing is in reach (o' <= 1/255 or o' <= 0); +-inf for a degenerate conic.
+__device__ __forceinline__ float2 reach_rows(const float4& sa, const float4& sb, const float2& sc) {
+    const float t = -2.0f * sc.y;  // |thr|
+    const float h2 = t * (1.0f / (-sa.z) + sa.w * sa.w / (-sb.x));
+    const float H = fmaf(sqrtf(h2), 1.0f + 0.00390625f, 0.015625f);
+    return make_float2(sa.y - H, sa.y + H);
+}
+
+// Whether a blend walking P pixels per thread compacts each batch to the entries that reach its
+// warp's rows first: with 1 or 2 pixels per thread a warp covers 2 or 4 of the tile's 16 rows
+// and skips most entries of a long run that way (measured on the single 800^2 view: forward
+// 0.475 -> 0.447 ms, backward 0.699 -> 0.647 ms); with 4 a warp covers half the tile, and the
+// list's registers cost the backward more than the skipped entries save (1.47 -> 1.53 ms on the
+// 8-view workload).
+template <int P>
+constexpr bool band_cull() { return P <= 2; }
+
+// The slots [j0, j1) of a staged batch whose reach rows meet the pixel-centre rows [ylo, yhi]
+// of this warp, in slot order, written to list (one warp's array of at least j1 - j0 bytes);
+// returns their number (the same in every lane).
+__device__ __forceinline__ int band_list(int j0, int j1, float ylo, float yhi, const float2* s_rows,
+                                         unsigned char* list) {
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+    for (int q = j0; q < j1; q += 32) {
+        const int j = q + lane;
+        bool hit = false;
+        if (j < j1) {
+            const float2 r = s_rows[j];
+            hit = r.x <= yhi && r.y >= ylo;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[n + __popc(m & ((1u << lane) - 1u))] = (unsigned char)j;
+        n += __popc(m);
+    }
+    __syncwarp();
+    return n;
+}
+
 // p2 in [2 mid, 0] (up to the rounding of p2 - mid, which can only admit p2 within an ulp of
 // an end: values that the alpha cut-off after the exponential decides exactly, or P ~ 0 at the
 // centre, a float32 near-tie of the P > 0 guard)

@@ -26,18 +26,100 @@ struct FwdPix {
     bool done[P];
 };
 
+// Front-to-back walk of the staged entries [j0, j1) of a batch whose first entry is entry b0 of
+// the tile's run, for this thread's P pixels, from their current state. Every lane of a warp
+// calls it with the same j0, j1 (the walk holds warp-wide votes); list is the warp's scratch
+// for the slots it walks. `last` records 1 + the position of the last added entry in the run.
+template <int P>
+__device__ __forceinline__ void fwd_batch(int j0, int j1, int b0, const TilePos& tp, FwdPix<P>& s,
+                                          const float4* s_a, const float4* s_b, const float2* s_c,
+                                          const float2* s_rows, unsigned char* list) {
+    constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
+    // with band_cull, only the slots whose reach rows meet this warp's rows (the others are out
+    // of reach of every pixel of the warp, which in_reach would decide entry by entry)
+    int nl = j1 - j0;
+    if constexpr (band_cull<P>()) {
+        const float ylo = (float)(tp.py0 - ((int)(threadIdx.x & 16u) >> 4) * P) + 0.5f;
+        nl = band_list(j0, j1, ylo, ylo + (float)(2 * P - 1), s_rows, list);
+    }
+    for (int i = 0; i < nl; ++i) {
+        const int j = band_cull<P>() ? (int)list[i] : j0 + i;
+        const float4 a = s_a[j];
+        const float4 bb = s_b[j];
+        const float2 cc = s_c[j];
+        float p2[P];
+        bool ok[P];
+        bool any = false;
+        RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
+#pragma unroll
+        for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, tp.fx, tp.fyg + 4.0f * (float)gq);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
+            ok[p] = !s.done[p] && in_reach(p2[p], cc.y);
+            any = any || ok[p];
+        }
+        if (__any_sync(0xffffffffu, any)) {
+            const unsigned idx = (unsigned)(b0 + j + 1);
+            // the P pixels update independently (predicated, no branches) so they interleave
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2[p]));
+                const bool okp = ok[p] && alpha >= kAlphaMin;
+                const float Tn = s.T[p] * (1.0f - alpha);
+                const bool stop = okp && Tn < kTMin;
+                const bool add = okp && !stop;
+                const float w = add ? alpha * s.T[p] : 0.0f;
+                s.C0[p] = fmaf(w, bb.z, s.C0[p]);
+                s.C1[p] = fmaf(w, bb.w, s.C1[p]);
+                s.C2[p] = fmaf(w, cc.x, s.C2[p]);
+                s.T[p] = add ? Tn : s.T[p];
+                s.last[p] = add ? idx : s.last[p];
+                s.done[p] = s.done[p] || stop;
+            }
+        }
+        if ((i & 7) == 7) {
+            bool mine = true;
+#pragma unroll
+            for (int p = 0; p < P; ++p) mine = mine && s.done[p];
+            if (__all_sync(0xffffffffu, mine)) break;
+        }
+    }
+}
+
+// Stages entry e of the tile's run (record values[run0 + e] of view base vbase) in slot `slot`.
+__device__ __forceinline__ void stage_entry(int slot, int e, const float2* __restrict__ xy,
+                                            const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
+                                            long long n, const unsigned* __restrict__ values, unsigned run0,
+                                            long long vbase, float4* s_a, float4* s_b, float2* s_c,
+                                            float2* s_rows) {
+    const unsigned g = values[run0 + e];
+    float4 sa, sb;
+    float2 sc;
+    if (g < (unsigned long long)n) {
+        const long long gi = vbase + g;
+        stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
+    } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
+        stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f), sa,
+                       sb, sc);
+    }
+    s_a[slot] = sa;
+    s_b[slot] = sb;
+    s_c[slot] = sc;
+    if (s_rows != nullptr) s_rows[slot] = reach_rows(sa, sb, sc);
+}
+
 // Front-to-back walk of the entries [e0, e1) of a tile's run for this thread's P pixels, from
 // their current state. The CTA stages batches of kBatch Gaussians in shared memory and leaves
 // as soon as every pixel is done (barrier count), so e0, e1 must be the same for every thread
-// of the CTA. `last` records 1 + the position of the last added entry in the run.
+// of the CTA.
 template <int P>
 __device__ __forceinline__ void fwd_walk(int e0, int e1, const float2* __restrict__ xy,
                                          const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
                                          long long n, const unsigned* __restrict__ values, unsigned run0,
                                          long long vbase, const TilePos& tp, FwdPix<P>& s, float4* s_a, float4* s_b,
-                                         float2* s_c) {
+                                         float2* s_c, float2* s_rows, unsigned char* s_list) {
     constexpr int NT = kTilePix / P;
-    constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
     for (int b0 = e0; b0 < e1; b0 += kBatch) {
         bool all = true;
 #pragma unroll
@@ -47,68 +129,15 @@ __device__ __forceinline__ void fwd_walk(int e0, int e1, const float2* __restric
         for (int q = 0; q < kBatch / NT; ++q) {
             const int slot = threadIdx.x + q * NT;
             const int e = b0 + slot;
-            if (e < e1) {
-                const unsigned g = values[run0 + e];
-                float4 sa, sb;
-                float2 sc;
-                if (g < (unsigned long long)n) {
-                    const long long gi = vbase + g;
-                    stage_gaussian(xy[gi], conic_o[gi], rgbd[gi], sa, sb, sc);
-                } else {  // never for a completed sort; a zero-opacity stand-in keeps reads in bounds
-                    stage_gaussian(make_float2(0.f, 0.f), make_float4(1.f, 0.f, 1.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                                   sa, sb, sc);
-                }
-                s_a[slot] = sa;
-                s_b[slot] = sb;
-                s_c[slot] = sc;
-            }
+            if (e < e1)
+                stage_entry(slot, e, xy, conic_o, rgbd, n, values, run0, vbase, s_a, s_b, s_c,
+                            band_cull<P>() ? s_rows : nullptr);
         }
         __syncthreads();
         // the walk below holds warp-wide votes: a warp skips or leaves it only as a whole
         if (__all_sync(0xffffffffu, all)) continue;
-        const int cnt = min(kBatch, e1 - b0);
-        for (int j = 0; j < cnt; ++j) {
-            const float4 a = s_a[j];
-            const float4 bb = s_b[j];
-            const float2 cc = s_c[j];
-            float p2[P];
-            bool ok[P];
-            bool any = false;
-            RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
-#pragma unroll
-            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, tp.fx, tp.fyg + 4.0f * (float)gq);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
-                ok[p] = !s.done[p] && in_reach(p2[p], cc.y);
-                any = any || ok[p];
-            }
-            if (__any_sync(0xffffffffu, any)) {
-                const unsigned idx = (unsigned)(b0 + j + 1);
-                // the P pixels update independently (predicated, no branches) so they interleave
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2[p]));
-                    const bool okp = ok[p] && alpha >= kAlphaMin;
-                    const float Tn = s.T[p] * (1.0f - alpha);
-                    const bool stop = okp && Tn < kTMin;
-                    const bool add = okp && !stop;
-                    const float w = add ? alpha * s.T[p] : 0.0f;
-                    s.C0[p] = fmaf(w, bb.z, s.C0[p]);
-                    s.C1[p] = fmaf(w, bb.w, s.C1[p]);
-                    s.C2[p] = fmaf(w, cc.x, s.C2[p]);
-                    s.T[p] = add ? Tn : s.T[p];
-                    s.last[p] = add ? idx : s.last[p];
-                    s.done[p] = s.done[p] || stop;
-                }
-            }
-            if ((j & 7) == 7) {
-                bool mine = true;
-#pragma unroll
-                for (int p = 0; p < P; ++p) mine = mine && s.done[p];
-                if (__all_sync(0xffffffffu, mine)) break;
-            }
-        }
+        unsigned char* list = s_list + (band_cull<P>() ? (threadIdx.x >> 5) * kBatch : 0);  // this warp's
+        fwd_batch<P>(0, min(kBatch, e1 - b0), b0, tp, s, s_a, s_b, s_c, s_rows, list);
     }
 }
 
@@ -124,6 +153,8 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
+    __shared__ float2 s_rows[band_cull<P>() ? kBatch : 1];
+    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBatch : 1];
     const long long tile = blockIdx.x;
     const uint2 rg = ranges[tile];
     // tile selection: split_min >= 0 keeps the runs of at most split_min entries (the others go
@@ -144,7 +175,8 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
         s.last[p] = 0;
         s.done[p] = !inside[p];
     }
-    fwd_walk<P>(0, (int)(rg.y - rg.x), xy, conic_o, rgbd, n, values, rg.x, (long long)v * n, tp, s, s_a, s_b, s_c);
+    fwd_walk<P>(0, (int)(rg.y - rg.x), xy, conic_o, rgbd, n, values, rg.x, (long long)v * n, tp, s, s_a, s_b, s_c,
+                s_rows, s_list);
 #pragma unroll
     for (int p = 0; p < P; ++p)
         if (inside[p]) {
@@ -182,6 +214,8 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
     __shared__ float4 s_a[kBatch];
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
+    __shared__ float2 s_rows[band_cull<P>() ? kBatch : 1];
+    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBatch : 1];
     __shared__ float s_T[kTilePix], s_C0[kTilePix], s_C1[kTilePix], s_C2[kTilePix];
     __shared__ unsigned s_last[kTilePix];
     __shared__ int s_state[kTilePix];  // after the walk: 1 stopped in the chunk; after the merge: 0 dropped,
@@ -211,7 +245,7 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
         s.done[p] = !inside[p];
     }
     // 1. every active CTA walks its chunk from T = 1 (CTA 0's walk is the sequential one)
-    if (active) fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, s, s_a, s_b, s_c);
+    if (active) fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, s, s_a, s_b, s_c, s_rows, s_list);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         s_T[pl[p]] = s.T[p];
@@ -252,7 +286,7 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
             r.last[p] = 0;
             r.done[p] = state[p] != 2;
         }
-        fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, r, s_a, s_b, s_c);
+        fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, r, s_a, s_b, s_c, s_rows, s_list);
 #pragma unroll
         for (int p = 0; p < P; ++p)
             if (state[p] == 2) {

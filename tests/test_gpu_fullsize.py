@@ -4,7 +4,8 @@ default launch shapes): sampled pixels and sampled-loss gradients against the FP
 * 1M Gaussians / 4 models / 8 views of 512^2..1280^2 (the benchmark workload): 128 random
   pixels per view compared with the oracle's per-pixel compositing; then a loss on 48 pixels
   per view whose decisions are not near a tie, and every parameter gradient compared.
-* 500k Gaussians / one 800^2 view: sampled pixels and gradients.
+* 500k Gaussians / one 800^2 view: sampled pixels and gradients; and pixels in its 8 heaviest
+  tiles with each walk of the long runs (sequential, split over CTA clusters).
 * 1.5M Gaussians / 6 models with colour, opacity and visibility edits, 16 views at 1024^2
   with an orbital light sweep: sampled pixels on 4 of the views.
 Images within 2e-4 outside oracle-certified near-ties; gradients within 1e-3 relative L2 and
@@ -16,6 +17,7 @@ import torch
 
 import oracle
 import scenegen as sg
+from oracle.certify import uncertain_pixels
 from tests import _gpu
 
 pytestmark = pytest.mark.gpu
@@ -36,7 +38,24 @@ def _sample(c, k, rng):
     return np.c_[rng.integers(0, c.W, k), rng.integers(0, c.H, k)]
 
 
-def _check_pixels(rast, w, views, per_view, seed):
+def _heaviest_tiles(rast, c, k_tiles, per_tile):
+    """A pick of per_tile random pixels in each of the k_tiles tiles with the longest runs of a
+    single-view call (the tiles the split walk takes)."""
+    def pick(v, cam, n, rng):
+        r = rast.ranges.cpu().numpy().view(np.uint32).reshape(-1, 2).astype(np.int64)
+        top = np.argsort(-(r[:, 1] - r[:, 0]), kind="stable")[:k_tiles]
+        gx = (cam.W + 15) // 16
+        out = []
+        for t in top:
+            xs = (t % gx) * 16 + rng.integers(0, 16, per_tile)
+            ys = (t // gx) * 16 + rng.integers(0, 16, per_tile)
+            keep = (xs < cam.W) & (ys < cam.H)
+            out.append(np.c_[xs[keep], ys[keep]])
+        return np.concatenate(out)
+    return pick
+
+
+def _check_pixels(rast, w, views, per_view, seed, pick=None, pixel_excuse=False):
     rng = np.random.default_rng(seed)
     comp = oracle.compose(w.models)
     table = oracle.edit_table(w.edits)
@@ -45,11 +64,14 @@ def _check_pixels(rast, w, views, per_view, seed):
     for v in views:
         c = w.cameras[v]
         p = oracle.project(comp, table, c)
-        pix = _sample(c, per_view, rng)
+        pix = _sample(c, per_view, rng) if pick is None else pick(v, c, per_view, rng)
         rgba, T, last, mg = oracle.render_pixels(p, c, pix, bg=w.bg)
         gimg = rast.view_image(v).cpu().numpy()[pix[:, 1], pix[:, 0]]
         unc = _gpu.uncertain_records(p)
-        tile_unc = _gpu.uncertain_tile_mask(p, unc, c.W, c.H)[pix[:, 1], pix[:, 0]]
+        if pixel_excuse:  # only pixels an uncertain record reaches (heavy tiles hold some in every tile)
+            tile_unc = uncertain_pixels(p, unc, pix)
+        else:
+            tile_unc = _gpu.uncertain_tile_mask(p, unc, c.W, c.H)[pix[:, 1], pix[:, 0]]
         err, excused, bad = _gpu.compare_image(gimg, rgba, mg, tile_unc)
         assert bad == 0, (v, err)
         total_excused += excused
@@ -102,6 +124,26 @@ def test_fullsize_500k_800_pixels_and_gradients():
     rast, comp_dev, table_dev = _render_capacity(w)
     sampled, comp, table = _check_pixels(rast, w, [0], 512, seed=13)
     _check_grads(rast, comp_dev, table_dev, w, sampled, comp, table, 128, seed=14)
+
+
+@pytest.mark.parametrize("walk", [2, 1], ids=["sequential", "split"])
+def test_fullsize_500k_800_heaviest_tiles(walk):
+    """The 8 tiles with the longest runs of the 800^2 view (several thousand entries each), 32
+    pixels in each, with one CTA per tile (sequential) and the split walk over CTA clusters:
+    pixels, last contributors and the gradients of a loss on them.
+    Every such tile is touched by some float32-uncertain record, so pixels are excused only where
+    an uncertain record reaches them (oracle.certify.uncertain_pixels)."""
+    from paper_2504_17954_gb300 import _native as N
+    old = N.ivrgs_get_option("render_split")
+    N.ivrgs_set_option("render_split", walk)
+    try:
+        w = sg.config2()
+        rast, comp_dev, table_dev = _render_capacity(w)
+        sampled, comp, table = _check_pixels(rast, w, [0], 256, seed=16,
+                                             pick=_heaviest_tiles(rast, w.cameras[0], 8, 32), pixel_excuse=True)
+        _check_grads(rast, comp_dev, table_dev, w, sampled, comp, table, 128, seed=17)
+    finally:
+        N.ivrgs_set_option("render_split", old)
 
 
 def test_fullsize_composed_edits_16_views_pixels():
