@@ -156,7 +156,7 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                 float raw_a, raw_b;
                 split(RAW, raw_a, raw_b);
                 const float al_a = fminf(kAlphaMax, raw_a), al_b = fminf(kAlphaMax, raw_b);
-                const bool ok_a = ok0[pa] && al_a >= kAlphaMin, ok_b = ok0[pb] && al_b >= kAlphaMin;
+                const bool ok_a = ok0[pa], ok_b = ok0[pb];
                 contrib = contrib || ok_a || ok_b;
                 const F2 A = f2(al_a, al_b);
                 float om_a, om_b;
@@ -214,7 +214,7 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                 const float G = fast_ex2(p2[p]);
                 const float raw = bb.y * G;
                 const float alpha = fminf(kAlphaMax, raw);
-                const bool ok = ok0[p] && alpha >= kAlphaMin;
+                const bool ok = ok0[p];
                 contrib = contrib || ok;
                 const float r = fast_rcp(1.0f - alpha);
                 const float Ti = T[p] * r;
@@ -468,7 +468,7 @@ __device__ __forceinline__ void bwd_chunk_partial(int lo, int hi, const float2* 
                 const float p2 = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
                 const bool ok = e < (int)st.my_last[p] && in_reach(p2, cc.y);
                 const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
-                const bool add = ok && alpha >= kAlphaMin;
+                const bool add = ok;
                 const float w = add ? alpha * Tk[p] : 0.0f;
                 const float4 dd = st.d[p];
                 Dk[p] = fmaf(w, dd.x * bb.z + dd.y * bb.w + dd.z * cc.x, Dk[p]);

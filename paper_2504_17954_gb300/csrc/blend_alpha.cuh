@@ -14,16 +14,17 @@ namespace ivrgs {
 //
 // staged Gaussian: sa = (u, v, C', beta), sb = (G', o', r, g), sc = (b, mid) with
 // C' = -c log2e / 2, beta = b / c, G' = -g log2e / 2 (so that p2 = log2(e) * P = C' y^2 + G' dx^2)
-// and mid = thr / 2, thr = log2(1 / (255 o')) - 1e-3: below thr, o' 2^p2 < 1/255 for certain
-// (the margin covers the rounding of log2 and of ex2.approx by orders of magnitude), so an
-// entry outside [thr, 0] can be skipped before the exponential without changing any decision.
-// The range test is one compare, |p2 - mid| <= -mid (in_reach); mid is NaN for o' <= 0, so
-// that nothing is in reach.
+// and mid = thr / 2, thr = log2(1 / (255 o')). The compositing's two range rules are decided on
+// the exponent, before the exponential: the P > 0 guard (p2 <= 0) and the 1/255 cut-off, since
+// o' 2^p2 >= 1/255 exactly when p2 >= thr. In float32 this decides the cut-off otherwise than
+// the exact alpha only within a few ulp of thr (the rounding of log2f, of p2 and of ex2.approx),
+// a float64 near-tie of |ln(255 alpha)| far below 1e-3. The range test is one compare,
+// |p2 - mid| <= -mid (in_reach); mid is NaN for o' <= 0, so that nothing is in reach.
 __device__ __forceinline__ void stage_gaussian(const float2 m, const float4 co, const float4 cd, float4& sa,
                                                float4& sb, float2& sc) {
     sa = make_float4(m.x, m.y, (-0.5f * kLog2e) * co.z, co.y / co.z);
     sb = make_float4((-0.5f * kLog2e) * co.x, co.w, cd.x, cd.y);
-    const float thr = co.w > 0.0f ? -log2f(255.0f * co.w) - 1e-3f : 0.0f;
+    const float thr = co.w > 0.0f ? -log2f(255.0f * co.w) : 0.0f;
     sc = make_float2(cd.z, co.w > 0.0f ? 0.5f * thr : __int_as_float(0x7fc00000));
 }
 
@@ -71,9 +72,9 @@ __device__ __forceinline__ int band_list(int j0, int j1, float ylo, float yhi, c
     return n;
 }
 
-// p2 in [2 mid, 0] (up to the rounding of p2 - mid, which can only admit p2 within an ulp of
-// an end: values that the alpha cut-off after the exponential decides exactly, or P ~ 0 at the
-// centre, a float32 near-tie of the P > 0 guard)
+// p2 in [2 mid, 0]: the entry is composited (up to the rounding of p2 - mid, which moves the
+// ends by an ulp of mid: a float32 near-tie of the cut-off, or P ~ 0 at the centre, one of the
+// P > 0 guard)
 __device__ __forceinline__ bool in_reach(float p2, float mid) { return fabsf(__fsub_rn(p2, mid)) <= -mid; }
 
 // p2 = log2(e) * P over an aligned group of 4 pixel rows of one column. With dx = u - px and
@@ -100,6 +101,7 @@ __device__ __forceinline__ RowGroup row_group(const float4& sa, const float4& sb
 }
 
 __device__ __forceinline__ float row_p2(const RowGroup& q, const float4& sa, int p) {
+    if (p == 0) return q.base;  // the expansion's terms are +-0 there (C' and k1 finite)
     return __fmaf_rn(sa.z, (float)(p * p), __fmaf_rn(-(float)p, q.k1, q.base));
 }
 

@@ -133,14 +133,14 @@ __global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restric
             if (__any_sync(0xffffffffu, ok)) {
                 // the forward blend's update (k_render), so that 1 - T equals its alpha bit for bit
                 const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
-                const bool okp = ok && alpha >= kAlphaMin;
                 const float Tn = T * (1.0f - alpha);
-                const bool stop = okp && Tn < kTMin;
-                const bool add = okp && !stop;
-                const float w = add ? alpha * T : 0.0f;
+                const bool stop = ok && Tn < kTMin;
+                const bool add = ok && !stop;
+                const float Tk = add ? Tn : T;
+                const float w = T - Tk;
 #pragma unroll
                 for (int k = 0; k < kAux; ++k) acc[k] = fmaf(w, s_x[k][j], acc[k]);
-                T = add ? Tn : T;
+                T = Tk;
                 done = done || stop;
             }
             if ((j & 7) == 7 && __all_sync(0xffffffffu, done)) break;
