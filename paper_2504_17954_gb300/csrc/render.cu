@@ -8,6 +8,7 @@
 // exponent is one FMA chain, opacity, colour), then every pixel walks it. The CTA leaves as
 // soon as every pixel has reached T < 1e-4 (barrier count).
 #include <climits>
+#include <type_traits>
 #include <cooperative_groups.h>
 
 #include "blend_alpha.cuh"
@@ -61,26 +62,31 @@ __device__ __forceinline__ void fwd_batch(int j0, int j1, int b0, const TilePos&
         }
         if (__any_sync(0xffffffffu, any)) {
             const unsigned idx = (unsigned)(b0 + j + 1);
-            // the P pixels update independently (predicated, no branches) so they interleave
+            // the P pixels update independently (predicated, no branches) so they interleave;
+            // instantiated with and without the 0.99 clamp (a uniform branch on the entry's o')
+            auto update = [&](auto clamp) {
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2[p]));
-                const float Tn = s.T[p] * (1.0f - alpha);
-                const bool stop = ok[p] && Tn < kTMin;
-                const bool add = ok[p] && !stop;
-                // the weight T alpha as the drop of T (exact: Sterbenz), so that one select
-                // serves both; it differs from the rounded product T alpha by the rounding of
-                // T (1 - alpha), at most 2^-24 T per entry, under 1.6e-5 in all (T falls by
-                // 1/255 at least per entry)
-                const float Tk = add ? Tn : s.T[p];
-                const float w = s.T[p] - Tk;
-                s.C0[p] = fmaf(w, bb.z, s.C0[p]);
-                s.C1[p] = fmaf(w, bb.w, s.C1[p]);
-                s.C2[p] = fmaf(w, cc.x, s.C2[p]);
-                s.T[p] = Tk;
-                s.last[p] = add ? idx : s.last[p];
-                s.done[p] = s.done[p] || stop;
-            }
+                for (int p = 0; p < P; ++p) {
+                    const float Tn =
+                        __fmul_rn(s.T[p], one_minus_alpha<decltype(clamp)::value>(bb.y, fast_ex2(p2[p])));
+                    const bool stop = ok[p] && Tn < kTMin;
+                    const bool add = ok[p] && !stop;
+                    // the weight T alpha as the drop of T (exact: Sterbenz), so that one select
+                    // serves both; it differs from the rounded product T alpha by the rounding of
+                    // T (1 - alpha), at most 2^-24 T per entry, under 1.6e-5 in all (T falls by
+                    // 1/255 at least per entry)
+                    const float Tk = add ? Tn : s.T[p];
+                    const float w = s.T[p] - Tk;
+                    s.C0[p] = fmaf(w, bb.z, s.C0[p]);
+                    s.C1[p] = fmaf(w, bb.w, s.C1[p]);
+                    s.C2[p] = fmaf(w, cc.x, s.C2[p]);
+                    s.T[p] = Tk;
+                    s.last[p] = add ? idx : s.last[p];
+                    s.done[p] = s.done[p] || stop;
+                }
+            };
+            if (bb.y > kNoClampOpacity) update(std::true_type{});
+            else update(std::false_type{});
         }
         if ((i & 7) == 7) {
             bool mine = true;

@@ -132,8 +132,10 @@ __global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restric
             const bool ok = !done && in_reach(p2, cc.y);
             if (__any_sync(0xffffffffu, ok)) {
                 // the forward blend's update (k_render), so that 1 - T equals its alpha bit for bit
-                const float alpha = fminf(kAlphaMax, bb.y * fast_ex2(p2));
-                const float Tn = T * (1.0f - alpha);
+                const float G = fast_ex2(p2);
+                const float om =
+                    bb.y > kNoClampOpacity ? one_minus_alpha<true>(bb.y, G) : one_minus_alpha<false>(bb.y, G);
+                const float Tn = __fmul_rn(T, om);
                 const bool stop = ok && Tn < kTMin;
                 const bool add = ok && !stop;
                 const float Tk = add ? Tn : T;
