@@ -619,6 +619,7 @@ def cfg5_bench(args, dev, K, pk, world, small):
     import scenegen as sg
     from paper_2504_17954_gb300 import _native as N
     from paper_2504_17954_gb300 import Gaussians, compose_edit
+    from paper_2504_17954_gb300 import autotune
     from paper_2504_17954_gb300.rasterizer import Rasterizer, WaveRasterizer
     w = workload("cfg5")
     M = len(w.models)
@@ -627,22 +628,23 @@ def cfg5_bench(args, dev, K, pk, world, small):
     arrs, mid = host_composed(w.models)
     packed, _ = sg.pack_mixed_arrays(**arrs, model_id=mid)
     g = upload_mixed(packed, M, dev)
-    waves = WaveRasterizer(w.cameras, g.n, M, device=dev, bg=w.bg, pixel_budget=16 << 20)
-    waves.size_buffers(g, table)
-    gen = torch.Generator(device=dev).manual_seed(5)
-    dls = [torch.randn((r.n_pix, 4), generator=gen, device=dev, dtype=torch.float32) * 1e-3 for r in waves.rasts]
-    full = waves.capture(g, table, dls)
-    fwd_graph = waves.capture(g, table)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    n_pix = sum(r.n_pix for r in waves.rasts)
 
-    def timed(graph):
+    def build(max_views, pixel_budget):
+        wv = WaveRasterizer(w.cameras, g.n, M, device=dev, bg=w.bg, max_views=max_views, pixel_budget=pixel_budget)
+        wv.size_buffers(g, table)
+        gen = torch.Generator(device=dev).manual_seed(5)
+        d = [torch.randn((r.n_pix, 4), generator=gen, device=dev, dtype=torch.float32) * 1e-3 for r in wv.rasts]
+        return wv, d, wv.capture(g, table, d)
+
+    def replay_ms(graph, wv, reps):
+        """Device time of reps graph replays (L2 flushed before each), after two untimed ones."""
         for _ in range(2):
             graph.replay()
         torch.cuda.synchronize()
         tot = 0.0
-        for _ in range(K):
+        for _ in range(reps):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -650,9 +652,26 @@ def cfg5_bench(args, dev, K, pk, world, small):
             b.record(stream)
             torch.cuda.synchronize()
             tot += a.elapsed_time(b)
-        if waves.overflowed():
+        if wv.overflowed():
             raise RuntimeError("cfg5: a wave's pair buffer overflowed during replay")
-        return max_over_ranks(tot, dev, world)
+        return tot
+
+    def measure(max_views, pixel_budget):
+        wv, d, graph = build(max_views, pixel_budget)
+        try:
+            return replay_ms(graph, wv, 3) / 3
+        finally:
+            del wv, d, graph
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+    # the batch shape (pixels and views per wave) picked by timing the whole captured step
+    shape = autotune.tune_waves(measure, w.cameras, g.n, f"{w.name}|{g.n}|{len(w.cameras)}", use_cache=False)
+    waves, dls, full = build(shape["max_views"], shape["pixel_budget"])
+    fwd_graph = waves.capture(g, table)
+    n_pix = sum(r.n_pix for r in waves.rasts)
+
+    def timed(graph):
+        return max_over_ranks(replay_ms(graph, waves, K), dev, world)
     ms_full = timed(full)
     ms_fwd = timed(fwd_graph)
     # per-kernel timing of K eager steps (all waves, forward and backward)
@@ -678,6 +697,9 @@ def cfg5_bench(args, dev, K, pk, world, small):
     roof["per_launch"] = f"work and time per launch averaged over the {nw} waves"
     res = {"workload": w.name, "gaussians": g.n, "models": M, "views": len(w.cameras), "pixels": n_pix,
            "waves": [len(x) for x in waves.waves], "pairs": pairs,
+           "wave_shape": {"pixel_budget": shape["pixel_budget"], "max_views": shape["max_views"],
+                          "picked_by": "autotune.tune_waves (captured fwd+bwd step timed per distinct wave plan)",
+                          "candidates": shape["candidates"]},
            "mpix_s": n_pix * world * K / (ms_full / 1e3) / 1e6, "fwd_mpix_s": n_pix * world * K / (ms_fwd / 1e3) / 1e6,
            "ms_per_step": ms_full / K, "launch": "one CUDA graph per step: every wave's forward and backward",
            "storage": "FP16 mean offsets, BF16 log-scale/dc/normal, FP16 q/o/k (44 B per Gaussian)",

@@ -1,18 +1,20 @@
-"""Autotuner for the library's launch shapes.
+"""Autotuner for the library's launch shapes and the batch shape of many-view rendering.
 
-Searches the options ``ivrgs_set_option`` accepts (pixels per thread of the forward and backward
-blend, the split walk of long runs over CTA clusters and its chunk length, radix ranking and
-offsets) on the caller's own workload with CUDA events: coordinate descent from the current
-setting, one option at a time over all its values, repeated until a sweep changes nothing (at
-most ``sweeps`` times). The choice is cached in a JSON file keyed by GPU name and a workload
-signature. Every option gives the same results (up to float32 rounding in the split walk), so
-tuning changes speed only.
+``tune`` searches the options ``ivrgs_set_option`` accepts (pixels per thread of the forward and
+backward blend, the split walk of long runs over CTA clusters and its chunk length, radix
+ranking and offsets) on the caller's own workload with CUDA events: coordinate descent from the
+current setting, one option at a time over all its values, repeated until a sweep changes
+nothing (at most ``sweeps`` times). ``tune_waves`` picks the view-wave shape of a
+``WaveRasterizer`` (pixels and views per binning call) by timing the caller's whole step for
+each distinct wave plan. Choices are cached in a JSON file keyed by GPU name and a workload
+signature. Every option and shape gives the same results (up to float32 rounding in the split
+walk), so tuning changes speed only.
 """
 from __future__ import annotations
 
 import json
 import os
-from typing import Callable, Dict, Optional
+from typing import Callable, Dict, Optional, Sequence
 
 import torch
 
@@ -27,6 +29,13 @@ SPACE = {
     "sort_scan": (0, 1),
     "sort_early": (0, 1),
 }
+
+
+# pixel budgets of a view wave: up to 2^16 tiles of 16 x 16 per binning call at 16M pixels (tile
+# ids sort in two 8-bit passes as 16-bit keys), more above it (three passes); fewer pixels per
+# wave mean more calls and launches
+WAVE_BUDGETS = (8 << 20, 16 << 20, 32 << 20)
+WAVE_VIEWS = (32,)
 
 
 def _cache_path() -> str:
@@ -67,13 +76,7 @@ def tune(step: Callable[[], None], signature: str, reps: int = 5, use_cache: boo
     space = SPACE if space is None else space
     key = f"{torch.cuda.get_device_name()}|{signature}"
     path = _cache_path()
-    cache = {}
-    if use_cache and os.path.exists(path):
-        try:
-            with open(path) as f:
-                cache = json.load(f)
-        except (OSError, ValueError):
-            cache = {}
+    cache = _load_cache(path) if use_cache else {}
     if use_cache and key in cache:
         choice = cache[key]["choice"]
         apply(choice)
@@ -104,10 +107,69 @@ def tune(step: Callable[[], None], signature: str, reps: int = 5, use_cache: boo
     apply(best)
     if use_cache:
         cache[key] = {"choice": best, "ms": best_ms, "default_ms": default_ms, "evaluated": len(seen)}
+        _store_cache(path, cache)
+    return best
+
+
+def _load_cache(path):
+    if os.path.exists(path):
         try:
-            os.makedirs(os.path.dirname(path), exist_ok=True)
-            with open(path, "w") as f:
-                json.dump(cache, f, indent=1)
-        except OSError:
-            pass
+            with open(path) as f:
+                return json.load(f)
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def _store_cache(path, cache):
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    except OSError:
+        pass
+
+
+def tune_waves(measure: Callable[[int, int], float], cams: Sequence, n_gaussians: int, signature: str,
+               budgets: Sequence[int] = WAVE_BUDGETS, max_views: Sequence[int] = WAVE_VIEWS,
+               use_cache: bool = True, device_name: Optional[str] = None) -> Dict:
+    """Pick the view-wave shape of a many-view render for the caller's own step.
+
+    ``measure(max_views, pixel_budget)`` builds the waves with that shape, runs the caller's
+    step (for instance a captured forward+backward over all waves) and returns its time in ms;
+    it may raise (a wave over the per-call pair limit, out of memory), and that shape is then
+    skipped. Shapes that give the same wave plan (``rasterizer.plan_waves``) are measured once.
+    Returns {"max_views", "pixel_budget", "waves" (views per wave), "ms", "candidates" (every
+    measured shape with its time or the error)}; cached per GPU name and ``signature``."""
+    from .rasterizer import plan_waves
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name()
+    key = f"{device_name}|waves|{signature}"
+    path = _cache_path()
+    cache = _load_cache(path) if use_cache else {}
+    if use_cache and key in cache:
+        return cache[key]
+    plans = {}
+    for mv in max_views:
+        for pb in budgets:
+            plan = tuple(len(w) for w in plan_waves(cams, n_gaussians, mv, pb))
+            plans.setdefault(plan, (mv, pb))  # the first shape that gives a plan stands for it
+    best = None
+    cands = []
+    for plan, (mv, pb) in plans.items():
+        try:
+            ms = float(measure(mv, pb))
+        except (RuntimeError, MemoryError) as e:
+            cands.append({"max_views": mv, "pixel_budget": pb, "waves": list(plan), "error": str(e)[:200]})
+            continue
+        cands.append({"max_views": mv, "pixel_budget": pb, "waves": list(plan), "ms": ms})
+        if best is None or ms < best["ms"]:
+            best = {"max_views": mv, "pixel_budget": pb, "waves": list(plan), "ms": ms}
+    if best is None:
+        raise RuntimeError(f"tune_waves: no wave shape could be measured: {cands}")
+    best["candidates"] = cands
+    if use_cache:
+        cache[key] = best
+        _store_cache(path, cache)
     return best
