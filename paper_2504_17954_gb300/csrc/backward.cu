@@ -16,6 +16,7 @@
 // The conic's gradient reaches Sigma' through the eigenbasis of Sigma', which keeps long, thin
 // Gaussians' scale and rotation gradients free of cancellation in float32.
 #include <climits>
+#include <type_traits>
 #include <cooperative_groups.h>
 
 #include "blend_alpha.cuh"
@@ -151,6 +152,10 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
         }
         if (!__any_sync(0xffffffffu, any)) continue;
         bool contrib = false;
+        // the pixels' chain rule, instantiated with and without the 0.99 clamp (a uniform branch
+        // on the entry's o': at or below kNoClampOpacity, alpha = o' G and dalpha/dP = o' G)
+        auto pixels = [&](auto clamp) {
+            constexpr bool CLAMP = decltype(clamp)::value;
         if constexpr (P % 2 == 0) {
             // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
             // the order in which a thread adds its pixels' moments differs)
@@ -164,7 +169,8 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                 const F2 RAW = mul2(O2, G);
                 float raw_a, raw_b;
                 split(RAW, raw_a, raw_b);
-                const float al_a = fminf(kAlphaMax, raw_a), al_b = fminf(kAlphaMax, raw_b);
+                const float al_a = CLAMP ? fminf(kAlphaMax, raw_a) : raw_a;
+                    const float al_b = CLAMP ? fminf(kAlphaMax, raw_b) : raw_b;
                 const bool ok_a = ok0[pa], ok_b = ok0[pb];
                 contrib = contrib || ok_a || ok_b;
                 const F2 A = f2(al_a, al_b);
@@ -172,24 +178,28 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                 split(sub2(one, A), om_a, om_b);
                 const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
                 const F2 TI = mul2(T2[h], R);
-                float wt_a, wt_b;
-                split(mul2(TI, A), wt_a, wt_b);
-                const F2 W = f2(ok_a ? wt_a : 0.0f, ok_b ? wt_b : 0.0f);
+                F2 TN;  // T in front of the entry: recovered for a contributor, unchanged otherwise
+                {
+                    float ti_a, ti_b, t_a, t_b;
+                    split(TI, ti_a, ti_b);
+                    split(T2[h], t_a, t_b);
+                    TN = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
+                }
+                // the weight T_i alpha_i as T_i - T_{i+1} (0 for a skipped pixel), so that one select
+                // serves both; it differs from the rounded product by the rounding of T_i, under
+                // 2^-24 T_i / alpha_i, relative 1.5e-5 at the cut-off
+                const F2 W = sub2(TN, T2[h]);
                 V6 = fma2(W, DX2[h], V6);
                 V7 = fma2(W, DY2[h], V7);
                 VB = fma2(W, DZ2[h], VB);
                 const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
                 const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
                 DS2[h] = fma2(W, DC, DS2[h]);
-                {
-                    float ti_a, ti_b, t_a, t_b;
-                    split(TI, ti_a, ti_b);
-                    split(T2[h], t_a, t_b);
-                    T2[h] = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
-                }
+                T2[h] = TN;
                 // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
                 // (selected after the product, so that an infinite G never reaches the sums)
-                const bool live_a = ok_a && raw_a < kAlphaMax, live_b = ok_b && raw_b < kAlphaMax;
+                const bool live_a = CLAMP ? ok_a && raw_a < kAlphaMax : ok_a;
+                    const bool live_b = CLAMP ? ok_b && raw_b < kAlphaMax : ok_b;
                 float dp_a, dp_b, dg_a, dg_b;
                 split(mul2(DA, RAW), dp_a, dp_b);
                 split(mul2(DA, G), dg_a, dg_b);
@@ -222,7 +232,7 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
             for (int p = 0; p < P; ++p) {
                 const float G = fast_ex2(p2[p]);
                 const float raw = bb.y * G;
-                const float alpha = fminf(kAlphaMax, raw);
+                const float alpha = CLAMP ? fminf(kAlphaMax, raw) : raw;
                 const bool ok = ok0[p];
                 contrib = contrib || ok;
                 const float r = fast_rcp(1.0f - alpha);
@@ -238,7 +248,7 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                 T[p] = ok ? Ti : T[p];
                 // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
                 // selected rather than multiplied so that an infinite G never reaches the sums)
-                const bool live = ok && raw < kAlphaMax;
+                const bool live = CLAMP ? ok && raw < kAlphaMax : ok;
                 const float dP = live ? dalpha * raw : 0.0f;
                 vv[5] += live ? dalpha * G : 0.0f;
                 const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
@@ -250,6 +260,9 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                 vv[4] = fmaf(py_, dyp, vv[4]);
             }
         }
+        };
+        if (bb.y > kNoClampOpacity) pixels(std::true_type{});
+        else pixels(std::false_type{});
         const unsigned m = __ballot_sync(0xffffffffu, contrib);
         if (m == 0u) continue;
         const long long gi = s_gi[j];
