@@ -56,6 +56,7 @@ def parse():
                     help="Gaussian order in memory: per model by Morton code (one-time reorder) or as composed")
     ap.add_argument("--no-cfg5", action="store_true", help="skip the 3M-Gaussian / 64-view wave-graph leg")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the sampled accuracy check against the oracle")
+    ap.add_argument("--tile-h", type=int, default=16, choices=[16, 8], help="tile height of the main workload")
     return ap.parse_args()
 
 
@@ -256,9 +257,10 @@ class Probe:
     host attributes the device holds (decoded float32 values), the edits, the cameras and the
     GPU's RGBA at the sampled pixels."""
 
-    def __init__(self, name, arrs, mid, n_models, w, views, per_view, seed, image_of):
+    def __init__(self, name, arrs, mid, n_models, w, views, per_view, seed, image_of, tile_h=16):
         import numpy as np
         self.name, self.arrs, self.mid, self.n_models, self.w = name, arrs, mid, n_models, w
+        self.tile_h = tile_h
         rng = np.random.default_rng(seed)
         self.pix, self.gpu = {}, {}
         for v in views:
@@ -283,7 +285,8 @@ class Harness:
         from paper_2504_17954_gb300 import _native as N
         self.args, self.w, self.comp, self.table, self.dev, self.world = args, w, comp, table, dev, world
         self.ed = w.edits
-        self.rast = Rasterizer(w.cameras, comp.n, len(w.models), device=dev, lowpass=w.lowpass, bg=w.bg)
+        self.rast = Rasterizer(w.cameras, comp.n, len(w.models), device=dev, lowpass=w.lowpass, bg=w.bg,
+                               tile_h=getattr(args, "tile_h", 16))
         self.rast.forward(comp, table, mode="exact")  # sizes the pair buffer
         torch.cuda.synchronize()
         self.n_pairs = self.rast.n_pairs
@@ -507,7 +510,8 @@ def run_gpu(args, rank, world):
     probes = []
     small = args.no_mixed or args.no_accuracy
     if not small:
-        probes.append(Probe("batched_fp32", arrs, mid, M, w, range(len(w.cameras)), 32, 21, h.rast.view_image))
+        probes.append(Probe("batched_fp32", arrs, mid, M, w, range(len(w.cameras)), 32, 21, h.rast.view_image,
+                            tile_h=args.tile_h))
 
     # the batched form with 16-bit attribute storage, same workload (encoded on the host)
     mixed = None
@@ -524,7 +528,7 @@ def run_gpu(args, rank, world):
                                                   "max_abs": max(x[1] for x in q), "views": len(q)}
         if not small:
             probes.append(Probe("batched_mixed", sg.decode_mixed_arrays(packed), packed["model_id"], M, w,
-                                range(len(w.cameras)), 32, 22, hm.rast.view_image))
+                                range(len(w.cameras)), 32, 22, hm.rast.view_image, tile_h=args.tile_h))
         del hm, gm
     # the vector-quantised storage (Sec. 4.4): k = 256 codebooks per model and attribute
     vqd = None
@@ -566,7 +570,8 @@ def run_gpu(args, rank, world):
                                                      "the scene with means + N(0, 0.01), albedo + U[-0.1, 0.1]",
                        "loss_value": float(h2.loss[0].item())})
         if not small:
-            probes.append(Probe("plain_single_view", a2, m2, len(ws.models), ws, [0], 128, 23, h2.rast.view_image))
+            probes.append(Probe("plain_single_view", a2, m2, len(ws.models), ws, [0], 128, 23, h2.rast.view_image,
+                                tile_h=args.tile_h))
         del h2
 
     cfg5 = None
@@ -586,7 +591,7 @@ def run_gpu(args, rank, world):
                       "pixels_per_replica": rast.n_pix, "pairs": n_pairs, "l2": "flushed between timed steps",
                       "layout": "per model in Morton order (one-time reorder)" if args.layout == "morton"
                       else "as composed",
-                      "options": opts,
+                      "options": opts, "tile": f"16x{args.tile_h}",
                       "parallelism": f"replicas x{world}"},
            "fwd_mpix_s": fwd_value, "fwd_ms_per_step": ms_fwd_total / K,
            "launch": "eager" if args.eager else "cuda-graph replay",
@@ -631,8 +636,9 @@ def cfg5_bench(args, dev, K, pk, world, small):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def build(max_views, pixel_budget):
-        wv = WaveRasterizer(w.cameras, g.n, M, device=dev, bg=w.bg, max_views=max_views, pixel_budget=pixel_budget)
+    def build(max_views, pixel_budget, tile_h):
+        wv = WaveRasterizer(w.cameras, g.n, M, device=dev, bg=w.bg, max_views=max_views, pixel_budget=pixel_budget,
+                            tile_h=tile_h)
         wv.size_buffers(g, table)
         gen = torch.Generator(device=dev).manual_seed(5)
         d = [torch.randn((r.n_pix, 4), generator=gen, device=dev, dtype=torch.float32) * 1e-3 for r in wv.rasts]
@@ -656,17 +662,18 @@ def cfg5_bench(args, dev, K, pk, world, small):
             raise RuntimeError("cfg5: a wave's pair buffer overflowed during replay")
         return tot
 
-    def measure(max_views, pixel_budget):
-        wv, d, graph = build(max_views, pixel_budget)
+    def measure(max_views, pixel_budget, tile_h):
+        wv, d, graph = build(max_views, pixel_budget, tile_h)
         try:
             return replay_ms(graph, wv, 3) / 3
         finally:
             del wv, d, graph
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
-    # the batch shape (pixels and views per wave) picked by timing the whole captured step
+    # the tile and batch shapes (tile height; pixels and views per wave) picked by timing the whole
+    # captured step
     shape = autotune.tune_waves(measure, w.cameras, g.n, f"{w.name}|{g.n}|{len(w.cameras)}", use_cache=False)
-    waves, dls, full = build(shape["max_views"], shape["pixel_budget"])
+    waves, dls, full = build(shape["max_views"], shape["pixel_budget"], shape["tile_h"])
     fwd_graph = waves.capture(g, table)
     n_pix = sum(r.n_pix for r in waves.rasts)
 
@@ -698,7 +705,8 @@ def cfg5_bench(args, dev, K, pk, world, small):
     res = {"workload": w.name, "gaussians": g.n, "models": M, "views": len(w.cameras), "pixels": n_pix,
            "waves": [len(x) for x in waves.waves], "pairs": pairs,
            "wave_shape": {"pixel_budget": shape["pixel_budget"], "max_views": shape["max_views"],
-                          "picked_by": "autotune.tune_waves (captured fwd+bwd step timed per distinct wave plan)",
+                          "tile": f"16x{shape['tile_h']}",
+                          "picked_by": "autotune.tune_waves (captured fwd+bwd step timed per distinct shape)",
                           "candidates": shape["candidates"]},
            "mpix_s": n_pix * world * K / (ms_full / 1e3) / 1e6, "fwd_mpix_s": n_pix * world * K / (ms_fwd / 1e3) / 1e6,
            "ms_per_step": ms_full / K, "launch": "one CUDA graph per step: every wave's forward and backward",
@@ -706,7 +714,7 @@ def cfg5_bench(args, dev, K, pk, world, small):
            "roofline": roof, "stage_fracs": {k: round(v["frac"], 4) for k, v in stages.items()}}
     # quantisation error: a 4-view subset from float32 storage (same kernels)
     subset = [0, 21, 42, 63]
-    r32 = Rasterizer([w.cameras[v] for v in subset], g.n, M, device=dev, bg=w.bg)
+    r32 = Rasterizer([w.cameras[v] for v in subset], g.n, M, device=dev, bg=w.bg, tile_h=shape["tile_h"])
     g32 = upload_fp32(arrs, mid, M, dev)
     r32.forward(g32, table)
     q = [psnr_vs(waves.view_image(v), r32.view_image(j)) for j, v in enumerate(subset)]
@@ -715,7 +723,7 @@ def cfg5_bench(args, dev, K, pk, world, small):
     probe = None
     if not small:
         probe = Probe("batched_mixed_cfg5", sg.decode_mixed_arrays(packed), packed["model_id"], M, w, subset, 32, 24,
-                      waves.view_image)
+                      waves.view_image, tile_h=shape["tile_h"])
     del waves, full, fwd_graph, r32, g32, g, gr
     torch.cuda.synchronize()
     return res, probe
@@ -891,9 +899,9 @@ def accuracy(probes):
             for v, pix in pr.pix.items():
                 c = pr.w.cameras[v]
                 p = parallel.project_parallel(pool, comp, table, c, threads)
-                rgba, T, last, mg = oracle.render_pixels(p, c, pix, bg=pr.w.bg)
-                unc = certify.uncertain_records(p)
-                tile_unc = certify.uncertain_tile_mask(p, unc, c.W, c.H)[pix[:, 1], pix[:, 0]]
+                rgba, T, last, mg = oracle.render_pixels(p, c, pix, bg=pr.w.bg, tile=(16, pr.tile_h))
+                unc = certify.uncertain_records(p, 16, pr.tile_h)
+                tile_unc = certify.uncertain_tile_mask(p, unc, c.W, c.H, 16, pr.tile_h)[pix[:, 1], pix[:, 0]]
                 err = np.abs(pr.gpu[v] - rgba).max(-1)
                 ex = certify.near_tie(mg) | tile_unc
                 excused += int(((err > 2e-4) & ex).sum())

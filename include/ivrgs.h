@@ -169,7 +169,7 @@ typedef struct {
    of each tile's run ((0, 0) for an empty tile). d_n_pairs: device uint64 scalar receiving the
    number of pairs (in CAPACITY mode a value > capacity means the outputs are incomplete). */
 typedef struct {
-    int32_t tile_w, tile_h; /* 16 x 16 in this library version */
+    int32_t tile_w, tile_h; /* tile_w = 16; tile_h = 16 or 8 (other shapes: IVRGS_ERR_UNSUPPORTED) */
     int64_t n_tiles;
     int64_t capacity;
     uint32_t* tiles;
@@ -240,15 +240,20 @@ ivrgs_status ivrgs_project(const ivrgs_gaussians* g, const float* d_edit_table, 
 
 /* Workspace bytes ivrgs_bin needs for p->n * n_views records (below IVRGS_MAX_PAIRS, i.e. 2^30, as
    for the pairs: the radix look-back carries 30-bit counts) and `capacity` pairs
-   (about 57 bytes per record plus 9 per pair). */
+   (about 57 bytes per record plus 9 per pair). Tiles are tile_w = 16 pixels wide and tile_h = 16
+   or 8 high (any other shape: IVRGS_ERR_UNSUPPORTED); the tile shape is not the paper's (it does
+   not fix one), a launch shape picked for speed, and it decides the tile lists (a Gaussian is
+   listed for every tile of its rectangle) and so, at pixels outside its 3-sigma radius but
+   inside its rectangle, the image. */
 ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera* cams, int32_t tile_w,
                                  int32_t tile_h, int64_t capacity, size_t* bytes);
 
 /* Tile binning by radix sort (the tile-based rasterisation of 3DGS that Sec. 3 builds on:
    projected Gaussians are composited in depth order per screen tile). Per record: tile
    rectangle (half-open) x0 = clamp(floor((u - r)/tile_w), 0, Gx),
-   x1 = clamp(floor((u + r)/tile_w) + 1, 0, Gx) (same for y) evaluated in float32; one pair per
-   covered tile. Ordering: the covered records are radix-sorted by the bits of their float
+   x1 = clamp(floor((u + r)/tile_w) + 1, 0, Gx) (the same for y with tile_h) evaluated in
+   float32; one pair per covered tile. out->tile_w and out->tile_h give the tile shape (16 x 16
+   or 16 x 8); every later call with these bins uses it. Ordering: the covered records are radix-sorted by the bits of their float
    depth (stable, 4 passes of 8 bits), their pairs are emitted in that order and then
    radix-sorted by tile id (stable, one pass per 8 bits of the largest tile id); both sorts
    are onesweep LSD sorts with decoupled look-back. The result equals the stable sort of all
@@ -278,7 +283,8 @@ ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32
 ivrgs_status ivrgs_bin_check(const void* d_workspace, void* stream);
 
 /* Front-to-back alpha compositing per tile (Sec. 3 second equation, C = sum T_i alpha_i c_i,
-   T_i = prod_{j<i}(1 - alpha_j); alpha channel as in Sec. 4.2). One CTA per 16x16 tile.
+   T_i = prod_{j<i}(1 - alpha_j); alpha channel as in Sec. 4.2). One CTA per tile (16 x 16 or
+   16 x 8, from b->tile_h).
    Outputs per packed pixel: d_rgba [.][4] = (C + T bg, 1 - T), d_final_T [.] = T after the
    last contributor, d_last [.] = 1 + position (within the tile's run) of the last
    contributing Gaussian, 0 if none. bg: host float[3]. */

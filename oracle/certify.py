@@ -40,20 +40,25 @@ def near_plane_uncertain(p: Projected, znear: float = ZNEAR) -> np.ndarray:
     return np.abs(p.depth - znear) < NEAR_MARGIN
 
 
-def uncertain_records(p: Projected, tile: int = 16) -> np.ndarray:
+def uncertain_records(p: Projected, tile: int = 16, tile_h: int = None) -> np.ndarray:
+    """Records whose float32 decisions may legitimately differ from the oracle's, for tiles of
+    tile x tile_h pixels (tile_h defaults to tile)."""
+    th = tile if tile_h is None else tile_h
     live = p.radius > 0
     unc = live & (p.radius_margin < RADIUS_MARGIN)
     unc |= depth_uncertain(p) | near_plane_uncertain(p)
     r = p.radius.astype(np.float64)
-    for e in (p.uv[:, 0] - r, p.uv[:, 0] + r, p.uv[:, 1] - r, p.uv[:, 1] + r):
-        q = e / tile
-        d = np.abs(q - np.round(q)) * tile
+    for e, t in ((p.uv[:, 0] - r, tile), (p.uv[:, 0] + r, tile), (p.uv[:, 1] - r, th), (p.uv[:, 1] + r, th)):
+        q = e / t
+        d = np.abs(q - np.round(q)) * t
         unc |= live & (d < RECT_MARGIN_PX)
     return unc
 
 
-def uncertain_tile_mask(p: Projected, unc: np.ndarray, W: int, H: int, tile: int = 16) -> np.ndarray:
-    gx, gy = (W + tile - 1) // tile, (H + tile - 1) // tile
+def uncertain_tile_mask(p: Projected, unc: np.ndarray, W: int, H: int, tile: int = 16,
+                        tile_h: int = None) -> np.ndarray:
+    th = tile if tile_h is None else tile_h
+    gx, gy = (W + tile - 1) // tile, (H + th - 1) // th
     mask = np.zeros((gy, gx), bool)
     if (unc & near_plane_uncertain(p)).any():  # a record at the near plane may cover any pixel
         mask[:] = True
@@ -62,11 +67,11 @@ def uncertain_tile_mask(p: Projected, unc: np.ndarray, W: int, H: int, tile: int
         r = p.radius[g] + 1
         x0 = max(int(math.floor((u - r) / tile)) - 1, 0)
         x1 = min(int(math.floor((u + r) / tile)) + 2, gx)
-        y0 = max(int(math.floor((v - r) / tile)) - 1, 0)
-        y1 = min(int(math.floor((v + r) / tile)) + 2, gy)
+        y0 = max(int(math.floor((v - r) / th)) - 1, 0)
+        y1 = min(int(math.floor((v + r) / th)) + 2, gy)
         if x0 < x1 and y0 < y1:
             mask[y0:y1, x0:x1] = True
-    return np.kron(mask, np.ones((tile, tile), bool))[:H, :W]
+    return np.kron(mask, np.ones((th, tile), bool))[:H, :W]
 
 
 def uncertain_pixels(p: Projected, unc: np.ndarray, pix: np.ndarray, margin: float = 1e-2) -> np.ndarray:

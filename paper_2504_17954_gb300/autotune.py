@@ -4,9 +4,9 @@
 backward blend, the split walk of long runs over CTA clusters and its chunk length, radix
 ranking and offsets) on the caller's own workload with CUDA events: coordinate descent from the
 current setting, one option at a time over all its values, repeated until a sweep changes
-nothing (at most ``sweeps`` times). ``tune_waves`` picks the view-wave shape of a
-``WaveRasterizer`` (pixels and views per binning call) by timing the caller's whole step for
-each distinct wave plan. Choices are cached in a JSON file keyed by GPU name and a workload
+nothing (at most ``sweeps`` times). ``tune_waves`` picks the tile height and the view-wave shape
+of a ``WaveRasterizer`` (pixels and views per binning call) by timing the caller's whole step
+for each distinct shape. Choices are cached in a JSON file keyed by GPU name and a workload
 signature. Every option and shape gives the same results (up to float32 rounding in the split
 walk), so tuning changes speed only.
 """
@@ -36,6 +36,9 @@ SPACE = {
 # wave mean more calls and launches
 WAVE_BUDGETS = (8 << 20, 16 << 20, 32 << 20)
 WAVE_VIEWS = (32,)
+# tile heights (tiles are 16 pixels wide): 8-pixel-high tiles shorten each tile's list and the
+# walk of a heavy tile, for more pairs to bin and sort
+TILE_HEIGHTS = (16, 8)
 
 
 def _cache_path() -> str:
@@ -130,17 +133,19 @@ def _store_cache(path, cache):
         pass
 
 
-def tune_waves(measure: Callable[[int, int], float], cams: Sequence, n_gaussians: int, signature: str,
+def tune_waves(measure: Callable[[int, int, int], float], cams: Sequence, n_gaussians: int, signature: str,
                budgets: Sequence[int] = WAVE_BUDGETS, max_views: Sequence[int] = WAVE_VIEWS,
-               use_cache: bool = True, device_name: Optional[str] = None) -> Dict:
-    """Pick the view-wave shape of a many-view render for the caller's own step.
+               tile_heights: Sequence[int] = TILE_HEIGHTS, use_cache: bool = True,
+               device_name: Optional[str] = None) -> Dict:
+    """Pick the tile shape and the view-wave shape of a many-view render for the caller's own step.
 
-    ``measure(max_views, pixel_budget)`` builds the waves with that shape, runs the caller's
-    step (for instance a captured forward+backward over all waves) and returns its time in ms;
-    it may raise (a wave over the per-call pair limit, out of memory), and that shape is then
-    skipped. Shapes that give the same wave plan (``rasterizer.plan_waves``) are measured once.
-    Returns {"max_views", "pixel_budget", "waves" (views per wave), "ms", "candidates" (every
-    measured shape with its time or the error)}; cached per GPU name and ``signature``."""
+    ``measure(max_views, pixel_budget, tile_h)`` builds the waves with that shape (tiles 16
+    pixels wide and tile_h high), runs the caller's step (for instance a captured forward+backward
+    over all waves) and returns its time in ms; it may raise (a wave over the per-call pair limit,
+    out of memory), and that shape is then skipped. Shapes that give the same tile height and wave
+    plan (``rasterizer.plan_waves``) are measured once. Returns {"max_views", "pixel_budget",
+    "tile_h", "waves" (views per wave), "ms", "candidates" (every measured shape with its time or
+    the error)}; cached per GPU name and ``signature``."""
     from .rasterizer import plan_waves
     if device_name is None:
         import torch
@@ -151,23 +156,25 @@ def tune_waves(measure: Callable[[int, int], float], cams: Sequence, n_gaussians
     if use_cache and key in cache:
         return cache[key]
     plans = {}
-    for mv in max_views:
-        for pb in budgets:
-            plan = tuple(len(w) for w in plan_waves(cams, n_gaussians, mv, pb))
-            plans.setdefault(plan, (mv, pb))  # the first shape that gives a plan stands for it
+    for th in tile_heights:
+        for mv in max_views:
+            for pb in budgets:
+                plan = tuple(len(w) for w in plan_waves(cams, n_gaussians, mv, pb))
+                plans.setdefault((th, plan), (mv, pb))  # the first shape that gives a plan stands for it
     best = None
     cands = []
-    for plan, (mv, pb) in plans.items():
+    for (th, plan), (mv, pb) in plans.items():
+        c = {"max_views": mv, "pixel_budget": pb, "tile_h": th, "waves": list(plan)}
         try:
-            ms = float(measure(mv, pb))
+            ms = float(measure(mv, pb, th))
         except (RuntimeError, MemoryError) as e:
-            cands.append({"max_views": mv, "pixel_budget": pb, "waves": list(plan), "error": str(e)[:200]})
+            cands.append(dict(c, error=str(e)[:200]))
             continue
-        cands.append({"max_views": mv, "pixel_budget": pb, "waves": list(plan), "ms": ms})
+        cands.append(dict(c, ms=ms))
         if best is None or ms < best["ms"]:
-            best = {"max_views": mv, "pixel_budget": pb, "waves": list(plan), "ms": ms}
+            best = dict(c, ms=ms)
     if best is None:
-        raise RuntimeError(f"tune_waves: no wave shape could be measured: {cands}")
+        raise RuntimeError(f"tune_waves: no shape could be measured: {cands}")
     best["candidates"] = cands
     if use_cache:
         cache[key] = best

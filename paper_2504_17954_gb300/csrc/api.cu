@@ -77,12 +77,16 @@ static ivrgs_status invalid(const std::string& msg) {
 
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb) {
+ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb, int th) {
+    if (!tile_height_ok(th)) {
+        set_error("tiles are 16 pixels wide and 16 or 8 high (got height " + std::to_string(th) + ")");
+        return IVRGS_ERR_UNSUPPORTED;
+    }
     if (!cams) return invalid("cams is NULL");
     if (n_views < 1 || n_views > IVRGS_MAX_VIEWS)
         return invalid("n_views must be in [1, " + std::to_string(IVRGS_MAX_VIEWS) + "]");
     cb->n = n_views;
-    cb->pad = 0;
+    cb->th = th;
     long long tiles = 0;
     for (int v = 0; v < n_views; ++v) {
         const ivrgs_camera& c = cams[v];
@@ -95,7 +99,7 @@ ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch*
         d.W = c.W;
         d.H = c.H;
         d.gx = (c.W + kTile - 1) / kTile;
-        d.gy = (c.H + kTile - 1) / kTile;
+        d.gy = (c.H + th - 1) / th;
         d.tile0 = tiles;
         tiles += (long long)d.gx * d.gy;
         d.pix0 = c.pix_offset;
@@ -179,10 +183,11 @@ static ivrgs_status check_projected(const ivrgs_projected* p, int64_t n, int32_t
 
 static ivrgs_status check_bins(const ivrgs_bins* b, const CamBatch& cb) {
     if (!b) return invalid("bins is NULL");
-    if (b->tile_w != kTile || b->tile_h != kTile) {
-        set_error("bins: only 16x16 tiles are implemented");
+    if (b->tile_w != kTile || !tile_height_ok(b->tile_h)) {
+        set_error("bins: tiles are 16 pixels wide and 16 or 8 high");
         return IVRGS_ERR_UNSUPPORTED;
     }
+    if (b->tile_h != cb.th) return invalid("bins: tile_h does not match the camera batch");
     if (b->n_tiles != cb.n_tiles)
         return invalid("bins: n_tiles = " + std::to_string(b->n_tiles) + " but the cameras have " +
                        std::to_string(cb.n_tiles) + " tiles");
@@ -326,13 +331,13 @@ ivrgs_status ivrgs_bin_workspace(int64_t n, int32_t n_views, const ivrgs_camera*
                                  int32_t tile_h, int64_t capacity, size_t* bytes) {
     set_error("");
     if (!bytes) return invalid("bytes is NULL");
-    if (tile_w != kTile || tile_h != kTile) {
-        set_error("only 16x16 tiles are implemented");
+    if (tile_w != kTile || !tile_height_ok(tile_h)) {
+        set_error("tiles are 16 pixels wide and 16 or 8 high");
         return IVRGS_ERR_UNSUPPORTED;
     }
     if (n < 0 || capacity < 0 || capacity >= IVRGS_MAX_PAIRS) return invalid("bad n or capacity");
     static thread_local CamBatch cb;
-    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb, tile_h);
     if (st) return st;
     if (n * (long long)n_views >= IVRGS_MAX_PAIRS) return invalid("n * n_views must be below 2^30 for binning");
     *bytes = plan_bin(n * (long long)n_views, cb.n_tiles, capacity).total_bytes;
@@ -357,7 +362,7 @@ ivrgs_status ivrgs_bin(const ivrgs_projected* p, const ivrgs_camera* cams, int32
                        void* d_workspace, size_t ws_bytes, ivrgs_bins* out, void* stream) {
     set_error("");
     static thread_local CamBatch cb;
-    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb, out ? out->tile_h : kTile);
     if (st) return st;
     if (!p) return invalid("projected is NULL");
     if ((st = check_projected(p, p->n, n_views))) return st;
@@ -417,7 +422,7 @@ ivrgs_status ivrgs_render(const ivrgs_projected* p, const ivrgs_bins* b, const i
                           const float* bg, float* d_rgba, float* d_final_T, uint32_t* d_last, void* stream) {
     set_error("");
     static thread_local CamBatch cb;
-    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb, b ? b->tile_h : kTile);
     if (st) return st;
     if (!p) return invalid("projected is NULL");
     if ((st = check_projected(p, p->n, n_views))) return st;
@@ -432,7 +437,7 @@ ivrgs_status ivrgs_render_aux(const ivrgs_gaussians* g, const float* d_edit_tabl
                               void* stream) {
     set_error("");
     static thread_local CamBatch cb;
-    ivrgs_status st = make_cam_batch(cams, n_views, &cb);
+    ivrgs_status st = make_cam_batch(cams, n_views, &cb, b ? b->tile_h : kTile);
     if (st) return st;
     if ((st = check_gaussians(g, "g", true, true))) return st;
     if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
@@ -466,7 +471,7 @@ static ivrgs_status render_backward_impl(int accumulate, const ivrgs_gaussians* 
     if (g->sh && (!grad->sh || grad->sh_degree != g->sh_degree))
         return invalid("g has SH colour: grad->sh must be set, with the same sh_degree");
     static thread_local CamBatch cb;
-    if ((st = make_cam_batch(cams, n_views, &cb))) return st;
+    if ((st = make_cam_batch(cams, n_views, &cb, b ? b->tile_h : kTile))) return st;
     if ((st = check_projected(p, g->n, n_views))) return st;
     if ((st = check_bins(b, cb))) return st;
     if (!d_edit_table || !bg || !d_final_T || !d_last || !d_dL_drgba || !d_edit_grad)

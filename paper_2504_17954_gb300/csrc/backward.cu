@@ -325,7 +325,7 @@ __device__ __forceinline__ void stage_entry_bwd(int slot, int e, const float2* _
 // from their state, adding the per-Gaussian record gradients; e_top is at most the CTA's largest
 // last contributor and w_top the warp's (entries at or beyond it are skipped by the whole warp).
 // e_lo and e_top are the same for every thread of the CTA.
-template <int P>
+template <int P, int TH>
 __device__ __forceinline__ void bwd_walk(int e_lo, int e_top, int w_top, const float2* __restrict__ xy,
                                          const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
                                          long long n, const unsigned* __restrict__ values, unsigned run0,
@@ -333,7 +333,7 @@ __device__ __forceinline__ void bwd_walk(int e_lo, int e_top, int w_top, const f
                                          float4* s_a, float4* s_b, float2* s_c, long long* s_gi, float2* s_rows,
                                          unsigned char* list, float4* __restrict__ g0, float4* __restrict__ g1,
                                          float* __restrict__ g2) {
-    constexpr int NT = kTilePix / P;
+    constexpr int NT = kTile * TH / P;
     float T[P], DS[P];
     float4 d[P];
     unsigned my_last[P];
@@ -379,10 +379,10 @@ __device__ __forceinline__ void bwd_walk(int e_lo, int e_top, int w_top, const f
 }
 
 // Per tile, P vertically adjacent pixels per thread; each warp covers a compact band of rows.
-// With 4 pixels per thread the register budget is set for 18 CTAs per SM (56 registers, no
-// spills), two more than the compiler's own choice.
-template <int P>
-__global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
+// With 4 pixels per thread on 16-pixel-high tiles the register budget is set for 18 CTAs per SM
+// (56 registers), two more than the compiler's own choice.
+template <int P, int TH>
+__global__ void __launch_bounds__(kTile * TH / P, P == 4 && TH == 16 ? 18 : 1) k_render_bwd(
     const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
     const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
     float3 bg, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
     __shared__ float2 s_c[kBwdBatch];
     __shared__ long long s_gi[kBwdBatch];
     __shared__ float2 s_rows[band_cull<P>() ? kBwdBatch : 1];
-    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBwdBatch : 1];
+    __shared__ unsigned char s_list[band_cull<P>() ? kTile * TH / P / 32 * kBwdBatch : 1];
     __shared__ unsigned s_max;
     const long long tile = blockIdx.x;
     const int v = view_of_tile(cb, tile);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
     const int local = (int)(tile - cam.tile0);
     const int tx = local % cam.gx, ty = local / cam.gx;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
+    const int py0 = ty * TH + (threadIdx.x / kTile) * P;
     const float fx = (float)px + 0.5f;
     // offset of this thread's first row in its 4-row group (0 whenever P is a multiple of 4,
     // since py0 is then one too: known at compile time, so the groups are indexed statically)
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
     const int len = min((int)(rg.y - rg.x), top);
     if (split_min >= 0 ? len > split_min : len <= -split_min - 1) return;
     const float ylo = (float)(py0 - ((int)(threadIdx.x & 16u) >> 4) * P) + 0.5f;  // this warp's first pixel row
-    bwd_walk<P>(0, top, (int)__reduce_max_sync(0xffffffffu, mx), xy, conic_o, rgbd, n, values, rg.x,
+    bwd_walk<P, TH>(0, top, (int)__reduce_max_sync(0xffffffffu, mx), xy, conic_o, rgbd, n, values, rg.x,
                 (long long)v * n, fx, fyg, q0, ylo, st, s_a, s_b, s_c, s_gi, s_rows,
                 s_list + (band_cull<P>() ? (threadIdx.x >> 5) * kBwdBatch : 0), g0, g1, g2);
 }
@@ -439,14 +439,14 @@ __global__ void __launch_bounds__(kTilePix / P, P == 4 ? 18 : 1) k_render_bwd(
 // ---------------------------------------------------------------------------------------------
 // Forward partials of the entries [lo, hi) over each pixel's contributors (entries before its
 // last contributor with alpha >= 1/255): T_k and D_k as above. lo, hi uniform per CTA.
-template <int P>
+template <int P, int TH>
 __device__ __forceinline__ void bwd_chunk_partial(int lo, int hi, const float2* __restrict__ xy,
                                                   const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
                                                   long long n, const unsigned* __restrict__ values, unsigned run0,
                                                   long long vbase, float fx, float fyg, int q0, const BwdPix<P>& st,
                                                   float (&Tk)[P], float (&Dk)[P], float4* s_a, float4* s_b,
                                                   float2* s_c) {
-    constexpr int NT = kTilePix / P;
+    constexpr int NT = kTile * TH / P;
     constexpr int NG = (P + 3) / 4;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -500,8 +500,8 @@ __device__ __forceinline__ void bwd_chunk_partial(int lo, int hi, const float2* 
     }
 }
 
-template <int P>
-__global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k_render_bwd_split(
+template <int P, int TH>
+__global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTile * TH / P) k_render_bwd_split(
     const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd, long long n,
     const unsigned* __restrict__ values, const uint2* __restrict__ ranges, const __grid_constant__ CamBatch cb,
     float3 bg, int split_min, const float* __restrict__ final_T, const unsigned* __restrict__ last_in,
@@ -511,8 +511,8 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k
     __shared__ float2 s_c[kBwdBatch];
     __shared__ long long s_gi[kBwdBatch];
     __shared__ float2 s_rows[band_cull<P>() ? kBwdBatch : 1];
-    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBwdBatch : 1];
-    __shared__ float s_T[kTilePix], s_D[kTilePix];
+    __shared__ unsigned char s_list[band_cull<P>() ? kTile * TH / P / 32 * kBwdBatch : 1];
+    __shared__ float s_T[kTile * TH], s_D[kTile * TH];
     __shared__ unsigned s_max;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -522,7 +522,7 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k
     const int local = (int)(tile - cam.tile0);
     const int tx = local % cam.gx, ty = local / cam.gx;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py0 = ty * kTile + (threadIdx.x / kTile) * P;
+    const int py0 = ty * TH + (threadIdx.x / kTile) * P;
     const float fx = (float)px + 0.5f;
     const int q0 = (P % 4 == 0) ? 0 : (py0 & 3);
     const float fyg = (float)(py0 - q0) + 0.5f;
@@ -544,7 +544,7 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k
     // 1. per-chunk forward partials (one chunk: not needed)
     float Tk[P], Dk[P];
     if (nc > 1 && rank < nc) {
-        bwd_chunk_partial<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, st, Tk, Dk, s_a, s_b, s_c);
+        bwd_chunk_partial<P, TH>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, st, Tk, Dk, s_a, s_b, s_c);
     } else {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -583,7 +583,7 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P) k
     if (rank < nc) {
         const int top = min(hi, cta_last);
         const float ylo = (float)(py0 - ((int)(threadIdx.x & 16u) >> 4) * P) + 0.5f;
-        bwd_walk<P>(lo, top, min(hi, warp_last), xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, ylo, st, s_a,
+        bwd_walk<P, TH>(lo, top, min(hi, warp_last), xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, ylo, st, s_a,
                     s_b, s_c, s_gi, s_rows, s_list + (band_cull<P>() ? (threadIdx.x >> 5) * kBwdBatch : 0), g0,
                     g1, g2);
     }
@@ -961,45 +961,24 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
         if (split && (e = split_fork(s, &side)) != cudaSuccess) return e;
         if (split && options().render_split == 4) {  // the long walks first, on the side stream, unsplit
             const int hs = -sm - 1;
-            if (ppt == 1)
-                k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
-                                                                            final_T, last, dl, g0, g1, g2, hs);
-            else if (ppt == 8)
-                k_render_bwd<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb,
-                                                                                bgc, final_T, last, dl, g0, g1, g2, hs);
-            else if (ppt == 4)
-                k_render_bwd<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb,
-                                                                                bgc, final_T, last, dl, g0, g1, g2, hs);
-            else
-                k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb,
-                                                                                bgc, final_T, last, dl, g0, g1, g2, hs);
+            blend_shape(ppt, cb.th, [&](auto P, auto TH) {
+                constexpr int kP = decltype(P)::value, kTH = decltype(TH)::value;
+                k_render_bwd<kP, kTH><<<(unsigned)cb.n_tiles, kTile * kTH / kP, 0, side>>>(
+                    xy, co, cd, p->n, b->values, rg, cb, bgc, final_T, last, dl, g0, g1, g2, hs);
+            });
         } else if (split) {
             const unsigned grid = (unsigned)(cb.n_tiles * kSplit);
-            if (ppt == 1)
-                k_render_bwd_split<1><<<grid, kTilePix, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
-                                                                   final_T, last, dl, g0, g1, g2);
-            else if (ppt == 8)
-                k_render_bwd_split<8><<<grid, kTilePix / 8, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
-                                                                       final_T, last, dl, g0, g1, g2);
-            else if (ppt == 4)
-                k_render_bwd_split<4><<<grid, kTilePix / 4, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
-                                                                       final_T, last, dl, g0, g1, g2);
-            else
-                k_render_bwd_split<2><<<grid, kTilePix / 2, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
-                                                                       final_T, last, dl, g0, g1, g2);
+            blend_shape(ppt, cb.th, [&](auto P, auto TH) {
+                constexpr int kP = decltype(P)::value, kTH = decltype(TH)::value;
+                k_render_bwd_split<kP, kTH><<<grid, kTile * kTH / kP, 0, side>>>(
+                    xy, co, cd, p->n, b->values, rg, cb, bgc, sm, final_T, last, dl, g0, g1, g2);
+            });
         }
-        if (ppt == 1)
-            k_render_bwd<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, final_T,
-                                                                     last, dl, g0, g1, g2, sm);
-        else if (ppt == 8)
-            k_render_bwd<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
-                                                                         final_T, last, dl, g0, g1, g2, sm);
-        else if (ppt == 4)
-            k_render_bwd<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
-                                                                         final_T, last, dl, g0, g1, g2, sm);
-        else
-            k_render_bwd<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, bgc,
-                                                                         final_T, last, dl, g0, g1, g2, sm);
+        blend_shape(ppt, cb.th, [&](auto P, auto TH) {
+            constexpr int kP = decltype(P)::value, kTH = decltype(TH)::value;
+            k_render_bwd<kP, kTH><<<(unsigned)cb.n_tiles, kTile * kTH / kP, 0, s>>>(
+                xy, co, cd, p->n, b->values, rg, cb, bgc, final_T, last, dl, g0, g1, g2, sm);
+        });
         if (split) {
             const cudaError_t el = cudaGetLastError();
             const cudaError_t ej = split_join(s);

@@ -53,9 +53,9 @@ __device__ __forceinline__ int view_of_record(long long i, long long n, long lon
     return total <= 0xffffffffll ? (int)((unsigned)i / (unsigned)n) : (int)(i / n);
 }
 
-// tile rows [ya, yb) of the rectangle whose band of pixel-centre rows [16 ty + 0.5, 16 ty + 15.5]
+// tile rows [ya, yb) of the rectangle whose band of pixel-centre rows [th ty + 0.5, th ty + th - 0.5]
 // meets the ellipse's height [v - Y, v + Y] (the rows in it are still tested one by one)
-__device__ __forceinline__ void cull_rows(const CullEll& e, int y0, int y1, int& ya, int& yb) {
+__device__ __forceinline__ void cull_rows(const CullEll& e, int y0, int y1, int th, int& ya, int& yb) {
     ya = y0;
     yb = y1;
     if (e.mode == 2) return;
@@ -63,27 +63,27 @@ __device__ __forceinline__ void cull_rows(const CullEll& e, int y0, int y1, int&
         yb = ya;
         return;
     }
-    const float inv = 1.0f / (float)kTile;
-    const float a = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(e.v, e.Y), (float)kTile - 0.5f), inv));
+    const float inv = 1.0f / (float)th;  // exact: th is 16 or 8
+    const float a = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(e.v, e.Y), (float)th - 0.5f), inv));
     const float b = floorf(__fmul_rn(__fsub_rn(__fadd_rn(e.v, e.Y), 0.5f), inv)) + 1.0f;
     ya = (int)fminf(fmaxf(a, (float)y0), (float)y1);
     yb = (int)fminf(fmaxf(b, (float)ya), (float)y1);
 }
 
 // number of pairs of record i: every tile of its rectangle, or with culling the kept tiles
-__device__ __forceinline__ unsigned record_pairs(float2 p, float4 co, int r, const CamDev& c, int cull) {
+__device__ __forceinline__ unsigned record_pairs(float2 p, float4 co, int r, const CamDev& c, int th, int cull) {
     if (r <= 0) return 0u;
     int x0, x1, y0, y1;
-    tile_rect(p.x, p.y, r, c.gx, c.gy, x0, x1, y0, y1);
+    tile_rect(p.x, p.y, r, c.gx, c.gy, th, x0, x1, y0, y1);
     if (!(x1 > x0 && y1 > y0)) return 0u;
     if (!cull) return (unsigned)((x1 - x0) * (y1 - y0));
     const CullEll e = cull_setup(p, co, 1);
     int ya, yb;
-    cull_rows(e, y0, y1, ya, yb);
+    cull_rows(e, y0, y1, th, ya, yb);
     unsigned tot = 0;
     for (int ty = ya; ty < yb; ++ty) {
         int lo, hi;
-        cull_row(e, ty, x0, x1, lo, hi);
+        cull_row(e, ty, th, x0, x1, lo, hi);
         tot += (unsigned)(hi - lo);
     }
     return tot;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kScanThreads) k_count(const float2* __restrict
         const Rec q = nxt;
         if (j + 1 < kScanItems) nxt = load(i + kScanThreads);
         if (i < total) {
-            const unsigned c = record_pairs(q.p, q.co, q.r, cb.c[view_of_record(i, n, total)], cull);
+            const unsigned c = record_pairs(q.p, q.co, q.r, cb.c[view_of_record(i, n, total)], cb.th, cull);
             cnt[i] = c;
             vis += c ? 1u : 0u;
             pairs += c;
@@ -400,9 +400,9 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                     c = cnts[k];
                     const float2 p = make_float2(r0.x, r0.y);
                     if (c && r > 0) {
-                        tile_rect(p.x, p.y, r, cb.c[v].gx, cb.c[v].gy, x0, x1, y0, y1);
+                        tile_rect(p.x, p.y, r, cb.c[v].gx, cb.c[v].gy, cb.th, x0, x1, y0, y1);
                         e = cull_setup(p, make_float4(r0.z, r0.w, r1.x, r1.y), cull);
-                        cull_rows(e, y0, y1, ya, yb);
+                        cull_rows(e, y0, y1, cb.th, ya, yb);
                         rows = (unsigned)(yb - ya);
                     }
                 }
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kScanThreads) k_emit(const float4* __restrict_
                 const uint4 mp = s_map[ti];
                 const CullEll e{q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, rc.x};
                 const int ty = rc.w + (int)(rr - s_rst[warp][k]);
-                cull_row(e, ty, rc.y, rc.z, lo, hi);
+                cull_row(e, ty, cb.th, rc.y, rc.z, lo, hi);
                 rowbase = mp.y + (unsigned)ty * mp.z;
                 g = mp.x;
                 if (hi > lo) {

@@ -2,6 +2,8 @@
 // blend so that both take identical float32 decisions (skip, cut-off, termination).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ivrgs {
@@ -122,19 +124,37 @@ __device__ __forceinline__ float row_p2(const RowGroup& q, const float4& sa, int
     return __fmaf_rn(sa.z, (float)(p * p), __fmaf_rn(-(float)p, q.k1, q.base));
 }
 
+// Calls f(P, TH) with the launch shape as integral constants: P pixels per thread (1, 2, 4 or 8),
+// tiles TH = 16 or 8 pixels high; with 8-pixel-high tiles at most 4 pixels per thread, so that a
+// tile keeps a full warp for the walks' votes (8 is taken as 4).
+template <typename F>
+inline void blend_shape(int ppt, int th, F&& f) {
+    using std::integral_constant;
+    if (th == 8) {
+        if (ppt == 1) f(integral_constant<int, 1>{}, integral_constant<int, 8>{});
+        else if (ppt == 2) f(integral_constant<int, 2>{}, integral_constant<int, 8>{});
+        else f(integral_constant<int, 4>{}, integral_constant<int, 8>{});
+        return;
+    }
+    if (ppt == 1) f(integral_constant<int, 1>{}, integral_constant<int, 16>{});
+    else if (ppt == 2) f(integral_constant<int, 2>{}, integral_constant<int, 16>{});
+    else if (ppt == 8) f(integral_constant<int, 8>{}, integral_constant<int, 16>{});
+    else f(integral_constant<int, 4>{}, integral_constant<int, 16>{});
+}
+
 // Position of a thread's pixels in its tile.
 struct TilePos {
     int px, py0, q0;
     float fx, fyg;
 };
 
-template <int P>
+template <int P, int TH>
 __device__ __forceinline__ TilePos tile_pos(const CamDev& cam, long long tile) {
     TilePos t;
     const int local = (int)(tile - cam.tile0);
     const int tx = local % cam.gx, ty = local / cam.gx;
     t.px = tx * kTile + (threadIdx.x & (kTile - 1));
-    t.py0 = ty * kTile + (threadIdx.x / kTile) * P;
+    t.py0 = ty * TH + (threadIdx.x / kTile) * P;
     t.fx = (float)t.px + 0.5f;
     t.q0 = t.py0 & 3;                              // offset of this thread's first row in its group
     t.fyg = (float)(t.py0 - t.q0) + 0.5f;          // centre of the group's first row

@@ -11,8 +11,7 @@
 
 namespace ivrgs {
 
-constexpr int kTile = 16;              // tile edge (pixels); one CTA of 256 threads per tile
-constexpr int kTilePix = kTile * kTile;
+constexpr int kTile = 16;              // tile width (pixels); the tile height is 16 or 8 (CamBatch::th)
 constexpr float kGuard = 1.3f;         // guard band of x/z, y/z inside the Jacobian
 constexpr float kAlphaMax = 0.99f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
@@ -33,7 +32,7 @@ struct CamDev {
 
 struct CamBatch {
     int n;
-    int pad;
+    int th;  // tile height (pixels): 16 or 8; tiles are kTile wide
     long long n_tiles;
     CamDev c[IVRGS_MAX_VIEWS];
 };
@@ -48,15 +47,17 @@ __device__ __forceinline__ int view_of_tile(const CamBatch& cb, long long t) {
     return lo;
 }
 
-// float32 tile rectangle, half-open: x0 = clamp(floor((u - r)/T), 0, G), x1 = clamp(floor((u + r)/T) + 1, 0, G)
-__device__ __forceinline__ void tile_rect(float u, float v, int r, int gx, int gy, int& x0, int& x1, int& y0,
-                                          int& y1) {
+// float32 tile rectangle, half-open: x0 = clamp(floor((u - r)/kTile), 0, G), x1 = clamp(floor((u + r)/kTile)
+// + 1, 0, G), and the same in y with the tile height th
+__device__ __forceinline__ void tile_rect(float u, float v, int r, int gx, int gy, int th, int& x0, int& x1,
+                                          int& y0, int& y1) {
     const float fr = (float)r;
     const float inv = 1.0f / (float)kTile;  // exact: power of two
+    const float invh = 1.0f / (float)th;    // exact: th is 16 or 8
     float a = floorf(__fmul_rn(__fsub_rn(u, fr), inv));
     float b = floorf(__fmul_rn(__fadd_rn(u, fr), inv)) + 1.0f;
-    float c = floorf(__fmul_rn(__fsub_rn(v, fr), inv));
-    float d = floorf(__fmul_rn(__fadd_rn(v, fr), inv)) + 1.0f;
+    float c = floorf(__fmul_rn(__fsub_rn(v, fr), invh));
+    float d = floorf(__fmul_rn(__fadd_rn(v, fr), invh)) + 1.0f;
     x0 = (int)fminf(fmaxf(a, 0.0f), (float)gx);
     x1 = (int)fminf(fmaxf(b, 0.0f), (float)gx);
     y0 = (int)fminf(fmaxf(c, 0.0f), (float)gy);
@@ -88,7 +89,9 @@ struct BinPlan {
         off_cnt, off_cnt2, off_prec, off_lookback_rec, off_lookback, off_keys_alt, off_vals_alt, total_bytes;
 };
 
-ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb);
+// tile heights the kernels are built for
+inline bool tile_height_ok(int th) { return th == 16 || th == 8; }
+ivrgs_status make_cam_batch(const ivrgs_camera* cams, int32_t n_views, CamBatch* cb, int th = kTile);
 
 // tunable launch shapes (set through ivrgs_set_option; read by the launchers)
 struct Options {

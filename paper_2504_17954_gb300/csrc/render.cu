@@ -123,13 +123,13 @@ __device__ __forceinline__ void stage_entry(int slot, int e, const float2* __res
 // their current state. The CTA stages batches of kBatch Gaussians in shared memory and leaves
 // as soon as every pixel is done (barrier count), so e0, e1 must be the same for every thread
 // of the CTA.
-template <int P>
+template <int P, int TH>
 __device__ __forceinline__ void fwd_walk(int e0, int e1, const float2* __restrict__ xy,
                                          const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
                                          long long n, const unsigned* __restrict__ values, unsigned run0,
                                          long long vbase, const TilePos& tp, FwdPix<P>& s, float4* s_a, float4* s_b,
                                          float2* s_c, float2* s_rows, unsigned char* s_list) {
-    constexpr int NT = kTilePix / P;
+    constexpr int NT = kTile * TH / P;
     for (int b0 = e0; b0 < e1; b0 += kBatch) {
         bool all = true;
 #pragma unroll
@@ -151,8 +151,8 @@ __device__ __forceinline__ void fwd_walk(int e0, int e1, const float2* __restric
     }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restrict__ xy,
+template <int P, int TH>
+__global__ void __launch_bounds__(kTile * TH / P) k_render(const float2* __restrict__ xy,
                                                          const float4* __restrict__ conic_o,
                                                          const float4* __restrict__ rgbd, long long n,
                                                          const unsigned* __restrict__ values,
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
     __shared__ float2 s_rows[band_cull<P>() ? kBatch : 1];
-    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBatch : 1];
+    __shared__ unsigned char s_list[band_cull<P>() ? kTile * TH / P / 32 * kBatch : 1];
     const long long tile = blockIdx.x;
     const uint2 rg = ranges[tile];
     // tile selection: split_min >= 0 keeps the runs of at most split_min entries (the others go
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
     if (split_min >= 0 ? len > split_min : len <= -split_min - 1) return;
     const int v = view_of_tile(cb, tile);
     const CamDev& cam = cb.c[v];
-    const TilePos tp = tile_pos<P>(cam, tile);
+    const TilePos tp = tile_pos<P, TH>(cam, tile);
     FwdPix<P> s;
     bool inside[P];
 #pragma unroll
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
         s.last[p] = 0;
         s.done[p] = !inside[p];
     }
-    fwd_walk<P>(0, (int)(rg.y - rg.x), xy, conic_o, rgbd, n, values, rg.x, (long long)v * n, tp, s, s_a, s_b, s_c,
+    fwd_walk<P, TH>(0, (int)(rg.y - rg.x), xy, conic_o, rgbd, n, values, rg.x, (long long)v * n, tp, s, s_a, s_b, s_c,
                 s_rows, s_list);
 #pragma unroll
     for (int p = 0; p < P; ++p)
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(kTilePix / P) k_render(const float2* __restric
 // Products regroup, so T can differ from the sequential walk in the last bits (a termination
 // decision only at a float32 near-tie).
 // ---------------------------------------------------------------------------------------------
-template <int P>
-__global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
+template <int P, int TH>
+__global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTile * TH / P)
     k_render_split(const float2* __restrict__ xy, const float4* __restrict__ conic_o, const float4* __restrict__ rgbd,
                    long long n, const unsigned* __restrict__ values, const uint2* __restrict__ ranges,
                    const __grid_constant__ CamBatch cb, float3 bg, int split_min, float4* __restrict__ rgba,
@@ -225,17 +225,18 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
     __shared__ float4 s_b[kBatch];
     __shared__ float2 s_c[kBatch];
     __shared__ float2 s_rows[band_cull<P>() ? kBatch : 1];
-    __shared__ unsigned char s_list[band_cull<P>() ? kTilePix / P / 32 * kBatch : 1];
-    __shared__ float s_T[kTilePix], s_C0[kTilePix], s_C1[kTilePix], s_C2[kTilePix];
-    __shared__ unsigned s_last[kTilePix];
-    __shared__ int s_state[kTilePix];  // after the walk: 1 stopped in the chunk; after the merge: 0 dropped,
+    __shared__ unsigned char s_list[band_cull<P>() ? kTile * TH / P / 32 * kBatch : 1];
+    constexpr int NPIX = kTile * TH;
+    __shared__ float s_T[NPIX], s_C0[NPIX], s_C1[NPIX], s_C2[NPIX];
+    __shared__ unsigned s_last[NPIX];
+    __shared__ int s_state[NPIX];  // after the walk: 1 stopped in the chunk; after the merge: 0 dropped,
                                        // 1 passed, 2 holds the termination
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const long long tile = blockIdx.x / kSplit;
     const int v = view_of_tile(cb, tile);
     const CamDev& cam = cb.c[v];
-    const TilePos tp = tile_pos<P>(cam, tile);
+    const TilePos tp = tile_pos<P, TH>(cam, tile);
     const uint2 rg = ranges[tile];
     const long long vbase = (long long)v * n;
     int nc, lo, hi;
@@ -255,7 +256,7 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
         s.done[p] = !inside[p];
     }
     // 1. every active CTA walks its chunk from T = 1 (CTA 0's walk is the sequential one)
-    if (active) fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, s, s_a, s_b, s_c, s_rows, s_list);
+    if (active) fwd_walk<P, TH>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, s, s_a, s_b, s_c, s_rows, s_list);
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         s_T[pl[p]] = s.T[p];
@@ -296,7 +297,7 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
             r.last[p] = 0;
             r.done[p] = state[p] != 2;
         }
-        fwd_walk<P>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, r, s_a, s_b, s_c, s_rows, s_list);
+        fwd_walk<P, TH>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, tp, r, s_a, s_b, s_c, s_rows, s_list);
 #pragma unroll
         for (int p = 0; p < P; ++p)
             if (state[p] == 2) {
@@ -347,18 +348,11 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTilePix / P)
 static cudaError_t launch_render_tiles(const float2* xy, const float4* co, const float4* cd, long long n,
                                        const ivrgs_bins* b, const uint2* rg, const CamBatch& cb, float3 bgc,
                                        float4* out, float* final_T, uint32_t* last, int ppt, int sm, cudaStream_t s) {
-    if (ppt == 1)
-        k_render<1><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
-                                                             last, sm);
-    else if (ppt == 8)
-        k_render<8><<<(unsigned)cb.n_tiles, kTilePix / 8, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
-                                                                 last, sm);
-    else if (ppt == 4)
-        k_render<4><<<(unsigned)cb.n_tiles, kTilePix / 4, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
-                                                                 last, sm);
-    else
-        k_render<2><<<(unsigned)cb.n_tiles, kTilePix / 2, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out, final_T,
-                                                                 last, sm);
+    blend_shape(ppt, cb.th, [&](auto P, auto TH) {
+        constexpr int kP = decltype(P)::value, kTH = decltype(TH)::value;
+        k_render<kP, kTH><<<(unsigned)cb.n_tiles, kTile * kTH / kP, 0, s>>>(xy, co, cd, n, b->values, rg, cb, bgc, out,
+                                                                          final_T, last, sm);
+    });
     return cudaGetLastError();
 }
 
@@ -392,18 +386,11 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
         cudaError_t e = split_fork(s, &side);
         if (e != cudaSuccess) return e;
         const unsigned grid = (unsigned)(cb.n_tiles * kSplit);
-        if (ppt == 1)
-            k_render_split<1><<<grid, kTilePix, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out, final_T,
-                                                            last);
-        else if (ppt == 8)
-            k_render_split<8><<<grid, kTilePix / 8, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out,
-                                                               final_T, last);
-        else if (ppt == 4)
-            k_render_split<4><<<grid, kTilePix / 4, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out,
-                                                               final_T, last);
-        else
-            k_render_split<2><<<grid, kTilePix / 2, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm, out,
-                                                               final_T, last);
+        blend_shape(ppt, cb.th, [&](auto P, auto TH) {
+            constexpr int kP = decltype(P)::value, kTH = decltype(TH)::value;
+            k_render_split<kP, kTH><<<grid, kTile * kTH / kP, 0, side>>>(xy, co, cd, p->n, b->values, rg, cb, bgc, sm,
+                                                                       out, final_T, last);
+        });
         e = cudaGetLastError();
         cudaError_t e2 = cudaSuccess;
         if (e == cudaSuccess) e2 = launch_render_tiles(xy, co, cd, p->n, b, rg, cb, bgc, out, final_T, last, ppt, sm, s);
@@ -412,6 +399,5 @@ cudaError_t launch_render(const ivrgs_projected* p, const ivrgs_bins* b, const C
     }
     return launch_render_tiles(xy, co, cd, p->n, b, rg, cb, bgc, out, final_T, last, ppt, sm, s);
 }
-
 
 }  // namespace ivrgs

@@ -7,13 +7,14 @@
 // pixel has exactly the contributors and weights T_i alpha_i of ivrgs_render (the last output
 // channel, 1 - T, equals the alpha of ivrgs_render bit for bit). Each staged entry carries
 // its 11 values: camera depth, unit normal (world), offset colour, edited k' = lambda k + b.
+#include <type_traits>
+
 #include "blend_alpha.cuh"
 #include "gauss_math.cuh"
 
 namespace ivrgs {
 
 constexpr int kAux = 11;
-constexpr int kAuxBatch = 256;
 
 // normal, offset colour and k of Gaussian i in either storage
 template <int PREC>
@@ -51,8 +52,8 @@ __device__ __forceinline__ void load_aux_attrs(const ivrgs_gaussians& g, long lo
     }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restrict__ xy,
+template <int PREC, int TH>
+__global__ void __launch_bounds__(kTile * TH) k_render_aux(const float2* __restrict__ xy,
                                                          const float4* __restrict__ conic_o,
                                                          const float4* __restrict__ rgbd, long long n,
                                                          const unsigned* __restrict__ values,
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restric
                                                          const __grid_constant__ CamBatch cb, const ivrgs_gaussians g,
                                                          const float* __restrict__ table, int n_models,
                                                          float4* __restrict__ out) {
+    constexpr int kAuxBatch = kTile * TH;  // one staged entry per thread (one pixel each)
     __shared__ float4 s_a[kAuxBatch];
     __shared__ float4 s_b[kAuxBatch];
     __shared__ float2 s_c[kAuxBatch];
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restric
     const int local = (int)(tile - cam.tile0);
     const int tx = local % cam.gx, ty = local / cam.gx;
     const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-    const int py = ty * kTile + (int)(threadIdx.x / kTile);
+    const int py = ty * TH + (int)(threadIdx.x / kTile);
     const float fx = (float)px + 0.5f;
     const int q0 = py & 3;
     const float fyg = (float)(py - q0) + 0.5f;
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(kTilePix) k_render_aux(const float2* __restric
     bool done = !inside;
     const int len = (int)(rg.y - rg.x);
     for (int b0 = 0; b0 < len; b0 += kAuxBatch) {
-        if (__syncthreads_count(done) == kTilePix) break;
+        if (__syncthreads_count(done) == kAuxBatch) break;
         {
             const int e = b0 + (int)threadIdx.x;
             if (e < len) {
@@ -165,15 +167,18 @@ cudaError_t launch_render_aux(const ivrgs_gaussians* g, const float* table, cons
     const float4* cd = reinterpret_cast<const float4*>(p->rgbd);
     const uint2* rg = reinterpret_cast<const uint2*>(b->ranges);
     float4* out = reinterpret_cast<float4*>(aux);
-    if (g->precision == IVRGS_VQ)
-        k_render_aux<IVRGS_VQ><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, *g,
-                                                                        table, g->n_models, out);
-    else if (g->precision == IVRGS_MIXED)
-        k_render_aux<IVRGS_MIXED><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, *g,
-                                                                           table, g->n_models, out);
-    else
-        k_render_aux<IVRGS_FP32><<<(unsigned)cb.n_tiles, kTilePix, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, *g,
-                                                                          table, g->n_models, out);
+    auto launch = [&](auto prec) {
+        constexpr int kPrec = decltype(prec)::value;
+        if (cb.th == 8)
+            k_render_aux<kPrec, 8><<<(unsigned)cb.n_tiles, kTile * 8, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb, *g,
+                                                                            table, g->n_models, out);
+        else
+            k_render_aux<kPrec, 16><<<(unsigned)cb.n_tiles, kTile * 16, 0, s>>>(xy, co, cd, p->n, b->values, rg, cb,
+                                                                              *g, table, g->n_models, out);
+    };
+    if (g->precision == IVRGS_VQ) launch(std::integral_constant<int, IVRGS_VQ>{});
+    else if (g->precision == IVRGS_MIXED) launch(std::integral_constant<int, IVRGS_MIXED>{});
+    else launch(std::integral_constant<int, IVRGS_FP32>{});
     return cudaGetLastError();
 }
 

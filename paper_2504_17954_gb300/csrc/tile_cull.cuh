@@ -10,7 +10,7 @@
 //
 // Per tile row the kept tiles are the columns whose box of pixel centres
 // [16 tx + 0.5, 16 tx + 15.5] meets the ellipse q <= tau' (tau' = tau + kCullSlack) within the
-// row's band of pixel-centre rows [16 ty + 0.5, 16 ty + 15.5]. For one e_y the ellipse's chord
+// row's band of pixel-centre rows [th ty + 0.5, th ty + th - 0.5] (th the tile height). For one e_y the ellipse's chord
 // is centred at -(b/a) e_y with half width sqrt(tau' a - det e_y^2) / a (det = a c - b^2). Over
 // a band of e_y its leftmost end lies at the e_y of the ellipse's leftmost point,
 // e_y = (b/c) X with X = sqrt(tau' c / det), clamped into the band (the left end is a convex
@@ -89,8 +89,8 @@ __device__ __forceinline__ float cull_chord_end(const CullEll& e, float ey, floa
     return __fadd_rn(__fsub_rn(e.u, __fmul_rn(e.ba, ey)), __fmul_rn(sign, hw));
 }
 
-// kept tile columns [lo, hi) of tile row ty within the rectangle's columns [x0, x1)
-__device__ __forceinline__ void cull_row(const CullEll& e, int ty, int x0, int x1, int& lo, int& hi) {
+// kept tile columns [lo, hi) of tile row ty (tiles th pixels high) within the rectangle's columns [x0, x1)
+__device__ __forceinline__ void cull_row(const CullEll& e, int ty, int th, int x0, int x1, int& lo, int& hi) {
     if (e.mode == 2) {
         lo = x0;
         hi = x1;
@@ -98,9 +98,9 @@ __device__ __forceinline__ void cull_row(const CullEll& e, int ty, int x0, int x
     }
     lo = hi = x0;
     if (e.mode == 0) return;
-    const float band0 = __fsub_rn(__fadd_rn((float)(ty * kTile), 0.5f), e.v);
+    const float band0 = __fsub_rn(__fadd_rn((float)(ty * th), 0.5f), e.v);
     const float y0 = fmaxf(band0, -e.Y);
-    const float y1 = fminf(__fadd_rn(band0, (float)(kTile - 1)), e.Y);
+    const float y1 = fminf(__fadd_rn(band0, (float)(th - 1)), e.Y);
     if (!(y0 <= y1)) return;
     const float eyR = fminf(fmaxf(e.eyR, y0), y1);
     const float eyL = fminf(fmaxf(-e.eyR, y0), y1);

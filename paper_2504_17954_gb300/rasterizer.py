@@ -224,8 +224,8 @@ def camera_structs(cams) -> (C.Array, int):
     return arr, off
 
 
-def n_tiles(cams, tile: int = 16) -> int:
-    return sum(((c.W + tile - 1) // tile) * ((c.H + tile - 1) // tile) for c in cams)
+def n_tiles(cams, tile_w: int = 16, tile_h: int = 16) -> int:
+    return sum(((c.W + tile_w - 1) // tile_w) * ((c.H + tile_h - 1) // tile_h) for c in cams)
 
 
 class Rasterizer:
@@ -236,13 +236,16 @@ class Rasterizer:
     pairs of tiles that the Gaussian's opacity cut-off ellipse misses (IVRGS_BIN_CULL): the same
     images and gradients from shorter tile lists; ``cull=False`` gives the full rectangle lists.
 
+    ``tile_h`` is the tile height (16 or 8; tiles are 16 pixels wide): a launch shape, which
+    the autotuner's ``tune_tiles`` can pick per workload.
+
     ``generation`` counts the eager calls that rewrite the per-render state (projection,
     binning, compositing); ``RenderFunction`` uses it to refuse a backward whose forward state
     has since been overwritten. Replays of a captured graph do not advance it.
     """
 
     def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", capacity: Optional[int] = None,
-                 lowpass: float = 0.3, bg=(0.0, 0.0, 0.0), cull: bool = True):
+                 lowpass: float = 0.3, bg=(0.0, 0.0, 0.0), cull: bool = True, tile_h: int = 16):
         self.cams = list(cams)
         self.V = len(self.cams)
         self.n = int(n_gaussians)
@@ -252,7 +255,10 @@ class Rasterizer:
         self.cull_flag = N.IVRGS_BIN_CULL if cull else 0
         self.cam_arr, self.n_pix = camera_structs(self.cams)
         self.bg = (C.c_float * 3)(*[float(x) for x in bg])
-        self.n_tiles = n_tiles(self.cams)
+        if tile_h not in (16, 8):
+            raise ValueError("tile_h must be 16 or 8")
+        self.tile_h = int(tile_h)
+        self.n_tiles = n_tiles(self.cams, 16, self.tile_h)
         VN = self.V * self.n
         dev = self.device
         self.xy = torch.empty((VN, 2), dtype=torch.float32, device=dev)
@@ -282,7 +288,7 @@ class Rasterizer:
         self.capacity = cap
         self.tiles = torch.empty(cap, dtype=torch.int32, device=self.device)
         self.values = torch.empty(cap, dtype=torch.int32, device=self.device)
-        self.ws_bin_bytes = N.ivrgs_bin_workspace(self.n, self.V, self.cam_arr, 16, 16, cap)
+        self.ws_bin_bytes = N.ivrgs_bin_workspace(self.n, self.V, self.cam_arr, 16, self.tile_h, cap)
         self.ws_bin = torch.empty(self.ws_bin_bytes, dtype=torch.uint8, device=self.device)
 
     def projected_struct(self) -> N.ivrgs_projected:
@@ -293,7 +299,7 @@ class Rasterizer:
 
     def bins_struct(self) -> N.ivrgs_bins:
         b = N.ivrgs_bins()
-        b.tile_w = b.tile_h = 16
+        b.tile_w, b.tile_h = 16, self.tile_h
         b.n_tiles = self.n_tiles
         b.capacity = self.capacity
         b.tiles, b.values = self.tiles.data_ptr(), self.values.data_ptr()
@@ -449,11 +455,12 @@ class WaveRasterizer:
     waves' gradients with ivrgs_render_backward_accumulate. Each wave owns a Rasterizer."""
 
     def __init__(self, cams, n_gaussians: int, n_models: int, device="cuda", lowpass: float = 0.3,
-                 bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20, cull: bool = True):
+                 bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20, cull: bool = True,
+                 tile_h: int = 16):
         self.cams = list(cams)
         self.waves: List[List[int]] = plan_waves(self.cams, n_gaussians, max_views, pixel_budget)
         self.rasts = [Rasterizer([self.cams[v] for v in wv], n_gaussians, n_models, device=device, lowpass=lowpass,
-                                 bg=bg, cull=cull) for wv in self.waves]
+                                 bg=bg, cull=cull, tile_h=tile_h) for wv in self.waves]
         self.n_models = n_models
         self.V = len(self.cams)
 

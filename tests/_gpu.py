@@ -30,12 +30,13 @@ def device_models(models) -> List[Gaussians]:
     return out
 
 
-def setup(w: sg.Workload, capacity=None, edits=None, cull=True):
+def setup(w: sg.Workload, capacity=None, edits=None, cull=True, tile_h=16):
     ed = w.edits if edits is None else edits
     dm = device_models(w.models)
     comp, table = compose_edit(dm, ed.palette, ed.opacity_scale, ed.visible, ed.lam, ed.bias,
                                light_dir=getattr(ed, "light_dir", None))
-    rast = Rasterizer(w.cameras, comp.n, len(w.models), capacity=capacity, lowpass=w.lowpass, bg=w.bg, cull=cull)
+    rast = Rasterizer(w.cameras, comp.n, len(w.models), capacity=capacity, lowpass=w.lowpass, bg=w.bg, cull=cull,
+                      tile_h=tile_h)
     return rast, comp, table
 
 
@@ -44,10 +45,11 @@ def last_gaussian(rast: Rasterizer, v: int, pix: np.ndarray) -> np.ndarray:
     `last` (a position in the pixel's tile run) and its tile lists; unlike the position it does
     not depend on which non-contributing entries a list holds."""
     c = rast.cams[v]
+    th = rast.tile_h
     gx = (c.W + 15) // 16
-    t0 = sum(((q.W + 15) // 16) * ((q.H + 15) // 16) for q in rast.cams[:v])
+    t0 = sum(((q.W + 15) // 16) * ((q.H + th - 1) // th) for q in rast.cams[:v])
     last = rast.view_image(v, rast.last).cpu().numpy()[pix[:, 1], pix[:, 0]].astype(np.int64)
-    tile = t0 + (pix[:, 1] // 16) * gx + pix[:, 0] // 16
+    tile = t0 + (pix[:, 1] // th) * gx + pix[:, 0] // 16
     start = rast.ranges.cpu().numpy().view(np.uint32)[tile, 0].astype(np.int64)
     vals = rast.values.cpu().numpy().view(np.uint32).astype(np.int64)
     out = np.full(len(pix), -1, np.int64)
@@ -73,7 +75,8 @@ def gpu_keys(rast: Rasterizer):
     t = rast.tiles[:n].cpu().numpy().view(np.uint32).astype(np.uint64)
     v = rast.values[:n].cpu().numpy().view(np.uint32)
     r = rast.ranges.cpu().numpy().view(np.uint32)
-    toff = np.cumsum([0] + [((c.W + 15) // 16) * ((c.H + 15) // 16) for c in rast.cams])
+    th = rast.tile_h
+    toff = np.cumsum([0] + [((c.W + 15) // 16) * ((c.H + th - 1) // th) for c in rast.cams])
     view = np.searchsorted(toff, t.astype(np.int64), side="right") - 1
     depth = rast.rgbd[:, 3].contiguous().cpu().numpy().view(np.uint32)
     bits = depth[view * rast.n + v.astype(np.int64)].astype(np.uint64)

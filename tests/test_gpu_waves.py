@@ -2,7 +2,7 @@
 backward summed across waves by ivrgs_render_backward_accumulate.
 
 * Waves vs one call: the same images bit for bit and the same gradients (1e-5 relative); the
-  wave shape picked by the autotuner renders the same images.
+  shape (tile height and waves) picked by the autotuner renders the images of one call.
 * The 3M-Gaussian / 8-model / 64-view workload (sides 512..2048) in 16-bit storage, the batched
   mixed-precision form: sampled pixels of a 4-view subset and the gradients of a loss on them
   against the FP64 oracle on the decoded values; the same views rendered from float32 storage
@@ -51,33 +51,37 @@ def test_waves_equal_one_call():
 
 
 def test_tuned_wave_shape_renders_the_same_views():
-    """autotune.tune_waves on a 6-view scene with small pixel budgets: it times each distinct wave
-    plan (captured forward+backward), and the picked shape renders every view bit for bit as one
-    call does."""
+    """autotune.tune_waves on a 6-view scene with small pixel budgets and both tile heights: it
+    times each distinct shape (captured forward+backward), and the picked shape renders every view
+    bit for bit as one call with the same tile height does."""
     from paper_2504_17954_gb300 import autotune
     base = sg.tiny_scene(4000, 64, 48, 53, log_scale_mu=-3.3, n_models=2)
     rng = np.random.default_rng(53)
     cams = [sg.look_at(3.0 * sg.random_direction(rng), 40 + 8 * i, 48) for i in range(6)]
     w = sg.Workload("tune", base.models, cams, sg.random_edits(base.models, seed=54))
-    one, comp, table = _gpu.setup(w)
-    one.forward(comp, table)
     timed = []
 
-    def measure(mv, pb):
-        wv = WaveRasterizer(cams, comp.n, 2, max_views=mv, pixel_budget=pb)
+    def measure(mv, pb, th):
+        wv = WaveRasterizer(cams, 4000, 2, max_views=mv, pixel_budget=pb, tile_h=th)
+        _, comp, table = _gpu.setup(w, tile_h=th)
         wv.size_buffers(comp, table)
         dls = [torch.zeros((r.n_pix, 4), device="cuda") for r in wv.rasts]
         graph = wv.capture(comp, table, dls)
         graph.replay()
         torch.cuda.synchronize()
         ms = autotune.time_ms(graph.replay, reps=3)
-        timed.append(len(wv.waves))
+        timed.append((th, len(wv.waves)))
         return ms
     budgets = (4000, 8000, 16000)
-    shape = autotune.tune_waves(measure, cams, comp.n, "test", budgets=budgets, max_views=(2, 32), use_cache=False)
-    assert len(timed) == len(set(tuple(c["waves"]) for c in shape["candidates"])) >= 3
+    shape = autotune.tune_waves(measure, cams, 4000, "test", budgets=budgets, max_views=(2, 32),
+                                tile_heights=(16, 8), use_cache=False)
+    assert len(timed) == len({(c["tile_h"], tuple(c["waves"])) for c in shape["candidates"]}) >= 6
     assert shape["ms"] == min(c["ms"] for c in shape["candidates"])
-    waves = WaveRasterizer(cams, comp.n, 2, max_views=shape["max_views"], pixel_budget=shape["pixel_budget"])
+    th = shape["tile_h"]
+    one, comp, table = _gpu.setup(w, tile_h=th)
+    one.forward(comp, table)
+    waves = WaveRasterizer(cams, comp.n, 2, max_views=shape["max_views"], pixel_budget=shape["pixel_budget"],
+                           tile_h=th)
     assert [len(x) for x in waves.waves] == shape["waves"]
     waves.forward(comp, table)
     torch.cuda.synchronize()

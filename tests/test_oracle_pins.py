@@ -502,14 +502,17 @@ def test_permutation_invariance_with_distinct_depths():
 
 
 # ------------------------------------------------------------------ binning / ordering
-def test_bin_matches_python_sort_with_ties():
+@pytest.mark.parametrize("th", [16, 8])
+def test_bin_matches_python_sort_with_ties(th):
+    """The oracle's tile lists against a plain Python rebuild (exact rectangles, a sort by
+    (tile, depth bits) with ties in emission order), for 16 x 16 and 16 x 8 tiles."""
     sizes = [(64, 48), (40, 40), (100, 30)]
     xy, rad, depth = sg.synthetic_projected(sizes, 300, seed=4)
-    b = oracle.bin_pairs(xy, rad, depth, sizes)
+    b = oracle.bin_pairs(xy, rad, depth, sizes, tile=(16, th))
     exp = []
     toff = 0
     for v, (W, H) in enumerate(sizes):
-        gx, gy = -(-W // 16), -(-H // 16)
+        gx, gy = -(-W // 16), -(-H // th)
         for g in range(300):
             r = int(rad[v, g])
             if r <= 0:
@@ -518,8 +521,8 @@ def test_bin_matches_python_sort_with_ties():
             # exact real-number rectangle (float32 inputs; r integer; u -+ r exact in float64)
             x0 = min(max(math.floor((u - r) / 16), 0), gx)
             x1 = min(max(math.floor((u + r) / 16) + 1, 0), gx)
-            y0 = min(max(math.floor((vv - r) / 16), 0), gy)
-            y1 = min(max(math.floor((vv + r) / 16) + 1, 0), gy)
+            y0 = min(max(math.floor((vv - r) / th), 0), gy)
+            y1 = min(max(math.floor((vv + r) / th) + 1, 0), gy)
             bits = int(np.float32(depth[v, g]).view(np.uint32))
             for ty in range(y0, y1):
                 for tx in range(x0, x1):
