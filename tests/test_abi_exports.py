@@ -39,7 +39,9 @@ def test_host_side_argument_checks(lib):
     assert st == N.IVRGS_ERR_INVALID_ARG and "overlap" in N.last_error()
     cams[1].pix_offset = 1024
     assert lib.ivrgs_bin_workspace(10, 2, cams, 16, 16, 1000, C.byref(b)) == N.IVRGS_OK and b.value > 0
-    assert lib.ivrgs_bin_workspace(10, 2, cams, 8, 8, 1000, C.byref(b)) == N.IVRGS_ERR_UNSUPPORTED
+    assert lib.ivrgs_bin_workspace(10, 2, cams, 16, 8, 1000, C.byref(b)) == N.IVRGS_OK and b.value > 0
+    for tw, th in ((8, 8), (16, 32), (16, 4), (32, 16)):  # tiles are 16 wide and 16 or 8 high
+        assert lib.ivrgs_bin_workspace(10, 2, cams, tw, th, 1000, C.byref(b)) == N.IVRGS_ERR_UNSUPPORTED
     assert lib.ivrgs_bin_workspace(10, 0, cams, 16, 16, 1000, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
     assert lib.ivrgs_bin_workspace(10, 2, cams, 16, 16, 1 << 30, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
     cams[0].headlight = 0  # orbital light with a zero direction
