@@ -156,110 +156,110 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
         // on the entry's o': at or below kNoClampOpacity, alpha = o' G and dalpha/dP = o' G)
         auto pixels = [&](auto clamp) {
             constexpr bool CLAMP = decltype(clamp)::value;
-        if constexpr (P % 2 == 0) {
-            // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
-            // the order in which a thread adds its pixels' moments differs)
-            const F2 zero = f2(0.f, 0.f), one = f2(1.f, 1.f);
-            const F2 O2 = f2(bb.y, bb.y), BZ = f2(bb.z, bb.z), BW = f2(bb.w, bb.w), BL = f2(blue, blue);
-            F2 V0 = zero, V1 = zero, V2 = zero, V3 = zero, V4 = zero, V5 = zero, V6 = zero, V7 = zero, VB = zero;
+            if constexpr (P % 2 == 0) {
+                // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
+                // the order in which a thread adds its pixels' moments differs)
+                const F2 zero = f2(0.f, 0.f), one = f2(1.f, 1.f);
+                const F2 O2 = f2(bb.y, bb.y), BZ = f2(bb.z, bb.z), BW = f2(bb.w, bb.w), BL = f2(blue, blue);
+                F2 V0 = zero, V1 = zero, V2 = zero, V3 = zero, V4 = zero, V5 = zero, V6 = zero, V7 = zero, VB = zero;
 #pragma unroll
-            for (int h = 0; h < P / 2; ++h) {
-                const int pa = 2 * h, pb = 2 * h + 1;
-                const F2 G = f2(fast_ex2(p2[pa]), fast_ex2(p2[pb]));
-                const F2 RAW = mul2(O2, G);
-                float raw_a, raw_b;
-                split(RAW, raw_a, raw_b);
-                const float al_a = CLAMP ? fminf(kAlphaMax, raw_a) : raw_a;
+                for (int h = 0; h < P / 2; ++h) {
+                    const int pa = 2 * h, pb = 2 * h + 1;
+                    const F2 G = f2(fast_ex2(p2[pa]), fast_ex2(p2[pb]));
+                    const F2 RAW = mul2(O2, G);
+                    float raw_a, raw_b;
+                    split(RAW, raw_a, raw_b);
+                    const float al_a = CLAMP ? fminf(kAlphaMax, raw_a) : raw_a;
                     const float al_b = CLAMP ? fminf(kAlphaMax, raw_b) : raw_b;
-                const bool ok_a = ok0[pa], ok_b = ok0[pb];
-                contrib = contrib || ok_a || ok_b;
-                const F2 A = f2(al_a, al_b);
-                float om_a, om_b;
-                split(sub2(one, A), om_a, om_b);
-                const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
-                const F2 TI = mul2(T2[h], R);
-                F2 TN;  // T in front of the entry: recovered for a contributor, unchanged otherwise
-                {
-                    float ti_a, ti_b, t_a, t_b;
-                    split(TI, ti_a, ti_b);
-                    split(T2[h], t_a, t_b);
-                    TN = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
-                }
-                // the weight T_i alpha_i as T_i - T_{i+1} (0 for a skipped pixel), so that one select
-                // serves both; it differs from the rounded product by the rounding of T_i, under
-                // 2^-24 T_i / alpha_i, relative 1.5e-5 at the cut-off
-                const F2 W = sub2(TN, T2[h]);
-                V6 = fma2(W, DX2[h], V6);
-                V7 = fma2(W, DY2[h], V7);
-                VB = fma2(W, DZ2[h], VB);
-                const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
-                const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
-                DS2[h] = fma2(W, DC, DS2[h]);
-                T2[h] = TN;
-                // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
-                // (selected after the product, so that an infinite G never reaches the sums)
-                const bool live_a = CLAMP ? ok_a && raw_a < kAlphaMax : ok_a;
+                    const bool ok_a = ok0[pa], ok_b = ok0[pb];
+                    contrib = contrib || ok_a || ok_b;
+                    const F2 A = f2(al_a, al_b);
+                    float om_a, om_b;
+                    split(sub2(one, A), om_a, om_b);
+                    const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
+                    const F2 TI = mul2(T2[h], R);
+                    F2 TN;  // T in front of the entry: recovered for a contributor, unchanged otherwise
+                    {
+                        float ti_a, ti_b, t_a, t_b;
+                        split(TI, ti_a, ti_b);
+                        split(T2[h], t_a, t_b);
+                        TN = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
+                    }
+                    // the weight T_i alpha_i as T_i - T_{i+1} (0 for a skipped pixel), so that one select
+                    // serves both; it differs from the rounded product by the rounding of T_i, under
+                    // 2^-24 T_i / alpha_i, relative 1.5e-5 at the cut-off
+                    const F2 W = sub2(TN, T2[h]);
+                    V6 = fma2(W, DX2[h], V6);
+                    V7 = fma2(W, DY2[h], V7);
+                    VB = fma2(W, DZ2[h], VB);
+                    const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
+                    const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
+                    DS2[h] = fma2(W, DC, DS2[h]);
+                    T2[h] = TN;
+                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
+                    // (selected after the product, so that an infinite G never reaches the sums)
+                    const bool live_a = CLAMP ? ok_a && raw_a < kAlphaMax : ok_a;
                     const bool live_b = CLAMP ? ok_b && raw_b < kAlphaMax : ok_b;
-                float dp_a, dp_b, dg_a, dg_b;
-                split(mul2(DA, RAW), dp_a, dp_b);
-                split(mul2(DA, G), dg_a, dg_b);
-                const F2 DP = f2(live_a ? dp_a : 0.0f, live_b ? dp_b : 0.0f);
-                V5 = add2(V5, f2(live_a ? dg_a : 0.0f, live_b ? dg_b : 0.0f));
-                const RowGroup& ga = rgp[(q0 + pa) >> 2];
-                const RowGroup& gb = rgp[(q0 + pb) >> 2];
-                const F2 DXP = f2(ga.dx, gb.dx);
-                const F2 DYP = f2(ga.dy0 - (float)((q0 + pa) & 3), gb.dy0 - (float)((q0 + pb) & 3));
-                const F2 PX = mul2(DP, DXP), PY = mul2(DP, DYP);
-                V0 = add2(V0, PX);
-                V1 = add2(V1, PY);
-                V2 = fma2(PX, DXP, V2);
-                V3 = fma2(PX, DYP, V3);
-                V4 = fma2(PY, DYP, V4);
-            }
-            const F2 Vs[8] = {V0, V1, V2, V3, V4, V5, V6, V7};
+                    float dp_a, dp_b, dg_a, dg_b;
+                    split(mul2(DA, RAW), dp_a, dp_b);
+                    split(mul2(DA, G), dg_a, dg_b);
+                    const F2 DP = f2(live_a ? dp_a : 0.0f, live_b ? dp_b : 0.0f);
+                    V5 = add2(V5, f2(live_a ? dg_a : 0.0f, live_b ? dg_b : 0.0f));
+                    const RowGroup& ga = rgp[(q0 + pa) >> 2];
+                    const RowGroup& gb = rgp[(q0 + pb) >> 2];
+                    const F2 DXP = f2(ga.dx, gb.dx);
+                    const F2 DYP = f2(ga.dy0 - (float)((q0 + pa) & 3), gb.dy0 - (float)((q0 + pb) & 3));
+                    const F2 PX = mul2(DP, DXP), PY = mul2(DP, DYP);
+                    V0 = add2(V0, PX);
+                    V1 = add2(V1, PY);
+                    V2 = fma2(PX, DXP, V2);
+                    V3 = fma2(PX, DYP, V3);
+                    V4 = fma2(PY, DYP, V4);
+                }
+                const F2 Vs[8] = {V0, V1, V2, V3, V4, V5, V6, V7};
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < 8; ++k) {
+                    float lo, hi;
+                    split(Vs[k], lo, hi);
+                    vv[k] = lo + hi;
+                }
                 float lo, hi;
-                split(Vs[k], lo, hi);
-                vv[k] = lo + hi;
-            }
-            float lo, hi;
-            split(VB, lo, hi);
-            vb = lo + hi;
-        } else {
-            // the P pixels update independently (predicated, no branches) so they interleave
+                split(VB, lo, hi);
+                vb = lo + hi;
+            } else {
+                // the P pixels update independently (predicated, no branches) so they interleave
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                const float G = fast_ex2(p2[p]);
-                const float raw = bb.y * G;
-                const float alpha = CLAMP ? fminf(kAlphaMax, raw) : raw;
-                const bool ok = ok0[p];
-                contrib = contrib || ok;
-                const float r = fast_rcp(1.0f - alpha);
-                const float Ti = T[p] * r;
-                const float w = ok ? Ti * alpha : 0.0f;
-                const float4 dd = d[p];
-                vv[6] = fmaf(w, dd.x, vv[6]);
-                vv[7] = fmaf(w, dd.y, vv[7]);
-                vb = fmaf(w, dd.z, vb);
-                const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
-                const float dalpha = Ti * dc - DS[p] * r;
-                DS[p] = fmaf(w, dc, DS[p]);
-                T[p] = ok ? Ti : T[p];
-                // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
-                // selected rather than multiplied so that an infinite G never reaches the sums)
-                const bool live = CLAMP ? ok && raw < kAlphaMax : ok;
-                const float dP = live ? dalpha * raw : 0.0f;
-                vv[5] += live ? dalpha * G : 0.0f;
-                const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
-                const float px_ = dP * dxp, py_ = dP * dyp;
-                vv[0] += px_;
-                vv[1] += py_;
-                vv[2] = fmaf(px_, dxp, vv[2]);
-                vv[3] = fmaf(px_, dyp, vv[3]);
-                vv[4] = fmaf(py_, dyp, vv[4]);
+                for (int p = 0; p < P; ++p) {
+                    const float G = fast_ex2(p2[p]);
+                    const float raw = bb.y * G;
+                    const float alpha = CLAMP ? fminf(kAlphaMax, raw) : raw;
+                    const bool ok = ok0[p];
+                    contrib = contrib || ok;
+                    const float r = fast_rcp(1.0f - alpha);
+                    const float Ti = T[p] * r;
+                    const float w = ok ? Ti * alpha : 0.0f;
+                    const float4 dd = d[p];
+                    vv[6] = fmaf(w, dd.x, vv[6]);
+                    vv[7] = fmaf(w, dd.y, vv[7]);
+                    vb = fmaf(w, dd.z, vb);
+                    const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
+                    const float dalpha = Ti * dc - DS[p] * r;
+                    DS[p] = fmaf(w, dc, DS[p]);
+                    T[p] = ok ? Ti : T[p];
+                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
+                    // selected rather than multiplied so that an infinite G never reaches the sums)
+                    const bool live = CLAMP ? ok && raw < kAlphaMax : ok;
+                    const float dP = live ? dalpha * raw : 0.0f;
+                    vv[5] += live ? dalpha * G : 0.0f;
+                    const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
+                    const float px_ = dP * dxp, py_ = dP * dyp;
+                    vv[0] += px_;
+                    vv[1] += py_;
+                    vv[2] = fmaf(px_, dxp, vv[2]);
+                    vv[3] = fmaf(px_, dyp, vv[3]);
+                    vv[4] = fmaf(py_, dyp, vv[4]);
+                }
             }
-        }
         };
         if (bb.y > kNoClampOpacity) pixels(std::true_type{});
         else pixels(std::false_type{});
@@ -544,7 +544,8 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTile * TH / P)
     // 1. per-chunk forward partials (one chunk: not needed)
     float Tk[P], Dk[P];
     if (nc > 1 && rank < nc) {
-        bwd_chunk_partial<P, TH>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, st, Tk, Dk, s_a, s_b, s_c);
+        bwd_chunk_partial<P, TH>(lo, hi, xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, st, Tk, Dk, s_a, s_b,
+                                 s_c);
     } else {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
@@ -583,9 +584,9 @@ __global__ void __cluster_dims__(kSplit, 1, 1) __launch_bounds__(kTile * TH / P)
     if (rank < nc) {
         const int top = min(hi, cta_last);
         const float ylo = (float)(py0 - ((int)(threadIdx.x & 16u) >> 4) * P) + 0.5f;
-        bwd_walk<P, TH>(lo, top, min(hi, warp_last), xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, ylo, st, s_a,
-                    s_b, s_c, s_gi, s_rows, s_list + (band_cull<P>() ? (threadIdx.x >> 5) * kBwdBatch : 0), g0,
-                    g1, g2);
+        bwd_walk<P, TH>(lo, top, min(hi, warp_last), xy, conic_o, rgbd, n, values, rg.x, vbase, fx, fyg, q0, ylo, st,
+                        s_a, s_b, s_c, s_gi, s_rows, s_list + (band_cull<P>() ? (threadIdx.x >> 5) * kBwdBatch : 0),
+                        g0, g1, g2);
     }
 }
 
