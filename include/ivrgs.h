@@ -187,7 +187,7 @@ int32_t ivrgs_version(void);
 
 /* Launch-shape options (process-wide; measurement-driven tuning, the paper has no counterpart):
    "render_pixels_per_thread" and "render_bwd_pixels_per_thread" (1, 2, 4 or 8, or 0 = by tile
-   count, the default: 4 from 3072 tiles per call, else 2 forward / 1 backward): pixels each thread
+   count, the default: 4 from 3072 tiles per call, else 1): pixels each thread
    of the forward / backward blend owns; "sort_match" (0 or 1): rank radix digits with warp
    ballots (0) or match.any (1); "sort_scan" (0 or 1): radix-pass offsets by decoupled
    look-back (0, one kernel per pass) or reduce-then-scan (1: a histogram kernel, a per-digit
