@@ -126,6 +126,93 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                                           float* __restrict__ g2) {
     constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
     const int lane = threadIdx.x & 31;
+    if constexpr (P == 1) {
+        // One pixel per thread: two list entries per step, their exponents and reach tests first,
+        // then the two chain-rule updates in walk order, then the two entries' record gradients,
+        // so that the dependent chains of the two entries (shared loads, exponent, ex2, the
+        // reductions and atomics) overlap; lone warps of the heaviest tiles are latency-bound
+        // (the 800^2 view: 0.541 -> 0.521 ms; the 10k-Gaussian 128^2 view: 0.091 -> 0.081 ms).
+        // Per pixel the same operations in the same order as the path below.
+        // The chain rule of one entry for the thread's pixel (as the odd-P path below):
+        auto chain = [&](const float4& bb, float blue, const RowGroup& rgq, float p2, bool ok, float (&vv)[8],
+                         float& vb, auto clamp) {
+            constexpr bool CLAMP = decltype(clamp)::value;
+            const float G = fast_ex2(p2);
+            const float raw = bb.y * G;
+            const float alpha = CLAMP ? fminf(kAlphaMax, raw) : raw;
+            const float r = fast_rcp(1.0f - alpha);
+            const float Ti = T[0] * r;
+            const float w = ok ? Ti * alpha : 0.0f;
+            const float4 dd = d[0];
+            vv[6] = fmaf(w, dd.x, vv[6]);
+            vv[7] = fmaf(w, dd.y, vv[7]);
+            vb = fmaf(w, dd.z, vb);
+            const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;
+            const float dalpha = Ti * dc - DS[0] * r;
+            DS[0] = fmaf(w, dc, DS[0]);
+            T[0] = ok ? Ti : T[0];
+            const bool live = CLAMP ? ok && raw < kAlphaMax : ok;
+            const float dP = live ? dalpha * raw : 0.0f;
+            vv[5] += live ? dalpha * G : 0.0f;
+            const float dxp = rgq.dx, dyp = rgq.dy0 - (float)(q0 & 3);
+            const float px_ = dP * dxp, py_ = dP * dyp;
+            vv[0] += px_;
+            vv[1] += py_;
+            vv[2] = fmaf(px_, dxp, vv[2]);
+            vv[3] = fmaf(px_, dyp, vv[3]);
+            vv[4] = fmaf(py_, dyp, vv[4]);
+        };
+        // the record gradients of one entry (as below)
+        auto emit = [&](const float4& a, const float4& bb, int j, const float (&vv)[8], float vb, bool contrib) {
+            const unsigned m = __ballot_sync(0xffffffffu, contrib);
+            if (m == 0u) return;
+            const long long gi = s_gi[j];
+            float* t0 = reinterpret_cast<float*>(g0 + gi);
+            float* t1 = reinterpret_cast<float*>(g1 + gi);
+            const float il = 2.0f / kLog2e;
+            const float tm = fmaf(a.w, vv[0], vv[1]);
+            if (__popc(m) <= kDirectLanes) {
+                if (contrib) {
+                    const float du = fmaf(bb.x, vv[0], a.z * a.w * tm) * il;
+                    const float dv = a.z * tm * il;
+                    atomicAdd(reinterpret_cast<float4*>(t0), make_float4(du, dv, -0.5f * vv[2], -vv[3]));
+                    atomicAdd(reinterpret_cast<float4*>(t1), make_float4(-0.5f * vv[4], vv[5], vv[6], vv[7]));
+                    atomicAdd(&g2[gi], vb);
+                }
+            } else {
+                const float tv[8] = {fmaf(bb.x, vv[0], a.z * a.w * tm) * il, a.z * tm * il,
+                                     -0.5f * vv[2], -vv[3], -0.5f * vv[4], vv[5], vv[6], vv[7]};
+                const float x = warp_sum8_transposed(tv, lane);
+                const float vbs = warp_sum(vb);
+                const int idx = lane >> 2;
+                if ((lane & 3) == 0) atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
+                if (lane == 0) atomicAdd(&g2[gi], vbs);
+            }
+        };
+        for (int i = 0; i < nl; i += 2) {
+            const bool has_b = i + 1 < nl;
+            const int ja = band_cull<P>() ? (int)list[i] : j0 + i;
+            const int jb = has_b ? (band_cull<P>() ? (int)list[i + 1] : j0 + i + 1) : ja;
+            const float4 aa = s_a[ja], ba = s_b[ja];
+            const float2 ca = s_c[ja];
+            const float4 ab = s_a[jb], bbb = s_b[jb];
+            const float2 cb = s_c[jb];
+            const RowGroup ra = row_group(aa, ba, fx, fyg), rb = row_group(ab, bbb, fx, fyg);
+            const float pa = row_p2(ra, aa, q0 & 3), pb = row_p2(rb, ab, q0 & 3);
+            const bool ok_a = b_end - 1 - ja < (int)my_last[0] && in_reach(pa, ca.y);
+            const bool ok_b = has_b && b_end - 1 - jb < (int)my_last[0] && in_reach(pb, cb.y);
+            if (!__any_sync(0xffffffffu, ok_a || ok_b)) continue;
+            float va[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, vba = 0.f;
+            float vbv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, vbb = 0.f;
+            if (ba.y > kNoClampOpacity) chain(ba, ca.x, ra, pa, ok_a, va, vba, std::true_type{});
+            else chain(ba, ca.x, ra, pa, ok_a, va, vba, std::false_type{});
+            if (bbb.y > kNoClampOpacity) chain(bbb, cb.x, rb, pb, ok_b, vbv, vbb, std::true_type{});
+            else chain(bbb, cb.x, rb, pb, ok_b, vbv, vbb, std::false_type{});
+            emit(aa, ba, ja, va, vba, ok_a);
+            emit(ab, bbb, jb, vbv, vbb, ok_b);
+        }
+        return;
+    }
     for (int i = 0; i < nl; ++i) {
         const int j = band_cull<P>() ? (int)list[i] : j0 + i;
         const int ee = b_end - 1 - j;
