@@ -83,6 +83,7 @@ constexpr int kBwdBatch = 256;  // entries staged per batch
 // 1.32 / 1.27 / 1.23 / 1.25 ms; always direct 2.14 ms. The single 800^2 view: 1.43 -> 1.31 ms
 // per step at 24.
 constexpr int kDirectLanes = 24;
+constexpr int kBwdSteps1 = 2;  // list entries per step of the one-pixel walk (1, 2 or 4)
 
 // The backward state of this thread's P pixels from the forward's final T and last contributor
 // and dL/dRGBA (DS = T_final (dL/dC . bg - dL/dA)); returns the largest last contributor.
@@ -127,12 +128,12 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
     constexpr int NG = (P + 3) / 4;  // 4-row exponent groups a thread spans
     const int lane = threadIdx.x & 31;
     if constexpr (P == 1) {
-        // One pixel per thread: two list entries per step, their exponents and reach tests first,
-        // then the two chain-rule updates in walk order, then the two entries' record gradients,
-        // so that the dependent chains of the two entries (shared loads, exponent, ex2, the
-        // reductions and atomics) overlap; lone warps of the heaviest tiles are latency-bound
-        // (the 800^2 view: 0.541 -> 0.521 ms; the 10k-Gaussian 128^2 view: 0.091 -> 0.081 ms).
-        // Per pixel the same operations in the same order as the path below.
+        // One pixel per thread: kBwdSteps1 list entries per step, their exponents and reach tests
+        // first, then the chain-rule updates in walk order, then the entries' record gradients,
+        // so that the dependent chains of the entries (shared loads, exponent, ex2, the reductions
+        // and atomics) overlap; lone warps of the heaviest tiles are latency-bound (two entries
+        // per step: the 800^2 view 0.541 -> 0.521 ms; the 10k-Gaussian 128^2 view 0.091 ->
+        // 0.081 ms). Per pixel the same operations in the same order as the path below.
         // The chain rule of one entry for the thread's pixel (as the odd-P path below):
         auto chain = [&](const float4& bb, float blue, const RowGroup& rgq, float p2, bool ok, float (&vv)[8],
                          float& vb, auto clamp) {
@@ -189,196 +190,211 @@ __device__ __forceinline__ void bwd_batch(const unsigned char* list, int j0, int
                 if (lane == 0) atomicAdd(&g2[gi], vbs);
             }
         };
-        for (int i = 0; i < nl; i += 2) {
-            const bool has_b = i + 1 < nl;
-            const int ja = band_cull<P>() ? (int)list[i] : j0 + i;
-            const int jb = has_b ? (band_cull<P>() ? (int)list[i + 1] : j0 + i + 1) : ja;
-            const float4 aa = s_a[ja], ba = s_b[ja];
-            const float2 ca = s_c[ja];
-            const float4 ab = s_a[jb], bbb = s_b[jb];
-            const float2 cb = s_c[jb];
-            const RowGroup ra = row_group(aa, ba, fx, fyg), rb = row_group(ab, bbb, fx, fyg);
-            const float pa = row_p2(ra, aa, q0 & 3), pb = row_p2(rb, ab, q0 & 3);
-            const bool ok_a = b_end - 1 - ja < (int)my_last[0] && in_reach(pa, ca.y);
-            const bool ok_b = has_b && b_end - 1 - jb < (int)my_last[0] && in_reach(pb, cb.y);
-            if (!__any_sync(0xffffffffu, ok_a || ok_b)) continue;
-            float va[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, vba = 0.f;
-            float vbv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, vbb = 0.f;
-            if (ba.y > kNoClampOpacity) chain(ba, ca.x, ra, pa, ok_a, va, vba, std::true_type{});
-            else chain(ba, ca.x, ra, pa, ok_a, va, vba, std::false_type{});
-            if (bbb.y > kNoClampOpacity) chain(bbb, cb.x, rb, pb, ok_b, vbv, vbb, std::true_type{});
-            else chain(bbb, cb.x, rb, pb, ok_b, vbv, vbb, std::false_type{});
-            emit(aa, ba, ja, va, vba, ok_a);
-            emit(ab, bbb, jb, vbv, vbb, ok_b);
+        for (int i = 0; i < nl; i += kBwdSteps1) {
+            float4 aq[kBwdSteps1], bq[kBwdSteps1];
+            float2 cq[kBwdSteps1];
+            RowGroup rq[kBwdSteps1];
+            float pq[kBwdSteps1];
+            bool okq[kBwdSteps1];
+            int jq[kBwdSteps1];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < kBwdSteps1; ++k) {
+                const bool has = i + k < nl;
+                const int ii = has ? i + k : i;  // past the end: a repeat of entry i, never in reach
+                jq[k] = band_cull<P>() ? (int)list[ii] : j0 + ii;
+                aq[k] = s_a[jq[k]];
+                bq[k] = s_b[jq[k]];
+                cq[k] = s_c[jq[k]];
+                rq[k] = row_group(aq[k], bq[k], fx, fyg);
+                pq[k] = row_p2(rq[k], aq[k], q0 & 3);
+                okq[k] = has && b_end - 1 - jq[k] < (int)my_last[0] && in_reach(pq[k], cq[k].y);
+                any = any || okq[k];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            float vq[kBwdSteps1][8], vbq[kBwdSteps1];
+#pragma unroll
+            for (int k = 0; k < kBwdSteps1; ++k) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m) vq[k][m] = 0.f;
+                vbq[k] = 0.f;
+                if (bq[k].y > kNoClampOpacity)
+                    chain(bq[k], cq[k].x, rq[k], pq[k], okq[k], vq[k], vbq[k], std::true_type{});
+                else
+                    chain(bq[k], cq[k].x, rq[k], pq[k], okq[k], vq[k], vbq[k], std::false_type{});
+            }
+#pragma unroll
+            for (int k = 0; k < kBwdSteps1; ++k) emit(aq[k], bq[k], jq[k], vq[k], vbq[k], okq[k]);
         }
-        return;
-    }
-    for (int i = 0; i < nl; ++i) {
-        const int j = band_cull<P>() ? (int)list[i] : j0 + i;
-        const int ee = b_end - 1 - j;
-        const float4 a = s_a[j];
-        const float4 bb = s_b[j];
-        const float2 cc = s_c[j];
-        const float blue = cc.x;
-        // per-thread sums over its pixels: vv = (m1, m2, m3, m4, m5, d o', d r, d g) with the
-        // moments m1 = sum dP dx, m2 = sum dP dy, m3 = sum dP dx^2, m4 = sum dP dx dy,
-        // m5 = sum dP dy^2 (the conic and mean gradients are linear in them); vb = d blue
-        float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float vb = 0.f;
-        float p2[P];
-        bool ok0[P];
-        bool any = false;
-        RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
+    } else {
+        for (int i = 0; i < nl; ++i) {
+            const int j = band_cull<P>() ? (int)list[i] : j0 + i;
+            const int ee = b_end - 1 - j;
+            const float4 a = s_a[j];
+            const float4 bb = s_b[j];
+            const float2 cc = s_c[j];
+            const float blue = cc.x;
+            // per-thread sums over its pixels: vv = (m1, m2, m3, m4, m5, d o', d r, d g) with the
+            // moments m1 = sum dP dx, m2 = sum dP dy, m3 = sum dP dx^2, m4 = sum dP dx dy,
+            // m5 = sum dP dy^2 (the conic and mean gradients are linear in them); vb = d blue
+            float vv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float vb = 0.f;
+            float p2[P];
+            bool ok0[P];
+            bool any = false;
+            RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
 #pragma unroll
-        for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
+            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, fx, fyg + 4.0f * (float)gq);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            p2[p] = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
-            ok0[p] = ee < (int)my_last[p] && in_reach(p2[p], cc.y);
-            any = any || ok0[p];
-        }
-        if (!__any_sync(0xffffffffu, any)) continue;
-        bool contrib = false;
-        // the pixels' chain rule, instantiated with and without the 0.99 clamp (a uniform branch
-        // on the entry's o': at or below kNoClampOpacity, alpha = o' G and dalpha/dP = o' G)
-        auto pixels = [&](auto clamp) {
-            constexpr bool CLAMP = decltype(clamp)::value;
-            if constexpr (P % 2 == 0) {
-                // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
-                // the order in which a thread adds its pixels' moments differs)
-                const F2 zero = f2(0.f, 0.f), one = f2(1.f, 1.f);
-                const F2 O2 = f2(bb.y, bb.y), BZ = f2(bb.z, bb.z), BW = f2(bb.w, bb.w), BL = f2(blue, blue);
-                F2 V0 = zero, V1 = zero, V2 = zero, V3 = zero, V4 = zero, V5 = zero, V6 = zero, V7 = zero, VB = zero;
+            for (int p = 0; p < P; ++p) {
+                p2[p] = row_p2(rgp[(q0 + p) >> 2], a, (q0 + p) & 3);
+                ok0[p] = ee < (int)my_last[p] && in_reach(p2[p], cc.y);
+                any = any || ok0[p];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            bool contrib = false;
+            // the pixels' chain rule, instantiated with and without the 0.99 clamp (a uniform branch
+            // on the entry's o': at or below kNoClampOpacity, alpha = o' G and dalpha/dP = o' G)
+            auto pixels = [&](auto clamp) {
+                constexpr bool CLAMP = decltype(clamp)::value;
+                if constexpr (P % 2 == 0) {
+                    // pixel pairs in paired float32 arithmetic (the same IEEE operations per pixel; only
+                    // the order in which a thread adds its pixels' moments differs)
+                    const F2 zero = f2(0.f, 0.f), one = f2(1.f, 1.f);
+                    const F2 O2 = f2(bb.y, bb.y), BZ = f2(bb.z, bb.z), BW = f2(bb.w, bb.w), BL = f2(blue, blue);
+                    F2 V0 = zero, V1 = zero, V2 = zero, V3 = zero, V4 = zero, V5 = zero, V6 = zero, V7 = zero;
+                    F2 VB = zero;
 #pragma unroll
-                for (int h = 0; h < P / 2; ++h) {
-                    const int pa = 2 * h, pb = 2 * h + 1;
-                    const F2 G = f2(fast_ex2(p2[pa]), fast_ex2(p2[pb]));
-                    const F2 RAW = mul2(O2, G);
-                    float raw_a, raw_b;
-                    split(RAW, raw_a, raw_b);
-                    const float al_a = CLAMP ? fminf(kAlphaMax, raw_a) : raw_a;
-                    const float al_b = CLAMP ? fminf(kAlphaMax, raw_b) : raw_b;
-                    const bool ok_a = ok0[pa], ok_b = ok0[pb];
-                    contrib = contrib || ok_a || ok_b;
-                    const F2 A = f2(al_a, al_b);
-                    float om_a, om_b;
-                    split(sub2(one, A), om_a, om_b);
-                    const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
-                    const F2 TI = mul2(T2[h], R);
-                    F2 TN;  // T in front of the entry: recovered for a contributor, unchanged otherwise
-                    {
-                        float ti_a, ti_b, t_a, t_b;
-                        split(TI, ti_a, ti_b);
-                        split(T2[h], t_a, t_b);
-                        TN = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
+                    for (int h = 0; h < P / 2; ++h) {
+                        const int pa = 2 * h, pb = 2 * h + 1;
+                        const F2 G = f2(fast_ex2(p2[pa]), fast_ex2(p2[pb]));
+                        const F2 RAW = mul2(O2, G);
+                        float raw_a, raw_b;
+                        split(RAW, raw_a, raw_b);
+                        const float al_a = CLAMP ? fminf(kAlphaMax, raw_a) : raw_a;
+                        const float al_b = CLAMP ? fminf(kAlphaMax, raw_b) : raw_b;
+                        const bool ok_a = ok0[pa], ok_b = ok0[pb];
+                        contrib = contrib || ok_a || ok_b;
+                        const F2 A = f2(al_a, al_b);
+                        float om_a, om_b;
+                        split(sub2(one, A), om_a, om_b);
+                        const F2 R = f2(fast_rcp(om_a), fast_rcp(om_b));
+                        const F2 TI = mul2(T2[h], R);
+                        F2 TN;  // T in front of the entry: recovered for a contributor, unchanged otherwise
+                        {
+                            float ti_a, ti_b, t_a, t_b;
+                            split(TI, ti_a, ti_b);
+                            split(T2[h], t_a, t_b);
+                            TN = f2(ok_a ? ti_a : t_a, ok_b ? ti_b : t_b);
+                        }
+                        // the weight T_i alpha_i as T_i - T_{i+1} (0 for a skipped pixel), so that one select
+                        // serves both; it differs from the rounded product by the rounding of T_i, under
+                        // 2^-24 T_i / alpha_i, relative 1.5e-5 at the cut-off
+                        const F2 W = sub2(TN, T2[h]);
+                        V6 = fma2(W, DX2[h], V6);
+                        V7 = fma2(W, DY2[h], V7);
+                        VB = fma2(W, DZ2[h], VB);
+                        const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
+                        const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
+                        DS2[h] = fma2(W, DC, DS2[h]);
+                        T2[h] = TN;
+                        // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
+                        // (selected after the product, so that an infinite G never reaches the sums)
+                        const bool live_a = CLAMP ? ok_a && raw_a < kAlphaMax : ok_a;
+                        const bool live_b = CLAMP ? ok_b && raw_b < kAlphaMax : ok_b;
+                        float dp_a, dp_b, dg_a, dg_b;
+                        split(mul2(DA, RAW), dp_a, dp_b);
+                        split(mul2(DA, G), dg_a, dg_b);
+                        const F2 DP = f2(live_a ? dp_a : 0.0f, live_b ? dp_b : 0.0f);
+                        V5 = add2(V5, f2(live_a ? dg_a : 0.0f, live_b ? dg_b : 0.0f));
+                        const RowGroup& ga = rgp[(q0 + pa) >> 2];
+                        const RowGroup& gb = rgp[(q0 + pb) >> 2];
+                        const F2 DXP = f2(ga.dx, gb.dx);
+                        const F2 DYP = f2(ga.dy0 - (float)((q0 + pa) & 3), gb.dy0 - (float)((q0 + pb) & 3));
+                        const F2 PX = mul2(DP, DXP), PY = mul2(DP, DYP);
+                        V0 = add2(V0, PX);
+                        V1 = add2(V1, PY);
+                        V2 = fma2(PX, DXP, V2);
+                        V3 = fma2(PX, DYP, V3);
+                        V4 = fma2(PY, DYP, V4);
                     }
-                    // the weight T_i alpha_i as T_i - T_{i+1} (0 for a skipped pixel), so that one select
-                    // serves both; it differs from the rounded product by the rounding of T_i, under
-                    // 2^-24 T_i / alpha_i, relative 1.5e-5 at the cut-off
-                    const F2 W = sub2(TN, T2[h]);
-                    V6 = fma2(W, DX2[h], V6);
-                    V7 = fma2(W, DY2[h], V7);
-                    VB = fma2(W, DZ2[h], VB);
-                    const F2 DC = fma2(DZ2[h], BL, fma2(DY2[h], BW, mul2(DX2[h], BZ)));  // dL/dC . c_i
-                    const F2 DA = sub2(mul2(TI, DC), mul2(DS2[h], R));                    // dL/dalpha
-                    DS2[h] = fma2(W, DC, DS2[h]);
-                    T2[h] = TN;
-                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp and for skipped pixels
-                    // (selected after the product, so that an infinite G never reaches the sums)
-                    const bool live_a = CLAMP ? ok_a && raw_a < kAlphaMax : ok_a;
-                    const bool live_b = CLAMP ? ok_b && raw_b < kAlphaMax : ok_b;
-                    float dp_a, dp_b, dg_a, dg_b;
-                    split(mul2(DA, RAW), dp_a, dp_b);
-                    split(mul2(DA, G), dg_a, dg_b);
-                    const F2 DP = f2(live_a ? dp_a : 0.0f, live_b ? dp_b : 0.0f);
-                    V5 = add2(V5, f2(live_a ? dg_a : 0.0f, live_b ? dg_b : 0.0f));
-                    const RowGroup& ga = rgp[(q0 + pa) >> 2];
-                    const RowGroup& gb = rgp[(q0 + pb) >> 2];
-                    const F2 DXP = f2(ga.dx, gb.dx);
-                    const F2 DYP = f2(ga.dy0 - (float)((q0 + pa) & 3), gb.dy0 - (float)((q0 + pb) & 3));
-                    const F2 PX = mul2(DP, DXP), PY = mul2(DP, DYP);
-                    V0 = add2(V0, PX);
-                    V1 = add2(V1, PY);
-                    V2 = fma2(PX, DXP, V2);
-                    V3 = fma2(PX, DYP, V3);
-                    V4 = fma2(PY, DYP, V4);
-                }
-                const F2 Vs[8] = {V0, V1, V2, V3, V4, V5, V6, V7};
+                    const F2 Vs[8] = {V0, V1, V2, V3, V4, V5, V6, V7};
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < 8; ++k) {
+                        float lo, hi;
+                        split(Vs[k], lo, hi);
+                        vv[k] = lo + hi;
+                    }
                     float lo, hi;
-                    split(Vs[k], lo, hi);
-                    vv[k] = lo + hi;
-                }
-                float lo, hi;
-                split(VB, lo, hi);
-                vb = lo + hi;
-            } else {
-                // the P pixels update independently (predicated, no branches) so they interleave
+                    split(VB, lo, hi);
+                    vb = lo + hi;
+                } else {
+                    // the P pixels update independently (predicated, no branches) so they interleave
 #pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float G = fast_ex2(p2[p]);
-                    const float raw = bb.y * G;
-                    const float alpha = CLAMP ? fminf(kAlphaMax, raw) : raw;
-                    const bool ok = ok0[p];
-                    contrib = contrib || ok;
-                    const float r = fast_rcp(1.0f - alpha);
-                    const float Ti = T[p] * r;
-                    const float w = ok ? Ti * alpha : 0.0f;
-                    const float4 dd = d[p];
-                    vv[6] = fmaf(w, dd.x, vv[6]);
-                    vv[7] = fmaf(w, dd.y, vv[7]);
-                    vb = fmaf(w, dd.z, vb);
-                    const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
-                    const float dalpha = Ti * dc - DS[p] * r;
-                    DS[p] = fmaf(w, dc, DS[p]);
-                    T[p] = ok ? Ti : T[p];
-                    // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
-                    // selected rather than multiplied so that an infinite G never reaches the sums)
-                    const bool live = CLAMP ? ok && raw < kAlphaMax : ok;
-                    const float dP = live ? dalpha * raw : 0.0f;
-                    vv[5] += live ? dalpha * G : 0.0f;
-                    const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
-                    const float px_ = dP * dxp, py_ = dP * dyp;
-                    vv[0] += px_;
-                    vv[1] += py_;
-                    vv[2] = fmaf(px_, dxp, vv[2]);
-                    vv[3] = fmaf(px_, dyp, vv[3]);
-                    vv[4] = fmaf(py_, dyp, vv[4]);
+                    for (int p = 0; p < P; ++p) {
+                        const float G = fast_ex2(p2[p]);
+                        const float raw = bb.y * G;
+                        const float alpha = CLAMP ? fminf(kAlphaMax, raw) : raw;
+                        const bool ok = ok0[p];
+                        contrib = contrib || ok;
+                        const float r = fast_rcp(1.0f - alpha);
+                        const float Ti = T[p] * r;
+                        const float w = ok ? Ti * alpha : 0.0f;
+                        const float4 dd = d[p];
+                        vv[6] = fmaf(w, dd.x, vv[6]);
+                        vv[7] = fmaf(w, dd.y, vv[7]);
+                        vb = fmaf(w, dd.z, vb);
+                        const float dc = dd.x * bb.z + dd.y * bb.w + dd.z * blue;  // dL/dC . c_i
+                        const float dalpha = Ti * dc - DS[p] * r;
+                        DS[p] = fmaf(w, dc, DS[p]);
+                        T[p] = ok ? Ti : T[p];
+                        // dalpha/dP = o' G while unclamped, 0 on the 0.99 clamp (and for skipped pixels,
+                        // selected rather than multiplied so that an infinite G never reaches the sums)
+                        const bool live = CLAMP ? ok && raw < kAlphaMax : ok;
+                        const float dP = live ? dalpha * raw : 0.0f;
+                        vv[5] += live ? dalpha * G : 0.0f;
+                        const float dxp = rgp[(q0 + p) >> 2].dx, dyp = rgp[(q0 + p) >> 2].dy0 - (float)((q0 + p) & 3);
+                        const float px_ = dP * dxp, py_ = dP * dyp;
+                        vv[0] += px_;
+                        vv[1] += py_;
+                        vv[2] = fmaf(px_, dxp, vv[2]);
+                        vv[3] = fmaf(px_, dyp, vv[3]);
+                        vv[4] = fmaf(py_, dyp, vv[4]);
+                    }
                 }
+            };
+            if (bb.y > kNoClampOpacity) pixels(std::true_type{});
+            else pixels(std::false_type{});
+            const unsigned m = __ballot_sync(0xffffffffu, contrib);
+            if (m == 0u) continue;
+            const long long gi = s_gi[j];
+            float* t0 = reinterpret_cast<float*>(g0 + gi);
+            float* t1 = reinterpret_cast<float*>(g1 + gi);
+            // moments -> (du, dv, da, db, dc): P = p2 / log2(e), p2 = C' (dy + beta dx)^2 + G' dx^2
+            //   (staged C' = a.z, beta = a.w, G' = bb.x), so with t = beta m1 + m2
+            //   du = 2 (G' m1 + C' beta t)/log2e, dv = 2 C' t/log2e,
+            //   da = -m3/2, db = -m4, dc = -m5/2
+            const float il = 2.0f / kLog2e;
+            const float tm = fmaf(a.w, vv[0], vv[1]);
+            if (__popc(m) <= kDirectLanes) {  // few contributing lanes: each adds its own, no reduction
+                if (contrib) {
+                    const float du = fmaf(bb.x, vv[0], a.z * a.w * tm) * il;
+                    const float dv = a.z * tm * il;
+                    atomicAdd(reinterpret_cast<float4*>(t0), make_float4(du, dv, -0.5f * vv[2], -vv[3]));
+                    atomicAdd(reinterpret_cast<float4*>(t1), make_float4(-0.5f * vv[4], vv[5], vv[6], vv[7]));
+                    atomicAdd(&g2[gi], vb);
+                }
+            } else {
+                // every lane turns its moments into (du, dv, da, db, dc) first (linear, so the sum
+                // is the same): no lane-dependent branches after the reduction
+                const float tv[8] = {fmaf(bb.x, vv[0], a.z * a.w * tm) * il, a.z * tm * il,
+                                     -0.5f * vv[2], -vv[3], -0.5f * vv[4], vv[5], vv[6], vv[7]};
+                const float x = warp_sum8_transposed(tv, lane);  // lane holds the total of index lane >> 2
+                vb = warp_sum(vb);
+                const int idx = lane >> 2;
+                if ((lane & 3) == 0) atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
+                if (lane == 0) atomicAdd(&g2[gi], vb);
             }
-        };
-        if (bb.y > kNoClampOpacity) pixels(std::true_type{});
-        else pixels(std::false_type{});
-        const unsigned m = __ballot_sync(0xffffffffu, contrib);
-        if (m == 0u) continue;
-        const long long gi = s_gi[j];
-        float* t0 = reinterpret_cast<float*>(g0 + gi);
-        float* t1 = reinterpret_cast<float*>(g1 + gi);
-        // moments -> (du, dv, da, db, dc): P = p2 / log2(e), p2 = C' (dy + beta dx)^2 + G' dx^2
-        //   (staged C' = a.z, beta = a.w, G' = bb.x), so with t = beta m1 + m2
-        //   du = 2 (G' m1 + C' beta t)/log2e, dv = 2 C' t/log2e,
-        //   da = -m3/2, db = -m4, dc = -m5/2
-        const float il = 2.0f / kLog2e;
-        const float tm = fmaf(a.w, vv[0], vv[1]);
-        if (__popc(m) <= kDirectLanes) {  // few contributing lanes: each adds its own, no reduction
-            if (contrib) {
-                const float du = fmaf(bb.x, vv[0], a.z * a.w * tm) * il;
-                const float dv = a.z * tm * il;
-                atomicAdd(reinterpret_cast<float4*>(t0), make_float4(du, dv, -0.5f * vv[2], -vv[3]));
-                atomicAdd(reinterpret_cast<float4*>(t1), make_float4(-0.5f * vv[4], vv[5], vv[6], vv[7]));
-                atomicAdd(&g2[gi], vb);
-            }
-        } else {
-            // every lane turns its moments into (du, dv, da, db, dc) first (linear, so the sum
-            // is the same): no lane-dependent branches after the reduction
-            const float tv[8] = {fmaf(bb.x, vv[0], a.z * a.w * tm) * il, a.z * tm * il,
-                                 -0.5f * vv[2], -vv[3], -0.5f * vv[4], vv[5], vv[6], vv[7]};
-            const float x = warp_sum8_transposed(tv, lane);  // lane holds the total of index lane >> 2
-            vb = warp_sum(vb);
-            const int idx = lane >> 2;
-            if ((lane & 3) == 0) atomicAdd(idx < 4 ? t0 + idx : t1 + (idx - 4), x);
-            if (lane == 0) atomicAdd(&g2[gi], vb);
         }
     }
 }

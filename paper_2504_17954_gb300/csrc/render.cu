@@ -18,6 +18,7 @@ namespace cg = cooperative_groups;
 namespace ivrgs {
 
 constexpr int kBatch = 256;
+constexpr int kSteps1 = 4;  // list entries per step of the one-pixel walk (1, 2, 4 or 8)
 
 // Per-thread state of P vertically adjacent pixels of one column of a tile.
 template <int P>
@@ -44,13 +45,15 @@ __device__ __forceinline__ void fwd_batch(int j0, int j1, int b0, const TilePos&
         nl = band_list(j0, j1, ylo, ylo + (float)(2 * P - 1), s_rows, list);
     }
     if constexpr (P == 1) {
-        // One pixel per thread: two list entries per step, both exponents, reach tests and
-        // exponentials first, then the two updates in order, so that a warp's chain of dependent
-        // operations per entry (shared loads, exponent, ex2, transmittance) overlaps between the
-        // two. At one pixel per thread a warp is the whole walk of its two rows, and on a view whose
-        // heaviest tiles set the launch time the lone warps that still run are latency-bound (the
-        // 800^2 view's heaviest tile alone on an SM: 374 -> 325 us; the launch 0.437 -> 0.410 ms).
-        // The same operations per pixel in the same order as below, so the same bits.
+        // One pixel per thread: kSteps1 list entries per step, all their exponents, reach tests
+        // and exponentials first, then the updates in order, so that a warp's chains of dependent
+        // operations per entry (shared loads, exponent, ex2) overlap. At one pixel per thread a
+        // warp is the whole walk of its two rows, and on a view whose heaviest tiles set the
+        // launch time the lone warps that still run are latency-bound: on the 800^2 view the
+        // heaviest tile alone on an SM takes 374 / 325 / 276 us at 1 / 2 / 4 entries per step, the
+        // launch 0.437 / 0.410 / 0.362 ms (62 registers at 4, so 4 CTAs per SM instead of 6: the
+        // shorter chains win all the same). The same operations per pixel in the same order as
+        // below, so the same bits.
         auto one = [&](bool ok, const float4& bb, const float2& cc, float G, unsigned idx, auto clamp) {
             const float Tn = __fmul_rn(s.T[0], one_minus_alpha<decltype(clamp)::value>(bb.y, G));
             const bool stop = ok && Tn < kTMin;
@@ -64,80 +67,91 @@ __device__ __forceinline__ void fwd_batch(int j0, int j1, int b0, const TilePos&
             s.last[0] = add ? idx : s.last[0];
             s.done[0] = s.done[0] || stop;
         };
-        for (int i = 0; i < nl; i += 2) {
-            const bool hasB = i + 1 < nl;
-            const int jA = band_cull<P>() ? (int)list[i] : j0 + i;
-            const int jB = hasB ? (band_cull<P>() ? (int)list[i + 1] : j0 + i + 1) : jA;
-            const float4 aA = s_a[jA], bA = s_b[jA];
-            const float2 cA = s_c[jA];
-            const float4 aB = s_a[jB], bB = s_b[jB];
-            const float2 cB = s_c[jB];
-            const float pA = row_p2(row_group(aA, bA, tp.fx, tp.fyg), aA, tp.q0);
-            const float pB = row_p2(row_group(aB, bB, tp.fx, tp.fyg), aB, tp.q0);
-            const bool okA = !s.done[0] && in_reach(pA, cA.y);
-            bool okB = hasB && !s.done[0] && in_reach(pB, cB.y);
-            if (__any_sync(0xffffffffu, okA || okB)) {
-                const float GA = fast_ex2(pA), GB = fast_ex2(pB);
-                if (bA.y > kNoClampOpacity) one(okA, bA, cA, GA, (unsigned)(b0 + jA + 1), std::true_type{});
-                else one(okA, bA, cA, GA, (unsigned)(b0 + jA + 1), std::false_type{});
-                okB = okB && !s.done[0];  // the first entry may have ended the pixel
-                if (bB.y > kNoClampOpacity) one(okB, bB, cB, GB, (unsigned)(b0 + jB + 1), std::true_type{});
-                else one(okB, bB, cB, GB, (unsigned)(b0 + jB + 1), std::false_type{});
+        for (int i = 0; i < nl; i += kSteps1) {
+            float4 bq[kSteps1];
+            float2 cq[kSteps1];
+            float pq[kSteps1];
+            bool okq[kSteps1];
+            int jq[kSteps1];
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < kSteps1; ++k) {
+                const bool has = i + k < nl;
+                const int ii = has ? i + k : i;  // past the end: a repeat of entry i, never in reach
+                jq[k] = band_cull<P>() ? (int)list[ii] : j0 + ii;
+                const float4 aq = s_a[jq[k]];
+                bq[k] = s_b[jq[k]];
+                cq[k] = s_c[jq[k]];
+                pq[k] = row_p2(row_group(aq, bq[k], tp.fx, tp.fyg), aq, tp.q0);
+                okq[k] = has && !s.done[0] && in_reach(pq[k], cq[k].y);
+                any = any || okq[k];
             }
-            if ((i & 7) == 6 && __all_sync(0xffffffffu, s.done[0])) break;
-        }
-        return;
-    }
-    for (int i = 0; i < nl; ++i) {
-        const int j = band_cull<P>() ? (int)list[i] : j0 + i;
-        const float4 a = s_a[j];
-        const float4 bb = s_b[j];
-        const float2 cc = s_c[j];
-        float p2[P];
-        bool ok[P];
-        bool any = false;
-        RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
+            if (__any_sync(0xffffffffu, any)) {
+                float gq[kSteps1];
 #pragma unroll
-        for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, tp.fx, tp.fyg + 4.0f * (float)gq);
+                for (int k = 0; k < kSteps1; ++k) gq[k] = fast_ex2(pq[k]);
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
-            ok[p] = !s.done[p] && in_reach(p2[p], cc.y);
-            any = any || ok[p];
-        }
-        if (__any_sync(0xffffffffu, any)) {
-            const unsigned idx = (unsigned)(b0 + j + 1);
-            // the P pixels update independently (predicated, no branches) so they interleave;
-            // instantiated with and without the 0.99 clamp (a uniform branch on the entry's o')
-            auto update = [&](auto clamp) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const float Tn =
-                        __fmul_rn(s.T[p], one_minus_alpha<decltype(clamp)::value>(bb.y, fast_ex2(p2[p])));
-                    const bool stop = ok[p] && Tn < kTMin;
-                    const bool add = ok[p] && !stop;
-                    // the weight T alpha as the drop of T (exact: Sterbenz), so that one select
-                    // serves both; it differs from the rounded product T alpha by the rounding of
-                    // T (1 - alpha), at most 2^-24 T per entry, under 1.6e-5 in all (T falls by
-                    // 1/255 at least per entry)
-                    const float Tk = add ? Tn : s.T[p];
-                    const float w = s.T[p] - Tk;
-                    s.C0[p] = fmaf(w, bb.z, s.C0[p]);
-                    s.C1[p] = fmaf(w, bb.w, s.C1[p]);
-                    s.C2[p] = fmaf(w, cc.x, s.C2[p]);
-                    s.T[p] = Tk;
-                    s.last[p] = add ? idx : s.last[p];
-                    s.done[p] = s.done[p] || stop;
+                for (int k = 0; k < kSteps1; ++k) {
+                    const bool ok = okq[k] && !s.done[0];  // an earlier entry may have ended the pixel
+                    const unsigned idx = (unsigned)(b0 + jq[k] + 1);
+                    if (bq[k].y > kNoClampOpacity) one(ok, bq[k], cq[k], gq[k], idx, std::true_type{});
+                    else one(ok, bq[k], cq[k], gq[k], idx, std::false_type{});
                 }
-            };
-            if (bb.y > kNoClampOpacity) update(std::true_type{});
-            else update(std::false_type{});
+            }
+            if (((i / kSteps1) & (8 / kSteps1 - 1)) == 8 / kSteps1 - 1 && __all_sync(0xffffffffu, s.done[0])) break;
         }
-        if ((i & 7) == 7) {
-            bool mine = true;
+    } else {
+        for (int i = 0; i < nl; ++i) {
+            const int j = band_cull<P>() ? (int)list[i] : j0 + i;
+            const float4 a = s_a[j];
+            const float4 bb = s_b[j];
+            const float2 cc = s_c[j];
+            float p2[P];
+            bool ok[P];
+            bool any = false;
+            RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
 #pragma unroll
-            for (int p = 0; p < P; ++p) mine = mine && s.done[p];
-            if (__all_sync(0xffffffffu, mine)) break;
+            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, tp.fx, tp.fyg + 4.0f * (float)gq);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
+                ok[p] = !s.done[p] && in_reach(p2[p], cc.y);
+                any = any || ok[p];
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                const unsigned idx = (unsigned)(b0 + j + 1);
+                // the P pixels update independently (predicated, no branches) so they interleave;
+                // instantiated with and without the 0.99 clamp (a uniform branch on the entry's o')
+                auto update = [&](auto clamp) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const float Tn =
+                            __fmul_rn(s.T[p], one_minus_alpha<decltype(clamp)::value>(bb.y, fast_ex2(p2[p])));
+                        const bool stop = ok[p] && Tn < kTMin;
+                        const bool add = ok[p] && !stop;
+                        // the weight T alpha as the drop of T (exact: Sterbenz), so that one select
+                        // serves both; it differs from the rounded product T alpha by the rounding of
+                        // T (1 - alpha), at most 2^-24 T per entry, under 1.6e-5 in all (T falls by
+                        // 1/255 at least per entry)
+                        const float Tk = add ? Tn : s.T[p];
+                        const float w = s.T[p] - Tk;
+                        s.C0[p] = fmaf(w, bb.z, s.C0[p]);
+                        s.C1[p] = fmaf(w, bb.w, s.C1[p]);
+                        s.C2[p] = fmaf(w, cc.x, s.C2[p]);
+                        s.T[p] = Tk;
+                        s.last[p] = add ? idx : s.last[p];
+                        s.done[p] = s.done[p] || stop;
+                    }
+                };
+                if (bb.y > kNoClampOpacity) update(std::true_type{});
+                else update(std::false_type{});
+            }
+            if ((i & 7) == 7) {
+                bool mine = true;
+#pragma unroll
+                for (int p = 0; p < P; ++p) mine = mine && s.done[p];
+                if (__all_sync(0xffffffffu, mine)) break;
+            }
         }
     }
 }
