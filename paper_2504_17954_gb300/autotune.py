@@ -159,7 +159,7 @@ def tune_waves(measure: Callable[[int, int, int], float], cams: Sequence, n_gaus
     for th in tile_heights:
         for mv in max_views:
             for pb in budgets:
-                plan = tuple(len(w) for w in plan_waves(cams, n_gaussians, mv, pb))
+                plan = tuple(len(w) for w in plan_waves(cams, n_gaussians, mv, pb, th))
                 plans.setdefault((th, plan), (mv, pb))  # the first shape that gives a plan stands for it
     best = None
     cands = []

@@ -430,20 +430,25 @@ class Rasterizer:
 
 
 # ----------------------------------------------------------------------------------------
-def plan_waves(cams, n_gaussians: int, max_views: int = 32, pixel_budget: int = 24 << 20) -> List[List[int]]:
+def plan_waves(cams, n_gaussians: int, max_views: int = 32, pixel_budget: int = 24 << 20, tile_h: int = 16,
+               max_tiles: int = 1 << 16) -> List[List[int]]:
     """Consecutive groups of view indices, in view order, each rendered by one set of calls:
     at most ``max_views`` views, and fewer than the library's 2^30 records (n_gaussians * views)
     per binning call; a wave closes before a view that would take its pixels over
-    ``pixel_budget`` (a single view larger than the budget forms a wave of its own)."""
+    ``pixel_budget`` or its tiles (16 x tile_h) over ``max_tiles`` (a single view larger than
+    either forms a wave of its own). With at most 2^16 tiles per call the tile ids travel through
+    the radix sort as 16-bit keys in two passes instead of three."""
     max_views = max(1, min(max_views, (N.IVRGS_MAX_PAIRS - 1) // max(n_gaussians, 1)))
     waves: List[List[int]] = []
-    cur, pix = [], 0
+    cur, pix, tiles = [], 0, 0
     for v, c in enumerate(cams):
-        if cur and (len(cur) >= max_views or pix + c.W * c.H > pixel_budget):
+        t = n_tiles([c], 16, tile_h)
+        if cur and (len(cur) >= max_views or pix + c.W * c.H > pixel_budget or tiles + t > max_tiles):
             waves.append(cur)
-            cur, pix = [], 0
+            cur, pix, tiles = [], 0, 0
         cur.append(v)
         pix += c.W * c.H
+        tiles += t
     if cur:
         waves.append(cur)
     return waves
@@ -458,7 +463,7 @@ class WaveRasterizer:
                  bg=(0.0, 0.0, 0.0), max_views: int = 32, pixel_budget: int = 24 << 20, cull: bool = True,
                  tile_h: int = 16):
         self.cams = list(cams)
-        self.waves: List[List[int]] = plan_waves(self.cams, n_gaussians, max_views, pixel_budget)
+        self.waves: List[List[int]] = plan_waves(self.cams, n_gaussians, max_views, pixel_budget, tile_h)
         self.rasts = [Rasterizer([self.cams[v] for v in wv], n_gaussians, n_models, device=device, lowpass=lowpass,
                                  bg=bg, cull=cull, tile_h=tile_h) for wv in self.waves]
         self.n_models = n_models
