@@ -98,7 +98,7 @@ __device__ __forceinline__ void fwd_batch(int j0, int j1, int b0, const TilePos&
                     else one(ok, bq[k], cq[k], gq[k], idx, std::false_type{});
                 }
             }
-            if (((i / kSteps1) & (8 / kSteps1 - 1)) == 8 / kSteps1 - 1 && __all_sync(0xffffffffu, s.done[0])) break;
+            if ((i & 7) + kSteps1 >= 8 && __all_sync(0xffffffffu, s.done[0])) break;  // every 8 entries
         }
     } else {
         for (int i = 0; i < nl; ++i) {
