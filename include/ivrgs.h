@@ -194,8 +194,8 @@ int32_t ivrgs_version(void);
    scan and the scatter; no device-side waits); "sort_early" (0 or 1): in the tile-id passes, a
    look-back radix tile publishes its digit counts after (0) or before (1) ranking its keys (the
    depth passes always publish before); "render_split" (0 to 4): both blends walk every tile's
-   run with one CTA (2), or cut runs longer than "render_split_min" entries (32, 64, 128, 256,
-   384 (default), 512, 768, 1024, 2048 or 4096) into up to 8 chunks walked by the 8 CTAs of a
+   run with one CTA (2), or cut runs longer than "render_split_min" entries (32, 64, 128,
+   256 (default), 384, 512, 768, 1024, 2048 or 4096) into up to 8 chunks walked by the 8 CTAs of a
    thread-block cluster whose partial results merge through distributed shared memory (1), or
    do so when the call has fewer than 304 tiles (0, the default: two tiles per SM, below which
    the heaviest tiles' serial walks are the whole launch), or do so in the backward only, below

@@ -104,7 +104,7 @@ struct Options {
                              // than kSplitTiles tiles (the default), 1 = always, 2 = never, 3 = the
                              // backward only (by tile count), 4 = no split, but the long runs in a
                              // launch of their own, first (by tile count)
-    int render_split_min = 384;  // entries per chunk at least (a run this long or shorter is one chunk)
+    int render_split_min = 256;  // entries per chunk at least (a run this long or shorter is one chunk)
 };
 Options& options();
 // Pixels per thread of a blend launch over n_tiles tiles: the option, or with 0 (the default) a

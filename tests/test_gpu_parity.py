@@ -225,11 +225,11 @@ def test_render_only_matches_oracle_on_shared_records(which):
 
 # ------------------------------------------------------------------ end to end forward
 # blend launch shapes: (pixels per thread, render_split (0 = split by tile count, the default,
-# which splits the small scenes here (few tiles) at 384 entries; 2 = one CTA per tile; 1 = split
+# which splits the small scenes here (few tiles) at 256 entries; 2 = one CTA per tile; 1 = split
 # always; 4 = long runs first), entries per chunk). "split32" cuts every run longer than 32
 # entries into up to 8 chunks over a CTA cluster, "longfirst32" walks the runs longer than 32
 # entries in a launch of their own, first.
-@pytest.fixture(params=[(0, 0, 384), (1, 2, 384), (2, 2, 384), (4, 2, 384), (8, 2, 384), (0, 2, 384), (0, 1, 32),
+@pytest.fixture(params=[(0, 0, 256), (1, 2, 384), (2, 2, 384), (4, 2, 384), (8, 2, 384), (0, 2, 384), (0, 1, 32),
                         (4, 1, 32), (1, 1, 32), (0, 4, 32)],
                 ids=["ppt_auto", "ppt1", "ppt2", "ppt4", "ppt8", "nosplit", "split32", "split32_ppt4", "split32_ppt1",
                      "longfirst32"])
