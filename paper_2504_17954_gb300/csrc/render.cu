@@ -101,57 +101,60 @@ __device__ __forceinline__ void fwd_batch(int j0, int j1, int b0, const TilePos&
             if ((i & 7) + kSteps1 >= 8 && __all_sync(0xffffffffu, s.done[0])) break;  // every 8 entries
         }
     } else {
-        for (int i = 0; i < nl; ++i) {
-            const int j = band_cull<P>() ? (int)list[i] : j0 + i;
-            const float4 a = s_a[j];
-            const float4 bb = s_b[j];
-            const float2 cc = s_c[j];
-            float p2[P];
-            bool ok[P];
-            bool any = false;
-            RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
+        // the entries in groups of 8, the termination vote after each group (no per-entry test of
+        // the position in the group: 0.715 -> 0.702 ms on the 1M-Gaussian, 8-view workload)
+        for (int i0 = 0; i0 < nl; i0 += 8) {
+            const int i1 = min(nl, i0 + 8);
+            for (int i = i0; i < i1; ++i) {
+                const int j = band_cull<P>() ? (int)list[i] : j0 + i;
+                const float4 a = s_a[j];
+                const float4 bb = s_b[j];
+                const float2 cc = s_c[j];
+                float p2[P];
+                bool ok[P];
+                bool any = false;
+                RowGroup rgp[NG];  // every aligned group of 4 rows has its own base, whatever P is
 #pragma unroll
-            for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, tp.fx, tp.fyg + 4.0f * (float)gq);
+                for (int gq = 0; gq < NG; ++gq) rgp[gq] = row_group(a, bb, tp.fx, tp.fyg + 4.0f * (float)gq);
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
-                ok[p] = !s.done[p] && in_reach(p2[p], cc.y);
-                any = any || ok[p];
+                for (int p = 0; p < P; ++p) {
+                    p2[p] = row_p2(rgp[(tp.q0 + p) >> 2], a, (tp.q0 + p) & 3);
+                    ok[p] = !s.done[p] && in_reach(p2[p], cc.y);
+                    any = any || ok[p];
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    const unsigned idx = (unsigned)(b0 + j + 1);
+                    // the P pixels update independently (predicated, no branches) so they interleave;
+                    // instantiated with and without the 0.99 clamp (a uniform branch on the entry's o')
+                    auto update = [&](auto clamp) {
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const float Tn =
+                                __fmul_rn(s.T[p], one_minus_alpha<decltype(clamp)::value>(bb.y, fast_ex2(p2[p])));
+                            const bool stop = ok[p] && Tn < kTMin;
+                            const bool add = ok[p] && !stop;
+                            // the weight T alpha as the drop of T (exact: Sterbenz), so that one select
+                            // serves both; it differs from the rounded product T alpha by the rounding of
+                            // T (1 - alpha), at most 2^-24 T per entry, under 1.6e-5 in all (T falls by
+                            // 1/255 at least per entry)
+                            const float Tk = add ? Tn : s.T[p];
+                            const float w = s.T[p] - Tk;
+                            s.C0[p] = fmaf(w, bb.z, s.C0[p]);
+                            s.C1[p] = fmaf(w, bb.w, s.C1[p]);
+                            s.C2[p] = fmaf(w, cc.x, s.C2[p]);
+                            s.T[p] = Tk;
+                            s.last[p] = add ? idx : s.last[p];
+                            s.done[p] = s.done[p] || stop;
+                        }
+                    };
+                    if (bb.y > kNoClampOpacity) update(std::true_type{});
+                    else update(std::false_type{});
+                }
             }
-            if (__any_sync(0xffffffffu, any)) {
-                const unsigned idx = (unsigned)(b0 + j + 1);
-                // the P pixels update independently (predicated, no branches) so they interleave;
-                // instantiated with and without the 0.99 clamp (a uniform branch on the entry's o')
-                auto update = [&](auto clamp) {
+            bool mine = true;
 #pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        const float Tn =
-                            __fmul_rn(s.T[p], one_minus_alpha<decltype(clamp)::value>(bb.y, fast_ex2(p2[p])));
-                        const bool stop = ok[p] && Tn < kTMin;
-                        const bool add = ok[p] && !stop;
-                        // the weight T alpha as the drop of T (exact: Sterbenz), so that one select
-                        // serves both; it differs from the rounded product T alpha by the rounding of
-                        // T (1 - alpha), at most 2^-24 T per entry, under 1.6e-5 in all (T falls by
-                        // 1/255 at least per entry)
-                        const float Tk = add ? Tn : s.T[p];
-                        const float w = s.T[p] - Tk;
-                        s.C0[p] = fmaf(w, bb.z, s.C0[p]);
-                        s.C1[p] = fmaf(w, bb.w, s.C1[p]);
-                        s.C2[p] = fmaf(w, cc.x, s.C2[p]);
-                        s.T[p] = Tk;
-                        s.last[p] = add ? idx : s.last[p];
-                        s.done[p] = s.done[p] || stop;
-                    }
-                };
-                if (bb.y > kNoClampOpacity) update(std::true_type{});
-                else update(std::false_type{});
-            }
-            if ((i & 7) == 7) {
-                bool mine = true;
-#pragma unroll
-                for (int p = 0; p < P; ++p) mine = mine && s.done[p];
-                if (__all_sync(0xffffffffu, mine)) break;
-            }
+            for (int p = 0; p < P; ++p) mine = mine && s.done[p];
+            if (__all_sync(0xffffffffu, mine)) break;
         }
     }
 }
