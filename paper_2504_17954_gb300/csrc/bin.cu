@@ -346,9 +346,9 @@ __global__ void __launch_bounds__(kScanThreads) k_count_sorted(const unsigned* _
 // ------------------------------------------------------------------------- emission
 // Every warp emits the pairs of its own range of kWarpRange depth-ordered records, 32 at a
 // time, starting at the range's pair offset (no block-wide step, so a warp with large records
-// does not hold up the others). Round 1: its lanes stride over the 32 records' tile rows (row
-// runs), evaluating each row's kept columns [lo, hi) once. Round 2, for every 32 row runs: its
-// lanes stride over those runs' pairs, so consecutive lanes write consecutive slots.
+// does not hold up the others). First stage: its lanes stride over the 32 records' tile rows
+// (row runs), evaluating each row's kept columns [lo, hi) once. Second stage, for every 32 row
+// runs: its lanes stride over those runs' pairs, so consecutive lanes write consecutive slots.
 // The pairs a warp writes must equal the sum of its records' counts from the count pass (the
 // same rounded arithmetic decides both); a mismatch sets bit 1 of the error flag.
 template <typename KT>
