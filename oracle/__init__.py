@@ -388,3 +388,64 @@ def render_aux(r: "Render", cams, tile=(16, 16)) -> List[np.ndarray]:
                                   C.c_int32(c.W), C.c_int32(c.H), C.c_int32(tile[0]), C.c_int32(tile[1]), _p(o))
         out.append(o)
     return out
+
+
+def render_aux_backward(r: "Render", cams, dL_daux: Sequence[np.ndarray], tile=(16, 16),
+                        lowpass: float = LOWPASS) -> Grads:
+    """Reverse mode of ``render_aux``: dL_daux[v] is [H, W, 12], the gradient of a loss on the
+    11 auxiliary channels and 1 - T. Returns the gradients of the stored attributes and of the
+    edit table; ``proj[v]["aux"]`` holds the per-Gaussian [N, 11] channel gradients of view v.
+
+    The auxiliary maps composite the per-Gaussian values x_i with the weights T_i alpha_i and no
+    background (Sec. 4.2 first equation), so their reverse mode is the compositing's with x in
+    place of the colour and bg = 0. That reverse mode is linear in the upstream gradient: the
+    channels are taken three at a time through the float64 compositing reverse mode of
+    ``render_backward`` (the 1 - T channel with the first three) and the contributions summed.
+    The 2D-quantity gradients then go through the projection's reverse mode with a zero colour
+    gradient (Sec. 3 first equation); the channels' own gradients through x_i: the camera depth
+    z = (R mu + t)_z, the unit normal n / |n|, the offset colour dc, and k' = lambda k + b."""
+    comp, table = r.comp, r.table
+    n, M = comp.n, comp.n_models
+    params = _grad_params(comp)
+    dedit = np.zeros_like(table)
+    dlight = np.zeros((len(cams), 3))
+    lam = table[M * EDIT_STRIDE:M * EDIT_STRIDE + 4]
+    nlen = np.linalg.norm(comp.normal, axis=1, keepdims=True)
+    nhat = comp.normal / nlen
+    zero_bg = np.zeros(3)
+    per_view = []
+    for v, (c, p) in enumerate(zip(cams, r.projs)):
+        x = aux_attributes(comp, table, p)
+        d = np.asarray(dL_daux[v], np.float64)
+        g = dict(uv=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)))
+        dx = np.zeros((n, len(AUX_CHANNELS)))
+        for k0 in range(0, len(AUX_CHANNELS), 3):
+            ks = list(range(k0, min(k0 + 3, len(AUX_CHANNELS))))
+            cols = np.zeros((n, 3))
+            cols[:, :len(ks)] = x[:, ks]
+            dl = np.zeros((c.H, c.W, 4))
+            dl[..., :len(ks)] = d[..., ks]
+            if k0 == 0:
+                dl[..., 3] = d[..., len(AUX_CHANNELS)]
+            gk = dict(uv=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)))
+            lib().orc_render_view_backward(_p(p.uv), _p(p.conic), _p(p.opacity), _p(np.ascontiguousarray(cols)),
+                                           _p(r.bins.values, C.c_uint32), _p(r.bins.ranges, C.c_uint32),
+                                           C.c_int64(int(r.bins.tile_offset[v])), C.c_int32(c.W), C.c_int32(c.H),
+                                           C.c_int32(tile[0]), C.c_int32(tile[1]), _p(zero_bg),
+                                           _p(np.ascontiguousarray(dl)), _p(gk["uv"]), _p(gk["conic"]),
+                                           _p(gk["opacity"]), _p(gk["rgb"]))
+            for key in ("uv", "conic", "opacity"):
+                g[key] += gk[key]
+            dx[:, ks] += gk["rgb"][:, :len(ks)]
+        _project_backward(comp, table, c, lowpass, g, params, dedit, dlight[v])
+        R = np.asarray(c.R, np.float64).reshape(3, 3)
+        params["mean"] += dx[:, 0:1] * R[2][None, :]
+        dn = dx[:, 1:4]
+        params["normal"] += (dn - nhat * (nhat * dn).sum(1, keepdims=True)) / nlen
+        params["dcolor"] += dx[:, 4:7]
+        dk = dx[:, 7:11]
+        params["kads"] += dk * lam[None, :]
+        dedit[M * EDIT_STRIDE:M * EDIT_STRIDE + 4] += (comp.kads * dk).sum(0)
+        dedit[M * EDIT_STRIDE + 4:M * EDIT_STRIDE + 8] += dk.sum(0)
+        per_view.append(dict(g, aux=dx))
+    return Grads(params, dedit, dlight, per_view)
