@@ -304,6 +304,26 @@ ivrgs_status ivrgs_render_aux(const ivrgs_gaussians* g, const float* d_edit_tabl
                               const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float* d_aux,
                               void* stream);
 
+/* Workspace bytes ivrgs_render_aux_backward needs for n Gaussians and n_views views. */
+ivrgs_status ivrgs_render_aux_backward_workspace(int64_t n, int32_t n_views, size_t* bytes);
+
+/* Reverse mode of ivrgs_render_aux (Sec. 4.2 first equation: the maps composite each Gaussian's
+   values with the weights T_i alpha_i, no background; the last channel is 1 - T). Inputs: the
+   same g, d_edit_table, p, b, cams and lowpass as the forward, ivrgs_render's d_final_T and
+   d_last, and d_dL_daux [.][12] = dL/d(the 11 channels of ivrgs_render_aux, 1 - T) per packed
+   pixel (16-byte aligned). The walk is the colour reverse mode's with the values in place of the
+   colour. Outputs (overwritten): grad arrays with the layout of g (float32, model_id unused) =
+   dL/d{mean, log_scale, quat, opacity_logit, dcolor, normal, kads} (SH coefficients, if g has
+   them, receive zero: the maps do not depend on the colour); d_edit_grad
+   (ivrgs_edit_table_floats(n_models) + 4 * n_views floats) = dL/d{opacity scale} per model and
+   dL/d{lambda, b} (palette colours and lights: zero). d_workspace: at least
+   ivrgs_render_aux_backward_workspace bytes, 256-byte aligned (IVRGS_ERR_CAPACITY if smaller). */
+ivrgs_status ivrgs_render_aux_backward(const ivrgs_gaussians* g, const float* d_edit_table,
+                                       const ivrgs_projected* p, const ivrgs_bins* b, const ivrgs_camera* cams,
+                                       int32_t n_views, float lowpass, const float* d_final_T,
+                                       const uint32_t* d_last, const float* d_dL_daux, void* d_workspace,
+                                       size_t ws_bytes, ivrgs_gaussians* grad, float* d_edit_grad, void* stream);
+
 /* Workspace bytes ivrgs_render_backward needs for n Gaussians and n_views views. */
 ivrgs_status ivrgs_render_backward_workspace(int64_t n, int32_t n_views, size_t* bytes);
 

@@ -96,6 +96,11 @@ _SIGNATURES = {
                                  _P(C.c_float), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ivrgs_render_aux": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_projected), _P(ivrgs_bins),
                                      _P(ivrgs_camera), C.c_int32, C.c_void_p, C.c_void_p]),
+    "ivrgs_render_aux_backward_workspace": (C.c_int32, [C.c_int64, C.c_int32, _P(C.c_size_t)]),
+    "ivrgs_render_aux_backward": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_projected), _P(ivrgs_bins),
+                                              _P(ivrgs_camera), C.c_int32, C.c_float, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_size_t, _P(ivrgs_gaussians), C.c_void_p,
+                                              C.c_void_p]),
     "ivrgs_render_backward_workspace": (C.c_int32, [C.c_int64, C.c_int32, _P(C.c_size_t)]),
     "ivrgs_render_backward": (C.c_int32, [_P(ivrgs_gaussians), C.c_void_p, _P(ivrgs_projected), _P(ivrgs_bins),
                                           _P(ivrgs_camera), C.c_int32, C.c_float, _P(C.c_float), C.c_void_p,
@@ -205,6 +210,18 @@ def ivrgs_bin_check(ws, stream, allow=(IVRGS_OK,)):
 
 def ivrgs_render(p, b, cams, n_views, bg, d_rgba, d_final_T, d_last, stream):
     return call("ivrgs_render", p, b, cams, n_views, bg, d_rgba, d_final_T, d_last, stream)
+
+
+def ivrgs_render_aux_backward_workspace(n, n_views) -> int:
+    b = C.c_size_t(0)
+    call("ivrgs_render_aux_backward_workspace", n, n_views, C.byref(b))
+    return int(b.value)
+
+
+def ivrgs_render_aux_backward(g, d_edit_table, p, b, cams, n_views, lowpass, d_final_T, d_last, d_dL, ws, ws_bytes,
+                              grad, d_edit_grad, stream):
+    return call("ivrgs_render_aux_backward", g, d_edit_table, p, b, cams, n_views, lowpass, d_final_T, d_last, d_dL,
+                ws, ws_bytes, grad, d_edit_grad, stream)
 
 
 def ivrgs_render_backward_workspace(n, n_views) -> int:

@@ -450,6 +450,47 @@ ivrgs_status ivrgs_render_aux(const ivrgs_gaussians* g, const float* d_edit_tabl
     return cuda_status(launch_render_aux(g, d_edit_table, p, b, cb, d_aux, (cudaStream_t)stream), "ivrgs_render_aux");
 }
 
+ivrgs_status ivrgs_render_aux_backward_workspace(int64_t n, int32_t n_views, size_t* bytes) {
+    set_error("");
+    if (!bytes || n < 0 || n_views < 1 || n_views > IVRGS_MAX_VIEWS) return invalid("bad arguments");
+    *bytes = aux_backward_workspace(n, n_views);
+    return IVRGS_OK;
+}
+
+ivrgs_status ivrgs_render_aux_backward(const ivrgs_gaussians* g, const float* d_edit_table, const ivrgs_projected* p,
+                                       const ivrgs_bins* b, const ivrgs_camera* cams, int32_t n_views, float lowpass,
+                                       const float* d_final_T, const uint32_t* d_last, const float* d_dL_daux,
+                                       void* d_workspace, size_t ws_bytes, ivrgs_gaussians* grad, float* d_edit_grad,
+                                       void* stream) {
+    set_error("");
+    ivrgs_status st = check_gaussians(g, "g", true, true);
+    if (st) return st;
+    if (g->n_models < 1 || g->n_models > IVRGS_MAX_MODELS) return invalid("g->n_models out of range");
+    if ((st = check_gaussians(grad, "grad", false))) return st;
+    if (grad->n != g->n) return invalid("grad->n must equal g->n");
+    if (g->sh && (!grad->sh || grad->sh_degree != g->sh_degree))
+        return invalid("g has SH colour: grad->sh must be set, with the same sh_degree");
+    static thread_local CamBatch cb;
+    if ((st = make_cam_batch(cams, n_views, &cb, b ? b->tile_h : kTile))) return st;
+    if (!p) return invalid("projected is NULL");
+    if ((st = check_projected(p, g->n, n_views))) return st;
+    if ((st = check_bins(b, cb))) return st;
+    if (!d_edit_table || !d_final_T || !d_last || !d_dL_daux || !d_edit_grad)
+        return invalid("NULL input/output array");
+    if (!aligned(d_dL_daux, 16)) return invalid("d_dL_daux must be 16-byte aligned");
+    if (!(lowpass >= 0.f) || !isfinite(lowpass)) return invalid("lowpass must be finite and >= 0");
+    const size_t need = aux_backward_workspace(g->n, n_views);
+    if (!d_workspace || ws_bytes < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return IVRGS_ERR_CAPACITY;
+    }
+    if (!aligned(d_workspace, 256)) return invalid("workspace must be 256-byte aligned");
+    return cuda_status(launch_render_aux_backward(g, d_edit_table, p, b, cb, lowpass, d_final_T, d_last, d_dL_daux,
+                                                  static_cast<char*>(d_workspace), grad, d_edit_grad,
+                                                  (cudaStream_t)stream),
+                       "ivrgs_render_aux_backward");
+}
+
 ivrgs_status ivrgs_render_backward_workspace(int64_t n, int32_t n_views, size_t* bytes) {
     set_error("");
     if (!bytes || n < 0 || n_views < 1 || n_views > IVRGS_MAX_VIEWS) return invalid("bad arguments");

@@ -1108,6 +1108,13 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
             if (ej != cudaSuccess) return ej;
         }
     }
+    return launch_project_backward(g, table, cb, lowpass, g0, g1, g2, grad, edit_grad, accumulate, s);
+}
+
+cudaError_t launch_project_backward(const ivrgs_gaussians* g, const float* table, const CamBatch& cb, float lowpass,
+                                    const float4* g0, const float4* g1, const float* g2, ivrgs_gaussians* grad,
+                                    float* edit_grad, int accumulate, cudaStream_t s) {
+    cudaError_t e;
     if (g->sh && !accumulate && g->n > 0) {  // SH gradients are added view by view
         const size_t nb = (size_t)(g->sh_degree + 1) * (g->sh_degree + 1);
         if ((e = cudaMemsetAsync(grad->sh, 0, sizeof(float) * 3 * nb * (size_t)g->n, s)) != cudaSuccess) return e;

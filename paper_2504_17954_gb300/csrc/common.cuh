@@ -172,5 +172,15 @@ cudaError_t launch_render_backward(const ivrgs_gaussians* g, const float* table,
                                    const ivrgs_bins* b, const CamBatch& cb, float lowpass, const float* bg,
                                    const float* final_T, const uint32_t* last, const float* dL, char* ws,
                                    ivrgs_gaussians* grad, float* edit_grad, int accumulate, cudaStream_t s);
+// the projection's reverse mode from the per-(view, Gaussian) gradients of the 2D quantities
+// g0 (du, dv, da, db), g1 (dc, do', dr, dg), g2 (db) (the second half of the backward)
+cudaError_t launch_project_backward(const ivrgs_gaussians* g, const float* table, const CamBatch& cb, float lowpass,
+                                    const float4* g0, const float4* g1, const float* g2, ivrgs_gaussians* grad,
+                                    float* edit_grad, int accumulate, cudaStream_t s);
+size_t aux_backward_workspace(long long n, int n_views);
+cudaError_t launch_render_aux_backward(const ivrgs_gaussians* g, const float* table, const ivrgs_projected* p,
+                                       const ivrgs_bins* b, const CamBatch& cb, float lowpass, const float* final_T,
+                                       const uint32_t* last, const float* dL, char* ws, ivrgs_gaussians* grad,
+                                       float* edit_grad, cudaStream_t s);
 
 }  // namespace ivrgs

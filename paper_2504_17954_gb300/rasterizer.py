@@ -361,6 +361,28 @@ class Rasterizer:
                            _vp(self.aux), _stream(stream))
         return self.aux
 
+    def render_aux_backward(self, g: Gaussians, edit_table: torch.Tensor, dL_daux: torch.Tensor,
+                            grad: Optional[Gaussians] = None, stream=None):
+        """Reverse mode of render_aux for the last forward (ivrgs_render_aux_backward): dL_daux
+        [n_pix, 12] over the channels of render_aux. Returns (grad, gradient of the edit table)."""
+        _check_cuda(dL_daux, "dL_daux")
+        if getattr(self, "ws_aux_bwd", None) is None:
+            self.ws_aux_bwd_bytes = N.ivrgs_render_aux_backward_workspace(self.n, self.V)
+            self.ws_aux_bwd = torch.empty(self.ws_aux_bwd_bytes, dtype=torch.uint8, device=self.device)
+        if grad is None:
+            grad = Gaussians.empty(self.n, self.n_models, self.device)
+            grad.model_id = None
+        if g.sh is not None and grad.sh is None:
+            grad.sh = torch.empty_like(g.sh)
+            grad.sh_degree = g.sh_degree
+        gs, gr = g.struct(), grad.struct()
+        p, b = self.projected_struct(), self.bins_struct()
+        eg = torch.empty_like(self.edit_grad)
+        N.ivrgs_render_aux_backward(C.byref(gs), _vp(edit_table), C.byref(p), C.byref(b), self.cam_arr, self.V,
+                                    self.lowpass, _vp(self.final_T), _vp(self.last), _vp(dL_daux), _vp(self.ws_aux_bwd),
+                                    self.ws_aux_bwd_bytes, C.byref(gr), _vp(eg), _stream(stream))
+        return grad, eg
+
     def backward(self, g: Gaussians, edit_table: torch.Tensor, dL_drgba: torch.Tensor, grad: Optional[Gaussians] = None,
                  stream=None, tensors=None, accumulate: bool = False, edit_grad: Optional[torch.Tensor] = None):
         _check_cuda(dL_drgba, "dL_drgba")
