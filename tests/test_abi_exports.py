@@ -47,6 +47,14 @@ def test_host_side_argument_checks(lib):
     cams[0].headlight = 0  # orbital light with a zero direction
     assert lib.ivrgs_bin_workspace(10, 2, cams, 16, 16, 1000, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
     assert lib.ivrgs_render_backward_workspace(10, 2, C.byref(b)) == N.IVRGS_OK and b.value >= 10 * 2 * 36
+    # the auxiliary maps' reverse mode: 36 bytes of 2D-quantity gradients and 48 of value gradients
+    # per (view, Gaussian); NULL arguments are refused before any device work
+    assert lib.ivrgs_render_aux_backward_workspace(10, 2, C.byref(b)) == N.IVRGS_OK and b.value >= 10 * 2 * 84
+    assert lib.ivrgs_render_aux_backward_workspace(-1, 2, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
+    assert lib.ivrgs_render_aux_backward_workspace(10, 0, C.byref(b)) == N.IVRGS_ERR_INVALID_ARG
+    st = lib.ivrgs_render_aux_backward(None, None, None, None, cams, 2, C.c_float(0.3), None, None, None, None,
+                                       C.c_size_t(0), None, None, None)
+    assert st == N.IVRGS_ERR_INVALID_ARG
     ed = (N.ivrgs_model_edit * 1)()
     li = N.ivrgs_light()
     assert lib.ivrgs_compose_edit(None, 0, ed, C.byref(li), None, None, None) == N.IVRGS_ERR_INVALID_ARG
